@@ -1,0 +1,158 @@
+"""FP64 CPU oracle for dexel dilation / erosion / closing / opening by a ball.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``.  The product path (the CUDA
+library and its binding) never imports it, and it imports nothing from the product.
+
+The arithmetic lives in ``oracle.c`` (plain brute-force gather, see its header):
+  * ``dilate``  -- Sec. 3.1 Eq. of D_r: union over in-grid columns c' with n = di^2+dj^2 <= k^2
+                   of [a - w, b + w], w = h sqrt(k^2 - n)  (the Sec. 4 brute force, as a gather);
+  * ``erode``   -- Sec. 3.1 "Erosion", written directly: intersection over c' of the union of
+                   [a + w, b - w]; zero-length results dropped;
+  * ``close`` = erode(dilate(S)), ``open`` = dilate(erode(S))   (Sec. 4 "Topological Cleaning").
+``complement`` builds the per-column complement with +-inf sentinels (Sec. 3.1: the complement
+is trivial in a ray representation); tests use it to check erosion/dilation duality.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` (closed forms
+with Pythagorean radii, point-membership brute force against the distance definition,
+duality, monotonicity, union commutation, extensivity, idempotence, k = 0 identity).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (IEEE double, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.oracle_offset.restype = ctypes.c_int64
+        lib.oracle_offset.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
+                                      ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
+        lib.oracle_free.restype = None
+        lib.oracle_free.argtypes = [ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def default_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+class Columns:
+    """Result of an oracle call: CSR over the requested columns (float64 endpoints)."""
+
+    def __init__(self, off: np.ndarray, z: np.ndarray, cols):
+        self.off = off
+        self.z = z
+        self.cols = cols
+
+    def column(self, t: int) -> np.ndarray:
+        return self.z[self.off[t]:self.off[t + 1]]
+
+    def __len__(self):
+        return len(self.off) - 1
+
+
+def _run(grid, k: float, erode: int, cols=None, threads: int | None = None) -> Columns:
+    lib = _load()
+    off_in = np.ascontiguousarray(grid.col_off, dtype=np.int64)
+    z_in = np.ascontiguousarray(grid.z, dtype=np.float64).reshape(-1)
+    if z_in.size == 0:
+        z_in = np.zeros(2, np.float64)
+    if cols is not None:
+        cols_arr = np.ascontiguousarray(cols, dtype=np.int64)
+        ncols = cols_arr.size
+        cptr = cols_arr.ctypes.data
+    else:
+        cols_arr = None
+        ncols = grid.nx * grid.ny
+        cptr = None
+    po = ctypes.POINTER(ctypes.c_int64)()
+    pz = ctypes.POINTER(ctypes.c_double)()
+    total = lib.oracle_offset(grid.nx, grid.ny, float(grid.h), float(k), off_in.ctypes.data,
+                              z_in.ctypes.data, erode, cptr, ncols,
+                              threads or default_threads(), ctypes.byref(po), ctypes.byref(pz))
+    if total < 0:
+        raise ValueError("oracle_offset rejected its arguments")
+    off = np.ctypeslib.as_array(po, shape=(ncols + 1,)).copy()
+    z = np.ctypeslib.as_array(pz, shape=(max(total, 1) * 2,))[: 2 * total].copy().reshape(-1, 2)
+    lib.oracle_free(ctypes.cast(po, ctypes.c_void_p))
+    lib.oracle_free(ctypes.cast(pz, ctypes.c_void_p))
+    return Columns(off, z, cols_arr)
+
+
+def _as_grid(template, res: Columns):
+    from synth.shapes import DexelGrid  # container only
+    return DexelGrid(template.nx, template.ny, template.h, res.off, res.z)
+
+
+def dilate(grid, k: float, cols=None, threads=None):
+    """Dilation by a ball of radius k*h.  With cols=None returns a full DexelGrid (float64)."""
+    r = _run(grid, k, 0, cols, threads)
+    return _as_grid(grid, r) if cols is None else r
+
+
+def erode(grid, k: float, cols=None, threads=None):
+    """Erosion by a ball of radius k*h (direct intersection form)."""
+    r = _run(grid, k, 1, cols, threads)
+    return _as_grid(grid, r) if cols is None else r
+
+
+def close(grid, k: float, threads=None):
+    """Closing = erosion of the dilation."""
+    return erode(dilate(grid, k, threads=threads), k, threads=threads)
+
+
+def open_(grid, k: float, threads=None):
+    """Opening = dilation of the erosion."""
+    return dilate(erode(grid, k, threads=threads), k, threads=threads)
+
+
+def complement(grid):
+    """Per-column complement within the grid: (-inf, a1], [b1, a2], ..., [bn, +inf).
+
+    An empty column becomes (-inf, +inf).  The closed complement intervals share endpoints
+    with the shape; the difference is measure-zero and is what erosion's zero-length rule
+    absorbs.
+    """
+    from synth.shapes import DexelGrid
+    zin = np.asarray(grid.z, np.float64)
+    cols = []
+    for c in range(grid.nx * grid.ny):
+        s0, s1 = grid.col_off[c], grid.col_off[c + 1]
+        pts = np.concatenate([[-np.inf], zin[s0:s1].reshape(-1), [np.inf]]).reshape(-1, 2)
+        # a shape piece reaching -inf or +inf leaves an empty (x, x) pair at that end
+        keep = ~((pts[:, 0] == pts[:, 1]) & np.isinf(pts[:, 0]))
+        cols.append(pts[keep])
+    cnt = np.array([len(p) for p in cols], np.int64)
+    off = np.zeros(grid.nx * grid.ny + 1, np.int64)
+    np.cumsum(cnt, out=off[1:])
+    z = np.concatenate(cols) if cols else np.zeros((0, 2))
+    return DexelGrid(grid.nx, grid.ny, grid.h, off, z)
