@@ -1,0 +1,338 @@
+"""Benchmark of the GB300 dexel offset path (one JSON line on rank 0).
+
+Workload (one step): the 512 x 512 grid of 200 seeded primitives (spheres, boxes, hollow
+shells; up to 16 segments per column, FP64 endpoints), dilated and eroded by balls of
+radius 2, 8 and 32 grid spacings -- six offsets per step.  Metric: output dexel columns per
+second (6 * 512^2 columns per step).  Inputs are resident in HBM when the timed region
+starts; the L2 is flushed (a 256 MiB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the FP64 CPU oracle is timed instead (on the host cores, on a bounded
+sample of columns of the same workload per step).  For N > 1 (torchrun) every rank runs its
+own replica of the workload (independent problems, no collective on the data path); the
+line reports the whole-job rate with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+RADII = (2.0, 8.0, 32.0)
+OPS = ("dilate", "erode")
+N = 512
+HBM_PEAK = None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload():
+    from synth import shapes
+    return shapes.config2()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        dist.init_process_group(backend)
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, ws, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args, rank, ws):
+    import numpy as np
+    import torch
+
+    import paper_1804_08968_gb300 as dx
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    g = workload()
+    grid = dx.Grid.from_synth(g, dtype=torch.float64)
+    ctx = dx.Context(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    units = len(OPS) * len(RADII) * g.nx * g.ny
+
+    def step(record=None):
+        launches = 0
+        outs = []
+        for op in OPS:
+            for k in RADII:
+                out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, grid, k, stream)
+                launches += ctx.last_launches
+                if record is not None:
+                    record.append((op, k, ctx.stage_ms(), ctx.stats()))
+                outs.append(out)
+        return launches, outs
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ctx.set_profiling(True)
+    rec = []
+    times = []
+    launches = 0
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            n, _ = step(rec)
+            e1.record(stream)
+            launches += n
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier(ws)
+    ctx.set_profiling(False)
+    ms_step = allmax(sum(times) / len(times), ws, device="cuda")
+    value = units * ws / (ms_step / 1e3)
+
+    # roofline of the dominant stage (pass 2: the y power-diagram sweep), per launch
+    s_bytes = 8
+    p2_ms = [r[2][2] for r in rec]
+    p1_ms = [r[2][1] for r in rec]
+    p2_bytes = [(2 * s_bytes + 2) * r[3][1] + s_bytes * 2 * r[3][3] + 8 * (g.nx * g.ny + 1)
+                for r in rec]
+    achieved = sum(p2_bytes) / (sum(p2_ms) / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    stages = [sum(r[2][q] for r in rec) for q in range(5)]
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    off_h = torch.from_numpy(np.asarray(g.col_off, np.int32)).pin_memory()
+    z_h = torch.from_numpy(np.asarray(g.z, np.float64)).pin_memory()
+    e2e_times = []
+    h2d = d2h = 0
+    for it in range(max(2, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        off_d = off_h.to("cuda", non_blocking=True)
+        z_d = z_h.to("cuda", non_blocking=True)
+        gd = dx.Grid(g.nx, g.ny, g.h, off_d, z_d)
+        b_in = off_h.numel() * 4 + z_h.numel() * 8
+        b_out = 0
+        for op in OPS:
+            for k in RADII:
+                out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, gd, k, stream)
+                o_off = out.col_off.to("cpu")
+                o_z = out.z.to("cpu")
+                b_out += o_off.numel() * 4 + o_z.numel() * 8
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        h2d, d2h = b_in, b_out
+    e2e_s = allmax(statistics.median(e2e_times), ws, device="cuda")
+
+    line = {
+        "metric": "output dexel columns/s", "value": value, "unit": "columns/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "512x512 grid, 200 seeded primitives (spheres/boxes/hollow shells, "
+                               "<=16 segs/col), dilation+erosion at k=2,8,32 spacings, FP64",
+                   "columns_per_step": units, "nseg_in": g.nseg, "l2": "flushed (256 MiB write) "
+                   "before every timed step", "parallelism": f"replica x{ws}"},
+        "e2e": {"value": units * ws / e2e_s, "unit": "columns/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_pass2 (y power-diagram sweep)",
+                     "peak_source": peak_kind},
+        "stage_ms_per_step": {"validate+tables": stages[0] / args.steps,
+                              "pass1": stages[1] / args.steps, "pass2": stages[2] / args.steps,
+                              "count+scan": stages[3] / args.steps, "write": stages[4] / args.steps},
+        "stats": {f"{op}_k{int(k)}": {"mid_pieces": st[1], "out_segs": st[3],
+                                      "max_pieces_col": st[4], "max_state": st[5]}
+                  for (op, k, _, st) in rec[: len(OPS) * len(RADII)]},
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0:
+        line["clocks"] = clk.summary()
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(g, args)
+        print(json.dumps(line), flush=True)
+
+
+def oracle_sample(g, cols_per_op, seed=0):
+    """Time the FP64 oracle on a bounded sample of columns of every offset of the step."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    n = 0
+    t = 0.0
+    for op in OPS:
+        for k in RADII:
+            cols = rng.choice(g.nx * g.ny, cols_per_op, replace=False)
+            t0 = time.perf_counter()
+            (oracle.dilate if op == "dilate" else oracle.erode)(g, k, cols=cols)
+            t += time.perf_counter() - t0
+            n += cols.size
+    return n, t
+
+
+def cpu_baseline(g, args):
+    import oracle
+    oracle.build()
+    n, t = oracle_sample(g, args.cpu_cols)
+    return {"value": n / t, "unit": "columns/s", "cores": oracle.default_threads(), "kind": "oracle",
+            "sample": f"{args.cpu_cols} random output columns per offset (6 offsets), FP64 brute-force "
+                      f"gather, {t:.1f} s"}
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    g = workload()
+    for _ in range(args.warmup):
+        oracle_sample(g, 50, seed=1)
+    times = []
+    n_tot = 0
+    for s in range(args.steps):
+        n, t = oracle_sample(g, args.ref_cols, seed=100 + s)
+        times.append(t)
+        n_tot += n
+    per_col = sum(times) / n_tot
+    units = len(OPS) * len(RADII) * g.nx * g.ny
+    value = 1.0 / per_col
+    line = {
+        "impl": "reference", "metric": "output dexel columns/s", "value": value, "unit": "columns/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": units * per_col * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "512x512 grid, 200 seeded primitives (spheres/boxes/hollow shells, "
+                               "<=16 segs/col), dilation+erosion at k=2,8,32 spacings, FP64",
+                   "columns_per_step": units, "nseg_in": g.nseg, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "columns/s", "cores": oracle.default_threads(),
+                         "kind": "oracle",
+                         "sample": f"{args.ref_cols} random output columns per offset per step"},
+        "e2e": {"value": value, "unit": "columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-cols", type=int, default=300)
+    ap.add_argument("--ref-cols", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, ws = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

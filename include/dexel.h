@@ -1,0 +1,160 @@
+/*
+ * dexel.h -- C ABI of the GB300 dexel offset library (libdexel.so).
+ *
+ * Morphological offsets of a shape stored as a dexel buffer (Sec. 3.1, "Dexel
+ * Representation"): a regular nx x ny grid of vertical rays; cell (i, j), centred at
+ * ((i+1/2)h, (j+1/2)h), holds the sorted disjoint segments [z_in, z_out] where its ray is
+ * inside the solid.  The library computes
+ *   dilation   D_r(S) = { p : |p - x| <= r for some x in S }      (Sec. 3.1, dilation eq.)
+ *   erosion    E_r(S) = complement of D_r(complement of S)         (Sec. 3.1, "Erosion")
+ *   closing    E_r(D_r(S)),  opening  D_r(E_r(S))                  (Sec. 4, "Topological Cleaning")
+ * exactly at the resolution of the input grid, by the two separable passes of Sec. 3.3:
+ * an extrusion along x that keeps, for every z, the distance to the nearest parent column
+ * (largest residual radius, Sec. 3.3 "3D Dilation"), then a dilation along y of those
+ * pieces split into extruded rectangles and endpoint disks, the latter computed with
+ * forward and backward half-space power diagrams of the endpoint seeds (Sec. 3.3
+ * "2D Power Diagram", Eq. of power cells, App. B), and a per-column merge of the reached
+ * intervals.  All work runs in CUDA kernels for sm_103a on one GPU.
+ *
+ * Layout (CSR, "col" numbers cells row-major: col = j*nx + i):
+ *   col_off : int32[nx*ny + 1], col_off[0] = 0, non-decreasing; column col owns segments
+ *             [col_off[col], col_off[col+1]).
+ *   z       : pairs (z_in, z_out), float (DEXEL_FP32_PRED64) or double (DEXEL_FP64),
+ *             2*nseg values; within a column z_in <= z_out < next z_in (strictly positive
+ *             gaps; zero-length segments are allowed and denote a tangent sample).
+ * The radius is given in grid spacings, k = r / h, so that the reach test
+ * n = di^2 + dj^2 <= k^2 is exact on integers.  The output grid is the input grid (same
+ * nx, ny, h); material pushed beyond the xy range of the grid is dropped, z is unbounded.
+ * Columns outside the grid take part neither in S nor in its complement.
+ *
+ * Memory: every pointer in dexel_grid_in / dexel_grid_out and the workspace are DEVICE
+ * pointers owned by the caller.  Inputs are never written.  Calls are ordered on the
+ * given CUDA stream (a cudaStream_t passed as void*; NULL = legacy default stream); they
+ * synchronise that stream internally to size intermediate buffers and return only after
+ * the result is complete.  No exception or abort crosses this boundary: every failure is a
+ * dexel_status.
+ */
+#ifndef DEXEL_H
+#define DEXEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DEXEL_OK = 0,
+  DEXEL_ERR_INVALID_ARG = -1, /* null pointer, bad size, k < 0 or not finite, h <= 0 ...  */
+  DEXEL_ERR_BAD_CSR = -2,     /* offsets not monotone, z_in > z_out, gap <= 0, NaN        */
+  DEXEL_ERR_CAPACITY = -3,    /* output or workspace too small; see dexel_last_required  */
+  DEXEL_ERR_CUDA = -4,        /* a CUDA runtime call failed                                */
+  DEXEL_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up                        */
+  DEXEL_ERR_NOMEM = -6        /* host-side allocation failed                               */
+} dexel_status;
+
+/* Storage precision of the endpoints (input, intermediate and output).
+ * DEXEL_FP64:        double endpoints, every computation in double.
+ * DEXEL_FP32_PRED64: float endpoints; the power-diagram breakpoint and dominance
+ *                    predicates and the merge comparisons are decided with double-accurate
+ *                    arithmetic (an error-bounded float filter, double when undecided);
+ *                    output endpoints are computed in double and rounded once to float. */
+typedef enum { DEXEL_FP64 = 0, DEXEL_FP32_PRED64 = 1 } dexel_mode;
+
+typedef enum { DEXEL_DILATE = 0, DEXEL_ERODE = 1, DEXEL_CLOSE = 2, DEXEL_OPEN = 3 } dexel_op;
+
+typedef struct {
+  int32_t nx, ny;         /* grid size, 1 <= nx, ny <= 32768                                */
+  double h;               /* xy spacing, in the same units as z (> 0)                       */
+  const int32_t* col_off; /* device, nx*ny + 1 entries                                      */
+  const void* z;          /* device, 2*nseg endpoints (float or double, see dexel_mode)      */
+  int64_t nseg;           /* number of segments (= col_off[nx*ny])                          */
+} dexel_grid_in;
+
+typedef struct {
+  int32_t* col_off;     /* device, nx*ny + 1 entries, written                              */
+  void* z;              /* device, room for 2*capacity_seg endpoints, written               */
+  int64_t capacity_seg; /* size of z in segments                                           */
+  int64_t nseg;         /* written on return: number of output segments (also when the
+                           call fails with DEXEL_ERR_CAPACITY, so the caller can retry)    */
+} dexel_grid_out;
+
+typedef struct dexel_ctx dexel_ctx;
+
+/* Create / destroy a context bound to CUDA device `device`.  The context owns only small
+ * tables (the half-width table w[n] = h sqrt(k^2 - n), reach table) and status words. */
+dexel_status dexel_ctx_create(dexel_ctx** ctx, int device);
+void dexel_ctx_destroy(dexel_ctx* ctx);
+
+/* Suggested workspace size in bytes for an offset of `in` by k spacings.  The true need is
+ * data dependent (intermediate pieces grow with k, Sec. 3.4); when a call finds the
+ * workspace too small it returns DEXEL_ERR_CAPACITY and dexel_last_required() gives the
+ * size that suffices.  Never returns less than the fixed part. */
+size_t dexel_workspace_size(const dexel_grid_in* in, double k, dexel_mode mode);
+
+/* Bytes of workspace the last call on ctx needed (valid after DEXEL_ERR_CAPACITY too). */
+size_t dexel_last_required(const dexel_ctx* ctx);
+
+/* Check a CSR grid on the device: offsets start at 0, are non-decreasing and end at nseg;
+ * every segment has z_in <= z_out, consecutive segments of a column have z_out < next
+ * z_in, no NaN.  Returns DEXEL_OK or DEXEL_ERR_BAD_CSR. */
+dexel_status dexel_validate(dexel_ctx* ctx, const dexel_grid_in* in, dexel_mode mode,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* Dilation of `in` by a ball of radius k*h (Sec. 3.1 dilation eq., Sec. 3.3 two passes).
+ * k >= 0 and finite.  On success out->col_off / out->z hold the result and out->nseg its
+ * size.  If out->capacity_seg is too small: DEXEL_ERR_CAPACITY, out->nseg = required
+ * size, out->z untouched.  If the workspace is too small: DEXEL_ERR_CAPACITY and
+ * dexel_last_required(ctx) > ws_bytes. */
+dexel_status dexel_dilate(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_mode mode,
+                          dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Erosion by a ball of radius k*h: the complement of the dilation of the complement
+ * (Sec. 3.1 "Erosion"), with the complement taken per column on the fly (+-inf sentinels)
+ * and undone when storing; results of zero length are dropped.  Same contract as
+ * dexel_dilate. */
+dexel_status dexel_erode(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_mode mode,
+                         dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Closing (erode after dilate) or opening (dilate after erode) by the same radius; the
+ * intermediate grid lives in the workspace.  op must be DEXEL_CLOSE or DEXEL_OPEN. */
+dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
+                         dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
+                         void* stream);
+
+/* Batched offsets: nshapes independent grids, each with its own radius and operation.
+ * ins / k / ops / outs are HOST arrays of nshapes entries whose grid pointers are device
+ * pointers.  d_status (device, nshapes int32) receives each shape's dexel_status.  The
+ * return value is the first failing status (or DEXEL_OK). */
+dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_in* ins,
+                                  const double* k, const dexel_op* ops, dexel_mode mode,
+                                  dexel_grid_out* outs, void* ws, size_t ws_bytes,
+                                  int32_t* d_status, void* stream);
+
+/* Static description of a status code. */
+const char* dexel_status_string(dexel_status s);
+
+/* Kernel launches issued by the last call on ctx (for launch accounting). */
+int64_t dexel_last_launches(const dexel_ctx* ctx);
+
+/* Turn per-stage timing on or off (off by default).  When on, each call brackets its
+ * stages with CUDA events on the call's stream; dexel_last_stage_ms then reports the
+ * device time of each stage of the last call (summed over both offsets of a closing or
+ * opening): [0] validation + tables, [1] pass 1 (x-extrusion sweep), [2] pass 2 (y power
+ * sweep), [3] output count + scan, [4] output write.  Returns the number of entries written
+ * (at most max). */
+void dexel_set_profiling(dexel_ctx* ctx, int on);
+int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max);
+
+/* Sizes seen by the last call (summed over both offsets of a closing or opening):
+ * [0] input segments, [1] S_mid pieces (pass-1 output), [2] pass-2 intervals before the final
+ * complement/rounding, [3] output segments, [4] max pieces in one S_mid column, [5] max live
+ * elements in one sweep state.  Returns the number of entries written (at most max). */
+int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEXEL_H */

@@ -1,0 +1,235 @@
+"""GB300 dexel offsets: Python binding of libdexel (include/dexel.h).
+
+Argument marshalling only: torch provides device memory and the CUDA stream, every step of
+the computation runs in the library's CUDA kernels.  There is no CPU fallback -- if the
+library cannot be loaded the import of ``lib()`` raises.
+
+Typical use::
+
+    import paper_1804_08968_gb300 as dx
+    g = dx.Grid.from_host(nx, ny, h, col_off, z, dtype=torch.float64)   # CSR on the GPU
+    d = dx.dilate(g, k=8.0)              # ball of radius 8 grid spacings
+    e = dx.erode(g, k=8.0)
+    c = dx.close(g, k=8.0)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Grid", "Context", "dilate", "erode", "close", "open_", "lib", "DexelError",
+           "FP64", "FP32_PRED64"]
+
+FP64 = 0
+FP32_PRED64 = 1
+DILATE, ERODE, CLOSE, OPEN = 0, 1, 2, 3
+STATUS = {0: "ok", -1: "invalid argument", -2: "malformed CSR dexel grid",
+          -3: "capacity too small", -4: "CUDA runtime error", -5: "device wait timeout",
+          -6: "out of memory"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libdexel.so")
+_lib = None
+
+
+class DexelError(RuntimeError):
+    def __init__(self, code, what=""):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class _In(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("h", ctypes.c_double),
+                ("col_off", ctypes.c_void_p), ("z", ctypes.c_void_p), ("nseg", ctypes.c_int64)]
+
+
+class _Out(ctypes.Structure):
+    _fields_ = [("col_off", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("capacity_seg", ctypes.c_int64), ("nseg", ctypes.c_int64)]
+
+
+def lib():
+    """Load libdexel.so (built by ``paper_1804_08968_gb300.build``); raise if missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIBPATH):
+            raise ImportError(f"libdexel.so not built ({_LIBPATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(_LIBPATH)
+        P = ctypes.c_void_p
+        L.dexel_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
+        L.dexel_ctx_destroy.argtypes = [P]
+        L.dexel_ctx_destroy.restype = None
+        for name in ("dexel_dilate", "dexel_erode"):
+            f = getattr(L, name)
+            f.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
+                          ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
+        L.dexel_morph.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
+        L.dexel_validate.argtypes = [P, ctypes.POINTER(_In), ctypes.c_int, P, ctypes.c_size_t, P]
+        L.dexel_offset_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(_In),
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                           ctypes.POINTER(_Out), P, ctypes.c_size_t, P, P]
+        L.dexel_workspace_size.argtypes = [ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int]
+        L.dexel_workspace_size.restype = ctypes.c_size_t
+        L.dexel_last_required.argtypes = [P]
+        L.dexel_last_required.restype = ctypes.c_size_t
+        L.dexel_last_launches.argtypes = [P]
+        L.dexel_last_launches.restype = ctypes.c_int64
+        L.dexel_status_string.argtypes = [ctypes.c_int]
+        L.dexel_status_string.restype = ctypes.c_char_p
+        L.dexel_set_profiling.argtypes = [P, ctypes.c_int]
+        L.dexel_set_profiling.restype = None
+        L.dexel_last_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.dexel_last_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Grid:
+    """A CSR dexel grid resident on the GPU (col_off int32, z (nseg, 2) float32/float64)."""
+
+    def __init__(self, nx, ny, h, col_off, z):
+        self.nx, self.ny, self.h = int(nx), int(ny), float(h)
+        self.col_off = col_off
+        self.z = z
+
+    @property
+    def nseg(self) -> int:
+        return int(self.z.shape[0])
+
+    @property
+    def mode(self) -> int:
+        return FP64 if self.z.dtype == _torch().float64 else FP32_PRED64
+
+    @classmethod
+    def from_host(cls, nx, ny, h, col_off, z, dtype=None, device="cuda"):
+        torch = _torch()
+        dtype = dtype or (torch.float32 if np.asarray(z).dtype == np.float32 else torch.float64)
+        off = torch.as_tensor(np.asarray(col_off, np.int32)).to(device)
+        zz = torch.as_tensor(np.asarray(z).reshape(-1, 2)).to(device=device, dtype=dtype)
+        return cls(nx, ny, h, off.contiguous(), zz.contiguous())
+
+    @classmethod
+    def from_synth(cls, g, dtype=None, device="cuda"):
+        return cls.from_host(g.nx, g.ny, g.h, g.col_off, g.z, dtype=dtype, device=device)
+
+    def to_host(self):
+        return self.col_off.cpu().numpy().astype(np.int64), self.z.cpu().numpy()
+
+    def _in(self) -> _In:
+        torch = _torch()
+        z = self.z if self.z.numel() else torch.zeros((1, 2), dtype=self.z.dtype, device=self.z.device)
+        self._keep = z
+        return _In(self.nx, self.ny, self.h, self.col_off.data_ptr(), z.data_ptr(), self.nseg)
+
+
+class Context:
+    """One libdexel context per device; owns the library's scratch between calls."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.ptr = ctypes.c_void_p()
+        rc = lib().dexel_ctx_create(ctypes.byref(self.ptr), device)
+        if rc != 0:
+            raise DexelError(rc, "dexel_ctx_create")
+        self._cap_hint = {}
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                lib().dexel_ctx_destroy(self.ptr)
+        except Exception:  # pragma: no cover
+            pass
+
+    @property
+    def last_launches(self) -> int:
+        return int(lib().dexel_last_launches(self.ptr))
+
+    def set_profiling(self, on: bool) -> None:
+        """Bracket each stage of every call with CUDA events on the call's stream."""
+        lib().dexel_set_profiling(self.ptr, 1 if on else 0)
+
+    def stage_ms(self):
+        """Device ms of [validate+tables, pass 1, pass 2, count+scan, write] of the last call."""
+        a = (ctypes.c_double * 5)()
+        n = lib().dexel_last_stage_ms(self.ptr, a, 5)
+        return [a[i] for i in range(n)]
+
+    def stats(self):
+        """[input segments, S_mid pieces, pass-2 intervals, output segments, max pieces per
+        S_mid column, max live sweep state] of the last call."""
+        a = (ctypes.c_int64 * 6)()
+        n = lib().dexel_last_stats(self.ptr, a, 6)
+        return [int(a[i]) for i in range(n)]
+
+    def _stream(self, stream):
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def run(self, op: int, g: Grid, k: float, stream=None, capacity=None) -> Grid:
+        torch = _torch()
+        key = (op, g.nx, g.ny, g.nseg, float(k), g.mode)
+        cap = capacity or self._cap_hint.get(key) or max(2 * g.nseg + g.nx * g.ny // 4, 1024)
+        gin = g._in()
+        st = self._stream(stream)
+        for _ in range(3):
+            off = torch.empty(g.nx * g.ny + 1, dtype=torch.int32, device=g.col_off.device)
+            z = torch.empty((cap, 2), dtype=g.z.dtype, device=g.z.device)
+            out = _Out(off.data_ptr(), z.data_ptr(), cap, 0)
+            if op == DILATE:
+                rc = lib().dexel_dilate(self.ptr, ctypes.byref(gin), k, g.mode, ctypes.byref(out), None, 0, st)
+            elif op == ERODE:
+                rc = lib().dexel_erode(self.ptr, ctypes.byref(gin), k, g.mode, ctypes.byref(out), None, 0, st)
+            else:
+                rc = lib().dexel_morph(self.ptr, ctypes.byref(gin), k, op, g.mode, ctypes.byref(out), None, 0, st)
+            if rc == -3 and out.nseg > cap:
+                cap = int(out.nseg) + 16
+                continue
+            if rc != 0:
+                raise DexelError(rc, "dexel offset")
+            self._cap_hint[key] = cap
+            return Grid(g.nx, g.ny, g.h, off, z[: out.nseg])
+        raise DexelError(-3, "dexel offset (output capacity)")
+
+    def validate(self, g: Grid, stream=None) -> int:
+        gin = g._in()
+        return int(lib().dexel_validate(self.ptr, ctypes.byref(gin), g.mode, None, 0, self._stream(stream)))
+
+
+_ctx = {}
+
+
+def _default_ctx(g: Grid) -> Context:
+    dev = g.col_off.device.index or 0
+    if dev not in _ctx:
+        _ctx[dev] = Context(dev)
+    return _ctx[dev]
+
+
+def dilate(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
+    """Dilation by a ball of radius k grid spacings (exact on the dexel grid)."""
+    return (ctx or _default_ctx(g)).run(DILATE, g, k, stream)
+
+
+def erode(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
+    """Erosion by a ball of radius k grid spacings (complement of the dilated complement)."""
+    return (ctx or _default_ctx(g)).run(ERODE, g, k, stream)
+
+
+def close(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
+    """Closing: erosion of the dilation."""
+    return (ctx or _default_ctx(g)).run(CLOSE, g, k, stream)
+
+
+def open_(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
+    """Opening: dilation of the erosion."""
+    return (ctx or _default_ctx(g)).run(OPEN, g, k, stream)

@@ -1,0 +1,745 @@
+// Host side of libdexel: the C ABI declared in include/dexel.h, workspace planning, and the
+// small kernels around the two sweeps (CSR validation, half-width table, output
+// compaction with the erosion complement and the final rounding).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dexel.h"
+#include "launch.h"
+
+using namespace dexel;
+
+struct dexel_ctx {
+  int device = 0;
+  int sm_count = 0;
+  // library-owned scratch, used when the caller passes ws == NULL
+  void* own = nullptr;
+  size_t own_bytes = 0;
+  // intermediate grid of closing / opening
+  void* mid = nullptr;
+  size_t mid_bytes = 0;
+  size_t last_required = 0;
+  long long launches = 0;
+  // capacities learnt from earlier calls (grown on overflow)
+  int capD = 1024, capR = 1024;
+  long long needF = 0, needM = 0, needO = 0;  // arena entries
+  Counters host_ctr{};
+  // optional per-stage timing with CUDA events on the call's stream
+  bool profiling = false;
+  cudaEvent_t ev[10] = {};
+  double stage_ms[5] = {0, 0, 0, 0, 0};
+  long long stats[6] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int reach_of(double kk) {
+  if (!(kk >= 0)) return -1;
+  long long R = (long long)std::floor(std::sqrt(kk));
+  while ((double)((R + 1) * (R + 1)) <= kk) ++R;
+  while (R > 0 && (double)(R * R) > kk) --R;
+  return (int)R;
+}
+
+// ------------------------------------------------------------------------------------------
+// small kernels
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_validate(int ncols, const int* off, const T* z, long long nseg, Counters* ctr) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  const int s0 = off[c], s1 = off[c + 1];
+  bool bad = false;
+  if (c == 0 && s0 != 0) bad = true;
+  if (c == ncols - 1 && (long long)s1 != nseg) bad = true;
+  if (s1 < s0 || s0 < 0 || (long long)s1 > nseg) bad = true;
+  if (!bad) {
+    for (int s = s0; s < s1; ++s) {
+      const T a = z[2LL * s], b = z[2LL * s + 1];
+      if (!(a <= b)) { bad = true; break; }  // also catches NaN
+      if (!(a > -(T)INFINITY) || !(b < (T)INFINITY)) { bad = true; break; }
+      if (s + 1 < s1 && !(b < z[2LL * (s + 1)])) { bad = true; break; }
+    }
+    atomicMax(&ctr->max_segs_in, s1 - s0);
+  }
+  if (bad) atomicOr(&ctr->status, ST_BAD_CSR);
+}
+
+__global__ void k_tables(double kk, double h, int nmax, int K, double* wtab, int* reach) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n <= nmax) wtab[n] = h * sqrt(kk - (double)n);  // half-width h sqrt(k^2 - n)
+  if (n <= K) {
+    // largest dy with n + dy^2 <= k^2 for n = dx^2
+    const long long d2 = (long long)n * n;
+    long long R = (long long)floor(sqrt(fmax(kk - (double)d2, 0.0)));
+    while ((double)(d2 + (R + 1) * (R + 1)) <= kk) ++R;
+    while (R > 0 && (double)(d2 + R * R) > kk) --R;
+    reach[n] = (int)R;
+  }
+}
+
+// One output column: optional complement (erosion), rounding to T, and re-merge of pieces
+// that touch after rounding.  Returns the count; writes pieces when out != nullptr.
+template <typename T>
+__device__ int finalize_column(const double* l, const double* r, int m, bool erode, T* out) {
+  int cnt = 0;
+  T ca = 0, cb = 0;
+  bool have = false;
+  auto push = [&](double a, double b) {
+    const T ta = (T)a, tb = (T)b;
+    if (erode && !(ta < tb)) return;
+    if (have && ta <= cb) {
+      if (tb > cb) cb = tb;
+      return;
+    }
+    if (have) {
+      if (out) { out[2 * cnt] = ca; out[2 * cnt + 1] = cb; }
+      ++cnt;
+    }
+    ca = ta;
+    cb = tb;
+    have = true;
+  };
+  if (!erode) {
+    for (int t = 0; t < m; ++t) push(l[t], r[t]);
+  } else if (m == 0) {
+    push(-INFINITY, INFINITY);
+  } else {
+    if (l[0] > -INFINITY) push(-INFINITY, l[0]);
+    for (int t = 0; t + 1 < m; ++t) push(r[t], l[t + 1]);
+    if (r[m - 1] < INFINITY) push(r[m - 1], INFINITY);
+  }
+  if (have) {
+    if (out) { out[2 * cnt] = ca; out[2 * cnt + 1] = cb; }
+    ++cnt;
+  }
+  return cnt;
+}
+
+template <typename T>
+__global__ void k_count(int ncols, const long long* ostart, const int* ocnt, const double* ol,
+                        const double* orr, int erode, long long* cnt) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  const long long s = ostart[c];
+  cnt[c] = finalize_column<T>(ol + s, orr + s, ocnt[c], erode != 0, nullptr);
+}
+
+template <typename T>
+__global__ void k_write(int ncols, const long long* ostart, const int* ocnt, const double* ol,
+                        const double* orr, int erode, const long long* pos, T* z) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  const long long s = ostart[c];
+  finalize_column<T>(ol + s, orr + s, ocnt[c], erode != 0, z + 2 * pos[c]);
+}
+
+// exclusive scan of cnt[0..n) (int64) in three launches; writes pos (int64) and col_off
+constexpr int kScanThreads = 256, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
+
+__global__ void k_scan1(long long n, const long long* cnt, long long* pos, long long* sums) {
+  __shared__ long long sh[kScanThreads];
+  const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+  long long v[kScanPer];
+  long long s = 0;
+  for (int q = 0; q < kScanPer; ++q) {
+    v[q] = base + q < n ? cnt[base + q] : 0;
+    s += v[q];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {
+    const long long u = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += u;
+    __syncthreads();
+  }
+  long long run = sh[threadIdx.x] - s;
+  for (int q = 0; q < kScanPer; ++q) {
+    if (base + q < n) pos[base + q] = run;
+    run += v[q];
+  }
+  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = sh[threadIdx.x];
+}
+
+__global__ void k_scan2(long long nb, long long* sums) {
+  __shared__ long long sh[kScanThreads];
+  long long carry = 0;
+  for (long long b0 = 0; b0 < nb; b0 += kScanThreads) {
+    const long long b = b0 + threadIdx.x;
+    const long long v = b < nb ? sums[b] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kScanThreads; o <<= 1) {
+      const long long u = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += u;
+      __syncthreads();
+    }
+    if (b < nb) sums[b] = carry + sh[threadIdx.x] - v;
+    const long long tot = sh[kScanThreads - 1];
+    __syncthreads();
+    carry += tot;
+  }
+  if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void k_scan3(long long n, long long* pos, const long long* sums, int* col_off,
+                        Counters* ctr) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    const long long p = pos[t] + sums[t / kScanTile];
+    pos[t] = p;
+    if (p > 0x7fffffffLL) atomicOr(&ctr->status, ST_TOO_MANY_OUT);
+    col_off[t] = (int)p;
+  }
+  if (t == n) {
+    const long long tot = sums[(n + kScanTile - 1) / kScanTile];
+    if (tot > 0x7fffffffLL) atomicOr(&ctr->status, ST_TOO_MANY_OUT);
+    col_off[n] = (int)tot;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// workspace carving
+// ------------------------------------------------------------------------------------------
+struct Carver {
+  char* base;
+  size_t cap;
+  size_t used = 0;
+  bool ok = true;
+  void* take(size_t bytes) {
+    used = align_up(used, 256);
+    void* p = base ? base + used : nullptr;
+    used += bytes;
+    if (used > cap) ok = false;
+    return ok ? p : nullptr;
+  }
+};
+
+struct Ws {
+  void* base;
+  size_t bytes;
+  bool owned;
+};
+
+void mark(dexel_ctx* ctx, int e, cudaStream_t st) {
+  if (!ctx->profiling) return;
+  if (!ctx->ev[e]) cudaEventCreate(&ctx->ev[e]);
+  cudaEventRecord(ctx->ev[e], st);
+}
+
+void reset_call(dexel_ctx* ctx) {
+  ctx->launches = 0;
+  for (double& m : ctx->stage_ms) m = 0;
+  for (long long& x : ctx->stats) x = 0;
+}
+
+dexel_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DEXEL_OK;
+  return e == cudaErrorMemoryAllocation ? DEXEL_ERR_NOMEM : DEXEL_ERR_CUDA;
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_status(e_);       \
+  } while (0)
+
+dexel_status ensure_owned(dexel_ctx* ctx, size_t bytes) {
+  if (ctx->own_bytes >= bytes) return DEXEL_OK;
+  if (ctx->own) {
+    cudaFree(ctx->own);
+    ctx->own = nullptr;
+    ctx->own_bytes = 0;
+  }
+  size_t b = align_up(bytes + bytes / 4, 1 << 20);
+  if (cudaMalloc(&ctx->own, b) != cudaSuccess) {
+    cudaGetLastError();
+    return DEXEL_ERR_NOMEM;
+  }
+  ctx->own_bytes = b;
+  return DEXEL_OK;
+}
+
+template <typename T>
+struct Offset {
+  // one offset (dilation of S or of its complement) of a grid into the output CSR
+  static dexel_status run(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erode,
+                          dexel_grid_out* out, void* ws, size_t ws_bytes, cudaStream_t st);
+};
+
+template <typename T>
+dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erode,
+                            dexel_grid_out* out, void* ws_user, size_t ws_user_bytes,
+                            cudaStream_t st) {
+  const int nx = in->nx, ny = in->ny;
+  const long long ncols = (long long)nx * ny;
+  const double kk = k * k;
+  const int K = reach_of(kk);
+  const int nmax = (int)std::floor(kk);
+  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
+  const int blocks = sms * 4;
+  const int nwarps = blocks * kWarpsPerBlock;
+
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    // ---------------- plan
+    // phase A: counters, tables, indices, validation
+    auto plan = [&](Carver& C, void** pctr, void** pwtab, void** preach, void** pmstart,
+                    void** pmcnt, void** postart, void** pocnt, void** pcnt, void** ppos,
+                    void** psums) {
+      *pctr = C.take(sizeof(Counters));
+      *pwtab = C.take(sizeof(double) * (nmax + 2));
+      *preach = C.take(sizeof(int) * (K + 2));
+      *pmstart = C.take(sizeof(long long) * ncols);
+      *pmcnt = C.take(sizeof(int) * ncols);
+      *postart = C.take(sizeof(long long) * ncols);
+      *pocnt = C.take(sizeof(int) * ncols);
+      *pcnt = C.take(sizeof(long long) * (ncols + 1));
+      *ppos = C.take(sizeof(long long) * (ncols + 1));
+      *psums = C.take(sizeof(long long) * ((ncols + kScanTile) / kScanTile + 2));
+    };
+    Carver probe{nullptr, (size_t)-1};
+    void *pctr, *pwtab, *preach, *pmstart, *pmcnt, *postart, *pocnt, *pcnt, *ppos, *psums;
+    plan(probe, &pctr, &pwtab, &preach, &pmstart, &pmcnt, &postart, &pocnt, &pcnt, &ppos, &psums);
+    const size_t fixed = align_up(probe.used, 256);
+    // input statistics first (needs only the fixed part)
+    Ws W;
+    if (ws_user) {
+      W = {ws_user, ws_user_bytes, false};
+      if (ws_user_bytes < fixed) {
+        ctx->last_required = fixed;
+        return DEXEL_ERR_CAPACITY;
+      }
+    } else {
+      dexel_status s = ensure_owned(ctx, fixed + (64u << 20));
+      if (s != DEXEL_OK) return s;
+      W = {ctx->own, ctx->own_bytes, true};
+    }
+    Carver C{(char*)W.base, W.bytes};
+    plan(C, &pctr, &pwtab, &preach, &pmstart, &pmcnt, &postart, &pocnt, &pcnt, &ppos, &psums);
+    Counters* ctr = (Counters*)pctr;
+    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+    mark(ctx, 0, st);
+    {
+      const int thr = 256;
+      k_validate<T><<<(unsigned)((ncols + thr - 1) / thr), thr, 0, st>>>(
+          (int)ncols, in->col_off, (const T*)in->z, in->nseg, ctr);
+      ++ctx->launches;
+      k_tables<<<(std::max(nmax, K) + 1 + 255) / 256, 256, 0, st>>>(kk, in->h, nmax, K,
+                                                                    (double*)pwtab, (int*)preach);
+      ++ctx->launches;
+      CK(cudaGetLastError());
+    }
+    mark(ctx, 1, st);
+    Counters hc;
+    CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hc.status & ST_BAD_CSR) return DEXEL_ERR_BAD_CSR;
+
+    // ---------------- pass 1 plan
+    const int capS = hc.max_segs_in + 2;
+    long long capF_ll = 2LL * (K + 1) * capS + 8;
+    const int capF = (int)std::min<long long>(capF_ll, 1 << 24);
+    const int items1_target = nwarps * 2;
+    int nch1 = std::max(1, std::min(nx, (items1_target + ny - 1) / ny));
+    int chunk1 = (nx + nch1 - 1) / nch1;
+    nch1 = (nx + chunk1 - 1) / chunk1;
+    const long long sb1 = p1_slot_bytes<T>(capF, capS, chunk1);
+    // arena estimates (entries)
+    const long long segs = std::max<long long>(in->nseg + ncols, 1024);
+    long long eM = std::max<long long>(ctx->needM, segs * std::min(K + 2, 16));
+    long long eF = std::max<long long>(ctx->needF, eM);
+    long long eO = std::max<long long>(ctx->needO, segs * 2);
+    const size_t bF = align_up((size_t)eF * std::max<size_t>(2 * sizeof(T) + 2, 16), 256);
+    const size_t bM = align_up((size_t)eM * (2 * sizeof(T) + 2), 256);
+    const size_t bO = align_up((size_t)eO * 16, 256);
+    // pass-2 slot estimate from the remembered capacities
+    const long long sb2_est = p2_slot_bytes<T>(std::max(capS * 4, 64), ctx->capR, ctx->capD, 1024);
+    const size_t slots = std::max((size_t)sb1, (size_t)sb2_est) * nwarps;
+    const size_t total = fixed + bF + bM + bO + slots + 4096;
+    if (ws_user && total > ws_user_bytes) {
+      ctx->last_required = total;
+      return DEXEL_ERR_CAPACITY;
+    }
+    if (!ws_user) {
+      dexel_status s = ensure_owned(ctx, total);
+      if (s != DEXEL_OK) return s;
+      if (ctx->own != W.base) {  // reallocated: the fixed part moved
+        continue;
+      }
+    }
+    char* aF = (char*)C.take(bF);
+    char* aM = (char*)C.take(bM);
+    char* aO = (char*)C.take(bO);
+    const size_t slot_room = (W.bytes > C.used + 256) ? W.bytes - align_up(C.used, 256) - 256 : 0;
+    char* pslots = (char*)C.take(slot_room);
+    if (!C.ok || !aF || !aM || !aO || !pslots) {
+      ctx->last_required = total;
+      if (ws_user) return DEXEL_ERR_CAPACITY;
+      continue;
+    }
+
+    // ---------------- pass 1
+    P1Params<T> p1{};
+    p1.nx = nx; p1.ny = ny; p1.K = K; p1.erode = erode ? 1 : 0;
+    p1.chunk = chunk1; p1.nchunks = nch1;
+    p1.col_off = in->col_off; p1.z = (const T*)in->z;
+    const long long capF1 = (long long)(bF / (2 * sizeof(T) + 2));
+    p1.f_a = (T*)aF; p1.f_b = (T*)aF + capF1; p1.f_l = (short*)((T*)aF + 2 * capF1);
+    p1.f_cap = capF1;
+    const long long capM = (long long)(bM / (2 * sizeof(T) + 2));
+    p1.m_a = (T*)aM; p1.m_b = (T*)aM + capM; p1.m_l = (short*)((T*)aM + 2 * capM);
+    p1.m_cap = capM;
+    p1.m_start = (long long*)pmstart; p1.m_cnt = (int*)pmcnt;
+    p1.blk = 256;
+    p1.ctr = ctr;
+    p1.slots = pslots; p1.slot_bytes = sb1;
+    p1.capF = capF; p1.capS = capS;
+    const int nw1 = (int)std::min<long long>(nwarps, (long long)(slot_room / sb1));
+    if (nw1 < kWarpsPerBlock) {
+      ctx->last_required = total + (size_t)sb1 * kWarpsPerBlock;
+      if (ws_user) return DEXEL_ERR_CAPACITY;
+      ensure_owned(ctx, ctx->last_required);
+      continue;
+    }
+    mark(ctx, 2, st);
+    CK(launch_pass1<T>(p1, nw1 / kWarpsPerBlock, st));
+    mark(ctx, 3, st);
+    ++ctx->launches;
+    CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->needF = std::max<long long>(ctx->needF, (long long)hc.arena_top[0]);
+    ctx->needM = std::max<long long>(ctx->needM, (long long)hc.arena_top[1]);
+    if (hc.status & (ST_OVERFLOW_SLOT | ST_OVERFLOW_ARENA)) {
+      ctx->last_required = total + (size_t)(hc.arena_top[0] + hc.arena_top[1]) * 16;
+      if (hc.status & ST_OVERFLOW_SLOT) return DEXEL_ERR_CAPACITY;  // bound exceeded: give up
+      if (ws_user) return DEXEL_ERR_CAPACITY;
+      continue;
+    }
+
+    // ---------------- pass 2
+    const int capP = std::max(hc.max_pieces, 1) + 2;
+    const int items2_target = nwarps * 2;
+    int nch2 = std::max(1, std::min(ny, (items2_target + nx - 1) / nx));
+    int chunk2 = (ny + nch2 - 1) / nch2;
+    nch2 = (ny + chunk2 - 1) / chunk2;
+    P2Params<T> p2{};
+    p2.nx = nx; p2.ny = ny; p2.K = K; p2.kk = kk; p2.h2 = in->h * in->h;
+    p2.chunk = chunk2; p2.nchunks = nch2;
+    p2.wtab = (const double*)pwtab; p2.reach = (const int*)preach;
+    p2.m_a = p1.m_a; p2.m_b = p1.m_b; p2.m_l = p1.m_l;
+    p2.m_start = p1.m_start; p2.m_cnt = p1.m_cnt;
+    const long long capF2 = (long long)(bF / 16);
+    p2.f_l = (double*)aF; p2.f_r = (double*)aF + capF2; p2.f_cap = capF2;
+    const long long capO = (long long)(bO / 16);
+    p2.o_l = (double*)aO; p2.o_r = (double*)aO + capO; p2.o_cap = capO;
+    p2.o_start = (long long*)postart; p2.o_cnt = (int*)pocnt;
+    p2.blk = 256;
+    p2.ctr = ctr;
+    p2.capP = capP; p2.capR = ctx->capR; p2.capD = ctx->capD;
+    const long long sb2 = p2_slot_bytes<T>(capP, p2.capR, p2.capD, chunk2);
+    p2.slots = pslots; p2.slot_bytes = sb2;
+    const int nw2 = (int)std::min<long long>(nwarps, (long long)(slot_room / sb2));
+    if (nw2 < kWarpsPerBlock) {
+      ctx->last_required = total + (size_t)sb2 * nwarps;
+      if (ws_user) return DEXEL_ERR_CAPACITY;
+      ensure_owned(ctx, ctx->last_required);
+      continue;
+    }
+    mark(ctx, 4, st);
+    CK(launch_pass2<T>(p2, nw2 / kWarpsPerBlock, st));
+    mark(ctx, 5, st);
+    ++ctx->launches;
+    CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->needF = std::max<long long>(ctx->needF, (long long)hc.arena_top[2] * 16 / (long long)(2 * sizeof(T) + 2) + 1);
+    ctx->needO = std::max<long long>(ctx->needO, (long long)hc.arena_top[3]);
+    if (hc.status & ST_OVERFLOW_SLOT) {
+      // a per-warp state outgrew its arrays: double them and retry
+      ctx->capD *= 2;
+      ctx->capR *= 2;
+      ctx->last_required = total + (size_t)p2_slot_bytes<T>(capP, ctx->capR, ctx->capD, chunk2) * nwarps;
+      if (ws_user) return DEXEL_ERR_CAPACITY;
+      continue;
+    }
+    if (hc.status & ST_OVERFLOW_ARENA) {
+      ctx->last_required = total + (size_t)(hc.arena_top[2] + hc.arena_top[3]) * 16;
+      if (ws_user) return DEXEL_ERR_CAPACITY;
+      continue;
+    }
+
+    // ---------------- compaction into the caller's CSR
+    const int thr = 256;
+    const unsigned gb = (unsigned)((ncols + thr - 1) / thr);
+    mark(ctx, 6, st);
+    k_count<T><<<gb, thr, 0, st>>>((int)ncols, (const long long*)postart, (const int*)pocnt,
+                                   p2.o_l, p2.o_r, erode ? 1 : 0, (long long*)pcnt);
+    const long long nb = (ncols + kScanTile - 1) / kScanTile;
+    k_scan1<<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, (const long long*)pcnt, (long long*)ppos,
+                                                  (long long*)psums);
+    k_scan2<<<1, kScanThreads, 0, st>>>(nb, (long long*)psums);
+    k_scan3<<<(unsigned)((ncols + 1 + thr - 1) / thr), thr, 0, st>>>(
+        ncols, (long long*)ppos, (const long long*)psums, out->col_off, ctr);
+    ctx->launches += 4;
+    CK(cudaGetLastError());
+    mark(ctx, 7, st);
+    long long total_out = 0;
+    CK(cudaMemcpyAsync(&total_out, (long long*)psums + nb, sizeof(long long),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out->nseg = total_out;
+    ctx->host_ctr = hc;
+    if (hc.status & ST_TOO_MANY_OUT) return DEXEL_ERR_CAPACITY;
+    if (total_out > out->capacity_seg) return DEXEL_ERR_CAPACITY;
+    mark(ctx, 8, st);
+    k_write<T><<<gb, thr, 0, st>>>((int)ncols, (const long long*)postart, (const int*)pocnt,
+                                   p2.o_l, p2.o_r, erode ? 1 : 0, (const long long*)ppos,
+                                   (T*)out->z);
+    ++ctx->launches;
+    CK(cudaGetLastError());
+    mark(ctx, 9, st);
+    CK(cudaStreamSynchronize(st));
+    if (ctx->profiling) {
+      for (int q = 0; q < 5; ++q) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, ctx->ev[2 * q], ctx->ev[2 * q + 1]) == cudaSuccess)
+          ctx->stage_ms[q] += ms;
+      }
+    }
+    ctx->stats[0] += in->nseg;
+    ctx->stats[1] += (long long)hc.mid_total;
+    ctx->stats[2] += (long long)hc.out_total;
+    ctx->stats[3] += total_out;
+    ctx->stats[4] = std::max<long long>(ctx->stats[4], hc.max_pieces);
+    ctx->stats[5] = std::max<long long>(ctx->stats[5], hc.max_state);
+    ctx->last_required = total;
+    return DEXEL_OK;
+  }
+  return DEXEL_ERR_CAPACITY;
+}
+
+dexel_status check_in(const dexel_grid_in* in, double k) {
+  if (!in || in->nx < 1 || in->ny < 1 || in->nx > 32768 || in->ny > 32768) return DEXEL_ERR_INVALID_ARG;
+  if (!(in->h > 0) || !std::isfinite(in->h)) return DEXEL_ERR_INVALID_ARG;
+  if (!(k >= 0) || !std::isfinite(k) || k > 4096) return DEXEL_ERR_INVALID_ARG;
+  if (!in->col_off || in->nseg < 0 || (in->nseg > 0 && !in->z)) return DEXEL_ERR_INVALID_ARG;
+  if ((long long)in->nx * in->ny > (1LL << 30)) return DEXEL_ERR_INVALID_ARG;
+  return DEXEL_OK;
+}
+
+dexel_status offset(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erode, dexel_mode mode,
+                    dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !out || !out->col_off || (out->capacity_seg > 0 && !out->z) || out->capacity_seg < 0)
+    return DEXEL_ERR_INVALID_ARG;
+  dexel_status s = check_in(in, k);
+  if (s != DEXEL_OK) return s;
+  if (mode != DEXEL_FP64 && mode != DEXEL_FP32_PRED64) return DEXEL_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DEXEL_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mode == DEXEL_FP64) return Offset<double>::run(ctx, in, k, erode, out, ws, ws_bytes, st);
+  return Offset<float>::run(ctx, in, k, erode, out, ws, ws_bytes, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
+  if (!ctx) return DEXEL_ERR_INVALID_ARG;
+  *ctx = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return DEXEL_ERR_CUDA;
+  }
+  dexel_ctx* c = new (std::nothrow) dexel_ctx();
+  if (!c) return DEXEL_ERR_NOMEM;
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  *ctx = c;
+  return DEXEL_OK;
+}
+
+void dexel_ctx_destroy(dexel_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->own) cudaFree(ctx->own);
+  if (ctx->mid) cudaFree(ctx->mid);
+  for (cudaEvent_t e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+size_t dexel_workspace_size(const dexel_grid_in* in, double k, dexel_mode mode) {
+  if (check_in(in, k) != DEXEL_OK) return 0;
+  const long long ncols = (long long)in->nx * in->ny;
+  const int K = reach_of(k * k);
+  const size_t es = mode == DEXEL_FP64 ? 8 : 4;
+  const long long segs = std::max<long long>(in->nseg + ncols, 1024);
+  const size_t fixed = (size_t)ncols * 48 + ((size_t)1 << 20);
+  const size_t arenas = (size_t)segs * std::min(K + 2, 16) * (2 * (2 * es + 2) + 16) + segs * 32;
+  return fixed + arenas + ((size_t)2 << 30);
+}
+
+size_t dexel_last_required(const dexel_ctx* ctx) { return ctx ? ctx->last_required : 0; }
+
+int64_t dexel_last_launches(const dexel_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+void dexel_set_profiling(dexel_ctx* ctx, int on) {
+  if (ctx) ctx->profiling = on != 0;
+}
+
+int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max) {
+  if (!ctx || !ms) return 0;
+  int n = max < 5 ? max : 5;
+  for (int q = 0; q < n; ++q) ms[q] = ctx->stage_ms[q];
+  return n;
+}
+
+int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max) {
+  if (!ctx || !stats) return 0;
+  int n = max < 6 ? max : 6;
+  for (int q = 0; q < n; ++q) stats[q] = ctx->stats[q];
+  return n;
+}
+
+dexel_status dexel_validate(dexel_ctx* ctx, const dexel_grid_in* in, dexel_mode mode, void* ws,
+                            size_t ws_bytes, void* stream) {
+  if (!ctx) return DEXEL_ERR_INVALID_ARG;
+  dexel_status s = check_in(in, 0.0);
+  if (s != DEXEL_OK) return s;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DEXEL_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  Counters* ctr = nullptr;
+  if (ws) {
+    if (ws_bytes < sizeof(Counters)) return DEXEL_ERR_CAPACITY;
+    ctr = (Counters*)ws;
+  } else {
+    s = ensure_owned(ctx, 1 << 20);
+    if (s != DEXEL_OK) return s;
+    ctr = (Counters*)ctx->own;
+  }
+  const long long ncols = (long long)in->nx * in->ny;
+  CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+  if (mode == DEXEL_FP64)
+    k_validate<double><<<(unsigned)((ncols + 255) / 256), 256, 0, st>>>((int)ncols, in->col_off,
+                                                                       (const double*)in->z, in->nseg, ctr);
+  else
+    k_validate<float><<<(unsigned)((ncols + 255) / 256), 256, 0, st>>>((int)ncols, in->col_off,
+                                                                      (const float*)in->z, in->nseg, ctr);
+  CK(cudaGetLastError());
+  Counters hc;
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return (hc.status & ST_BAD_CSR) ? DEXEL_ERR_BAD_CSR : DEXEL_OK;
+}
+
+dexel_status dexel_dilate(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_mode mode,
+                          dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream) {
+  if (ctx) reset_call(ctx);
+  return offset(ctx, in, k, false, mode, out, ws, ws_bytes, stream);
+}
+
+dexel_status dexel_erode(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_mode mode,
+                         dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream) {
+  if (ctx) reset_call(ctx);
+  return offset(ctx, in, k, true, mode, out, ws, ws_bytes, stream);
+}
+
+dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
+                         dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
+                         void* stream) {
+  if (!ctx || (op != DEXEL_CLOSE && op != DEXEL_OPEN)) return DEXEL_ERR_INVALID_ARG;
+  reset_call(ctx);
+  dexel_status s = check_in(in, k);
+  if (s != DEXEL_OK) return s;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DEXEL_ERR_CUDA;
+  const long long ncols = (long long)in->nx * in->ny;
+  const size_t es = mode == DEXEL_FP64 ? 8 : 4;
+  // intermediate grid: offsets + endpoints, grown until the first stage fits
+  long long cap = std::max<long long>(2 * in->nseg + ncols / 4, 1024);
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    const size_t need = align_up((size_t)(ncols + 1) * 4, 256) + (size_t)cap * 2 * es;
+    if (ctx->mid_bytes < need) {
+      if (ctx->mid) cudaFree(ctx->mid);
+      ctx->mid = nullptr;
+      ctx->mid_bytes = 0;
+      if (cudaMalloc(&ctx->mid, need) != cudaSuccess) { cudaGetLastError(); return DEXEL_ERR_NOMEM; }
+      ctx->mid_bytes = need;
+    }
+    dexel_grid_out mid{(int32_t*)ctx->mid, (char*)ctx->mid + align_up((size_t)(ncols + 1) * 4, 256),
+                       cap, 0};
+    const bool first_erode = op == DEXEL_OPEN;
+    s = offset(ctx, in, k, first_erode, mode, &mid, ws, ws_bytes, stream);
+    if (s == DEXEL_ERR_CAPACITY && mid.nseg > cap) {
+      cap = mid.nseg + 1024;
+      reset_call(ctx);
+      continue;
+    }
+    if (s != DEXEL_OK) return s;
+    dexel_grid_in in2{in->nx, in->ny, in->h, mid.col_off, mid.z, mid.nseg};
+    return offset(ctx, &in2, k, !first_erode, mode, out, ws, ws_bytes, stream);
+  }
+  return DEXEL_ERR_CAPACITY;
+}
+
+dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_in* ins,
+                                  const double* k, const dexel_op* ops, dexel_mode mode,
+                                  dexel_grid_out* outs, void* ws, size_t ws_bytes,
+                                  int32_t* d_status, void* stream) {
+  if (!ctx || nshapes < 0 || (nshapes > 0 && (!ins || !k || !ops || !outs))) return DEXEL_ERR_INVALID_ARG;
+  dexel_status first = DEXEL_OK;
+  std::vector<int32_t> st(nshapes > 0 ? nshapes : 1, 0);
+  long long launches = 0;
+  double stage[5] = {0, 0, 0, 0, 0};
+  long long stats[6] = {0, 0, 0, 0, 0, 0};
+  for (int s = 0; s < nshapes; ++s) {
+    dexel_status r;
+    switch (ops[s]) {
+      case DEXEL_DILATE: r = dexel_dilate(ctx, &ins[s], k[s], mode, &outs[s], ws, ws_bytes, stream); break;
+      case DEXEL_ERODE: r = dexel_erode(ctx, &ins[s], k[s], mode, &outs[s], ws, ws_bytes, stream); break;
+      default: r = dexel_morph(ctx, &ins[s], k[s], ops[s], mode, &outs[s], ws, ws_bytes, stream); break;
+    }
+    launches += ctx->launches;
+    for (int q = 0; q < 5; ++q) stage[q] += ctx->stage_ms[q];
+    for (int q = 0; q < 4; ++q) stats[q] += ctx->stats[q];
+    for (int q = 4; q < 6; ++q) stats[q] = std::max(stats[q], ctx->stats[q]);
+    st[s] = (int32_t)r;
+    if (r != DEXEL_OK && first == DEXEL_OK) first = r;
+  }
+  ctx->launches = launches;
+  for (int q = 0; q < 5; ++q) ctx->stage_ms[q] = stage[q];
+  for (int q = 0; q < 6; ++q) ctx->stats[q] = stats[q];
+  if (d_status && nshapes > 0) {
+    if (cudaMemcpyAsync(d_status, st.data(), sizeof(int32_t) * nshapes, cudaMemcpyHostToDevice,
+                        (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+      return DEXEL_ERR_CUDA;
+  }
+  return first;
+}
+
+const char* dexel_status_string(dexel_status s) {
+  switch (s) {
+    case DEXEL_OK: return "ok";
+    case DEXEL_ERR_INVALID_ARG: return "invalid argument";
+    case DEXEL_ERR_BAD_CSR: return "malformed CSR dexel grid";
+    case DEXEL_ERR_CAPACITY: return "output or workspace capacity too small";
+    case DEXEL_ERR_CUDA: return "CUDA runtime error";
+    case DEXEL_ERR_TIMEOUT: return "bounded device wait gave up";
+    case DEXEL_ERR_NOMEM: return "out of memory";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

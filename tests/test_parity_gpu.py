@@ -1,0 +1,167 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 endpoints within 1e-10 of the depth extent (Z = 1), FP32
+mode within 4e-6; segment counts identical, except in FP32 mode where the oracle's gap at
+that place is below one float ulp (it cannot be represented and the two pieces merge).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import shapes
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 4e-6
+
+
+@pytest.fixture(scope="module")
+def dx():
+    import torch  # noqa: F401
+    import paper_1804_08968_gb300 as m
+    return m
+
+
+def _gpu(dx, g, op, k, f32=False):
+    import torch
+    gg = shapes.to_float32(g) if f32 else g
+    dg = dx.Grid.from_synth(gg, dtype=torch.float32 if f32 else torch.float64)
+    fn = {"dilate": dx.dilate, "erode": dx.erode, "close": dx.close, "open": dx.open_}[op]
+    out = fn(dg, k)
+    torch.cuda.synchronize()
+    off, z = out.to_host()
+    return gg, off, z.astype(np.float64)
+
+
+def _ref(g, op, k, cols=None):
+    if op == "dilate":
+        return oracle.dilate(g, k, cols=cols)
+    if op == "erode":
+        return oracle.erode(g, k, cols=cols)
+    if op == "close":
+        return oracle.close(g, k)
+    return oracle.open_(g, k)
+
+
+def _compare_full(off, z, ref, f32, what):
+    rc = np.diff(ref.col_off)
+    gc = np.diff(off)
+    bad = np.flatnonzero(rc != gc)
+    if f32:
+        # a count may differ only where the oracle has a gap below one float ulp
+        for c in bad:
+            segs = ref.z[ref.col_off[c]:ref.col_off[c + 1]]
+            gaps = segs[1:, 0] - segs[:-1, 1]
+            scale = np.maximum(np.abs(segs[1:, 0]), 1.0)
+            assert gaps.size and np.min(gaps / scale) < 2 ** -23, f"{what}: count mismatch col {c}"
+        bad = []
+    assert len(bad) == 0, f"{what}: count mismatch at {bad[:8]}"
+    if (rc == gc).all() and z.size:
+        err = np.max(np.abs(z - ref.z))
+        assert err <= (TOL32 if f32 else TOL64), f"{what}: max endpoint error {err}"
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_random_small(dx, seed, op):
+    rng = np.random.default_rng(1000 + seed)
+    nx, ny = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+    g = shapes.random_grid(rng, nx, ny, 5, fill=0.7, point_frac=0.05, h=1 / 32)
+    for k in [0.0, 0.5, 1.0, math.sqrt(2.0), 2.0, 3.7, 7.0, 12.5]:
+        gg, off, z = _gpu(dx, g, op, k)
+        _compare_full(off, z, _ref(gg, op, k), False, f"{op} seed={seed} k={k} {nx}x{ny}")
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_random_fp32(dx, op):
+    rng = np.random.default_rng(77)
+    g = shapes.random_grid(rng, 37, 29, 6, fill=0.8, point_frac=0.05, h=1 / 40)
+    for k in [1.0, 4.2, 9.0]:
+        gg, off, z = _gpu(dx, g, op, k, f32=True)
+        _compare_full(off, z, _ref(gg, op, k), True, f"fp32 {op} k={k}")
+
+
+def test_config1_dilation(dx):
+    """64 x 64, 8 spheres, k = 4, FP64 (the smallest workload)."""
+    g = shapes.config1()
+    gg, off, z = _gpu(dx, g, "dilate", 4.0)
+    _compare_full(off, z, _ref(gg, "dilate", 4.0), False, "config1")
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+@pytest.mark.parametrize("k", [2.0, 8.0])
+def test_config2_full(dx, op, k):
+    """512 x 512, 200 primitives: every column compared with the oracle."""
+    g = shapes.config2()
+    gg, off, z = _gpu(dx, g, op, k)
+    _compare_full(off, z, _ref(gg, op, k), False, f"config2 {op} k={k}")
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_config2_k32_sampled(dx, op):
+    """k = 32 at 512 x 512: 3000 sampled columns plus two full lines against the oracle."""
+    g = shapes.config2()
+    k = 32.0
+    gg, off, z = _gpu(dx, g, op, k)
+    rng = np.random.default_rng(5)
+    cols = np.concatenate([rng.choice(512 * 512, 3000, replace=False),
+                           np.arange(512) + 200 * 512, np.arange(512) * 512 + 300])
+    ref = _ref(gg, op, k, cols=cols)
+    for t, c in enumerate(cols):
+        got = z[off[c]:off[c + 1]]
+        exp = ref.column(t)
+        assert got.shape == exp.shape, (op, c, got, exp)
+        if exp.size:
+            assert np.max(np.abs(got - exp)) <= TOL64
+
+
+@pytest.mark.parametrize("op", ["close", "open"])
+def test_morphology_small(dx, op):
+    g = shapes.raycast(shapes.config2_prims(80, seed=3), 96)
+    for k in [2.0, 5.0]:
+        gg, off, z = _gpu(dx, g, op, k)
+        _compare_full(off, z, _ref(gg, op, k), False, f"{op} k={k}")
+
+
+def test_edge_cases(dx):
+    # empty grid
+    g = shapes.from_columns(7, 5, 0.1, {})
+    for op in ("dilate", "erode"):
+        gg, off, z = _gpu(dx, g, op, 2.0)
+        assert off[-1] == 0
+    # single column, single segment; a 1 x n and n x 1 grid
+    for (nx, ny, i, j) in [(1, 1, 0, 0), (1, 9, 0, 4), (9, 1, 4, 0)]:
+        g = shapes.from_columns(nx, ny, 1 / 16, {(i, j): [(0.25, 0.5)]})
+        for op in ("dilate", "erode"):
+            for k in (0.0, 1.0, 3.0):
+                gg, off, z = _gpu(dx, g, op, k)
+                _compare_full(off, z, _ref(gg, op, k), False, f"edge {nx}x{ny} {op} {k}")
+    # zero-length segments only
+    g = shapes.from_columns(6, 6, 1 / 8, {(2, 2): [(0.5, 0.5)], (3, 3): [(0.25, 0.25), (0.5, 0.5)]})
+    for k in (0.0, 1.0, 2.5):
+        gg, off, z = _gpu(dx, g, "dilate", k)
+        _compare_full(off, z, _ref(gg, "dilate", k), False, f"points k={k}")
+
+
+def test_bad_csr_rejected(dx):
+    import torch
+    g = shapes.from_columns(4, 4, 0.25, {(1, 1): [(0.2, 0.4), (0.3, 0.6)]})  # overlapping
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    with pytest.raises(dx.DexelError) as e:
+        dx.dilate(dg, 1.0)
+    assert e.value.code == -2
+    assert dx._default_ctx(dg).validate(dg) == -2
+
+
+def test_output_capacity_retry(dx):
+    """A too-small output buffer reports the needed size; the binding retries."""
+    import torch
+    g = shapes.config1()
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    ctx = dx.Context(0)
+    out = ctx.run(dx.DILATE, dg, 4.0, capacity=3)
+    ref = oracle.dilate(g, 4.0)
+    assert out.nseg == ref.nseg
