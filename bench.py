@@ -275,7 +275,11 @@ def oracle_sample(g, cols_per_op, seed=0):
 def cpu_baseline(g, args):
     import oracle
     oracle.build()
-    n, t = oracle_sample(g, args.cpu_cols)
+    # size the sample for about args.cpu_seconds of oracle work (bounded, same workload)
+    n0, t0 = oracle_sample(g, 40, seed=7)
+    cols = int(min(g.nx * g.ny, max(40, 40 * args.cpu_seconds / max(t0, 1e-3))))
+    args.cpu_cols = cols
+    n, t = oracle_sample(g, cols)
     return {"value": n / t, "unit": "columns/s", "cores": oracle.default_threads(), "kind": "oracle",
             "sample": f"{args.cpu_cols} random output columns per offset (6 offsets), FP64 brute-force "
                       f"gather, {t:.1f} s"}
@@ -323,8 +327,19 @@ def main():
     ap.add_argument("--cpu-cols", type=int, default=300)
     ap.add_argument("--ref-cols", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one dilation (k=8) of the workload and exit (for ncu captures)")
     args = ap.parse_args()
     rank, ws = dist_init(args)
+    if args.profile_case:
+        import torch
+        import paper_1804_08968_gb300 as dx
+        g = workload()
+        grid = dx.Grid.from_synth(g, dtype=torch.float64)
+        dx.dilate(grid, 8.0)
+        torch.cuda.synchronize()
+        return
     if args.impl == "reference":
         run_reference(args, rank, ws)
     else:

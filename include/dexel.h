@@ -150,7 +150,10 @@ int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max);
 /* Sizes seen by the last call (summed over both offsets of a closing or opening):
  * [0] input segments, [1] S_mid pieces (pass-1 output), [2] pass-2 intervals before the final
  * complement/rounding, [3] output segments, [4] max pieces in one S_mid column, [5] max live
- * elements in one sweep state.  Returns the number of entries written (at most max). */
+ * elements in one sweep state, [6] device status bits of the last attempt (1: a per-warp
+ * state array overflowed, 2: an arena overflowed, 4: malformed CSR, 8: output beyond int32
+ * offsets), [7] attempts the last offset needed (the library grows its scratch and retries
+ * when it owns the workspace).  Returns the number of entries written (at most max). */
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max);
 
 #ifdef __cplusplus

@@ -166,8 +166,8 @@ class Context:
     def stats(self):
         """[input segments, S_mid pieces, pass-2 intervals, output segments, max pieces per
         S_mid column, max live sweep state] of the last call."""
-        a = (ctypes.c_int64 * 6)()
-        n = lib().dexel_last_stats(self.ptr, a, 6)
+        a = (ctypes.c_int64 * 8)()
+        n = lib().dexel_last_stats(self.ptr, a, 8)
         return [int(a[i]) for i in range(n)]
 
     def _stream(self, stream):
@@ -195,7 +195,8 @@ class Context:
                 cap = int(out.nseg) + 16
                 continue
             if rc != 0:
-                raise DexelError(rc, "dexel offset")
+                raise DexelError(rc, f"dexel offset (stats {self.stats()}, "
+                                     f"required {lib().dexel_last_required(self.ptr)} B)")
             self._cap_hint[key] = cap
             return Grid(g.nx, g.ny, g.h, off, z[: out.nseg])
         raise DexelError(-3, "dexel offset (output capacity)")

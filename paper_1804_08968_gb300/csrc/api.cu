@@ -34,7 +34,7 @@ struct dexel_ctx {
   bool profiling = false;
   cudaEvent_t ev[10] = {};
   double stage_ms[5] = {0, 0, 0, 0, 0};
-  long long stats[6] = {0, 0, 0, 0, 0, 0};
+  long long stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -290,7 +290,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
   const int blocks = sms * 4;
   const int nwarps = blocks * kWarpsPerBlock;
 
-  for (int attempt = 0; attempt < 8; ++attempt) {
+  for (int attempt = 0; attempt < 24; ++attempt) {
     // ---------------- plan
     // phase A: counters, tables, indices, validation
     auto plan = [&](Carver& C, void** pctr, void** pwtab, void** preach, void** pmstart,
@@ -356,9 +356,9 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     const long long sb1 = p1_slot_bytes<T>(capF, capS, chunk1);
     // arena estimates (entries)
     const long long segs = std::max<long long>(in->nseg + ncols, 1024);
-    long long eM = std::max<long long>(ctx->needM, segs * std::min(K + 2, 16));
-    long long eF = std::max<long long>(ctx->needF, eM);
-    long long eO = std::max<long long>(ctx->needO, segs * 2);
+    long long eM = std::max<long long>(ctx->needM + ctx->needM / 8, segs * std::min(K + 2, 64));
+    long long eF = std::max<long long>(ctx->needF + ctx->needF / 8, eM);
+    long long eO = std::max<long long>(ctx->needO + ctx->needO / 8, segs * 2);
     const size_t bF = align_up((size_t)eF * std::max<size_t>(2 * sizeof(T) + 2, 16), 256);
     const size_t bM = align_up((size_t)eM * (2 * sizeof(T) + 2), 256);
     const size_t bO = align_up((size_t)eO * 16, 256);
@@ -419,6 +419,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     CK(cudaStreamSynchronize(st));
     ctx->needF = std::max<long long>(ctx->needF, (long long)hc.arena_top[0]);
     ctx->needM = std::max<long long>(ctx->needM, (long long)hc.arena_top[1]);
+    ctx->stats[6] = hc.status;
+    ctx->stats[7] = attempt + 1;
     if (hc.status & (ST_OVERFLOW_SLOT | ST_OVERFLOW_ARENA)) {
       ctx->last_required = total + (size_t)(hc.arena_top[0] + hc.arena_top[1]) * 16;
       if (hc.status & ST_OVERFLOW_SLOT) return DEXEL_ERR_CAPACITY;  // bound exceeded: give up
@@ -463,10 +465,13 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     CK(cudaStreamSynchronize(st));
     ctx->needF = std::max<long long>(ctx->needF, (long long)hc.arena_top[2] * 16 / (long long)(2 * sizeof(T) + 2) + 1);
     ctx->needO = std::max<long long>(ctx->needO, (long long)hc.arena_top[3]);
+    ctx->stats[6] = hc.status;
+    ctx->stats[7] = attempt + 1;
     if (hc.status & ST_OVERFLOW_SLOT) {
-      // a per-warp state outgrew its arrays: double them and retry
-      ctx->capD *= 2;
-      ctx->capR *= 2;
+      // a per-warp state outgrew its arrays: grow them past the size that was needed
+      const int need = std::max(hc.max_state, 1);
+      ctx->capD = std::max(ctx->capD * 2, need + need / 2);
+      ctx->capR = std::max(ctx->capR * 2, need + need / 2);
       ctx->last_required = total + (size_t)p2_slot_bytes<T>(capP, ctx->capR, ctx->capD, chunk2) * nwarps;
       if (ws_user) return DEXEL_ERR_CAPACITY;
       continue;
@@ -608,7 +613,7 @@ int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max) {
 
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max) {
   if (!ctx || !stats) return 0;
-  int n = max < 6 ? max : 6;
+  int n = max < 8 ? max : 8;
   for (int q = 0; q < n; ++q) stats[q] = ctx->stats[q];
   return n;
 }
@@ -702,7 +707,7 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
   std::vector<int32_t> st(nshapes > 0 ? nshapes : 1, 0);
   long long launches = 0;
   double stage[5] = {0, 0, 0, 0, 0};
-  long long stats[6] = {0, 0, 0, 0, 0, 0};
+  long long stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int s = 0; s < nshapes; ++s) {
     dexel_status r;
     switch (ops[s]) {
@@ -713,13 +718,13 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
     launches += ctx->launches;
     for (int q = 0; q < 5; ++q) stage[q] += ctx->stage_ms[q];
     for (int q = 0; q < 4; ++q) stats[q] += ctx->stats[q];
-    for (int q = 4; q < 6; ++q) stats[q] = std::max(stats[q], ctx->stats[q]);
+    for (int q = 4; q < 8; ++q) stats[q] = std::max(stats[q], ctx->stats[q]);
     st[s] = (int32_t)r;
     if (r != DEXEL_OK && first == DEXEL_OK) first = r;
   }
   ctx->launches = launches;
   for (int q = 0; q < 5; ++q) ctx->stage_ms[q] = stage[q];
-  for (int q = 0; q < 6; ++q) ctx->stats[q] = stats[q];
+  for (int q = 0; q < 8; ++q) ctx->stats[q] = stats[q];
   if (d_status && nshapes > 0) {
     if (cudaMemcpyAsync(d_status, st.data(), sizeof(int32_t) * nshapes, cudaMemcpyHostToDevice,
                         (cudaStream_t)stream) != cudaSuccess ||

@@ -98,12 +98,15 @@ DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<T>& W, in
         }
       wsync();
       if (2 * (nq + nn) > p2_ce(P.capR, P.capD, P.capP)) {
-        if (L.lane == 0) set_status(status, ST_OVERFLOW_SLOT);
+        if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nq + nn); }
         return;
       }
       nr = merge_runs<T, false>(L, W.qa, W.qb, W.qt, nq, W.na, W.nb, W.nt, nn, W.X, W.c0, W.c1,
                                 W.c2, W.c3, W.c4, W.c5, W.ra, W.rb, W.rt);
-      if (nr > P.capR) { if (L.lane == 0) set_status(status, ST_OVERFLOW_SLOT); return; }
+      if (nr > P.capR) {
+        if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nr); }
+        return;
+      }
 
       // ---- seeds: drop dead or pruned ones
       for (int t = L.lane; t < ns; t += L.nl)
@@ -152,7 +155,10 @@ DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<T>& W, in
       for (int t = L.lane; t < nc; t += L.nl)
         if (W.c0[t]) { W.X[W.c1[t]] = W.nz[t]; W.c2[W.c1[t]] = W.nd[t]; }
       wsync();
-      if (nu + nw > P.capD) { if (L.lane == 0) set_status(status, ST_OVERFLOW_SLOT); return; }
+      if (nu + nw > P.capD) {
+        if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nu + nw); }
+        return;
+      }
       // merge old (uz...) and new (X, c2) seeds by z, old first on ties -> (sz, sj, sd, so)
       for (int t = L.lane; t < nu; t += L.nl) {
         const int pos = t + lower_bound(W.X, nw, W.uz[t]);
