@@ -156,6 +156,11 @@ int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max);
  * when it owns the workspace).  Returns the number of entries written (at most max). */
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max);
 
+/* Diagnostic counters of the last call: clock cycles per phase of the y sweep and mean
+ * state sizes, filled only by builds compiled with -DDEXEL_PHASES (zero otherwise).
+ * Returns the number of entries written (at most max, 16 in all). */
+int dexel_last_phases(const dexel_ctx* ctx, uint64_t* ph, int max);
+
 #ifdef __cplusplus
 }
 #endif

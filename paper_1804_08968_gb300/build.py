@@ -15,6 +15,7 @@ SOURCES = ["api.cu", "pass1.cu", "pass2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+FLAGS += os.environ.get("DEXEL_NVCC_FLAGS", "").split()
 
 
 def _stale(target, deps):

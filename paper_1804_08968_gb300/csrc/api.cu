@@ -27,7 +27,7 @@ struct dexel_ctx {
   size_t last_required = 0;
   long long launches = 0;
   // capacities learnt from earlier calls (grown on overflow)
-  int capD = 1024, capR = 1024;
+  int capA = 1024, capR = 1024, capS = 4096;
   long long needF = 0, needM = 0, needO = 0;  // arena entries
   Counters host_ctr{};
   // optional per-stage timing with CUDA events on the call's stream
@@ -35,6 +35,7 @@ struct dexel_ctx {
   cudaEvent_t ev[10] = {};
   double stage_ms[5] = {0, 0, 0, 0, 0};
   long long stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long phase[16] = {};
 };
 
 namespace {
@@ -89,7 +90,7 @@ __global__ void k_tables(double kk, double h, int nmax, int K, double* wtab, int
 // One output column: optional complement (erosion), rounding to T, and re-merge of pieces
 // that touch after rounding.  Returns the count; writes pieces when out != nullptr.
 template <typename T>
-__device__ int finalize_column(const double* l, const double* r, int m, bool erode, T* out) {
+__device__ int finalize_column(const ukey* lk, const ukey* rk, int m, bool erode, T* out) {
   int cnt = 0;
   T ca = 0, cb = 0;
   bool have = false;
@@ -108,14 +109,16 @@ __device__ int finalize_column(const double* l, const double* r, int m, bool ero
     cb = tb;
     have = true;
   };
+  auto l = [&](int t) { return dval(lk[t]); };
+  auto r = [&](int t) { return dval(rk[t]); };
   if (!erode) {
-    for (int t = 0; t < m; ++t) push(l[t], r[t]);
+    for (int t = 0; t < m; ++t) push(l(t), r(t));
   } else if (m == 0) {
     push(-INFINITY, INFINITY);
   } else {
-    if (l[0] > -INFINITY) push(-INFINITY, l[0]);
-    for (int t = 0; t + 1 < m; ++t) push(r[t], l[t + 1]);
-    if (r[m - 1] < INFINITY) push(r[m - 1], INFINITY);
+    if (l(0) > -INFINITY) push(-INFINITY, l(0));
+    for (int t = 0; t + 1 < m; ++t) push(r(t), l(t + 1));
+    if (r(m - 1) < INFINITY) push(r(m - 1), INFINITY);
   }
   if (have) {
     if (out) { out[2 * cnt] = ca; out[2 * cnt + 1] = cb; }
@@ -125,8 +128,8 @@ __device__ int finalize_column(const double* l, const double* r, int m, bool ero
 }
 
 template <typename T>
-__global__ void k_count(int ncols, const long long* ostart, const int* ocnt, const double* ol,
-                        const double* orr, int erode, long long* cnt) {
+__global__ void k_count(int ncols, const long long* ostart, const int* ocnt, const ukey* ol,
+                        const ukey* orr, int erode, long long* cnt) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncols) return;
   const long long s = ostart[c];
@@ -134,8 +137,8 @@ __global__ void k_count(int ncols, const long long* ostart, const int* ocnt, con
 }
 
 template <typename T>
-__global__ void k_write(int ncols, const long long* ostart, const int* ocnt, const double* ol,
-                        const double* orr, int erode, const long long* pos, T* z) {
+__global__ void k_write(int ncols, const long long* ostart, const int* ocnt, const ukey* ol,
+                        const ukey* orr, int erode, const long long* pos, T* z) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncols) return;
   const long long s = ostart[c];
@@ -239,6 +242,7 @@ void mark(dexel_ctx* ctx, int e, cudaStream_t st) {
 
 void reset_call(dexel_ctx* ctx) {
   ctx->launches = 0;
+  for (unsigned long long& x : ctx->phase) x = 0;
   for (double& m : ctx->stage_ms) m = 0;
   for (long long& x : ctx->stats) x = 0;
 }
@@ -281,6 +285,7 @@ template <typename T>
 dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erode,
                             dexel_grid_out* out, void* ws_user, size_t ws_user_bytes,
                             cudaStream_t st) {
+  typedef typename H<T>::K Key;
   const int nx = in->nx, ny = in->ny;
   const long long ncols = (long long)nx * ny;
   const double kk = k * k;
@@ -353,17 +358,18 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     int nch1 = std::max(1, std::min(nx, (items1_target + ny - 1) / ny));
     int chunk1 = (nx + nch1 - 1) / nch1;
     nch1 = (nx + chunk1 - 1) / chunk1;
-    const long long sb1 = p1_slot_bytes<T>(capF, capS, chunk1);
+    const long long sb1 = p1_slot_bytes<Key>(capF, capS, chunk1);
     // arena estimates (entries)
     const long long segs = std::max<long long>(in->nseg + ncols, 1024);
     long long eM = std::max<long long>(ctx->needM + ctx->needM / 8, segs * std::min(K + 2, 64));
     long long eF = std::max<long long>(ctx->needF + ctx->needF / 8, eM);
     long long eO = std::max<long long>(ctx->needO + ctx->needO / 8, segs * 2);
-    const size_t bF = align_up((size_t)eF * std::max<size_t>(2 * sizeof(T) + 2, 16), 256);
-    const size_t bM = align_up((size_t)eM * (2 * sizeof(T) + 2), 256);
+    const size_t bF = align_up((size_t)eF * std::max<size_t>(2 * sizeof(Key) + 2, 16), 256);
+    const size_t bM = align_up((size_t)eM * (2 * sizeof(Key) + 2), 256);
     const size_t bO = align_up((size_t)eO * 16, 256);
     // pass-2 slot estimate from the remembered capacities
-    const long long sb2_est = p2_slot_bytes<T>(std::max(capS * 4, 64), ctx->capR, ctx->capD, 1024);
+    const long long sb2_est =
+        p2_slot_bytes<Key>(std::max(capS * 4, 64), ctx->capR, ctx->capA, ctx->capS, 1024);
     const size_t slots = std::max((size_t)sb1, (size_t)sb2_est) * nwarps;
     const size_t total = fixed + bF + bM + bO + slots + 4096;
     if (ws_user && total > ws_user_bytes) {
@@ -393,11 +399,11 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     p1.nx = nx; p1.ny = ny; p1.K = K; p1.erode = erode ? 1 : 0;
     p1.chunk = chunk1; p1.nchunks = nch1;
     p1.col_off = in->col_off; p1.z = (const T*)in->z;
-    const long long capF1 = (long long)(bF / (2 * sizeof(T) + 2));
-    p1.f_a = (T*)aF; p1.f_b = (T*)aF + capF1; p1.f_l = (short*)((T*)aF + 2 * capF1);
+    const long long capF1 = (long long)(bF / (2 * sizeof(Key) + 2));
+    p1.f_a = (Key*)aF; p1.f_b = (Key*)aF + capF1; p1.f_l = (short*)((Key*)aF + 2 * capF1);
     p1.f_cap = capF1;
-    const long long capM = (long long)(bM / (2 * sizeof(T) + 2));
-    p1.m_a = (T*)aM; p1.m_b = (T*)aM + capM; p1.m_l = (short*)((T*)aM + 2 * capM);
+    const long long capM = (long long)(bM / (2 * sizeof(Key) + 2));
+    p1.m_a = (Key*)aM; p1.m_b = (Key*)aM + capM; p1.m_l = (short*)((Key*)aM + 2 * capM);
     p1.m_cap = capM;
     p1.m_start = (long long*)pmstart; p1.m_cnt = (int*)pmcnt;
     p1.blk = 256;
@@ -435,20 +441,21 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     int chunk2 = (ny + nch2 - 1) / nch2;
     nch2 = (ny + chunk2 - 1) / chunk2;
     P2Params<T> p2{};
-    p2.nx = nx; p2.ny = ny; p2.K = K; p2.kk = kk; p2.h2 = in->h * in->h;
+    p2.nx = nx; p2.ny = ny; p2.R = K; p2.kk = kk; p2.h2 = in->h * in->h;
+    p2.h2f = (float)p2.h2;
     p2.chunk = chunk2; p2.nchunks = nch2;
     p2.wtab = (const double*)pwtab; p2.reach = (const int*)preach;
     p2.m_a = p1.m_a; p2.m_b = p1.m_b; p2.m_l = p1.m_l;
     p2.m_start = p1.m_start; p2.m_cnt = p1.m_cnt;
     const long long capF2 = (long long)(bF / 16);
-    p2.f_l = (double*)aF; p2.f_r = (double*)aF + capF2; p2.f_cap = capF2;
+    p2.f_l = (ukey*)aF; p2.f_r = (ukey*)aF + capF2; p2.f_cap = capF2;
     const long long capO = (long long)(bO / 16);
-    p2.o_l = (double*)aO; p2.o_r = (double*)aO + capO; p2.o_cap = capO;
+    p2.o_l = (ukey*)aO; p2.o_r = (ukey*)aO + capO; p2.o_cap = capO;
     p2.o_start = (long long*)postart; p2.o_cnt = (int*)pocnt;
     p2.blk = 256;
     p2.ctr = ctr;
-    p2.capP = capP; p2.capR = ctx->capR; p2.capD = ctx->capD;
-    const long long sb2 = p2_slot_bytes<T>(capP, p2.capR, p2.capD, chunk2);
+    p2.capP = capP; p2.capR = ctx->capR; p2.capA = ctx->capA; p2.capS = ctx->capS;
+    const long long sb2 = p2_slot_bytes<Key>(capP, p2.capR, p2.capA, p2.capS, chunk2);
     p2.slots = pslots; p2.slot_bytes = sb2;
     const int nw2 = (int)std::min<long long>(nwarps, (long long)(slot_room / sb2));
     if (nw2 < kWarpsPerBlock) {
@@ -463,16 +470,18 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     ++ctx->launches;
     CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    ctx->needF = std::max<long long>(ctx->needF, (long long)hc.arena_top[2] * 16 / (long long)(2 * sizeof(T) + 2) + 1);
+    ctx->needF = std::max<long long>(ctx->needF, (long long)hc.arena_top[2] * 16 / (long long)(2 * sizeof(Key) + 2) + 1);
     ctx->needO = std::max<long long>(ctx->needO, (long long)hc.arena_top[3]);
     ctx->stats[6] = hc.status;
     ctx->stats[7] = attempt + 1;
     if (hc.status & ST_OVERFLOW_SLOT) {
       // a per-warp state outgrew its arrays: grow them past the size that was needed
       const int need = std::max(hc.max_state, 1);
-      ctx->capD = std::max(ctx->capD * 2, need + need / 2);
+      ctx->capA = std::max(ctx->capA * 2, need + need / 2);
       ctx->capR = std::max(ctx->capR * 2, need + need / 2);
-      ctx->last_required = total + (size_t)p2_slot_bytes<T>(capP, ctx->capR, ctx->capD, chunk2) * nwarps;
+      ctx->capS = std::max(ctx->capS * 2, need + need / 2);
+      ctx->last_required =
+          total + (size_t)p2_slot_bytes<Key>(capP, ctx->capR, ctx->capA, ctx->capS, chunk2) * nwarps;
       if (ws_user) return DEXEL_ERR_CAPACITY;
       continue;
     }
@@ -521,6 +530,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           ctx->stage_ms[q] += ms;
       }
     }
+    for (int q = 0; q < 16; ++q) ctx->phase[q] += hc.phase[q];
     ctx->stats[0] += in->nseg;
     ctx->stats[1] += (long long)hc.mid_total;
     ctx->stats[2] += (long long)hc.out_total;
@@ -608,6 +618,13 @@ int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max) {
   if (!ctx || !ms) return 0;
   int n = max < 5 ? max : 5;
   for (int q = 0; q < n; ++q) ms[q] = ctx->stage_ms[q];
+  return n;
+}
+
+int dexel_last_phases(const dexel_ctx* ctx, uint64_t* ph, int max) {
+  if (!ctx || !ph) return 0;
+  int n = max < 16 ? max : 16;
+  for (int q = 0; q < n; ++q) ph[q] = ctx->phase[q];
   return n;
 }
 

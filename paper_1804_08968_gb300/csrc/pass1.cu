@@ -8,7 +8,8 @@ template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_pass1(P1Params<T> P) {
   const Lanes L{(int)(threadIdx.x & 31), 32};
   const long long gw = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const P1Slot<T> W = p1_slot<T>(P.slots + gw * P.slot_bytes, P.capF, P.capS, P.chunk);
+  typedef typename H<T>::K Key;
+  const P1Slot<Key> W = p1_slot<Key>(P.slots + gw * P.slot_bytes, P.capF, P.capS, P.chunk);
   ArenaCursor cf{0, 0}, cm{0, 0};
   const int nitems = P.ny * P.nchunks;
   for (;;) {

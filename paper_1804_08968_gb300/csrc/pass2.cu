@@ -8,7 +8,9 @@ template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_pass2(P2Params<T> P) {
   const Lanes L{(int)(threadIdx.x & 31), 32};
   const long long gw = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const P2Slot<T> W = p2_slot<T>(P.slots + gw * P.slot_bytes, P.capP, P.capR, P.capD, P.chunk);
+  typedef typename H<T>::K Key;
+  const P2Slot<Key> W =
+      p2_slot<Key>(P.slots + gw * P.slot_bytes, P.capP, P.capR, P.capA, P.capS, P.chunk);
   ArenaCursor cf{0, 0}, co{0, 0};
   const int nitems = P.nx * P.nchunks;
   for (;;) {

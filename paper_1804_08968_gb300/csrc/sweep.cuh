@@ -21,7 +21,7 @@
 // "not yet born" case of Fig. power-vertex).  Forward and backward results are united per
 // column; a column's output is the union of its rectangles and disks.
 #pragma once
-#include "warp_array.cuh"
+#include "heights.cuh"
 
 namespace dexel {
 
@@ -48,7 +48,26 @@ struct Counters {
   int pad;
   unsigned long long mid_total;   // S_mid pieces written
   unsigned long long out_total;   // pass-2 intervals written
+  unsigned long long phase[16];   // optional per-phase clock totals (DEXEL_PHASES builds)
 };
+
+// Optional phase timing of the sweeps (diagnostic builds with -DDEXEL_PHASES): lane 0 adds
+// the clock cycles spent in each phase to Counters::phase.
+#if defined(DEXEL_PHASES) && defined(__CUDA_ARCH__)
+#define PHASE_BEGIN() long long ph_t0_ = clock64()
+#define PHASE(k)                                                          \
+  do {                                                                    \
+    const long long ph_t1_ = clock64();                                   \
+    if ((threadIdx.x & 31) == 0) atomicAdd(&P.ctr->phase[k], (unsigned long long)(ph_t1_ - ph_t0_)); \
+    ph_t0_ = ph_t1_;                                                      \
+  } while (0)
+#define PHASE_COUNT(k, v) \
+  do { if ((threadIdx.x & 31) == 0) atomicAdd(&P.ctr->phase[k], (unsigned long long)(v)); } while (0)
+#else
+#define PHASE_BEGIN() do {} while (0)
+#define PHASE(k) do {} while (0)
+#define PHASE_COUNT(k, v) do {} while (0)
+#endif
 
 struct ArenaCursor {
   long long cur, end;
@@ -191,6 +210,7 @@ DXN int merge_runs(const Lanes& L, const T* aa, const T* ab, const int* av, int 
 // ------------------------------------------------------------------------------------------
 template <typename T>
 struct P1Params {
+  typedef typename H<T>::K Key;
   int nx, ny;
   int K;          // reach in columns (largest integer with K^2 <= k^2)
   int erode;      // complement the input on load
@@ -199,8 +219,8 @@ struct P1Params {
   const int* col_off;
   const T* z;     // input pairs
   // arena 0: forward states (scratch), arena 1: S_mid pieces
-  T* f_a; T* f_b; short* f_l; long long f_cap;
-  T* m_a; T* m_b; short* m_l; long long m_cap;
+  Key* f_a; Key* f_b; short* f_l; long long f_cap;
+  Key* m_a; Key* m_b; short* m_l; long long m_cap;
   long long* m_start;   // S_mid index in line-2 order q = i*ny + j
   int* m_cnt;
   long long blk;
@@ -259,23 +279,25 @@ DXI P1Slot<T> p1_slot(char* base, int capF, int capS, int chunk) {
   return s;
 }
 
-// segments of input column c (complemented for erosion) into sa/sb; returns count
+// segments of input column c (complemented for erosion) into sa/sb as height keys
 template <typename T>
-DXI int load_segments(const Lanes& L, const P1Params<T>& P, int c, T* sa, T* sb) {
+DXI int load_segments(const Lanes& L, const P1Params<T>& P, int c, typename H<T>::K* sa,
+                      typename H<T>::K* sb) {
+  typedef H<T> HT;
   const int s0 = P.col_off[c], s1 = P.col_off[c + 1];
   const int cnt = s1 - s0;
   if (!P.erode) {
     for (int t = L.lane; t < cnt; t += L.nl) {
-      sa[t] = P.z[2 * (long long)(s0 + t)];
-      sb[t] = P.z[2 * (long long)(s0 + t) + 1];
+      sa[t] = HT::key(P.z[2 * (long long)(s0 + t)]);
+      sb[t] = HT::key(P.z[2 * (long long)(s0 + t) + 1]);
     }
     wsync();
     return cnt;
   }
   // complement: (-inf, a0], [b0, a1], ..., [b_{n-1}, +inf)
   for (int t = L.lane; t <= cnt; t += L.nl) {
-    sa[t] = t == 0 ? (T)-DEXEL_INF : P.z[2 * (long long)(s0 + t - 1) + 1];
-    sb[t] = t == cnt ? (T)DEXEL_INF : P.z[2 * (long long)(s0 + t)];
+    sa[t] = t == 0 ? HT::ninf() : HT::key(P.z[2 * (long long)(s0 + t - 1) + 1]);
+    sb[t] = t == cnt ? HT::pinf() : HT::key(P.z[2 * (long long)(s0 + t)]);
   }
   wsync();
   return cnt + 1;
@@ -478,8 +500,8 @@ DXN int min_merge(const Lanes& L, const P1Slot<T>& W, int nF, int nB, int capF, 
 
 // Work item: row j, columns [c0, c1).  Writes S_mid(i, j) for i in [c0, c1).
 template <typename T>
-DXN void pass1_item(const Lanes& L, const P1Params<T>& P, const P1Slot<T>& W, int j, int c0,
-                    int c1, ArenaCursor& curF, ArenaCursor& curM) {
+DXN void pass1_item(const Lanes& L, const P1Params<T>& P, const P1Slot<typename H<T>::K>& W,
+                    int j, int c0, int c1, ArenaCursor& curF, ArenaCursor& curM) {
   int* status = &P.ctr->status;
   const int N = P.nx;
   const int K = P.K;
@@ -547,231 +569,6 @@ DXN void pass1_item(const Lanes& L, const P1Params<T>& P, const P1Slot<T>& W, in
     }
   }
   if (L.lane == 0) add_total(&P.ctr->mid_total, item_total);
-}
-
-// ------------------------------------------------------------------------------------------
-// PASS 2
-// ------------------------------------------------------------------------------------------
-template <typename T>
-struct P2Params {
-  int nx, ny;
-  int K;
-  double kk;       // k^2
-  double h2;       // h^2
-  int chunk, nchunks;
-  const double* wtab;  // w[n] = h sqrt(k^2 - n), n = 0..floor(k^2)
-  const int* reach;    // reach[dx] = largest dy with dx^2 + dy^2 <= k^2
-  const T* m_a; const T* m_b; const short* m_l;
-  const long long* m_start; const int* m_cnt;
-  // arena 2: forward results (scratch), arena 3: final per-column intervals
-  double* f_l; double* f_r; long long f_cap;
-  double* o_l; double* o_r; long long o_cap;
-  long long* o_start;  // per output column, row-major c = j*nx + i
-  int* o_cnt;
-  long long blk;
-  Counters* ctr;
-  char* slots; long long slot_bytes;
-  int capP;   // pieces of one S_mid column
-  int capR;   // rectangle state
-  int capD;   // seed state
-};
-
-template <typename T>
-struct P2Slot {
-  // new column pieces
-  T *pa, *pb; int* pd;
-  // rectangles (state, next, new)
-  T *ra, *rb, *qa, *qb, *na, *nb; int *rt, *qt, *nt;
-  // seeds (state, next, new)
-  T *sz, *uz, *nz; int *sj, *uj, *nj, *sd, *ud, *nd, *so, *uo;
-  // emission / scratch
-  double *el, *er, *gl, *gr, *hl, *hr, *xl, *xr;
-  T* X;
-  int *c0, *c1, *c2, *c3, *c4, *c5, *E;
-  long long* fstart;
-  int* fcnt;
-};
-
-DXI long long p2_ce(int capR, int capD, int capP) {
-  long long a = 2LL * (capR + capP) + 8;
-  long long b = (long long)capD + 2LL * capP + 8;
-  long long c = (long long)capR + capD + 8;
-  long long m = a > b ? a : b;
-  m = m > 2 * c ? m : 2 * c;
-  return m;
-}
-
-template <typename T>
-DXI long long p2_slot_bytes(int capP, int capR, int capD, int chunk) {
-  const long long ce = p2_ce(capR, capD, capP);
-  long long b = 0;
-  b += (2LL * capP + 4LL * capP) * sizeof(T) + 2LL * capP * sizeof(int);   // pa pb na nb nz(2) | pd nt
-  b += 4LL * ce * sizeof(T) + 2LL * ce * sizeof(int);                      // ra rb qa qb | rt qt
-  b += 2LL * capD * sizeof(T) + 6LL * capD * sizeof(int);                  // sz uz | sj uj sd ud so uo
-  b += 4LL * capP * sizeof(int);                                           // nj nd
-  b += 8LL * ce * sizeof(double) + ce * sizeof(T) + 7LL * ce * sizeof(int);
-  b += (long long)chunk * (sizeof(long long) + sizeof(int));
-  return (b + 2048 + 255) & ~255LL;
-}
-
-template <typename T>
-DXI P2Slot<T> p2_slot(char* base, int capP, int capR, int capD, int chunk) {
-  P2Slot<T> s;
-  const long long ce = p2_ce(capR, capD, capP);
-  char* p = base;
-  s.fstart = (long long*)p; p += (long long)chunk * sizeof(long long);
-  double** dd[] = {&s.el, &s.er, &s.gl, &s.gr, &s.hl, &s.hr, &s.xl, &s.xr};
-  for (double** q : dd) { *q = (double*)p; p += ce * sizeof(double); }
-  T** tp[] = {&s.pa, &s.pb, &s.na, &s.nb};
-  for (T** q : tp) { *q = (T*)p; p += (long long)capP * sizeof(T); }
-  s.nz = (T*)p; p += 2LL * capP * sizeof(T);
-  T** tr[] = {&s.ra, &s.rb, &s.qa, &s.qb, &s.X};
-  for (T** q : tr) { *q = (T*)p; p += ce * sizeof(T); }
-  s.sz = (T*)p; p += (long long)capD * sizeof(T);
-  s.uz = (T*)p; p += (long long)capD * sizeof(T);
-  p = (char*)(((unsigned long long)p + 7) & ~7ULL);
-  s.pd = (int*)p; p += (long long)capP * sizeof(int);
-  s.nt = (int*)p; p += (long long)capP * sizeof(int);
-  s.rt = (int*)p; p += ce * sizeof(int);
-  s.qt = (int*)p; p += ce * sizeof(int);
-  int** sd[] = {&s.sj, &s.uj, &s.sd, &s.ud, &s.so, &s.uo};
-  for (int** q : sd) { *q = (int*)p; p += (long long)capD * sizeof(int); }
-  s.nj = (int*)p; p += 2LL * capP * sizeof(int);
-  s.nd = (int*)p; p += 2LL * capP * sizeof(int);
-  int** ie[] = {&s.c0, &s.c1, &s.c2, &s.c3, &s.c4, &s.c5, &s.E};
-  for (int** q : ie) { *q = (int*)p; p += ce * sizeof(int); }
-  s.fcnt = (int*)p;
-  return s;
-}
-
-// power-diagram dominance (Eq. of power cells; App. B): seeds e have power
-// pi_e(z) = (z - z_e)^2 - h^2 (k^2 - n_e).  With z_p < z_s < z_n the middle seed s is
-// dominated (pi_s >= min(pi_p, pi_n) everywhere) iff the bisector of (p, s) lies at or
-// above the bisector of (s, n):
-//     Q (W_p - W_s) + P (W_n - W_s) >= P Q (P + Q),  P = z_s - z_p, Q = z_n - z_s,
-// with W_p - W_s = h^2 (n_s - n_p) exact on integers.  Equal centres: larger weight wins.
-DXI bool dominated3(double zp, int np, double zs, int ns, double zn, int nn, double h2) {
-  if (zp == zs) return np <= ns;
-  if (zn == zs) return nn <= ns;
-  const double P = zs - zp, Q = zn - zs;
-  const double lhs = h2 * (Q * (double)(ns - np) + P * (double)(ns - nn));
-  const double rhs = P * Q * (P + Q);
-  return lhs >= rhs;
-}
-
-// Sorted-interval utilities on doubles ------------------------------------------------------
-
-// C := merge of sorted interval lists A and B by left end (A first on ties)
-DXN int merge_intervals(const Lanes& L, const double* al, const double* ar, int na,
-                        const double* bl, const double* br, int nb, double* cl, double* cr) {
-  for (int t = L.lane; t < na; t += L.nl) {
-    const int pos = t + lower_bound(bl, nb, al[t]);
-    cl[pos] = al[t]; cr[pos] = ar[t];
-  }
-  for (int u = L.lane; u < nb; u += L.nl) {
-    const int pos = u + upper_bound(al, na, bl[u]);
-    cl[pos] = bl[u]; cr[pos] = br[u];
-  }
-  wsync();
-  return na + nb;
-}
-
-// U := union of intervals sorted by left end (closed: touching intervals join).
-// Scratch: flag/pos int arrays of n.  Output may alias nothing.
-DXN int union_sorted(const Lanes& L, const double* cl, const double* cr, int n, int* start,
-                     int* pos, double* ul, double* ur, double* pmax) {
-  // exclusive prefix max of right ends
-  double carry = -DEXEL_INF;
-  for (int base = 0; base < n; base += L.nl) {
-    const int t = base + L.lane;
-    const double v = t < n ? cr[t] : -DEXEL_INF;
-    const double inc = w_incl_maxd(v, L.lane);
-#if defined(__CUDA_ARCH__)
-    double prev = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (L.lane == 0) prev = -DEXEL_INF;
-#else
-    const double prev = -DEXEL_INF;
-#endif
-    if (t < n) {
-      const double ex = prev > carry ? prev : carry;
-      start[t] = (t == 0) || (cl[t] > ex);
-      pmax[t] = fmax(ex, v);  // inclusive
-    }
-    carry = fmax(carry, w_bcastd(inc, L.nl - 1));
-  }
-  wsync();
-  for (int t = L.lane; t < n; t += L.nl) pos[t] = start[t];
-  wsync();
-  const int nu = scan_excl(L, pos, n);
-  // run end = element before the next start (or last); run right = inclusive pmax there
-  for (int t = L.lane; t < n; t += L.nl) {
-    if (start[t]) ul[pos[t]] = cl[t];
-    const bool last = (t == n - 1) || start[t + 1];
-    if (last) ur[pos[t] - (start[t] ? 0 : 1)] = pmax[t];
-  }
-  wsync();
-  return nu;
-}
-
-// Run-union of disks of an exact lower envelope given in z order (left ends need not be
-// sorted, but no disk reaches past a gap of the union, so each run spans a contiguous
-// range): run = [min left, max right].
-DXN int union_envelope(const Lanes& L, const double* dl, const double* dr, int n, int* start,
-                       int* pos, double* ul, double* ur, double* pmax, double* smin) {
-  double carry = -DEXEL_INF;
-  for (int base = 0; base < n; base += L.nl) {
-    const int t = base + L.lane;
-    const double v = t < n ? dr[t] : -DEXEL_INF;
-    const double inc = w_incl_maxd(v, L.lane);
-#if defined(__CUDA_ARCH__)
-    double prev = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (L.lane == 0) prev = -DEXEL_INF;
-#else
-    const double prev = -DEXEL_INF;
-#endif
-    if (t < n) {
-      const double ex = prev > carry ? prev : carry;
-      start[t] = (t == 0) || (dl[t] > ex);
-      pmax[t] = fmax(ex, v);
-    }
-    carry = fmax(carry, w_bcastd(inc, L.nl - 1));
-  }
-  wsync();
-  // segmented min of left ends
-  double cmin = DEXEL_INF;
-  for (int base = 0; base < n; base += L.nl) {
-    const int t = base + L.lane;
-    double v = t < n ? dl[t] : DEXEL_INF;
-    int f = t < n ? start[t] : 0;
-#if defined(__CUDA_ARCH__)
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double u = __shfl_up_sync(0xffffffffu, v, o);
-      const int g = __shfl_up_sync(0xffffffffu, f, o);
-      if (L.lane >= o) {
-        if (!f) v = fmin(v, u);
-        f |= g;
-      }
-    }
-#endif
-    if (!f) v = fmin(v, cmin);
-    if (t < n) smin[t] = v;
-    cmin = w_bcastd(v, L.nl - 1);
-  }
-  wsync();
-  for (int t = L.lane; t < n; t += L.nl) pos[t] = start[t];
-  wsync();
-  const int nu = scan_excl(L, pos, n);
-  for (int t = L.lane; t < n; t += L.nl) {
-    const bool last = (t == n - 1) || start[t + 1];
-    if (last) {
-      const int r = pos[t] - (start[t] ? 0 : 1);
-      ul[r] = smin[t];
-      ur[r] = pmax[t];
-    }
-  }
-  wsync();
-  return nu;
 }
 
 }  // namespace dexel

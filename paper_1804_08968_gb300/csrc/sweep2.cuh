@@ -1,85 +1,459 @@
-// Pass 2 of the dexel offset: per column line, forward and backward sweeps over the
-// S_mid pieces with the rectangle envelope and the half-space power diagram of the
-// endpoint seeds (Sec. 3.3 "2D Power Diagram", Fig. segments-separate, Fig. power-vertex).
+// Pass 2 of the dexel offset: per column line, forward and backward sweeps over the S_mid
+// pieces (Sec. 3.3 "2D Power Diagram", Fig. segments-separate, Fig. power-vertex).
+//
+// A piece (a, b, dx) of S_mid at line position j' reaches position j with the capsule slice
+// [a - w, b + w], w = h sqrt(k^2 - n), n = dx^2 + (j - j')^2 <= k^2.  The capsule is the
+// extruded rectangle [a, b] (alive while n <= k^2) plus the disks of its two endpoints.
+//
+// Rectangles: a max-expiry envelope over z (for every height, the furthest sweep position
+// still reached), merged with the new column's pieces at every step.
+//
+// Endpoint disks: seeds e = (z_e, o_e, dx_e) with power pi_e(z) = (z - z_e)^2 - h^2 (k^2 - n_e)
+// (Eq. of power cells, App. B).  Along the current line the covered set is
+// {z : min_e pi_e(z) <= 0}; only the seeds of the lower envelope of the pi_e matter.  The
+// envelope A is kept across steps; at every step the new column's seeds and the seeds due
+// to wake up are merged in and parity rounds remove every seed dominated by its two
+// neighbours (the three-seed power-vertex test of App. B, written without division).  For
+// a removed seed s the domination margin V by its neighbours is linear in the sweep
+// position (dV/du = 2 h^2 (Q (o_p - o_s) + P (o_n - o_s))): if dV/du >= 0 the seed stays
+// dominated for the rest of the sweep and is discarded (in particular when both neighbours
+// are newer -- older seeds only lose ground); otherwise it sleeps until the first position
+// where V may turn negative and is tested again then (the "not yet born" seeds of
+// Fig. power-vertex, which the paper handles with power-vertex events).  A sleeping seed's
+// disk stays inside the union of the envelope's disks, so the envelope alone gives the
+// covered set.
+//
+// Predicates are evaluated in float with a forward error bound and re-evaluated in double
+// only when the float value is too close to zero to decide.  Heights are compared as
+// order-preserving keys (heights.cuh); double arithmetic is left to the undecided
+// predicates and the emitted endpoints z -/+ w.
 #pragma once
 #include "sweep.cuh"
 
 namespace dexel {
 
-// seed flags
-enum : int { SEED_WAIT = 0, SEED_ENV = 1, SEED_GONE = -1 };
-
 template <typename T>
-DXI int seed_n(const int* sd, const int* sj, int t, int j) {
-  const int dy = j - sj[t];
-  return sd[t] + dy * dy;
+struct P2Params {
+  typedef typename H<T>::K Key;
+  int nx, ny;
+  int R;           // reach in grid steps (largest integer with R^2 <= k^2)
+  double kk;       // k^2
+  double h2;       // h^2
+  float h2f;
+  int chunk, nchunks;
+  const double* wtab;  // w[n] = h sqrt(k^2 - n), n = 0..floor(k^2)
+  const int* reach;    // reach[dx] = largest dy with dx^2 + dy^2 <= k^2
+  const Key* m_a; const Key* m_b; const short* m_l;
+  const long long* m_start; const int* m_cnt;
+  // arena 2: forward results (scratch), arena 3: final per-column intervals (height keys)
+  ukey* f_l; ukey* f_r; long long f_cap;
+  ukey* o_l; ukey* o_r; long long o_cap;
+  long long* o_start;  // per output column, row-major c = j*nx + i
+  int* o_cnt;
+  long long blk;
+  Counters* ctr;
+  char* slots; long long slot_bytes;
+  int capP;   // pieces of one S_mid column
+  int capR;   // rectangle envelope
+  int capA;   // envelope seeds (with the step's new and woken seeds)
+  int capS;   // sleeping seeds
+};
+
+template <typename Key>
+struct P2Slot {
+  Key *pa, *pb; int* pd;                 // the column's pieces
+  Key *ra, *rb, *qa, *qb; int *rt, *qt;  // rectangle envelope (state, next)
+  Key *na, *nb; int* nt;                 // new rectangles
+  Key *az, *bz; int *ao, *ad, *bo, *bd;  // envelope seeds (two buffers): height, order, dx
+  Key* nz; int* nd;                      // new seeds of the column
+  Key* wz; int *wo, *wd;                 // woken seeds
+  Key* sz; int *so, *sd, *sw;            // sleeping seeds: height, order, dx, wake-up position
+  ukey *el, *er, *gl, *gr, *hl, *hr, *xl, *xr;  // interval scratch
+  Key* X;
+  int *c0, *c1, *c2, *c3, *c4, *c5;
+  long long* fstart;
+  int* fcnt;
+};
+
+DXI long long p2_ce(int capR, int capA, int capP, int capS) {
+  long long m = 2LL * (capR + capP) + 8;
+  const long long b = 2LL * capA + 2LL * capP + 8;
+  const long long c = 2LL * (capR + capA) + 8;
+  const long long d = (long long)capS + 8;
+  m = m > b ? m : b;
+  m = m > c ? m : c;
+  m = m > d ? m : d;
+  return m;
 }
 
-// Is seed s dominated by its on-envelope neighbours p (below, or -1) and n (above, or -1)?
-// *perm is set when the dominating seeds are all newer-or-equal in sweep order, so that
-// the domination holds for the rest of the sweep.
-template <typename T>
-DXI bool seed_dominated(const T* z, const int* sj, const int* sd, int j, int dir, int p, int s,
-                        int n, double h2, bool* perm) {
-  const double zs = (double)z[s];
-  const int ns = seed_n<T>(sd, sj, s, j);
-  const int os = dir * sj[s];
-  *perm = false;
-  if (p >= 0 && n >= 0) {
-    const double zp = (double)z[p], zn = (double)z[n];
-    const int np = seed_n<T>(sd, sj, p, j), nn = seed_n<T>(sd, sj, n, j);
-    if (zp == zs) {
-      if (np <= ns) { *perm = dir * sj[p] >= os; return true; }
-      return false;
-    }
-    if (zn == zs) {
-      if (nn <= ns) { *perm = dir * sj[n] >= os; return true; }
-      return false;
-    }
-    if (dominated3(zp, np, zs, ns, zn, nn, h2)) {
-      *perm = dir * sj[p] >= os && dir * sj[n] >= os;
-      return true;
-    }
-    return false;
-  }
-  const int q = p >= 0 ? p : n;
-  if (q < 0) return false;
-  if ((double)z[q] == zs && seed_n<T>(sd, sj, q, j) <= ns) {
-    *perm = dir * sj[q] >= os;
-    return true;
-  }
-  return false;
+template <typename Key>
+DXI long long p2_slot_bytes(int capP, int capR, int capA, int capS, int chunk) {
+  const long long ce = p2_ce(capR, capA, capP, capS);
+  long long b = 0;
+  b += (long long)chunk * (sizeof(long long) + sizeof(int)) + 64;
+  b += 8LL * ce * sizeof(ukey);
+  b += 5LL * ce * sizeof(Key) + 8LL * ce * sizeof(int);
+  b += 6LL * capP * sizeof(Key) + 4LL * capP * sizeof(int);
+  b += 3LL * capA * sizeof(Key) + 6LL * capA * sizeof(int);
+  b += (long long)capS * sizeof(Key) + 3LL * capS * sizeof(int);
+  return (b + 4096 + 255) & ~255LL;
 }
 
+template <typename Key>
+DXI P2Slot<Key> p2_slot(char* base, int capP, int capR, int capA, int capS, int chunk) {
+  P2Slot<Key> s;
+  const long long ce = p2_ce(capR, capA, capP, capS);
+  char* p = base;
+  s.fstart = (long long*)p;
+  p += (long long)chunk * sizeof(long long);
+  p = (char*)(((unsigned long long)p + 15) & ~15ULL);
+  ukey** uu[] = {&s.el, &s.er, &s.gl, &s.gr, &s.hl, &s.hr, &s.xl, &s.xr};
+  for (ukey** q : uu) { *q = (ukey*)p; p += ce * sizeof(ukey); }
+  Key** kp[] = {&s.pa, &s.pb, &s.na, &s.nb};
+  for (Key** q : kp) { *q = (Key*)p; p += (long long)capP * sizeof(Key); }
+  s.nz = (Key*)p; p += 2LL * capP * sizeof(Key);
+  Key** kr[] = {&s.ra, &s.rb, &s.qa, &s.qb, &s.X};
+  for (Key** q : kr) { *q = (Key*)p; p += ce * sizeof(Key); }
+  Key** ka[] = {&s.az, &s.bz, &s.wz};
+  for (Key** q : ka) { *q = (Key*)p; p += (long long)capA * sizeof(Key); }
+  s.sz = (Key*)p; p += (long long)capS * sizeof(Key);
+  p = (char*)(((unsigned long long)p + 15) & ~15ULL);
+  s.pd = (int*)p; p += (long long)capP * sizeof(int);
+  s.nt = (int*)p; p += (long long)capP * sizeof(int);
+  s.nd = (int*)p; p += 2LL * capP * sizeof(int);
+  s.rt = (int*)p; p += ce * sizeof(int);
+  s.qt = (int*)p; p += ce * sizeof(int);
+  int** ia[] = {&s.ao, &s.ad, &s.bo, &s.bd, &s.wo, &s.wd};
+  for (int** q : ia) { *q = (int*)p; p += (long long)capA * sizeof(int); }
+  int** is[] = {&s.so, &s.sd, &s.sw};
+  for (int** q : is) { *q = (int*)p; p += (long long)capS * sizeof(int); }
+  int** ie[] = {&s.c0, &s.c1, &s.c2, &s.c3, &s.c4, &s.c5};
+  for (int** q : ie) { *q = (int*)p; p += ce * sizeof(int); }
+  s.fcnt = (int*)p;
+  return s;
+}
+
+// heights of a piece/seed key as an interval key (always the double encoding)
+DXI ukey ikey(ukey k) { return k; }
+DXI ukey ikey(float k) { return dkey((double)k); }
+
+// float approximation of a height key by truncation (integer operations only for doubles);
+// relative error below 2^-23, magnitudes below 2^-126 flush to 0
+DXI float keyf(float k) { return k; }
+DXI float keyf(ukey k) {
+  const long long s = (long long)k;
+  const unsigned long long b = s < 0 ? (k ^ 0x8000000000000000ULL) : ~k;  // double bits
+  const unsigned sign = (unsigned)(b >> 63);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  unsigned f;
+  if (e <= 0)
+    f = sign << 31;
+  else if (e >= 255)
+    f = (sign << 31) | 0x7f800000u;
+  else
+    f = (sign << 31) | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffULL);
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(f);
+#else
+  float x;
+  memcpy(&x, &f, 4);
+  return x;
+#endif
+}
+DXI double keyd(float k) { return (double)k; }
+DXI double keyd(ukey k) { return dval(k); }
+
+constexpr int FATE_KEEP = -1;
+constexpr int FATE_DROP = 0x7fffffff;
+
+DXI int seed_n(int dx, int o, int u) { return dx * dx + (u - o) * (u - o); }
+
+// seed s dominated by a seed t at the same height (n_t <= n_s): dominated while
+// n_s - n_t >= 0, a margin that changes by 2 (o_t - o_s) per step
+DXI int equal_fate(int ot, int nt, int os, int ns, int u) {
+  if (ot >= os) return FATE_DROP;
+  const long long V = (long long)ns - nt;
+  const long long dec = 2LL * (os - ot);
+  const long long w = (long long)u + V / dec + 1;
+  return w < FATE_DROP ? (int)w : FATE_DROP - 1;
+}
+
+// Fate of seed s against its envelope neighbours p (below, -1 if none) and n (above) at
+// sweep position u: FATE_KEEP, FATE_DROP, or the position at which to test it again.
+template <typename Key>
+DXI int seed_fate(const Key* z, const int* o, const int* d, int p, int s, int n, int u,
+                  double h2, float h2f) {
+  const Key zs = z[s];
+  const int os = o[s];
+  const int ns = seed_n(d[s], os, u);
+  const bool eqp = p >= 0 && z[p] == zs;
+  const bool eqn = n >= 0 && z[n] == zs;
+  if (eqp || eqn) {
+    int fate = FATE_KEEP;
+    if (eqp) {
+      const int np = seed_n(d[p], o[p], u);
+      if (np <= ns) fate = equal_fate(o[p], np, os, ns, u);
+    }
+    if (eqn) {
+      const int nn = seed_n(d[n], o[n], u);
+      if (nn <= ns) {
+        const int f = equal_fate(o[n], nn, os, ns, u);
+        fate = fate == FATE_KEEP ? f : (f > fate ? f : fate);
+      }
+    }
+    return fate;
+  }
+  if (p < 0 || n < 0) return FATE_KEEP;
+  const int op = o[p], on = o[n];
+  const int A = ns - seed_n(d[p], op, u);  // (W_p - W_s) / h^2
+  const int B = ns - seed_n(d[n], on, u);  // (W_n - W_s) / h^2
+  // float filter for V = h^2 (Q A + P B) - P Q (P + Q),  P = z_s - z_p, Q = z_n - z_s
+  const float zpf = keyf(z[p]), zsf = keyf(zs), znf = keyf(z[n]);
+  const float Pf = zsf - zpf, Qf = znf - zsf;
+  const float uc = 1.1920929e-7f;  // 2^-23: key to float truncation
+  const float ur = 5.9604645e-8f;  // 2^-24: float rounding
+  const float eP = uc * (fabsf(zsf) + fabsf(zpf)) + ur * fabsf(Pf) + 1e-37f;
+  const float eQ = uc * (fabsf(znf) + fabsf(zsf)) + ur * fabsf(Qf) + 1e-37f;
+  const float fA = (float)A, fB = (float)B;
+  const float PQ = Pf + Qf;
+  const float T3 = Pf * Qf * PQ;
+  const float Vf = h2f * (Qf * fA + Pf * fB) - T3;
+  float E = h2f * (fabsf(fA) * eQ + fabsf(fB) * eP) + (Qf * PQ + Pf * Qf) * eP +
+            (Pf * PQ + Pf * Qf) * eQ + 4.0f * (eP + eQ) * (eP + eQ) * (PQ + eP + eQ) +
+            8.0f * ur * (h2f * (fabsf(Qf * fA) + fabsf(Pf * fB)) + fabsf(T3));
+  E *= 2.0f;
+  float Vlo;
+  if (Vf > E) {
+    Vlo = Vf - E;
+  } else if (Vf < -E) {
+    return FATE_KEEP;
+  } else {
+    const double zp = keyd(z[p]), zsd = keyd(zs), zn = keyd(z[n]);
+    const double P = zsd - zp, Q = zn - zsd;
+    const double V = h2 * (Q * (double)A + P * (double)B) - P * Q * (P + Q);
+    if (!(V >= 0.0)) return FATE_KEEP;
+    Vlo = 0.0f;
+  }
+  // dominated now; dV/du = 2 h^2 (Q a + P b)
+  const int a = op - os, b = on - os;
+  if (a >= 0 && b >= 0) return FATE_DROP;
+  const float fa = (float)a, fb = (float)b;
+  const float Gf = 2.0f * h2f * (Qf * fa + Pf * fb);
+  const float EG = 2.0f * h2f * (fabsf(fa) * eQ + fabsf(fb) * eP) +
+                   16.0f * ur * h2f * (fabsf(Qf * fa) + fabsf(Pf * fb)) + 1e-37f;
+  if (Gf > 2.0f * EG) return FATE_DROP;
+  if (Gf < -2.0f * EG) {
+    const float steps = Vlo / (2.0f * EG - Gf) * 0.999f;
+    const long long w = (long long)u + 1 + (long long)(steps < 1.0e9f ? steps : 1.0e9f);
+    return w < FATE_DROP ? (int)w : FATE_DROP - 1;
+  }
+  return u + 1;
+}
+
+// ---------------------------------------------------------------------------------------
+// sorted interval utilities on height keys
+// ---------------------------------------------------------------------------------------
+DXI ukey w_incl_maxk(ukey v, int lane) {
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const ukey w = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o && w > v) v = w;
+  }
+#else
+  (void)lane;
+#endif
+  return v;
+}
+DXI ukey w_bcastk(ukey v, int src) {
+#if defined(__CUDA_ARCH__)
+  return __shfl_sync(0xffffffffu, v, src);
+#else
+  (void)src;
+  return v;
+#endif
+}
+DXI ukey w_shift_up(ukey v, int lane, ukey fill) {
+#if defined(__CUDA_ARCH__)
+  const ukey w = __shfl_up_sync(0xffffffffu, v, 1);
+  return lane == 0 ? fill : w;
+#else
+  (void)v;
+  (void)lane;
+  return fill;
+#endif
+}
+
+// C := merge of sorted interval lists A and B by left end (A first on ties)
+DXN int merge_intervals(const Lanes& L, const ukey* al, const ukey* ar, int na, const ukey* bl,
+                        const ukey* br, int nb, ukey* cl, ukey* cr) {
+  for (int t = L.lane; t < na; t += L.nl) {
+    const int pos = t + lower_bound(bl, nb, al[t]);
+    cl[pos] = al[t];
+    cr[pos] = ar[t];
+  }
+  for (int t = L.lane; t < nb; t += L.nl) {
+    const int pos = t + upper_bound(al, na, bl[t]);
+    cl[pos] = bl[t];
+    cr[pos] = br[t];
+  }
+  wsync();
+  return na + nb;
+}
+
+// Run-union of closed intervals (touching ones join).  With sorted = true the left ends are
+// sorted; otherwise the list is an exact lower envelope in z order, whose disks never
+// reach past a gap of the union, so every run is a contiguous range and its left end is
+// the minimum over the run (smin scratch needed).
+DXN int union_runs(const Lanes& L, const ukey* cl, const ukey* cr, int n, bool sorted,
+                   int* start, int* pos, ukey* ul, ukey* ur, ukey* pmax, ukey* smin) {
+  ukey carry = 0;
+  for (int base = 0; base < n; base += L.nl) {
+    const int t = base + L.lane;
+    const ukey v = t < n ? cr[t] : 0;
+    const ukey inc = w_incl_maxk(v, L.lane);
+    const ukey prev = w_shift_up(inc, L.lane, 0);
+    if (t < n) {
+      const ukey ex = prev > carry ? prev : carry;
+      start[t] = (t == 0) || (cl[t] > ex);
+      pmax[t] = ex > v ? ex : v;
+    }
+    const ukey last = w_bcastk(inc, L.nl - 1);
+    carry = last > carry ? last : carry;
+  }
+  wsync();
+  if (!sorted) {
+    ukey cmin = ~0ULL;
+    for (int base = 0; base < n; base += L.nl) {
+      const int t = base + L.lane;
+      ukey v = t < n ? cl[t] : ~0ULL;
+      int f = t < n ? start[t] : 0;
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const ukey w = __shfl_up_sync(0xffffffffu, v, o);
+        const int g = __shfl_up_sync(0xffffffffu, f, o);
+        if (L.lane >= o) {
+          if (!f && w < v) v = w;
+          f |= g;
+        }
+      }
+#endif
+      if (!f && cmin < v) v = cmin;
+      if (t < n) smin[t] = v;
+      cmin = w_bcastk(v, L.nl - 1);
+    }
+    wsync();
+  }
+  for (int t = L.lane; t < n; t += L.nl) pos[t] = start[t];
+  wsync();
+  const int nu = scan_excl(L, pos, n);
+  for (int t = L.lane; t < n; t += L.nl) {
+    const bool last = (t == n - 1) || start[t + 1];
+    const int r = pos[t] - (start[t] ? 0 : 1);
+    if (sorted) {
+      if (start[t]) ul[r] = cl[t];
+    } else if (last) {
+      ul[r] = smin[t];
+    }
+    if (last) ur[r] = pmax[t];
+  }
+  wsync();
+  return nu;
+}
+
+// Covered set of an exact lower envelope of disks D_t = [l_t, r_t] (z order), as sorted
+// disjoint runs.  Seed t owns the cell between its bisectors with t-1 and t+1, so the covered
+// set is the ordered union of C_t = D_t ∩ cell_t.  Whether a bisector clips D_t is decided by
+// key comparisons alone: the bisector with t-1 lies above l_t iff l_t is strictly inside
+// D_{t-1} (t-1 has the lower power there), and below r_t iff r_t is strictly inside D_{t+1}.
+// A clipped side touches the neighbour's C; runs start at unclipped left ends and finish at
+// unclipped right ends, so every run endpoint is an exact disk endpoint z -/+ w.  If the
+// envelope is not exact (a near tie decided the other way) the runs could come out of
+// order; that is detected and the disks are then sorted by left end and united directly.
+DXN int envelope_runs(const Lanes& L, const ukey* dl, const ukey* dr, int n, int* start,
+                      int* stop, int* pos, ukey* ul, ukey* ur, ukey* sl, ukey* sr) {
+  for (int t = L.lane; t < n; t += L.nl) {
+    const ukey lt = dl[t], rt = dr[t];
+    const bool lT = t > 0 && dl[t - 1] < lt && lt < dr[t - 1];
+    const bool rT = t + 1 < n && dl[t + 1] < rt && rt < dr[t + 1];
+    bool ne;
+    if (lT == rT)
+      ne = true;
+    else if (lT)
+      ne = rt >= dr[t - 1];
+    else
+      ne = lt <= dl[t + 1];
+    start[t] = ne && !lT;
+    stop[t] = ne && !rT;
+  }
+  wsync();
+  for (int t = L.lane; t < n; t += L.nl) pos[t] = start[t];
+  wsync();
+  const int nu = scan_excl(L, pos, n);
+  for (int t = L.lane; t < n; t += L.nl) {
+    if (start[t]) ul[pos[t]] = dl[t];
+    if (stop[t]) ur[pos[t] + start[t] - 1] = dr[t];
+  }
+  wsync();
+  int bad = 0;
+  for (int r = L.lane; r < nu; r += L.nl) bad |= !(ul[r] <= ur[r]) || (r > 0 && !(ur[r - 1] < ul[r]));
+  if (!w_any(bad)) return nu;
+  // fallback: rank-sort the disks by left end, then a sorted union
+  for (int t = L.lane; t < n; t += L.nl) {
+    const ukey x = dl[t];
+    int rk = 0;
+    for (int v = 0; v < n; ++v) rk += dl[v] < x || (dl[v] == x && v < t);
+    sl[rk] = x;
+    sr[rk] = dr[t];
+  }
+  wsync();
+  // (the running maximum may overwrite sr: each right end is read before it is replaced)
+  return union_runs(L, sl, sr, n, true, start, pos, ul, ur, sr, nullptr);
+}
+
+// ---------------------------------------------------------------------------------------
+// the work item: column line i, output positions [c0, c1)
+// ---------------------------------------------------------------------------------------
 template <typename T>
-DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<T>& W, int i, int c0,
-                    int c1, ArenaCursor& curF, ArenaCursor& curO) {
+DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<typename H<T>::K>& W,
+                    int i, int c0, int c1, ArenaCursor& curF, ArenaCursor& curO) {
+  typedef typename H<T>::K Key;
   int* status = &P.ctr->status;
   const int N = P.ny;
-  const int K = P.K;
-  const double kk = P.kk;
+  const int R = P.R;
+  const long long ce = p2_ce(P.capR, P.capA, P.capP, P.capS);
   long long item_total = 0;
   for (int dir = 1; dir >= -1; dir -= 2) {
-    int nr = 0, ns = 0;
-    const int jb = dir > 0 ? (c0 - K > 0 ? c0 - K : 0) : (c1 - 1 + K < N - 1 ? c1 - 1 + K : N - 1);
+    int nr = 0;   // rectangles
+    int na = 0;   // envelope seeds
+    int nsl = 0;  // sleeping seeds
+    Key* Az = W.az; int* Ao = W.ao; int* Ad = W.ad;  // envelope (current buffer)
+    Key* Bz = W.bz; int* Bo = W.bo; int* Bd = W.bd;  // other buffer
+    const int jb = dir > 0 ? (c0 - R > 0 ? c0 - R : 0) : (c1 - 1 + R < N - 1 ? c1 - 1 + R : N - 1);
     const int je = dir > 0 ? c1 : c0 - 1;
     for (int j = jb; j != je; j += dir) {
-      const int cur = dir * j;
+      const int u = dir > 0 ? j : N - 1 - j;  // sweep position: 0, 1, 2, ... in sweep order
       const bool emit = j >= c0 && j < c1;
+      PHASE_BEGIN();
       // ---- load S_mid(i, j)
       const long long q = (long long)i * P.ny + j;
       const int np = P.m_cnt[q];
       const long long ms = P.m_start[q];
-      if (np > P.capP) { if (L.lane == 0) set_status(status, ST_OVERFLOW_SLOT); return; }
+      if (np > P.capP) {
+        if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, np); }
+        return;
+      }
       for (int t = L.lane; t < np; t += L.nl) {
         W.pa[t] = P.m_a[ms + t];
         W.pb[t] = P.m_b[ms + t];
-        const int dx = P.m_l[ms + t];
-        W.pd[t] = dx;
+        W.pd[t] = P.m_l[ms + t];
       }
       wsync();
-      // ---- rectangles: expire, new ones, max-expiry merge
-      for (int t = L.lane; t < nr; t += L.nl) W.c0[t] = W.rt[t] >= cur;
+
+      PHASE(0);
+      // ---- rectangles: expire, add the column's, max-expiry merge
+      for (int t = L.lane; t < nr; t += L.nl) W.c0[t] = W.rt[t] >= u;
       wsync();
       for (int t = L.lane; t < nr; t += L.nl) W.c1[t] = W.c0[t];
       wsync();
@@ -94,38 +468,73 @@ DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<T>& W, in
       for (int t = L.lane; t < np; t += L.nl)
         if (W.c2[t]) {
           const int o = W.c3[t];
-          W.na[o] = W.pa[t]; W.nb[o] = W.pb[t]; W.nt[o] = cur + P.reach[W.pd[t]];
+          W.na[o] = W.pa[t]; W.nb[o] = W.pb[t]; W.nt[o] = u + P.reach[W.pd[t]];
         }
       wsync();
-      if (2 * (nq + nn) > p2_ce(P.capR, P.capD, P.capP)) {
+      if (2LL * (nq + nn) + 8 > ce) {
         if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nq + nn); }
         return;
       }
-      nr = merge_runs<T, false>(L, W.qa, W.qb, W.qt, nq, W.na, W.nb, W.nt, nn, W.X, W.c0, W.c1,
-                                W.c2, W.c3, W.c4, W.c5, W.ra, W.rb, W.rt);
+      nr = merge_runs<Key, false>(L, W.qa, W.qb, W.qt, nq, W.na, W.nb, W.nt, nn, W.X, W.c0, W.c1,
+                                  W.c2, W.c3, W.c4, W.c5, W.ra, W.rb, W.rt);
       if (nr > P.capR) {
         if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nr); }
         return;
       }
 
-      // ---- seeds: drop dead or pruned ones
-      for (int t = L.lane; t < ns; t += L.nl)
-        W.c0[t] = W.so[t] != SEED_GONE && seed_n<T>(W.sd, W.sj, t, j) <= kk;
-      wsync();
-      for (int t = L.lane; t < ns; t += L.nl) W.c1[t] = W.c0[t];
-      wsync();
-      const int nu = scan_excl(L, W.c1, ns);
-      for (int t = L.lane; t < ns; t += L.nl)
-        if (W.c0[t]) {
-          const int o = W.c1[t];
-          W.uz[o] = W.sz[t]; W.uj[o] = W.sj[t]; W.ud[o] = W.sd[t]; W.uo[o] = W.so[t];
+      PHASE(1);
+      // ---- sleeping seeds due now: wake the live ones, drop the dead ones
+      int nw = 0;
+      {
+        int any = 0;
+        for (int t = L.lane; t < nsl; t += L.nl) any |= W.sw[t] <= u;
+        if (w_any(any)) {
+          for (int t = L.lane; t < nsl; t += L.nl) {
+            const bool due = W.sw[t] <= u;
+            W.c0[t] = !due;
+            W.c1[t] = due && (u - W.so[t] <= P.reach[W.sd[t]]);
+          }
+          wsync();
+          for (int t = L.lane; t < nsl; t += L.nl) { W.c2[t] = W.c0[t]; W.c3[t] = W.c1[t]; }
+          wsync();
+          const int keep = scan_excl(L, W.c2, nsl);
+          nw = scan_excl(L, W.c3, nsl);
+          if (nw > P.capA) {
+            if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nw); }
+            return;
+          }
+          for (int t = L.lane; t < nsl; t += L.nl)
+            if (W.c1[t]) { const int o = W.c3[t]; W.X[o] = W.sz[t]; W.c4[o] = W.so[t]; W.c5[o] = W.sd[t]; }
+          wsync();
+          // in-place stable compaction of the pool: every lane reads its element, then writes
+          for (int base = 0; base < nsl; base += L.nl) {
+            const int t = base + L.lane;
+            Key z0 = Key();
+            int o0 = 0, d0 = 0, w0 = 0, dst = -1;
+            if (t < nsl && W.c0[t]) { z0 = W.sz[t]; o0 = W.so[t]; d0 = W.sd[t]; w0 = W.sw[t]; dst = W.c2[t]; }
+            wsync();
+            if (dst >= 0) { W.sz[dst] = z0; W.so[dst] = o0; W.sd[dst] = d0; W.sw[dst] = w0; }
+            wsync();
+          }
+          nsl = keep;
+          // woken seeds sorted by height (rank sort; usually a handful)
+          for (int t = L.lane; t < nw; t += L.nl) {
+            const Key x = W.X[t];
+            int r = 0;
+            for (int v = 0; v < nw; ++v) r += (W.X[v] < x) || (W.X[v] == x && v < t);
+            W.wz[r] = x; W.wo[r] = W.c4[t]; W.wd[r] = W.c5[t];
+          }
+          wsync();
         }
-      wsync();
-      // new seeds: bottom and top endpoints of the pieces (finite, top only if b > a)
+      }
+
+      PHASE(2);
+      // ---- new seeds: piece endpoints (finite; top only if b > a); equal heights keep
+      //      the smallest dx
       for (int t = L.lane; t < np; t += L.nl) {
-        const T a = W.pa[t], b = W.pb[t];
-        const int ca = (a > (T)-DEXEL_INF && a < (T)DEXEL_INF) ? 1 : 0;
-        const int cb = (b > (T)-DEXEL_INF && b < (T)DEXEL_INF && b != a) ? 1 : 0;
+        const Key a = W.pa[t], b = W.pb[t];
+        const int ca = (a > H<T>::ninf() && a < H<T>::pinf()) ? 1 : 0;
+        const int cb = (b > H<T>::ninf() && b < H<T>::pinf() && b != a) ? 1 : 0;
         W.c2[t] = ca + cb;
       }
       wsync();
@@ -133,14 +542,13 @@ DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<T>& W, in
       wsync();
       const int nc = scan_excl(L, W.c3, np);
       for (int t = L.lane; t < np; t += L.nl) {
-        const T a = W.pa[t], b = W.pb[t];
+        const Key a = W.pa[t], b = W.pb[t];
         int o = W.c3[t];
-        const int d2 = W.pd[t] * W.pd[t];
-        if (a > (T)-DEXEL_INF && a < (T)DEXEL_INF) { W.nz[o] = a; W.nd[o] = d2; ++o; }
-        if (b > (T)-DEXEL_INF && b < (T)DEXEL_INF && b != a) { W.nz[o] = b; W.nd[o] = d2; }
+        const int dx = W.pd[t];
+        if (a > H<T>::ninf() && a < H<T>::pinf()) { W.nz[o] = a; W.nd[o] = dx; ++o; }
+        if (b > H<T>::ninf() && b < H<T>::pinf() && b != a) { W.nz[o] = b; W.nd[o] = dx; }
       }
       wsync();
-      // equal heights within the column: keep the smallest dx (largest weight)
       for (int t = L.lane; t < nc; t += L.nl) {
         bool keep = true;
         if (t + 1 < nc && W.nz[t + 1] == W.nz[t] && W.nd[t + 1] <= W.nd[t]) keep = false;
@@ -150,115 +558,114 @@ DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<T>& W, in
       wsync();
       for (int t = L.lane; t < nc; t += L.nl) W.c1[t] = W.c0[t];
       wsync();
-      const int nw = scan_excl(L, W.c1, nc);
-      // compact new seeds into (X as z, c2 as d2) to free nz/nd
+      const int nv = scan_excl(L, W.c1, nc);
       for (int t = L.lane; t < nc; t += L.nl)
         if (W.c0[t]) { W.X[W.c1[t]] = W.nz[t]; W.c2[W.c1[t]] = W.nd[t]; }
       wsync();
-      if (nu + nw > P.capD) {
-        if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nu + nw); }
+
+      PHASE(3);
+      // ---- envelope of the previous step minus the dead, into B
+      for (int t = L.lane; t < na; t += L.nl) W.c0[t] = u - Ao[t] <= P.reach[Ad[t]];
+      wsync();
+      for (int t = L.lane; t < na; t += L.nl) W.c1[t] = W.c0[t];
+      wsync();
+      const int nb = scan_excl(L, W.c1, na);
+      for (int t = L.lane; t < na; t += L.nl)
+        if (W.c0[t]) { const int o = W.c1[t]; Bz[o] = Az[t]; Bo[o] = Ao[t]; Bd[o] = Ad[t]; }
+      wsync();
+      na = nb + nv + nw;
+      if (na > P.capA) {
+        if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, na); }
         return;
       }
-      // merge old (uz...) and new (X, c2) seeds by z, old first on ties -> (sz, sj, sd, so)
-      for (int t = L.lane; t < nu; t += L.nl) {
-        const int pos = t + lower_bound(W.X, nw, W.uz[t]);
-        W.sz[pos] = W.uz[t]; W.sj[pos] = W.uj[t]; W.sd[pos] = W.ud[t]; W.so[pos] = W.uo[t];
+      // three-way merge by height into A: previous envelope, then new, then woken on ties
+      for (int t = L.lane; t < nb; t += L.nl) {
+        const Key x = Bz[t];
+        const int pos = t + lower_bound(W.X, nv, x) + lower_bound(W.wz, nw, x);
+        Az[pos] = x; Ao[pos] = Bo[t]; Ad[pos] = Bd[t];
+      }
+      for (int t = L.lane; t < nv; t += L.nl) {
+        const Key x = W.X[t];
+        const int pos = t + upper_bound(Bz, nb, x) + lower_bound(W.wz, nw, x);
+        Az[pos] = x; Ao[pos] = u; Ad[pos] = W.c2[t];
       }
       for (int t = L.lane; t < nw; t += L.nl) {
-        const int pos = t + upper_bound(W.uz, nu, W.X[t]);
-        W.sz[pos] = W.X[t]; W.sj[pos] = j; W.sd[pos] = W.c2[t]; W.so[pos] = SEED_ENV;
-      }
-      ns = nu + nw;
-      wsync();
-      // waiting seeds: re-test against their on-envelope neighbours
-      for (int t = L.lane; t < ns; t += L.nl) W.c0[t] = W.so[t] == SEED_ENV;
-      wsync();
-      scan_last_flag(L, W.c0, W.c1, ns);
-      scan_next_flag(L, W.c0, W.c2, ns);
-      for (int t = L.lane; t < ns; t += L.nl) {
-        int f = W.so[t];
-        if (f == SEED_WAIT) {
-          const int p = W.c1[t];
-          const int n = W.c2[t] < ns ? W.c2[t] : -1;
-          bool perm = false;
-          const bool dom = seed_dominated<T>(W.sz, W.sj, W.sd, j, dir, p, t, n, P.h2, &perm);
-          f = dom ? (perm ? SEED_GONE : SEED_WAIT) : SEED_ENV;
-        }
-        W.c3[t] = f;
+        const Key x = W.wz[t];
+        const int pos = t + upper_bound(Bz, nb, x) + upper_bound(W.X, nv, x);
+        Az[pos] = x; Ao[pos] = W.wo[t]; Ad[pos] = W.wd[t];
       }
       wsync();
-      for (int t = L.lane; t < ns; t += L.nl) W.so[t] = W.c3[t];
-      wsync();
-      // envelope list E: indices of on-envelope seeds, then parity rounds
-      for (int t = L.lane; t < ns; t += L.nl) W.c0[t] = W.so[t] == SEED_ENV;
-      wsync();
-      for (int t = L.lane; t < ns; t += L.nl) W.c1[t] = W.c0[t];
-      wsync();
-      int ne = scan_excl(L, W.c1, ns);
-      for (int t = L.lane; t < ns; t += L.nl)
-        if (W.c0[t]) W.E[W.c1[t]] = t;
-      wsync();
+
+      PHASE(4);
+      // ---- parity rounds: discard or put to sleep every seed its neighbours dominate
       int quiet = 0;
-      for (int round = 0; quiet < 2 && ne > 1; ++round) {
+      PHASE_COUNT(10, na);
+      PHASE_COUNT(11, nr);
+      PHASE_COUNT(12, nsl);
+      PHASE_COUNT(13, 1);
+      for (int round = 0; quiet < 2 && na > 1; ++round) {
         const int parity = round & 1;
         int removed = 0;
-        for (int qq = L.lane; qq < ne; qq += L.nl) {
-          int r = 0;
-          if ((qq & 1) == parity) {
-            const int s = W.E[qq];
-            const int p = qq > 0 ? W.E[qq - 1] : -1;
-            const int n = qq + 1 < ne ? W.E[qq + 1] : -1;
-            bool perm = false;
-            if (seed_dominated<T>(W.sz, W.sj, W.sd, j, dir, p, s, n, P.h2, &perm)) {
-              r = 1;
-              W.so[s] = perm ? SEED_GONE : SEED_WAIT;
-            }
-          }
-          W.c0[qq] = !r;
-          removed |= r;
+        PHASE_COUNT(14, 1);
+        for (int t = L.lane; t < na; t += L.nl) {
+          int fate = FATE_KEEP;
+          if ((t & 1) == parity)
+            fate = seed_fate<Key>(Az, Ao, Ad, t > 0 ? t - 1 : -1, t, t + 1 < na ? t + 1 : -1, u,
+                                  P.h2, P.h2f);
+          W.c0[t] = fate == FATE_KEEP;
+          W.c1[t] = fate != FATE_KEEP && fate != FATE_DROP;
+          W.c4[t] = fate;
+          removed |= fate != FATE_KEEP;
         }
         wsync();
-        removed = w_any(removed);
-        if (!removed) { ++quiet; continue; }
+        if (!w_any(removed)) { ++quiet; continue; }
         quiet = 0;
-        for (int qq = L.lane; qq < ne; qq += L.nl) W.c1[qq] = W.c0[qq];
+        for (int t = L.lane; t < na; t += L.nl) { W.c2[t] = W.c0[t]; W.c3[t] = W.c1[t]; }
         wsync();
-        const int ne2 = scan_excl(L, W.c1, ne);
-        for (int qq = L.lane; qq < ne; qq += L.nl)
-          if (W.c0[qq]) W.c4[W.c1[qq]] = W.E[qq];
+        const int na2 = scan_excl(L, W.c2, na);
+        const int ns2 = scan_excl(L, W.c3, na);
+        if (nsl + ns2 > P.capS) {
+          if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nsl + ns2); }
+          return;
+        }
+        for (int t = L.lane; t < na; t += L.nl) {
+          if (W.c0[t]) { const int o = W.c2[t]; Bz[o] = Az[t]; Bo[o] = Ao[t]; Bd[o] = Ad[t]; }
+          if (W.c1[t]) {
+            const int o = nsl + W.c3[t];
+            const int dead = Ao[t] + P.reach[Ad[t]] + 1;  // first position where it is dead
+            const int wk = W.c4[t] < dead ? W.c4[t] : dead;
+            W.sz[o] = Az[t]; W.so[o] = Ao[t]; W.sd[o] = Ad[t]; W.sw[o] = wk;
+          }
+        }
         wsync();
-        for (int qq = L.lane; qq < ne2; qq += L.nl) W.E[qq] = W.c4[qq];
-        wsync();
-        ne = ne2;
+        nsl += ns2;
+        na = na2;
+        Key* tz = Az; Az = Bz; Bz = tz;
+        int* to = Ao; Ao = Bo; Bo = to;
+        int* td = Ad; Ad = Bd; Bd = td;
       }
-      if (L.lane == 0) note_max(&P.ctr->max_state, ns > nr ? ns : nr);
-#ifdef DEXEL_TRACE
-      if (i == DEXEL_TRACE) {
-        printf("i=%d j=%d dir=%d np=%d nr=%d ns=%d ne=%d\n", i, j, dir, np, nr, ns, ne);
-        for (int t = 0; t < np; ++t) printf("   piece %.6f %.6f dx=%d\n", (double)W.pa[t], (double)W.pb[t], W.pd[t]);
-        for (int t = 0; t < nr; ++t) printf("   rect %.6f %.6f t=%d\n", (double)W.ra[t], (double)W.rb[t], W.rt[t]);
-        for (int t = 0; t < ns; ++t) printf("   seed %.6f js=%d d2=%d flag=%d\n", (double)W.sz[t], W.sj[t], W.sd[t], W.so[t]);
-        for (int t = 0; t < ne; ++t) printf("   env %d\n", W.E[t]);
+      if (L.lane == 0) {
+        int m = nsl > na ? nsl : na;
+        note_max(&P.ctr->max_state, m > nr ? m : nr);
       }
-#endif
+      PHASE(5);
       if (!emit) continue;
 
-      // ---- emission: rectangles (el, er) and envelope disks (hl, hr)
-      for (int t = L.lane; t < nr; t += L.nl) { W.el[t] = (double)W.ra[t]; W.er[t] = (double)W.rb[t]; }
-      for (int qq = L.lane; qq < ne; qq += L.nl) {
-        const int s = W.E[qq];
-        const double w = P.wtab[seed_n<T>(W.sd, W.sj, s, j)];
-        const double zz = (double)W.sz[s];
-        W.xl[qq] = zz - w;
-        W.xr[qq] = zz + w;
+      // ---- emission: rectangles (el, er) and envelope disks
+      for (int t = L.lane; t < nr; t += L.nl) { W.el[t] = ikey(W.ra[t]); W.er[t] = ikey(W.rb[t]); }
+      for (int t = L.lane; t < na; t += L.nl) {
+        const double w = P.wtab[seed_n(Ad[t], Ao[t], u)];
+        const double zz = keyd(Az[t]);
+        W.xl[t] = dkey(zz - w);
+        W.xr[t] = dkey(zz + w);
       }
       wsync();
-      const int nd = union_envelope(L, W.xl, W.xr, ne, W.c0, W.c1, W.hl, W.hr, W.gl, W.gr);
+      const int nd = envelope_runs(L, W.xl, W.xr, na, W.c0, W.c1, W.c2, W.hl, W.hr, W.gl, W.gr);
+      PHASE(6);
       int nm = merge_intervals(L, W.el, W.er, nr, W.hl, W.hr, nd, W.gl, W.gr);
-      const double* srcl = W.gl;
-      const double* srcr = W.gr;
+      const ukey* srcl = W.gl;
+      const ukey* srcr = W.gr;
       if (dir < 0) {
-        // united with the forward result of this column
         const long long fs = W.fstart[j - c0];
         const int nf = W.fcnt[j - c0];
         if (fs < 0) continue;
@@ -268,8 +675,9 @@ DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<T>& W, in
         srcl = W.xl;
         srcr = W.xr;
       }
-      const int no = union_sorted(L, srcl, srcr, nm, W.c0, W.c1, W.hl, W.hr,
-                                  dir < 0 ? W.gl : W.el);
+      const int no = union_runs(L, srcl, srcr, nm, true, W.c0, W.c1, W.hl, W.hr,
+                                dir < 0 ? W.gl : W.el, nullptr);
+      PHASE(7);
       if (dir > 0) {
         const long long s = arena_take(L, &P.ctr->arena_top[2], P.blk, curF, no);
         const bool fits = s + no <= P.f_cap;
