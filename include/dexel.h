@@ -132,6 +132,23 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
                                   dexel_grid_out* outs, void* ws, size_t ws_bytes,
                                   int32_t* d_status, void* stream);
 
+/* Allocation-free dilation or erosion for small grids (the paper has no counterpart; this is
+ * a deployment variant).  For callers that cannot allocate device memory when they need an
+ * offset -- an application whose own pool owns the GPU's memory, a real-time loop that must
+ * not pay cudaMalloc's implicit synchronisation, code running where allocation is
+ * forbidden.  It runs the same kernels as dexel_dilate / dexel_erode, but every byte of
+ * scratch comes from one static 64 MiB device array inside the library, held by every GPU
+ * that loads it until the process exits; nothing is allocated or freed (no ctx either).
+ *   in, out : as for dexel_dilate (device buffers owned by the caller; out->nseg written).
+ *   op      : DEXEL_DILATE or DEXEL_ERODE.
+ * Limits: nx*ny <= 65536 and k <= 32; beyond them, or when the data need more scratch than
+ * the array holds, the call returns DEXEL_ERR_CAPACITY and writes no partial CSR.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (other streams or threads) race.  The call synchronises `stream`. */
+dexel_status dexel_offset_noalloc(const dexel_grid_in* in, double k, dexel_op op, dexel_mode mode,
+                                  dexel_grid_out* out, void* stream);
+
 /* Static description of a status code. */
 const char* dexel_status_string(dexel_status s);
 

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "../../include/dexel.h"
@@ -567,6 +568,168 @@ dexel_status offset(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erod
 
 }  // namespace
 
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free offset for small grids
+//
+// Some callers cannot allocate device memory at the moment they need an offset: a host
+// application that owns every byte of the GPU through its own pool, a real-time loop that
+// must not pay cudaMalloc's implicit synchronisation, or code running where allocation is
+// forbidden.  dexel_offset_noalloc serves them: it runs the same kernels as dexel_dilate /
+// dexel_erode with all of their scratch (counters, tables, indices, arenas, per-warp sweep
+// state) carved from one file-scope static device array.  Every GPU that loads the library
+// holds that array until the process exits.  All calls on a device share it, so calls that
+// overlap on the GPU (different streams or threads) race; the counters that must start at
+// zero are cleared at the start of every call.
+// ------------------------------------------------------------------------------------------
+constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // 64 MiB per device
+constexpr long long kNoAllocMaxColumns = 256 * 256;
+constexpr double kNoAllocMaxK = 32.0;
+constexpr int kNoAllocWarps = 8;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+std::mutex g_noalloc_lock;
+void* g_noalloc_ptr[256] = {};
+
+// Device address of the static scratch on the current device, looked up once per device.
+dexel_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return DEXEL_ERR_CUDA;
+  std::lock_guard<std::mutex> g(g_noalloc_lock);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return DEXEL_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return DEXEL_OK;
+}
+
+template <typename T>
+dexel_status noalloc_offset(const dexel_grid_in* in, double k, bool erode, dexel_grid_out* out,
+                            cudaStream_t st) {
+  typedef typename H<T>::K Key;
+  void* base = nullptr;
+  dexel_status s = noalloc_scratch(&base);
+  if (s != DEXEL_OK) return s;
+  const int nx = in->nx, ny = in->ny;
+  const long long ncols = (long long)nx * ny;
+  const double kk = k * k;
+  const int K = reach_of(kk);
+  const int nmax = (int)std::floor(kk);
+  Carver C{(char*)base, kNoAllocBytes};
+  Counters* ctr = (Counters*)C.take(sizeof(Counters));
+  double* wtab = (double*)C.take(sizeof(double) * (nmax + 2));
+  int* reach = (int*)C.take(sizeof(int) * (K + 2));
+  long long* mstart = (long long*)C.take(sizeof(long long) * ncols);
+  int* mcnt = (int*)C.take(sizeof(int) * ncols);
+  long long* ostart = (long long*)C.take(sizeof(long long) * ncols);
+  int* ocnt = (int*)C.take(sizeof(int) * ncols);
+  long long* cnt = (long long*)C.take(sizeof(long long) * (ncols + 1));
+  long long* pos = (long long*)C.take(sizeof(long long) * (ncols + 1));
+  long long* sums = (long long*)C.take(sizeof(long long) * ((ncols + kScanTile) / kScanTile + 2));
+  if (!C.ok) return DEXEL_ERR_CAPACITY;
+  CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+  const int thr = 256;
+  k_validate<T><<<(unsigned)((ncols + thr - 1) / thr), thr, 0, st>>>((int)ncols, in->col_off,
+                                                                    (const T*)in->z, in->nseg, ctr);
+  k_tables<<<(std::max(nmax, K) + 1 + 255) / 256, 256, 0, st>>>(kk, in->h, nmax, K, wtab, reach);
+  CK(cudaGetLastError());
+  Counters hc;
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hc.status & ST_BAD_CSR) return DEXEL_ERR_BAD_CSR;
+
+  // per-warp state for pass 1, then pass 2 (the same region), then the arenas
+  const int capS = hc.max_segs_in + 2;
+  const int capF = 2 * (K + 1) * capS + 8;
+  const int chunk1 = nx, chunk2 = ny;  // one work item per line
+  const size_t slot_region = (size_t)12 << 20;
+  const long long sb1 = p1_slot_bytes<Key>(capF, capS, chunk1);
+  if ((long long)slot_region < sb1 * kWarpsPerBlock) return DEXEL_ERR_CAPACITY;
+  char* slots = (char*)C.take(slot_region);
+  const size_t rest = C.cap > C.used + 4096 ? C.cap - align_up(C.used, 256) - 4096 : 0;
+  const size_t bF = align_up(rest / 100 * 30, 256), bM = align_up(rest / 100 * 45, 256);
+  const size_t bO = align_up(rest / 100 * 20, 256);
+  char* aF = (char*)C.take(bF);
+  char* aM = (char*)C.take(bM);
+  char* aO = (char*)C.take(bO);
+  if (!C.ok || !slots || !aF || !aM || !aO) return DEXEL_ERR_CAPACITY;
+
+  P1Params<T> p1{};
+  p1.nx = nx; p1.ny = ny; p1.K = K; p1.erode = erode ? 1 : 0;
+  p1.chunk = chunk1; p1.nchunks = 1;
+  p1.col_off = in->col_off; p1.z = (const T*)in->z;
+  const long long capF1 = (long long)(bF / (2 * sizeof(Key) + 2));
+  p1.f_a = (Key*)aF; p1.f_b = (Key*)aF + capF1; p1.f_l = (short*)((Key*)aF + 2 * capF1);
+  p1.f_cap = capF1;
+  const long long capM = (long long)(bM / (2 * sizeof(Key) + 2));
+  p1.m_a = (Key*)aM; p1.m_b = (Key*)aM + capM; p1.m_l = (short*)((Key*)aM + 2 * capM);
+  p1.m_cap = capM;
+  p1.m_start = mstart; p1.m_cnt = mcnt;
+  p1.blk = 64;
+  p1.ctr = ctr;
+  p1.slots = slots; p1.slot_bytes = sb1;
+  p1.capF = capF; p1.capS = capS;
+  const int nw1 = (int)std::min<long long>(kNoAllocWarps, (long long)(slot_region / sb1));
+  CK(launch_pass1<T>(p1, nw1 / kWarpsPerBlock, st));
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hc.status & (ST_OVERFLOW_SLOT | ST_OVERFLOW_ARENA)) return DEXEL_ERR_CAPACITY;
+
+  P2Params<T> p2{};
+  p2.nx = nx; p2.ny = ny; p2.R = K; p2.kk = kk; p2.h2 = in->h * in->h;
+  p2.h2f = (float)p2.h2;
+  p2.chunk = chunk2; p2.nchunks = 1;
+  p2.wtab = wtab; p2.reach = reach;
+  p2.m_a = p1.m_a; p2.m_b = p1.m_b; p2.m_l = p1.m_l;
+  p2.m_start = mstart; p2.m_cnt = mcnt;
+  const long long capF2 = (long long)(bF / 16);
+  p2.f_l = (ukey*)aF; p2.f_r = (ukey*)aF + capF2; p2.f_cap = capF2;
+  const long long capO = (long long)(bO / 16);
+  p2.o_l = (ukey*)aO; p2.o_r = (ukey*)aO + capO; p2.o_cap = capO;
+  p2.o_start = ostart; p2.o_cnt = ocnt;
+  p2.blk = 64;
+  p2.ctr = ctr;
+  p2.capP = std::max(hc.max_pieces, 1) + 2;
+  p2.capR = 1024; p2.capA = 1024; p2.capS = 4096;
+  const long long sb2 = p2_slot_bytes<Key>(p2.capP, p2.capR, p2.capA, p2.capS, chunk2);
+  if ((long long)slot_region < sb2 * kWarpsPerBlock) return DEXEL_ERR_CAPACITY;
+  p2.slots = slots; p2.slot_bytes = sb2;
+  const int nw2 = (int)std::min<long long>(kNoAllocWarps, (long long)(slot_region / sb2));
+  CK(launch_pass2<T>(p2, nw2 / kWarpsPerBlock, st));
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hc.status & (ST_OVERFLOW_SLOT | ST_OVERFLOW_ARENA)) return DEXEL_ERR_CAPACITY;
+
+  const unsigned gb = (unsigned)((ncols + thr - 1) / thr);
+  k_count<T><<<gb, thr, 0, st>>>((int)ncols, ostart, ocnt, p2.o_l, p2.o_r, erode ? 1 : 0, cnt);
+  const long long nb = (ncols + kScanTile - 1) / kScanTile;
+  k_scan1<<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, cnt, pos, sums);
+  k_scan2<<<1, kScanThreads, 0, st>>>(nb, sums);
+  k_scan3<<<(unsigned)((ncols + 1 + thr - 1) / thr), thr, 0, st>>>(ncols, pos, sums, out->col_off, ctr);
+  CK(cudaGetLastError());
+  long long total_out = 0;
+  CK(cudaMemcpyAsync(&total_out, sums + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  out->nseg = total_out;
+  if ((hc.status & ST_TOO_MANY_OUT) || total_out > out->capacity_seg) return DEXEL_ERR_CAPACITY;
+  k_write<T><<<gb, thr, 0, st>>>((int)ncols, ostart, ocnt, p2.o_l, p2.o_r, erode ? 1 : 0, pos,
+                                 (T*)out->z);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return DEXEL_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
@@ -749,6 +912,21 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
       return DEXEL_ERR_CUDA;
   }
   return first;
+}
+
+dexel_status dexel_offset_noalloc(const dexel_grid_in* in, double k, dexel_op op, dexel_mode mode,
+                                  dexel_grid_out* out, void* stream) {
+  if (!out || !out->col_off || (out->capacity_seg > 0 && !out->z) || out->capacity_seg < 0)
+    return DEXEL_ERR_INVALID_ARG;
+  if (op != DEXEL_DILATE && op != DEXEL_ERODE) return DEXEL_ERR_INVALID_ARG;
+  if (mode != DEXEL_FP64 && mode != DEXEL_FP32_PRED64) return DEXEL_ERR_INVALID_ARG;
+  const dexel_status s = check_in(in, k);
+  if (s != DEXEL_OK) return s;
+  if ((long long)in->nx * in->ny > kNoAllocMaxColumns || k > kNoAllocMaxK) return DEXEL_ERR_CAPACITY;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool erode = op == DEXEL_ERODE;
+  if (mode == DEXEL_FP64) return noalloc_offset<double>(in, k, erode, out, st);
+  return noalloc_offset<float>(in, k, erode, out, st);
 }
 
 const char* dexel_status_string(dexel_status s) {
