@@ -188,7 +188,7 @@ def run_ours(args, rank, ws):
     ms_step = allmax(sum(times) / len(times), ws, device="cuda")
     value = units * ws / (ms_step / 1e3)
 
-    # roofline of the dominant stage (pass 2: the y power-diagram sweep), per launch
+    # roofline of the dominant stage (pass 2: the y dilation), per launch
     s_bytes = 8
     p2_ms = [r[2][2] for r in rec]
     p1_ms = [r[2][1] for r in rec]
@@ -237,13 +237,13 @@ def run_ours(args, rank, ws):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_pass2 (y power-diagram sweep)",
+                     "kernel": "k_pass2r (y dilation with per-piece radius, window gather)",
                      "peak_source": peak_kind},
         "stage_ms_per_step": {"validate+tables": stages[0] / args.steps,
                               "pass1": stages[1] / args.steps, "pass2": stages[2] / args.steps,
                               "count+scan": stages[3] / args.steps, "write": stages[4] / args.steps},
         "stats": {f"{op}_k{int(k)}": {"mid_pieces": st[1], "out_segs": st[3],
-                                      "max_pieces_col": st[4], "max_state": st[5]}
+                                      "max_pieces_col": st[4], "redo_cols": st[5]}
                   for (op, k, _, st) in rec[: len(OPS) * len(RADII)]},
         "wall_s_timed": t_wall,
     }
@@ -329,7 +329,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-case", action="store_true",
-                    help="run one dilation (k=8) of the workload and exit (for ncu captures)")
+                    help="run one offset of the workload and exit (for ncu captures)")
+    ap.add_argument("--profile-k", type=float, default=8.0)
+    ap.add_argument("--profile-op", choices=["dilate", "erode"], default="dilate")
     args = ap.parse_args()
     rank, ws = dist_init(args)
     if args.profile_case:
@@ -337,7 +339,7 @@ def main():
         import paper_1804_08968_gb300 as dx
         g = workload()
         grid = dx.Grid.from_synth(g, dtype=torch.float64)
-        dx.dilate(grid, 8.0)
+        (dx.dilate if args.profile_op == "dilate" else dx.erode)(grid, args.profile_k)
         torch.cuda.synchronize()
         return
     if args.impl == "reference":

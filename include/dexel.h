@@ -158,16 +158,17 @@ int64_t dexel_last_launches(const dexel_ctx* ctx);
 /* Turn per-stage timing on or off (off by default).  When on, each call brackets its
  * stages with CUDA events on the call's stream; dexel_last_stage_ms then reports the
  * device time of each stage of the last call (summed over both offsets of a closing or
- * opening): [0] validation + tables, [1] pass 1 (x-extrusion sweep), [2] pass 2 (y power
- * sweep), [3] output count + scan, [4] output write.  Returns the number of entries written
+ * opening): [0] validation + tables, [1] pass 1 (x-extrusion sweep), [2] pass 2 (y dilation
+ * with per-piece radius), [3] output count + scan, [4] output write.  Returns the number of entries written
  * (at most max). */
 void dexel_set_profiling(dexel_ctx* ctx, int on);
 int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max);
 
 /* Sizes seen by the last call (summed over both offsets of a closing or opening):
  * [0] input segments, [1] S_mid pieces (pass-1 output), [2] pass-2 intervals before the final
- * complement/rounding, [3] output segments, [4] max pieces in one S_mid column, [5] max live
- * elements in one sweep state, [6] device status bits of the last attempt (1: a per-warp
+ * complement/rounding, [3] output segments, [4] max pieces in one S_mid column, [5] window
+ * gather: output columns redone by the shared-memory fallback kernel; per-line sweep: max
+ * live elements in one sweep state, [6] device status bits of the last attempt (1: a per-warp
  * state array overflowed, 2: an arena overflowed, 4: malformed CSR, 8: output beyond int32
  * offsets), [7] attempts the last offset needed (the library grows its scratch and retries
  * when it owns the workspace).  Returns the number of entries written (at most max). */

@@ -165,7 +165,8 @@ class Context:
 
     def stats(self):
         """[input segments, S_mid pieces, pass-2 intervals, output segments, max pieces per
-        S_mid column, max live sweep state] of the last call."""
+        S_mid column, columns redone by the fallback gather (sweep: max live state), status
+        bits, attempts] of the last call."""
         a = (ctypes.c_int64 * 8)()
         n = lib().dexel_last_stats(self.ptr, a, 8)
         return [int(a[i]) for i in range(n)]

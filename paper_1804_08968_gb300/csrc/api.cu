@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <mutex>
@@ -29,6 +30,11 @@ struct dexel_ctx {
   long long launches = 0;
   // capacities learnt from earlier calls (grown on overflow)
   int capA = 1024, capR = 1024, capS = 4096;
+  bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
+  char gather = 'r';    // first gather kernel: 'r' register stacks, 'g' staged shared-memory stacks
+  int stcap = 16;       // gather: stack entries per lane (shared-memory fallback kernel)
+  int rcap = 0;         // gather: intervals per column bucket of the register-stack kernel
+  int bcap = 0;         // gather: intervals per output column (0 = derive from the radius)
   long long needF = 0, needM = 0, needO = 0;  // arena entries
   Counters host_ctr{};
   // optional per-stage timing with CUDA events on the call's stream
@@ -75,9 +81,13 @@ __global__ void k_validate(int ncols, const int* off, const T* z, long long nseg
   if (bad) atomicOr(&ctr->status, ST_BAD_CSR);
 }
 
-__global__ void k_tables(double kk, double h, int nmax, int K, double* wtab, int* reach) {
+__global__ void k_tables(double kk, double h, int nmax, int K, double* wtab, int* reach,
+                         float* wtabf) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n <= nmax) wtab[n] = h * sqrt(kk - (double)n);  // half-width h sqrt(k^2 - n)
+  if (n <= nmax) {
+    wtab[n] = h * sqrt(kk - (double)n);  // half-width h sqrt(k^2 - n)
+    if (wtabf) wtabf[n] = (float)wtab[n];
+  }
   if (n <= K) {
     // largest dy with n + dy^2 <= k^2 for n = dx^2
     const long long d2 = (long long)n * n;
@@ -299,11 +309,13 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
   for (int attempt = 0; attempt < 24; ++attempt) {
     // ---------------- plan
     // phase A: counters, tables, indices, validation
+    void* pwtabf = nullptr;
     auto plan = [&](Carver& C, void** pctr, void** pwtab, void** preach, void** pmstart,
                     void** pmcnt, void** postart, void** pocnt, void** pcnt, void** ppos,
                     void** psums) {
       *pctr = C.take(sizeof(Counters));
       *pwtab = C.take(sizeof(double) * (nmax + 2));
+      pwtabf = C.take(sizeof(float) * (nmax + 2));
       *preach = C.take(sizeof(int) * (K + 2));
       *pmstart = C.take(sizeof(long long) * ncols);
       *pmcnt = C.take(sizeof(int) * ncols);
@@ -340,8 +352,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       k_validate<T><<<(unsigned)((ncols + thr - 1) / thr), thr, 0, st>>>(
           (int)ncols, in->col_off, (const T*)in->z, in->nseg, ctr);
       ++ctx->launches;
-      k_tables<<<(std::max(nmax, K) + 1 + 255) / 256, 256, 0, st>>>(kk, in->h, nmax, K,
-                                                                    (double*)pwtab, (int*)preach);
+      k_tables<<<(std::max(nmax, K) + 1 + 255) / 256, 256, 0, st>>>(
+          kk, in->h, nmax, K, (double*)pwtab, (int*)preach, (float*)pwtabf);
       ++ctx->launches;
       CK(cudaGetLastError());
     }
@@ -435,7 +447,107 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       continue;
     }
 
-    // ---------------- pass 2
+    // ---------------- pass 2: window gather (default) or per-line sweep
+    bool use_sweep = ctx->sweep2;
+    P2GParams<T> pg{};
+    long long smem_b = 0;
+    if (!use_sweep) {
+      pg.nx = nx; pg.ny = ny; pg.R = K; pg.kk = kk;
+      pg.wtab = (const double*)pwtab; pg.wtabf = (const float*)pwtabf; pg.reach = (const int*)preach;
+      pg.m_a = p1.m_a; pg.m_b = p1.m_b; pg.m_l = p1.m_l;
+      pg.m_start = p1.m_start; pg.m_cnt = p1.m_cnt;
+      const long long capO = (long long)(bO / 16);
+      pg.o_l = (ukey*)aO; pg.o_r = (ukey*)aO + capO; pg.o_cap = capO;
+      pg.o_start = (long long*)postart; pg.o_cnt = (int*)pocnt;
+      pg.blk = 256;
+      pg.ctr = ctr;
+      if (ctx->bcap < 2 * (2 * K + 1)) {
+        int b = 64;
+        while (b < 2 * (2 * K + 1)) b <<= 1;
+        ctx->bcap = b;
+      }
+      pg.stcap = ctx->stcap;
+      pg.bcap = ctx->bcap;
+      pg.warps_per_block = 8;
+      // staging area: what remains of ~200 KB after the warps' scratch; the tile is the
+      // largest whose window of pieces is expected to fit
+      const long long wbytes = pass2g_smem(pg.warps_per_block, pg.stcap, pg.bcap, 1, K, 0);
+      const long long room = (200LL << 10) - wbytes - 4096;
+      pg.stage_cap = room > 0 ? (int)std::min<long long>(room / 9, 1 << 20) : 0;
+      const double per_col = (double)hc.mid_total / (double)std::max<long long>(ncols, 1);
+      pg.tile = 64;
+      while (pg.tile > 8 && (pg.tile + 2.0 * K + 1) * per_col * 1.3 > pg.stage_cap) pg.tile >>= 1;
+      // fallback kernel geometry: shrink the staging area, then the warps, until it fits
+      smem_b = pass2g_smem(pg.warps_per_block, pg.stcap, pg.bcap, pg.tile, K, pg.stage_cap);
+      while (smem_b > (220LL << 10) && pg.warps_per_block > 1) {
+        pg.stage_cap = 0;
+        pg.warps_per_block >>= 1;
+        smem_b = pass2g_smem(pg.warps_per_block, pg.stcap, pg.bcap, pg.tile, K, pg.stage_cap);
+      }
+      if (smem_b > (220LL << 10)) use_sweep = true;  // windows too crowded for the gather
+    }
+    if (!use_sweep) {
+      const int per_sm = (int)std::max<long long>(1, (220LL << 10) / smem_b);
+      const int gblocks = sms * per_sm;
+      // first the register-stack kernel; the columns that need a deeper stack or a larger
+      // bucket are marked and redone by the shared-memory kernel
+      const int W = 2 * K + 1;
+      const int G = W <= 16 ? 32 / W : 1;
+      if (ctx->rcap < 2 * W) {
+        int b = 64;
+        while (b < 2 * W) b <<= 1;
+        ctx->rcap = b;
+      }
+      while (ctx->rcap > 64 && pass2r_smem(4, G, ctx->rcap) > (110LL << 10)) ctx->rcap >>= 1;
+      mark(ctx, 4, st);
+      int redo = 0;
+      if (ctx->gather == 'r') {
+        P2GParams<T> pr = pg;
+        pr.bcap = ctx->rcap;
+        const long long rsm = pass2r_smem(4, G, pr.bcap);
+        const int rblocks = sms * (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / rsm));
+        CK(launch_pass2r<T>(pr, G, rblocks, st));
+        ++ctx->launches;
+        CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
+          redo = hc.redo_cols;
+          if (hc.max_state > ctx->rcap) {  // next call: a bucket as large as the columns needed
+            int b = ctx->rcap;
+            while (b < hc.max_state) b <<= 1;
+            if (pass2r_smem(4, G, b) <= (110LL << 10)) ctx->rcap = b;
+          }
+          CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+          pg.redo = 1;
+          CK(launch_pass2g<T>(pg, gblocks, st));
+          ++ctx->launches;
+          CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+        }
+      } else {
+        CK(launch_pass2g<T>(pg, gblocks, st));
+        ++ctx->launches;
+        CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+      }
+      ctx->stats[5] = redo;
+      mark(ctx, 5, st);
+      ctx->needO = std::max<long long>(ctx->needO, (long long)hc.arena_top[3]);
+      ctx->stats[6] = hc.status;
+      ctx->stats[7] = attempt + 1;
+      if (hc.status & ST_OVERFLOW_ARENA) {
+        ctx->last_required = total + (size_t)hc.arena_top[3] * 16;
+        if (ws_user) return DEXEL_ERR_CAPACITY;
+        continue;
+      }
+      if (hc.status & ST_OVERFLOW_SLOT) {  // the shared-memory kernel's stacks or bucket
+        ctx->stcap *= 2;
+        ctx->bcap *= 2;
+        if (ws_user) return DEXEL_ERR_CAPACITY;
+        continue;
+      }
+    }
+    if (use_sweep) {
     const int capP = std::max(hc.max_pieces, 1) + 2;
     const int items2_target = nwarps * 2;
     int nch2 = std::max(1, std::min(ny, (items2_target + nx - 1) / nx));
@@ -491,13 +603,17 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       if (ws_user) return DEXEL_ERR_CAPACITY;
       continue;
     }
+    }  // pass 2 variants
 
     // ---------------- compaction into the caller's CSR
     const int thr = 256;
     const unsigned gb = (unsigned)((ncols + thr - 1) / thr);
     mark(ctx, 6, st);
+    const long long capOut = (long long)(bO / 16);
+    const ukey* out_l = (const ukey*)aO;
+    const ukey* out_r = (const ukey*)aO + capOut;
     k_count<T><<<gb, thr, 0, st>>>((int)ncols, (const long long*)postart, (const int*)pocnt,
-                                   p2.o_l, p2.o_r, erode ? 1 : 0, (long long*)pcnt);
+                                   out_l, out_r, erode ? 1 : 0, (long long*)pcnt);
     const long long nb = (ncols + kScanTile - 1) / kScanTile;
     k_scan1<<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, (const long long*)pcnt, (long long*)ppos,
                                                   (long long*)psums);
@@ -518,7 +634,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     if (total_out > out->capacity_seg) return DEXEL_ERR_CAPACITY;
     mark(ctx, 8, st);
     k_write<T><<<gb, thr, 0, st>>>((int)ncols, (const long long*)postart, (const int*)pocnt,
-                                   p2.o_l, p2.o_r, erode ? 1 : 0, (const long long*)ppos,
+                                   out_l, out_r, erode ? 1 : 0, (const long long*)ppos,
                                    (T*)out->z);
     ++ctx->launches;
     CK(cudaGetLastError());
@@ -639,7 +755,8 @@ dexel_status noalloc_offset(const dexel_grid_in* in, double k, bool erode, dexel
   const int thr = 256;
   k_validate<T><<<(unsigned)((ncols + thr - 1) / thr), thr, 0, st>>>((int)ncols, in->col_off,
                                                                     (const T*)in->z, in->nseg, ctr);
-  k_tables<<<(std::max(nmax, K) + 1 + 255) / 256, 256, 0, st>>>(kk, in->h, nmax, K, wtab, reach);
+  k_tables<<<(std::max(nmax, K) + 1 + 255) / 256, 256, 0, st>>>(kk, in->h, nmax, K, wtab, reach,
+                                                                nullptr);
   CK(cudaGetLastError());
   Counters hc;
   CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
@@ -744,6 +861,9 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   if (!c) return DEXEL_ERR_NOMEM;
   c->device = device;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  const char* mode = getenv("DEXEL_PASS2");
+  c->sweep2 = mode && strcmp(mode, "sweep") == 0;
+  if (mode && strcmp(mode, "g") == 0) c->gather = 'g';
   *ctx = c;
   return DEXEL_OK;
 }

@@ -45,7 +45,7 @@ struct Counters {
   int max_out;        // max intervals of an output column
   int max_state;      // max live elements seen in a slot array (for resizing)
   int max_segs_in;    // max input segments per column
-  int pad;
+  int redo_cols;      // gather: output columns handed to the fallback kernel
   unsigned long long mid_total;   // S_mid pieces written
   unsigned long long out_total;   // pass-2 intervals written
   unsigned long long phase[16];   // optional per-phase clock totals (DEXEL_PHASES builds)

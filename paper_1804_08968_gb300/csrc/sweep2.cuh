@@ -67,10 +67,11 @@ struct P2Slot {
   Key *az, *bz; int *ao, *ad, *bo, *bd;  // envelope seeds (two buffers): height, order, dx
   Key* nz; int* nd;                      // new seeds of the column
   Key* wz; int *wo, *wd;                 // woken seeds
-  Key* sz; int *so, *sd, *sw;            // sleeping seeds: height, order, dx, wake-up position
+  Key* sz; int *so, *sd, *sw;            // sleeping seeds due soon: height, order, dx, wake-up
+  Key* fz; int *fo, *fd, *fw;            // sleeping seeds due later (scanned every kFarEvery steps)
   ukey *el, *er, *gl, *gr, *hl, *hr, *xl, *xr;  // interval scratch
   Key* X;
-  int *c0, *c1, *c2, *c3, *c4, *c5;
+  int *c0, *c1, *c2, *c3, *c4, *c5, *E;
   long long* fstart;
   int* fcnt;
 };
@@ -92,10 +93,10 @@ DXI long long p2_slot_bytes(int capP, int capR, int capA, int capS, int chunk) {
   long long b = 0;
   b += (long long)chunk * (sizeof(long long) + sizeof(int)) + 64;
   b += 8LL * ce * sizeof(ukey);
-  b += 5LL * ce * sizeof(Key) + 8LL * ce * sizeof(int);
+  b += 5LL * ce * sizeof(Key) + 9LL * ce * sizeof(int);
   b += 6LL * capP * sizeof(Key) + 4LL * capP * sizeof(int);
   b += 3LL * capA * sizeof(Key) + 6LL * capA * sizeof(int);
-  b += (long long)capS * sizeof(Key) + 3LL * capS * sizeof(int);
+  b += 2LL * capS * sizeof(Key) + 6LL * capS * sizeof(int);
   return (b + 4096 + 255) & ~255LL;
 }
 
@@ -117,6 +118,7 @@ DXI P2Slot<Key> p2_slot(char* base, int capP, int capR, int capA, int capS, int 
   Key** ka[] = {&s.az, &s.bz, &s.wz};
   for (Key** q : ka) { *q = (Key*)p; p += (long long)capA * sizeof(Key); }
   s.sz = (Key*)p; p += (long long)capS * sizeof(Key);
+  s.fz = (Key*)p; p += (long long)capS * sizeof(Key);
   p = (char*)(((unsigned long long)p + 15) & ~15ULL);
   s.pd = (int*)p; p += (long long)capP * sizeof(int);
   s.nt = (int*)p; p += (long long)capP * sizeof(int);
@@ -125,9 +127,9 @@ DXI P2Slot<Key> p2_slot(char* base, int capP, int capR, int capA, int capS, int 
   s.qt = (int*)p; p += ce * sizeof(int);
   int** ia[] = {&s.ao, &s.ad, &s.bo, &s.bd, &s.wo, &s.wd};
   for (int** q : ia) { *q = (int*)p; p += (long long)capA * sizeof(int); }
-  int** is[] = {&s.so, &s.sd, &s.sw};
+  int** is[] = {&s.so, &s.sd, &s.sw, &s.fo, &s.fd, &s.fw};
   for (int** q : is) { *q = (int*)p; p += (long long)capS * sizeof(int); }
-  int** ie[] = {&s.c0, &s.c1, &s.c2, &s.c3, &s.c4, &s.c5};
+  int** ie[] = {&s.c0, &s.c1, &s.c2, &s.c3, &s.c4, &s.c5, &s.E};
   for (int** q : ie) { *q = (int*)p; p += ce * sizeof(int); }
   s.fcnt = (int*)p;
   return s;
@@ -164,6 +166,7 @@ DXI double keyd(float k) { return (double)k; }
 DXI double keyd(ukey k) { return dval(k); }
 
 constexpr int FATE_KEEP = -1;
+constexpr int kFarEvery = 16;  // the far sleeper pool is scanned once per this many steps
 constexpr int FATE_DROP = 0x7fffffff;
 
 DXI int seed_n(int dx, int o, int u) { return dx * dx + (u - o) * (u - o); }
@@ -427,7 +430,9 @@ DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<typename 
   for (int dir = 1; dir >= -1; dir -= 2) {
     int nr = 0;   // rectangles
     int na = 0;   // envelope seeds
-    int nsl = 0;  // sleeping seeds
+    int nsl = 0;  // sleeping seeds due soon
+    int nfar = 0;  // sleeping seeds due later
+    int next_far = 0;  // position of the next scan of the far pool
     Key* Az = W.az; int* Ao = W.ao; int* Ad = W.ad;  // envelope (current buffer)
     Key* Bz = W.bz; int* Bo = W.bo; int* Bd = W.bd;  // other buffer
     const int jb = dir > 0 ? (c0 - R > 0 ? c0 - R : 0) : (c1 - 1 + R < N - 1 ? c1 - 1 + R : N - 1);
@@ -483,6 +488,46 @@ DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<typename 
       }
 
       PHASE(1);
+      // ---- far sleepers due within the next kFarEvery steps move to the near pool
+      if (u >= next_far) {
+        next_far = u + kFarEvery;
+        int any = 0;
+        for (int t = L.lane; t < nfar; t += L.nl) any |= W.fw[t] < next_far;
+        if (w_any(any)) {
+          for (int t = L.lane; t < nfar; t += L.nl) {
+            const bool mv = W.fw[t] < next_far;
+            W.c0[t] = !mv;
+            W.c1[t] = mv;
+          }
+          wsync();
+          for (int t = L.lane; t < nfar; t += L.nl) { W.c2[t] = W.c0[t]; W.c3[t] = W.c1[t]; }
+          wsync();
+          const int keep = scan_excl(L, W.c2, nfar);
+          const int mv = scan_excl(L, W.c3, nfar);
+          if (nsl + mv > P.capS) {
+            if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nsl + mv); }
+            return;
+          }
+          for (int t = L.lane; t < nfar; t += L.nl)
+            if (W.c1[t]) {
+              const int o = nsl + W.c3[t];
+              W.sz[o] = W.fz[t]; W.so[o] = W.fo[t]; W.sd[o] = W.fd[t]; W.sw[o] = W.fw[t];
+            }
+          wsync();
+          for (int base = 0; base < nfar; base += L.nl) {
+            const int t = base + L.lane;
+            Key z0 = Key();
+            int o0 = 0, d0 = 0, w0 = 0, dst = -1;
+            if (t < nfar && W.c0[t]) { z0 = W.fz[t]; o0 = W.fo[t]; d0 = W.fd[t]; w0 = W.fw[t]; dst = W.c2[t]; }
+            wsync();
+            if (dst >= 0) { W.fz[dst] = z0; W.fo[dst] = o0; W.fd[dst] = d0; W.fw[dst] = w0; }
+            wsync();
+          }
+          nsl += mv;
+          nfar = keep;
+        }
+      }
+
       // ---- sleeping seeds due now: wake the live ones, drop the dead ones
       int nw = 0;
       {
@@ -597,55 +642,103 @@ DXN void pass2_item(const Lanes& L, const P2Params<T>& P, const P2Slot<typename 
       wsync();
 
       PHASE(4);
-      // ---- parity rounds: discard or put to sleep every seed its neighbours dominate
-      int quiet = 0;
+      // ---- lower envelope of the merged seeds: one monotone-stack pass (lane 0); a seed
+      //      popped because the seed below it and the incoming one dominate it is discarded
+      //      or put to sleep according to seed_fate
       PHASE_COUNT(10, na);
       PHASE_COUNT(11, nr);
       PHASE_COUNT(12, nsl);
       PHASE_COUNT(13, 1);
-      for (int round = 0; quiet < 2 && na > 1; ++round) {
-        const int parity = round & 1;
-        int removed = 0;
-        PHASE_COUNT(14, 1);
+      if (L.lane == 0) {
+        int* stk = W.c5;
+        int top = -1;
+        for (int t = 0; t < na; ++t) {
+          bool pushed = true;
+          while (top >= 0) {
+            const int s = stk[top];
+            if (Az[s] == Az[t]) {
+              const int nS = seed_n(Ad[s], Ao[s], u), nT = seed_n(Ad[t], Ao[t], u);
+              if (nS <= nT) {  // the incoming seed is dominated by the stack top
+                W.c4[t] = equal_fate(Ao[s], nS, Ao[t], nT, u);
+                pushed = false;
+                break;
+              }
+              W.c4[s] = equal_fate(Ao[t], nT, Ao[s], nS, u);
+              --top;
+              continue;
+            }
+            if (top == 0) break;
+            const int f = seed_fate<Key>(Az, Ao, Ad, stk[top - 1], s, t, u, P.h2, P.h2f);
+            if (f == FATE_KEEP) break;
+            W.c4[s] = f;
+            --top;
+          }
+          if (pushed) {
+            stk[++top] = t;
+            W.c4[t] = FATE_KEEP;
+          }
+        }
+      }
+      wsync();
+      {
         for (int t = L.lane; t < na; t += L.nl) {
-          int fate = FATE_KEEP;
-          if ((t & 1) == parity)
-            fate = seed_fate<Key>(Az, Ao, Ad, t > 0 ? t - 1 : -1, t, t + 1 < na ? t + 1 : -1, u,
-                                  P.h2, P.h2f);
+          const int fate = W.c4[t];
           W.c0[t] = fate == FATE_KEEP;
           W.c1[t] = fate != FATE_KEEP && fate != FATE_DROP;
-          W.c4[t] = fate;
-          removed |= fate != FATE_KEEP;
         }
         wsync();
-        if (!w_any(removed)) { ++quiet; continue; }
-        quiet = 0;
         for (int t = L.lane; t < na; t += L.nl) { W.c2[t] = W.c0[t]; W.c3[t] = W.c1[t]; }
+        wsync();
+        // sleepers split by wake-up: before the next far scan -> near pool, else far pool
+        for (int t = L.lane; t < na; t += L.nl) {
+          int wk = W.c4[t];
+          if (W.c1[t]) {
+            const int dead = Ao[t] + P.reach[Ad[t]] + 1;  // first position where it is dead
+            wk = wk < dead ? wk : dead;
+            W.c4[t] = wk;
+          }
+          W.c5[t] = W.c1[t] && wk >= next_far;
+          W.c1[t] = W.c1[t] && wk < next_far;
+        }
+        wsync();
+        for (int t = L.lane; t < na; t += L.nl) W.c3[t] = W.c1[t];
         wsync();
         const int na2 = scan_excl(L, W.c2, na);
         const int ns2 = scan_excl(L, W.c3, na);
-        if (nsl + ns2 > P.capS) {
-          if (L.lane == 0) { set_status(status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, nsl + ns2); }
+        int* fpos = W.E;
+        for (int t = L.lane; t < na; t += L.nl) fpos[t] = W.c5[t];
+        wsync();
+        const int nf2 = scan_excl(L, fpos, na);
+        if (nsl + ns2 > P.capS || nfar + nf2 > P.capS) {
+          if (L.lane == 0) {
+            set_status(status, ST_OVERFLOW_SLOT);
+            note_max(&P.ctr->max_state, nsl + ns2 > nfar + nf2 ? nsl + ns2 : nfar + nf2);
+          }
           return;
         }
         for (int t = L.lane; t < na; t += L.nl) {
           if (W.c0[t]) { const int o = W.c2[t]; Bz[o] = Az[t]; Bo[o] = Ao[t]; Bd[o] = Ad[t]; }
           if (W.c1[t]) {
             const int o = nsl + W.c3[t];
-            const int dead = Ao[t] + P.reach[Ad[t]] + 1;  // first position where it is dead
-            const int wk = W.c4[t] < dead ? W.c4[t] : dead;
-            W.sz[o] = Az[t]; W.so[o] = Ao[t]; W.sd[o] = Ad[t]; W.sw[o] = wk;
+            W.sz[o] = Az[t]; W.so[o] = Ao[t]; W.sd[o] = Ad[t]; W.sw[o] = W.c4[t];
+          }
+          if (W.c5[t]) {
+            const int o = nfar + fpos[t];
+            W.fz[o] = Az[t]; W.fo[o] = Ao[t]; W.fd[o] = Ad[t]; W.fw[o] = W.c4[t];
           }
         }
         wsync();
         nsl += ns2;
+        nfar += nf2;
         na = na2;
         Key* tz = Az; Az = Bz; Bz = tz;
         int* to = Ao; Ao = Bo; Bo = to;
         int* td = Ad; Ad = Bd; Bd = td;
       }
+      PHASE_COUNT(14, na);
       if (L.lane == 0) {
         int m = nsl > na ? nsl : na;
+        m = m > nfar ? m : nfar;
         note_max(&P.ctr->max_state, m > nr ? m : nr);
       }
       PHASE(5);
