@@ -237,7 +237,7 @@ def run_ours(args, rank, ws):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_pass2r (y dilation with per-piece radius, window gather)",
+                     "kernel": "k_pass2t (y dilation with per-piece radius, tiled window gather)",
                      "peak_source": peak_kind},
         "stage_ms_per_step": {"validate+tables": stages[0] / args.steps,
                               "pass1": stages[1] / args.steps, "pass2": stages[2] / args.steps,

@@ -27,6 +27,10 @@ def _stale(target, deps):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "flags.txt")
+    want = " ".join([NVCC, *ARCH, *FLAGS])
+    if not os.path.exists(stamp) or open(stamp).read() != want:
+        force = True  # other compiler flags than the objects were built with
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "dexel.h"))
     objs = []
@@ -54,6 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         tmp = LIB + f".{os.getpid()}.tmp"
         run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
         os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(want)
     return LIB
 
 

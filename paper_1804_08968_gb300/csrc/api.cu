@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <mutex>
 #include <vector>
@@ -31,10 +32,9 @@ struct dexel_ctx {
   // capacities learnt from earlier calls (grown on overflow)
   int capA = 1024, capR = 1024, capS = 4096;
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
-  char gather = 'r';    // first gather kernel: 'r' register stacks, 'g' staged shared-memory stacks
-  int stcap = 16;       // gather: stack entries per lane (shared-memory fallback kernel)
-  int rcap = 0;         // gather: intervals per column bucket of the register-stack kernel
-  int bcap = 0;         // gather: intervals per output column (0 = derive from the radius)
+  // gather: bucket entries per column, learnt per (radius, op): grown when many columns
+  // needed the redo launch
+  std::map<int, int> ccap;
   long long needF = 0, needM = 0, needO = 0;  // arena entries
   Counters host_ctr{};
   // optional per-stage timing with CUDA events on the call's stream
@@ -159,13 +159,14 @@ __global__ void k_write(int ncols, const long long* ostart, const int* ocnt, con
 // exclusive scan of cnt[0..n) (int64) in three launches; writes pos (int64) and col_off
 constexpr int kScanThreads = 256, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
 
-__global__ void k_scan1(long long n, const long long* cnt, long long* pos, long long* sums) {
+template <typename C>
+__global__ void k_scan1(long long n, const C* cnt, long long* pos, long long* sums) {
   __shared__ long long sh[kScanThreads];
   const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
   long long v[kScanPer];
   long long s = 0;
   for (int q = 0; q < kScanPer; ++q) {
-    v[q] = base + q < n ? cnt[base + q] : 0;
+    v[q] = base + q < n ? (long long)cnt[base + q] : 0;
     s += v[q];
   }
   sh[threadIdx.x] = s;
@@ -182,6 +183,36 @@ __global__ void k_scan1(long long n, const long long* cnt, long long* pos, long 
     run += v[q];
   }
   if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = sh[threadIdx.x];
+}
+
+// Line-contiguous float copy of S_mid for the gather: column q = i*ny + j gets the range
+// c_start[q] = pos[q] + sums[q / kScanTile] (exclusive scan of the piece counts in q order), so
+// that the pieces of any run of sources of a line are one contiguous range; ends as float
+// approximations (keyf), dx as short.  Also records max |finite end| for the float filter.
+template <typename Key>
+__global__ void k_mid_pack(long long ncols, const long long* m_start, const int* m_cnt,
+                           const Key* m_a, const Key* m_b, const short* m_l,
+                           const long long* pos, const long long* sums, long long* c_start,
+                           float* c_af, float* c_bf, short* c_dx, Counters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  float zm = 0.0f;
+  for (long long q = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < ncols; q += nw) {
+    const long long c = pos[q] + sums[q / kScanTile];
+    if (lane == 0) c_start[q] = c;
+    const long long ms = m_start[q];
+    const int n = m_cnt[q];
+    for (int p = lane; p < n; p += 32) {
+      const float a = keyf(m_a[ms + p]), b = keyf(m_b[ms + p]);
+      c_af[c + p] = a;
+      c_bf[c + p] = b;
+      c_dx[c + p] = m_l[ms + p];
+      if (fabsf(a) < __builtin_huge_valf()) zm = fmaxf(zm, fabsf(a));
+      if (fabsf(b) < __builtin_huge_valf()) zm = fmaxf(zm, fabsf(b));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) zm = fmaxf(zm, __shfl_xor_sync(0xffffffffu, zm, o));
+  if (lane == 0 && zm > 0.0f) atomicMax(&ctr->zmax_bits, __float_as_uint(zm));
 }
 
 __global__ void k_scan2(long long nb, long long* sums) {
@@ -448,11 +479,10 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     }
 
     // ---------------- pass 2: window gather (default) or per-line sweep
-    bool use_sweep = ctx->sweep2;
-    P2GParams<T> pg{};
-    long long smem_b = 0;
+    bool use_sweep = ctx->sweep2 || K > kGatherMaxReach;
     if (!use_sweep) {
-      pg.nx = nx; pg.ny = ny; pg.R = K; pg.kk = kk;
+      P2GParams<T> pg{};
+      pg.nx = nx; pg.ny = ny; pg.R = K; pg.kk = kk; pg.nmax = nmax;
       pg.wtab = (const double*)pwtab; pg.wtabf = (const float*)pwtabf; pg.reach = (const int*)preach;
       pg.m_a = p1.m_a; pg.m_b = p1.m_b; pg.m_l = p1.m_l;
       pg.m_start = p1.m_start; pg.m_cnt = p1.m_cnt;
@@ -461,74 +491,81 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       pg.o_start = (long long*)postart; pg.o_cnt = (int*)pocnt;
       pg.blk = 256;
       pg.ctr = ctr;
-      if (ctx->bcap < 2 * (2 * K + 1)) {
-        int b = 64;
-        while (b < 2 * (2 * K + 1)) b <<= 1;
-        ctx->bcap = b;
-      }
-      pg.stcap = ctx->stcap;
-      pg.bcap = ctx->bcap;
-      pg.warps_per_block = 8;
-      // staging area: what remains of ~200 KB after the warps' scratch; the tile is the
-      // largest whose window of pieces is expected to fit
-      const long long wbytes = pass2g_smem(pg.warps_per_block, pg.stcap, pg.bcap, 1, K, 0);
-      const long long room = (200LL << 10) - wbytes - 4096;
-      pg.stage_cap = room > 0 ? (int)std::min<long long>(room / 9, 1 << 20) : 0;
-      const double per_col = (double)hc.mid_total / (double)std::max<long long>(ncols, 1);
-      pg.tile = 64;
-      while (pg.tile > 8 && (pg.tile + 2.0 * K + 1) * per_col * 1.3 > pg.stage_cap) pg.tile >>= 1;
-      // fallback kernel geometry: shrink the staging area, then the warps, until it fits
-      smem_b = pass2g_smem(pg.warps_per_block, pg.stcap, pg.bcap, pg.tile, K, pg.stage_cap);
-      while (smem_b > (220LL << 10) && pg.warps_per_block > 1) {
-        pg.stage_cap = 0;
-        pg.warps_per_block >>= 1;
-        smem_b = pass2g_smem(pg.warps_per_block, pg.stcap, pg.bcap, pg.tile, K, pg.stage_cap);
-      }
-      if (smem_b > (220LL << 10)) use_sweep = true;  // windows too crowded for the gather
-    }
-    if (!use_sweep) {
-      const int per_sm = (int)std::max<long long>(1, (220LL << 10) / smem_b);
-      const int gblocks = sms * per_sm;
-      // first the register-stack kernel; the columns that need a deeper stack or a larger
-      // bucket are marked and redone by the shared-memory kernel
-      const int W = 2 * K + 1;
-      const int G = W <= 16 ? 32 / W : 1;
-      if (ctx->rcap < 2 * W) {
-        int b = 64;
-        while (b < 2 * W) b <<= 1;
-        ctx->rcap = b;
-      }
-      while (ctx->rcap > 64 && pass2r_smem(4, G, ctx->rcap) > (110LL << 10)) ctx->rcap >>= 1;
       mark(ctx, 4, st);
-      int redo = 0;
-      if (ctx->gather == 'r') {
-        P2GParams<T> pr = pg;
-        pr.bcap = ctx->rcap;
-        const long long rsm = pass2r_smem(4, G, pr.bcap);
-        const int rblocks = sms * (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / rsm));
-        CK(launch_pass2r<T>(pr, G, rblocks, st));
+      // line-contiguous float copy of S_mid in the (now free) pass-1 forward arena
+      {
+        const long long capC = (long long)(bF / 10);
+        if ((long long)hc.mid_total > capC) return DEXEL_ERR_CAPACITY;  // not reached: bF >= 16 eM
+        float* c_af = (float*)aF;
+        float* c_bf = c_af + capC;
+        short* c_dx = (short*)(c_bf + capC);
+        const long long nb = (ncols + kScanTile - 1) / kScanTile;
+        k_scan1<int><<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, (const int*)pmcnt, (long long*)ppos,
+                                                        (long long*)psums);
+        k_scan2<<<1, kScanThreads, 0, st>>>(nb, (long long*)psums);
+        k_mid_pack<Key><<<sms * 8, 256, 0, st>>>(ncols, p1.m_start, p1.m_cnt, p1.m_a, p1.m_b, p1.m_l,
+                                                 (const long long*)ppos, (const long long*)psums,
+                                                 (long long*)pcnt, c_af, c_bf, c_dx, ctr);
+        ctx->launches += 3;
+        CK(cudaGetLastError());
+        pg.c_start = (const long long*)pcnt;
+        pg.c_af = c_af; pg.c_bf = c_bf; pg.c_dx = c_dx;
+      }
+      int& cc = ctx->ccap[2 * K + (erode ? 1 : 0)];
+      if (cc < 128) cc = 128;
+      pg.bcap = cc;
+      // tiled kernel geometry: the first of (warps a block, blocks an SM) = (16, 2) (the
+      // kernel compiled for 64 registers, for short windows), (16, 1), (8, 1), (4, 1) whose
+      // shared memory leaves room to stage the window of a tile of >= 16 columns (the
+      // per-warp buckets compete with the staging area)
+      {
+        const int ntab = nmax + 1 <= 4096 ? nmax + 1 : 0;
+        const double avg = (double)hc.mid_total / (double)std::max<long long>(ncols, 1);
+        int tw = 16, tc = 0, per_sm = 2, stage_cap = 0;
+        const int cand[4][2] = {{16, 2}, {16, 1}, {8, 1}, {4, 1}};
+        for (const auto& cd : cand) {
+          if (cd[1] == 2 && K > 12) continue;
+          tw = cd[0];
+          per_sm = cd[1];
+          const long long budget = per_sm == 2 ? (108LL << 10) : (220LL << 10);
+          const P2TLayout base = p2t_layout(K, 128, ntab, 0, tw, pg.bcap);
+          const long long room = budget - base.total - 64;
+          stage_cap = room > 0 ? (int)std::min<long long>(room / 10, 1 << 22) : 0;
+          for (tc = 128; tc >= 16; tc >>= 1)
+            if ((tc + 2.0 * K + 1) * avg * 1.25 <= stage_cap) break;
+          if (tc >= 16) break;
+        }
+        if (tc < 16) tc = 16;
+        if (stage_cap < 256) return DEXEL_ERR_CAPACITY;  // not reached for K <= kGatherMaxReach
+        const int ntiles_cap = nx * ((ny + tc - 1) / tc);
+        const int tblocks = std::max(1, std::min(sms * per_sm, ntiles_cap));
+        CK(launch_pass2t<T>(pg, tw, tc, ntab, stage_cap, kRoundAppends, kRoundPieces, per_sm,
+                            tblocks, st));
         ++ctx->launches;
-        CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
-          redo = hc.redo_cols;
-          if (hc.max_state > ctx->rcap) {  // next call: a bucket as large as the columns needed
-            int b = ctx->rcap;
-            while (b < hc.max_state) b <<= 1;
-            if (pass2r_smem(4, G, b) <= (110LL << 10)) ctx->rcap = b;
-          }
+      }
+      CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      int redo = 0;
+      if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
+        // columns whose union outgrew the bucket: k_pass2c with one bucket for the whole window
+        redo = hc.redo_cols;
+        int b = 4096;  // the whole window's appends in one bucket: as large as fits
+        while (b > 4 * pg.bcap && pass2c_warp_bytes(K, b) > (200LL << 10)) b >>= 1;
+        const long long wbytes = pass2c_warp_bytes(K, b);
+        if (wbytes <= (200LL << 10)) {
+          int w = 8;
+          while (w > 1 && w * wbytes > (100LL << 10)) w >>= 1;
+          const int per_sm = (int)std::max<long long>(1, std::min<long long>(64 / w, (220LL << 10) / (w * wbytes)));
+          if (redo * 64LL > ncols) cc = std::min(2 * cc, 1024);  // next calls: a larger bucket
+          P2GParams<T> pr = pg;
+          pr.bcap = b;
+          pr.redo = 1;
           CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
-          pg.redo = 1;
-          CK(launch_pass2g<T>(pg, gblocks, st));
+          CK(launch_pass2c<T>(pr, w, sms * per_sm, st));
           ++ctx->launches;
           CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
           CK(cudaStreamSynchronize(st));
         }
-      } else {
-        CK(launch_pass2g<T>(pg, gblocks, st));
-        ++ctx->launches;
-        CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
       }
       ctx->stats[5] = redo;
       mark(ctx, 5, st);
@@ -540,11 +577,13 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         if (ws_user) return DEXEL_ERR_CAPACITY;
         continue;
       }
-      if (hc.status & ST_OVERFLOW_SLOT) {  // the shared-memory kernel's stacks or bucket
-        ctx->stcap *= 2;
-        ctx->bcap *= 2;
-        if (ws_user) return DEXEL_ERR_CAPACITY;
-        continue;
+      if (hc.status & ST_OVERFLOW_SLOT) {
+        // a column's union beyond any bucket: the per-line sweep does this call's pass 2
+        CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(&ctr->arena_top[3], 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(&ctr->out_total, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(&ctr->max_state, 0, sizeof(int), st));
+        use_sweep = true;
       }
     }
     if (use_sweep) {
@@ -615,7 +654,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     k_count<T><<<gb, thr, 0, st>>>((int)ncols, (const long long*)postart, (const int*)pocnt,
                                    out_l, out_r, erode ? 1 : 0, (long long*)pcnt);
     const long long nb = (ncols + kScanTile - 1) / kScanTile;
-    k_scan1<<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, (const long long*)pcnt, (long long*)ppos,
+    k_scan1<long long><<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, (const long long*)pcnt, (long long*)ppos,
                                                   (long long*)psums);
     k_scan2<<<1, kScanThreads, 0, st>>>(nb, (long long*)psums);
     k_scan3<<<(unsigned)((ncols + 1 + thr - 1) / thr), thr, 0, st>>>(
@@ -828,7 +867,7 @@ dexel_status noalloc_offset(const dexel_grid_in* in, double k, bool erode, dexel
   const unsigned gb = (unsigned)((ncols + thr - 1) / thr);
   k_count<T><<<gb, thr, 0, st>>>((int)ncols, ostart, ocnt, p2.o_l, p2.o_r, erode ? 1 : 0, cnt);
   const long long nb = (ncols + kScanTile - 1) / kScanTile;
-  k_scan1<<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, cnt, pos, sums);
+  k_scan1<long long><<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, cnt, pos, sums);
   k_scan2<<<1, kScanThreads, 0, st>>>(nb, sums);
   k_scan3<<<(unsigned)((ncols + 1 + thr - 1) / thr), thr, 0, st>>>(ncols, pos, sums, out->col_off, ctr);
   CK(cudaGetLastError());
@@ -863,7 +902,6 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   const char* mode = getenv("DEXEL_PASS2");
   c->sweep2 = mode && strcmp(mode, "sweep") == 0;
-  if (mode && strcmp(mode, "g") == 0) c->gather = 'g';
   *ctx = c;
   return DEXEL_OK;
 }

@@ -11,17 +11,18 @@
 // per-source sets over the 2R + 1 sources of the window -- the paper's forward and backward
 // half-space diagrams together (Sec. 3.2: Omega_i within the union of the two half cells).
 //
-// GB300 mapping: one warp per output column.  Every lane builds the covered sets of its
-// sources (lane l takes dy = l - R, l - R + 32, ...) with a one-pass stack union over the
-// source's pieces in height order -- a capsule of a later piece always ends above the left
-// end of every earlier capsule, so a stack suffices.  The lanes' intervals are sorted by left
-// end in shared memory (bitonic) and united.  There is no state carried from column to
-// column, so no sequential sweep: the work is the window times the pieces, spread over 32
-// lanes, with the sources of neighbouring output columns shared through L1.
+// GB300 mapping: one warp per output column, no state carried from column to column.  The
+// window's pieces are split evenly over the 32 lanes; a lane unites the slices of its range
+// one at a time into an open interval and appends it to the column's bucket when the next
+// slice cannot be merged for certain.  The bucket is sorted by left end (bitonic, shared
+// memory) and united exactly; with the tiled kernel this happens in rounds, so that the
+// bucket stays small.  Blocks take tiles of consecutive columns of a line and stage the
+// tile's window (float ends, dx) in shared memory once for all its columns.
 //
-// Decisions are taken on float approximations with a forward error bound; the double
-// endpoints a - w and b + w are computed only when the float values cannot decide and for
-// the final endpoints, so the result equals the all-double computation bit for bit.
+// Merge decisions are taken on float approximations with an error bound and are only an
+// optimisation (an undecided pair is appended as two intervals); the appended ends are the
+// exact doubles a - w and b + w, and the final union compares exact keys, so the result
+// equals the all-double computation bit for bit.
 #pragma once
 #include "sweep2.cuh"
 
@@ -43,208 +44,16 @@ struct P2GParams {
   int* o_cnt;
   long long blk;
   Counters* ctr;
-  int stcap;      // stack entries per lane
-  int bcap;       // intervals per output column (power of two)
-  int tile;       // output columns per block tile
-  int stage_cap;  // pieces the block can stage in shared memory
-  int warps_per_block;
-  int redo;  // k_pass2g: redo only the columns whose count is -1
+  int bcap;  // bucket entries per output column (power of two)
+  int redo;  // k_pass2c: only the columns whose count is -1
+  int nmax;  // largest n = dx^2 + t^2 with n <= k^2
+  // line-contiguous float copy of S_mid (k_mid_pack): pieces of column q = i*ny + j at
+  // c_start[q] ..; float ends and dx
+  const long long* c_start;
+  const float* c_af;
+  const float* c_bf;
+  const short* c_dx;
 };
-
-// a stack entry of the per-source union: float approximations of the interval ends and the
-// pieces (indices within the source) whose exact ends they approximate
-struct PEnt {
-  float lf, rf;
-  unsigned short li, ri;
-};
-
-// one source column seen by the cover: float approximations (staged in shared memory or
-// null) and the exact height keys in global memory
-template <typename Key>
-struct Src {
-  const float* af;           // float approximations of the bottoms (or null: derive from a)
-  const float* bf;           // ... of the tops
-  const unsigned char* d8;   // dx (staged) or null
-  const Key* a;              // exact bottoms
-  const Key* b;              // exact tops
-  const short* dx;           // exact dx
-  int np;
-};
-
-template <typename Key>
-DXI double src_lo(const Src<Key>& S, int p, int t, const double* wtab) {
-  const int d = S.dx[p];
-  return keyd(S.a[p]) - wtab[d * d + t * t];
-}
-template <typename Key>
-DXI double src_hi(const Src<Key>& S, int p, int t, const double* wtab) {
-  const int d = S.dx[p];
-  return keyd(S.b[p]) + wtab[d * d + t * t];
-}
-
-// Union of the capsules of one source column's pieces at level t, appended as exact
-// interval keys through the warp's shared counter.  The union runs in one pass over the
-// pieces in height order: a capsule of a later piece ends above the left end of every earlier
-// capsule, so it either starts a new interval or merges with the top ones of a stack.
-// Comparisons use the float ends with the bound e(x) = eps (|x| + 2 w_max); the exact double
-// ends decide when the floats cannot.  Returns false when the stack or the buffer would
-// overflow.
-template <typename Key>
-DXI bool source_cover(const Src<Key>& S, int t, const int* reach, const double* wtab,
-                      const float* wtabf, float wmax2, PEnt* st, int stcap, ukey* bl, ukey* br,
-                      int* bcount, int bcap) {
-  const float eps = 2.5e-7f;
-  int top = -1;
-  for (int p = 0; p < S.np; ++p) {
-    const int dx = S.d8 ? (int)S.d8[p] : (int)S.dx[p];
-    if (t > reach[dx]) continue;  // this piece no longer reaches level t
-    const float wf = wtabf[dx * dx + t * t];
-    const float af = S.af ? S.af[p] : keyf(S.a[p]);
-    const float bf = S.bf ? S.bf[p] : keyf(S.b[p]);
-    PEnt e;
-    e.lf = af - wf;  // -inf stays -inf, +inf stays +inf
-    e.rf = bf + wf;
-    e.li = (unsigned short)p;
-    e.ri = (unsigned short)p;
-    while (top >= 0) {
-      const PEnt s = st[top];
-      const float ee = eps * (fabsf(e.lf) + fabsf(s.rf) + wmax2);
-      bool overlap;
-      if (e.lf == -__builtin_huge_valf() || s.rf == __builtin_huge_valf()) overlap = true;
-      else if (e.lf - s.rf > ee) overlap = false;
-      else if (s.rf - e.lf > ee) overlap = true;
-      else overlap = src_lo(S, e.li, t, wtab) <= src_hi(S, s.ri, t, wtab);
-      if (!overlap) break;
-      // merged interval: left = min, right = max
-      const float el = eps * (fabsf(e.lf) + fabsf(s.lf) + wmax2);
-      bool left_from_s;
-      if (s.lf == -__builtin_huge_valf()) left_from_s = true;
-      else if (e.lf == -__builtin_huge_valf()) left_from_s = false;
-      else if (e.lf - s.lf > el) left_from_s = true;
-      else if (s.lf - e.lf > el) left_from_s = false;
-      else left_from_s = src_lo(S, s.li, t, wtab) <= src_lo(S, e.li, t, wtab);
-      if (left_from_s) { e.lf = s.lf; e.li = s.li; }
-      const float er = eps * (fabsf(e.rf) + fabsf(s.rf) + wmax2);
-      bool right_from_s;
-      if (s.rf == __builtin_huge_valf()) right_from_s = true;
-      else if (e.rf == __builtin_huge_valf()) right_from_s = false;
-      else if (s.rf - e.rf > er) right_from_s = true;
-      else if (e.rf - s.rf > er) right_from_s = false;
-      else right_from_s = src_hi(S, s.ri, t, wtab) >= src_hi(S, e.ri, t, wtab);
-      if (right_from_s) { e.rf = s.rf; e.ri = s.ri; }
-      --top;
-    }
-    if (top + 1 >= stcap) return false;
-    st[++top] = e;
-  }
-  if (top < 0) return true;
-  int pos;
-#if defined(__CUDA_ARCH__)
-  pos = atomicAdd(bcount, top + 1);
-#else
-  pos = *bcount;
-  *bcount += top + 1;
-#endif
-  if (pos + top + 1 > bcap) return false;
-  for (int q = 0; q <= top; ++q) {
-    bl[pos + q] = dkey(src_lo(S, st[q].li, t, wtab));
-    br[pos + q] = dkey(src_hi(S, st[q].ri, t, wtab));
-  }
-  return true;
-}
-
-// The same union with the stack held in registers (kRegStack entries).  An interval whose
-// right end lies more than w_max below the current bottom a can never be reached by a later
-// capsule (their left ends are at least a - w_max) and is emitted at once; if the stack is
-// still full the function gives up (false) and the caller falls back to the shared-memory
-// version.
-constexpr int kRegStack = 8;
-
-// SHARED: the count is shared by several lanes (atomic); otherwise it is the lane's own.
-template <typename Key, bool SHARED>
-DXI void emit_interval(const Src<Key>& S, const PEnt& e, int t, const double* wtab, ukey* bl,
-                       ukey* br, int* bcount, int bcap, bool& ok) {
-  int pos;
-#if defined(__CUDA_ARCH__)
-  if (SHARED) pos = atomicAdd(bcount, 1);
-  else pos = (*bcount)++;
-#else
-  pos = (*bcount)++;
-#endif
-  if (pos >= bcap) { ok = false; return; }
-  bl[pos] = dkey(src_lo(S, e.li, t, wtab));
-  br[pos] = dkey(src_hi(S, e.ri, t, wtab));
-}
-
-template <typename Key, bool SHARED>
-DXI bool source_cover_reg(const Src<Key>& S, int t, const int* reach, const double* wtab,
-                          const float* wtabf, float wmaxf, ukey* bl, ukey* br, int* bcount,
-                          int bcap) {
-  const float eps = 2.5e-7f;
-  const float wmax2 = 2.0f * wmaxf;
-  PEnt st[kRegStack];
-  int depth = 0;
-  bool ok = true;
-  for (int p = 0; p < S.np; ++p) {
-    const int dx = S.d8 ? (int)S.d8[p] : (int)S.dx[p];
-    if (t > reach[dx]) continue;
-    const float wf = wtabf[dx * dx + t * t];
-    const float af = S.af ? S.af[p] : keyf(S.a[p]);
-    const float bf = S.bf ? S.bf[p] : keyf(S.b[p]);
-    PEnt e;
-    e.lf = af - wf;
-    e.rf = bf + wf;
-    e.li = (unsigned short)p;
-    e.ri = (unsigned short)p;
-    while (depth > 0) {
-      const PEnt s = st[0];
-      const float ee = eps * (fabsf(e.lf) + fabsf(s.rf) + wmax2);
-      bool overlap;
-      if (e.lf == -__builtin_huge_valf() || s.rf == __builtin_huge_valf()) overlap = true;
-      else if (e.lf - s.rf > ee) overlap = false;
-      else if (s.rf - e.lf > ee) overlap = true;
-      else overlap = src_lo(S, e.li, t, wtab) <= src_hi(S, s.ri, t, wtab);
-      if (!overlap) break;
-      const float el = eps * (fabsf(e.lf) + fabsf(s.lf) + wmax2);
-      bool left_from_s;
-      if (s.lf == -__builtin_huge_valf()) left_from_s = true;
-      else if (e.lf == -__builtin_huge_valf()) left_from_s = false;
-      else if (e.lf - s.lf > el) left_from_s = true;
-      else if (s.lf - e.lf > el) left_from_s = false;
-      else left_from_s = src_lo(S, s.li, t, wtab) <= src_lo(S, e.li, t, wtab);
-      if (left_from_s) { e.lf = s.lf; e.li = s.li; }
-      const float er = eps * (fabsf(e.rf) + fabsf(s.rf) + wmax2);
-      bool right_from_s;
-      if (s.rf == __builtin_huge_valf()) right_from_s = true;
-      else if (e.rf == __builtin_huge_valf()) right_from_s = false;
-      else if (s.rf - e.rf > er) right_from_s = true;
-      else if (e.rf - s.rf > er) right_from_s = false;
-      else right_from_s = src_hi(S, s.ri, t, wtab) >= src_hi(S, e.ri, t, wtab);
-      if (right_from_s) { e.rf = s.rf; e.ri = s.ri; }
-#pragma unroll
-      for (int q = 0; q < kRegStack - 1; ++q) st[q] = st[q + 1];
-      --depth;
-    }
-    if (depth == kRegStack) {
-      // the bottom entry can be emitted if no later capsule can reach it
-      const PEnt& bot = st[kRegStack - 1];
-      const float reach_lo = af - wmaxf;
-      if (!(bot.rf != __builtin_huge_valf() &&
-            reach_lo - bot.rf > eps * (fabsf(reach_lo) + fabsf(bot.rf) + wmax2)))
-        return false;
-      emit_interval<Key, SHARED>(S, bot, t, wtab, bl, br, bcount, bcap, ok);
-      --depth;
-    }
-#pragma unroll
-    for (int q = kRegStack - 1; q > 0; --q) st[q] = st[q - 1];
-    st[0] = e;
-    ++depth;
-  }
-#pragma unroll
-  for (int q = 0; q < kRegStack; ++q)
-    if (q < depth) emit_interval<Key, SHARED>(S, st[q], t, wtab, bl, br, bcount, bcap, ok);
-  return ok;
-}
 
 // In-place bitonic sort of (key, val) pairs by key, n a power of two, one warp.
 DXI void warp_bitonic(const Lanes& L, ukey* key, ukey* val, int n) {
@@ -266,86 +75,348 @@ DXI void warp_bitonic(const Lanes& L, ukey* key, ukey* val, int n) {
   }
 }
 
-// Per-warp scratch of the gather: per-lane stacks, the interval buffer (left keys, right
-// keys), union flags and outputs.
-struct GatherWarp {
-  PEnt* st;      // 32 * stcap
-  ukey* bl;      // bcap
-  ukey* br;      // bcap
-  int* f0;       // bcap
-  int* f1;       // bcap
-  ukey* ul;      // bcap
-  ukey* ur;      // bcap
-  int* count;    // 1
-};
-
 DXI int pow2_at_least(int n) {
   int m = 1;
   while (m < n) m <<= 1;
   return m;
 }
 
-DXI long long gather_warp_bytes(int stcap, int bcap) {
-  return 32LL * stcap * sizeof(PEnt) + 4LL * bcap * sizeof(ukey) + 2LL * bcap * sizeof(int) + 16;
+}  // namespace dexel
+
+namespace dexel {
+
+// Balanced cover of one output column (i, j): the pieces of the window's sources, taken in
+// (source, height) order, are cut into 32 equal contiguous ranges, one per lane, so that the
+// lanes' work does not depend on how the pieces spread over the sources.  A lane unites the
+// capsule slices of its range one at a time into a single open interval and appends it to the
+// column's bucket when the next slice cannot be merged for certain (float ends with the error
+// bound e(x) = eps (|x| + |y| + 2 w_max)) or when its range passes to another source.  An
+// undecided merge is left to the final exact union, so no double arithmetic is needed until
+// the exact ends of an appended interval are formed.  Appended intervals may overlap; the
+// caller sorts and unites them.
+// Per-warp shared memory of the balanced gather kernel (window offsets, bucket, union).
+DXI long long pass2c_warp_bytes(int R, int bcap) {
+  const long long off = ((2LL * R + 2) * sizeof(int) + 15) & ~15LL;
+  return off + 4LL * bcap * sizeof(ukey) + 2LL * bcap * sizeof(int) + 16;
 }
 
-DXI GatherWarp gather_warp(unsigned char* p, int stcap, int bcap) {
-  GatherWarp g;
-  g.bl = (ukey*)p; p += (long long)bcap * sizeof(ukey);
-  g.br = (ukey*)p; p += (long long)bcap * sizeof(ukey);
-  g.ul = (ukey*)p; p += (long long)bcap * sizeof(ukey);
-  g.ur = (ukey*)p; p += (long long)bcap * sizeof(ukey);
-  g.st = (PEnt*)p; p += 32LL * stcap * sizeof(PEnt);
-  g.f0 = (int*)p; p += (long long)bcap * sizeof(int);
-  g.f1 = (int*)p; p += (long long)bcap * sizeof(int);
-  g.count = (int*)p;
-  return g;
+struct CoverCur {
+  float lf, rf;   // float approximations of the interval's ends
+  int li, ri;     // pieces (within the source) of the exact ends
+  int n_l, n_r;   // their squared offsets dx^2 + t^2
+};
+
+template <typename Key>
+DXI void cover_emit(const Key* a, const Key* b, const double* wtab, const CoverCur& c,
+                    ukey* bl, ukey* br, int* bcount, int bcap) {
+  int pos;
+#if defined(__CUDA_ARCH__)
+  pos = atomicAdd(bcount, 1);
+#else
+  pos = (*bcount)++;
+#endif
+  if (pos < bcap) {
+    bl[pos] = dkey(keyd(a[c.li]) - wtab[c.n_l]);
+    br[pos] = dkey(keyd(b[c.ri]) + wtab[c.n_r]);
+  }
 }
 
-// One output column (i, j): the covers of the window's sources (lane l takes dy = l - R,
-// l - R + 32, ...), a sort by left end, the union, and the write to the output arena.
-// src(q) gives the view of source column j' = q.  bcap must be a power of two.
-template <typename T, typename SrcFn>
-DXN void gather_column(const Lanes& L, const P2GParams<T>& P, int i, int j, const GatherWarp& G,
-                       int stcap, int bcap, float wmax2, SrcFn src, ArenaCursor& cur) {
+// Merges the slice [lf, rf] (piece p, offset n) into the current interval when they overlap
+// for certain and the float ends say for certain which end of the union comes from which.
+DXI bool cover_merge(CoverCur& c, float lf, float rf, int p, int n, float wmax2) {
+  const float eps = 2.5e-7f;
+  const float INF = __builtin_huge_valf();
+  bool merge;
+  if (c.rf == INF || lf == -INF) merge = true;
+  else merge = c.rf - lf > eps * (fabsf(lf) + fabsf(c.rf) + wmax2);
+  if (!merge) return false;
+  int lsel, rsel;  // 1: current, 2: new, 0: undecided
+  if (c.lf == -INF) lsel = 1;
+  else if (lf == -INF) lsel = 2;
+  else {
+    const float e = eps * (fabsf(lf) + fabsf(c.lf) + wmax2);
+    lsel = lf - c.lf > e ? 1 : (c.lf - lf > e ? 2 : 0);
+  }
+  if (c.rf == INF) rsel = 1;
+  else if (rf == INF) rsel = 2;
+  else {
+    const float e = eps * (fabsf(rf) + fabsf(c.rf) + wmax2);
+    rsel = c.rf - rf > e ? 1 : (rf - c.rf > e ? 2 : 0);
+  }
+  if (!lsel || !rsel) return false;
+  if (lsel == 2) { c.lf = lf; c.li = p; c.n_l = n; }
+  if (rsel == 2) { c.rf = rf; c.ri = p; c.n_r = n; }
+  return true;
+}
+
+// Covers the pieces g0 <= g < g1 of the window (sources s0 .. s0 + ns - 1 of line i, piece
+// offsets srcoff[]), appending to the bucket.
+template <typename T>
+DXI void cover_range(const P2GParams<T>& P, long long qb, int j, int s0, int ns,
+                     const int* srcoff, int g0, int g1, float wmax2, ukey* bl, ukey* br,
+                     int* bcount, int bcap) {
   typedef typename H<T>::K Key;
-  if (L.lane == 0) *G.count = 0;
-  wsync();
-  bool ok = true;
-  for (int dy = -P.R + L.lane; dy <= P.R; dy += L.nl) {
-    const int jj = j + dy;
-    if (jj < 0 || jj >= P.ny) continue;
-    const Src<Key> S = src(jj);
-    ok = source_cover<Key>(S, dy < 0 ? -dy : dy, P.reach, P.wtab, P.wtabf, wmax2,
-                           G.st + L.lane * stcap, stcap, G.bl, G.br, G.count, bcap);
-    if (!ok) break;
+  if (g0 >= g1) return;
+  // source of the first piece: the last q with srcoff[q] <= g0
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (srcoff[mid] <= g0) lo = mid;
+    else hi = mid - 1;
+  }
+  int q = lo;
+  while (q < ns - 1 && srcoff[q + 1] <= g0) ++q;  // skip empty sources
+  int g = g0;
+  while (g < g1) {
+    const int send = min(g1, srcoff[q + 1]);
+    const int jj = s0 + q;
+    const int t = jj > j ? jj - j : j - jj;
+    const long long ms = P.m_start[qb + jj];
+    const Key* a = P.m_a + ms;
+    const Key* b = P.m_b + ms;
+    const short* dxa = P.m_l + ms;
+    bool have = false;
+    CoverCur c{};
+    for (int p = g - srcoff[q], pe = send - srcoff[q]; p < pe; ++p) {
+      const int dx = dxa[p];
+      const int n = dx * dx + t * t;
+      if (n > P.nmax) continue;
+      const float wf = P.wtabf[n];
+      const float lf = keyf(a[p]) - wf;
+      const float rf = keyf(b[p]) + wf;
+      if (have && cover_merge(c, lf, rf, p, n, wmax2)) continue;
+      if (have) cover_emit<Key>(a, b, P.wtab, c, bl, br, bcount, bcap);
+      c.lf = lf; c.rf = rf; c.li = p; c.ri = p; c.n_l = n; c.n_r = n;
+      have = true;
+    }
+    if (have) cover_emit<Key>(a, b, P.wtab, c, bl, br, bcount, bcap);
+    g = send;
+    ++q;
+  }
+}
+
+// The same cover with the window's pieces staged in shared memory by the block (float
+// approximations of the ends and dx; staged index g, pieces of source q at soff[q] ..
+// soff[q + 1] - 1, exact keys at sbase[q] + g in global memory).  The lane's interval is
+// carried across source boundaries, and odd sources are walked from the top, so that the
+// top interval of one source meets the top pieces of the next one (and the bottom ones the
+// bottom): the overlap test is therefore two-sided.
+struct CoverCurG {
+  float lf, rf;         // float approximations of the interval's ends
+  long long kl, kr;     // global key indices of the pieces giving the exact ends
+  int n_l, n_r;         // their squared offsets dx^2 + t^2
+};
+
+// Merge with a fixed bound E on the difference between a float end and the double it
+// approximates, summed over the two ends compared: E = 2^-20 (max |z| + w_max) (each float
+// end is within 2^-22 (|z| + w) of the double: key truncation 2^-23 |z|, rounding of w and of
+// the difference 2^-24 each).  Infinite ends need no special case: inf - E = inf.
+DXI bool cover_merge2(CoverCurG& c, float lf, float rf, long long kidx, int n, float E) {
+  if (!(lf <= c.rf - E && rf >= c.lf + E)) return false;  // overlap not certain
+  const bool l_new = lf <= c.lf - E, l_cur = lf >= c.lf + E;
+  const bool r_new = rf >= c.rf + E, r_cur = rf <= c.rf - E;
+  if (!(l_new || l_cur) || !(r_new || r_cur)) return false;  // an end undecided
+  if (l_new) { c.lf = lf; c.kl = kidx; c.n_l = n; }
+  if (r_new) { c.rf = rf; c.kr = kidx; c.n_r = n; }
+  return true;
+}
+
+template <typename Key>
+DXI void cover_emit2(const Key* ma, const Key* mb, const double* wtab, const CoverCurG& c,
+                     ukey* bl, ukey* br, int* bcount, int bcap) {
+  int pos;
+#if defined(__CUDA_ARCH__)
+  pos = atomicAdd(bcount, 1);
+#else
+  pos = (*bcount)++;
+#endif
+  if (pos < bcap) {
+    bl[pos] = dkey(keyd(ma[c.kl]) - wtab[c.n_l]);
+    br[pos] = dkey(keyd(mb[c.kr]) + wtab[c.n_r]);
+  }
+}
+
+// Resumable walk of a lane over its range of staged pieces (see cover_staged): the current
+// source q, its segment [lo, hi) of the range, the pieces taken so far in it (u) and the
+// interval under construction.
+struct LaneWalk {
+  int q, lo, hi, u;
+  int tt;          // squared level of source q
+  bool down;       // source q is walked from the top
+  bool have, done;
+  long long kb;    // global key index of staged piece 0 of source q (sbase[q])
+  CoverCurG c;
+};
+
+template <typename T>
+DXI void walk_source(LaneWalk& w, int j, int s0, const int* soff, const long long* sbase, int g1) {
+  const int jj = s0 + w.q;
+  const int t = jj > j ? jj - j : j - jj;
+  w.tt = t * t;
+  w.down = (jj & 1) != 0;
+  w.kb = sbase[w.q];
+  w.hi = min(g1, soff[w.q + 1]);
+  w.u = 0;
+}
+
+template <typename T>
+DXI void walk_init(LaneWalk& w, int j, int s0, const int* soff, const long long* sbase,
+                   int qlo, int qhi, int g0, int g1) {
+  w.have = false;
+  w.done = g0 >= g1;
+  w.c = CoverCurG{};
+  if (w.done) return;
+  int lo = qlo, hi = qhi;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (soff[mid] <= g0) lo = mid;
+    else hi = mid - 1;
+  }
+  w.q = lo;
+  w.lo = g0;
+  walk_source<T>(w, j, s0, soff, sbase, g1);
+}
+
+// One round of the lane's walk: takes at most M pieces, unites their slices into the current
+// interval and appends at most Q intervals to the bucket (through the warp's shared counter);
+// the state is kept for the next round.  The piece budget keeps the lanes of a round in step.
+template <typename T>
+DXI void cover_round(const P2GParams<T>& P, LaneWalk& w, int j, int s0, const int* soff,
+                     const long long* sbase, const float* saf, const float* sbf,
+                     const short* sdx, const float* wt, int g1, float E, int Q, int M,
+                     ukey* bl, ukey* br, int* bcount, int bcap) {
+  typedef typename H<T>::K Key;
+  int emitted = 0;
+  while (!w.done && emitted < Q && M > 0) {
+    if (w.u == w.hi - w.lo) {  // segment done
+      if (w.hi >= g1) {
+        if (w.have) {
+          cover_emit2<Key>(P.m_a, P.m_b, P.wtab, w.c, bl, br, bcount, bcap);
+          ++emitted;
+          w.have = false;
+        }
+        w.done = true;
+        break;
+      }
+      ++w.q;
+      w.lo = w.hi;
+      walk_source<T>(w, j, s0, soff, sbase, g1);
+      continue;
+    }
+    const int gg = w.down ? w.hi - 1 - w.u : w.lo + w.u;
+    ++w.u;
+    --M;
+    // straight-line body (selects, no early exits) so that the lanes stay converged; only
+    // the rare append branches
+    const int dx = sdx[gg];
+    const int n = dx * dx + w.tt;
+    const bool v = n <= P.nmax;
+    const float wf = wt[v ? n : 0];
+    const float lf = saf[gg] - wf;
+    const float rf = sbf[gg] + wf;
+    const long long kidx = w.kb + gg;
+    const bool ov = lf <= w.c.rf - E && rf >= w.c.lf + E;  // certain overlap
+    const bool l_new = lf <= w.c.lf - E, l_cur = lf >= w.c.lf + E;
+    const bool r_new = rf >= w.c.rf + E, r_cur = rf <= w.c.rf - E;
+    const bool merge = v && w.have && ov && (l_new || l_cur) && (r_new || r_cur);
+    if (v && w.have && !merge) {
+      cover_emit2<Key>(P.m_a, P.m_b, P.wtab, w.c, bl, br, bcount, bcap);
+      ++emitted;
+    }
+    const bool fresh = v && !merge;  // starts a new interval
+    const bool tl = fresh || (merge && l_new);
+    const bool tr = fresh || (merge && r_new);
+    w.c.lf = tl ? lf : w.c.lf;
+    w.c.kl = tl ? kidx : w.c.kl;
+    w.c.n_l = tl ? n : w.c.n_l;
+    w.c.rf = tr ? rf : w.c.rf;
+    w.c.kr = tr ? kidx : w.c.kr;
+    w.c.n_r = tr ? n : w.c.n_r;
+    w.have = w.have || v;
+  }
+}
+
+// Union of n intervals sorted by left key (closed: touching ones join), in two steps so that
+// the runs can be written straight to their final place: union_count marks run starts
+// (start[]), turns cr[] into running maxima and pos[] into run indices, and returns the run
+// count; union_write stores the runs.
+DXI int union_count(const Lanes& L, const ukey* cl, ukey* cr, int n, int* start, int* pos) {
+  ukey carry = 0;
+  for (int base = 0; base < n; base += L.nl) {
+    const int t = base + L.lane;
+    const ukey v = t < n ? cr[t] : 0;
+    const ukey inc = w_incl_maxk(v, L.lane);
+    const ukey prev = w_shift_up(inc, L.lane, 0);
+    if (t < n) {
+      const ukey ex = prev > carry ? prev : carry;
+      const int st = (t == 0) || (cl[t] > ex);
+      start[t] = st;
+      pos[t] = st;
+      cr[t] = ex > v ? ex : v;
+    }
+    const ukey last = w_bcastk(inc, L.nl - 1);
+    carry = last > carry ? last : carry;
   }
   wsync();
-  if (w_any(!ok)) {
-    if (L.lane == 0) { set_status(&P.ctr->status, ST_OVERFLOW_SLOT); note_max(&P.ctr->max_state, 2 * bcap); }
-    return;
+  return scan_excl(L, pos, n);
+}
+
+DXI void union_write(const Lanes& L, const ukey* cl, const ukey* cr, int n, const int* start,
+                     const int* pos, ukey* ol, ukey* orr) {
+  for (int t = L.lane; t < n; t += L.nl) {
+    const bool last = (t == n - 1) || start[t + 1];
+    const int r = pos[t] - (start[t] ? 0 : 1);
+    if (start[t]) ol[r] = cl[t];
+    if (last) orr[r] = cr[t];
   }
-  const int total = *G.count;
-  const int n2 = pow2_at_least(total);
-  for (int t = total + L.lane; t < n2; t += L.nl) { G.bl[t] = ~0ULL; G.br[t] = ~0ULL; }
-  wsync();
-  if (n2 > 1) warp_bitonic(L, G.bl, G.br, n2);
-  const int no = total > 0 ? union_runs(L, G.bl, G.br, total, true, G.f0, G.f1, G.ul, G.ur, G.br, nullptr) : 0;
-  const long long s = arena_take(L, &P.ctr->arena_top[3], P.blk, cur, no);
-  const bool fits = s + no <= P.o_cap;
-  if (!fits) {
-    if (L.lane == 0) set_status(&P.ctr->status, ST_OVERFLOW_ARENA);
-  } else {
-    for (int q = L.lane; q < no; q += L.nl) { P.o_l[s + q] = G.ul[q]; P.o_r[s + q] = G.ur[q]; }
+}
+
+// union_write into the front of the same arrays (run r <= element t): each chunk of 32 is
+// read into registers before any lane writes.
+DXI void union_write_inplace(const Lanes& L, ukey* cl, ukey* cr, int n, const int* start,
+                             const int* pos) {
+  for (int base = 0; base < n; base += L.nl) {
+    const int t = base + L.lane;
+    ukey l = 0, r = 0;
+    int idx = -1;
+    bool st = false, last = false;
+    if (t < n) {
+      l = cl[t];
+      r = cr[t];
+      st = start[t] != 0;
+      last = (t == n - 1) || start[t + 1];
+      idx = pos[t] - (st ? 0 : 1);
+    }
+    wsync();
+    if (t < n) {
+      if (st) cl[idx] = l;
+      if (last) cr[idx] = r;
+    }
+    wsync();
   }
-  if (L.lane == 0) {
-    const long long c = (long long)j * P.nx + i;
-    P.o_start[c] = fits ? s : 0;
-    P.o_cnt[c] = no;
-    note_max(&P.ctr->max_out, no);
-    add_total(&P.ctr->out_total, no);
-  }
-  wsync();
+}
+
+// Shared-memory layout of the tiled balanced kernel: the tile window's piece offsets, the
+// w table, the staged pieces, and per warp a bucket with the union's flags.
+struct P2TLayout {
+  long long soff, sbase, swt, saf, sbf, sdx, warps, warp_bytes, total;
+};
+
+DXI long long align16(long long x) { return (x + 15) & ~15LL; }
+
+DXI P2TLayout p2t_layout(int R, int tc, int ntab, int stage_cap, int nwarps, int bcap) {
+  P2TLayout o;
+  long long x = 0;
+  o.soff = x; x = align16(x + (long long)(tc + 2 * R + 2) * sizeof(int));
+  o.sbase = x; x = align16(x + (long long)(tc + 2 * R + 2) * sizeof(long long));
+  o.swt = x; x = align16(x + (long long)ntab * sizeof(float));
+  o.saf = x; x += (long long)stage_cap * sizeof(float);
+  o.sbf = x; x += (long long)stage_cap * sizeof(float);
+  o.sdx = x; x = align16(x + (long long)stage_cap * sizeof(short));
+  o.warp_bytes = align16(2LL * bcap * sizeof(ukey) + 2LL * bcap * sizeof(int) + 16);
+  o.warps = x; x += nwarps * o.warp_bytes;
+  o.total = x;
+  return o;
 }
 
 }  // namespace dexel

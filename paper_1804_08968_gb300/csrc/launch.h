@@ -6,17 +6,20 @@
 namespace dexel {
 
 constexpr int kWarpsPerBlock = 4;
+// window gather (pass 2): largest reach it takes (beyond it the per-line sweep runs), and the
+// per-round limits of a lane in k_pass2t (appended intervals, pieces taken)
+constexpr int kGatherMaxReach = 1024;
+constexpr int kRoundAppends = 2;
+constexpr int kRoundPieces = 32;
 
 template <typename T>
 cudaError_t launch_pass1(const P1Params<T>& P, int blocks, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pass2(const P2Params<T>& P, int blocks, cudaStream_t st);
 template <typename T>
-cudaError_t launch_pass2g(const P2GParams<T>& P, int blocks, cudaStream_t st);
-long long pass2g_smem(int warps, int stcap, int bcap, int tile, int R, int stage_cap);
+cudaError_t launch_pass2t(const P2GParams<T>& P, int warps_per_block, int tc, int ntab,
+                          int stage_cap, int Q, int M, int minb, int blocks, cudaStream_t st);
 template <typename T>
-cudaError_t launch_pass2r(const P2GParams<T>& P, int G, int blocks, cudaStream_t st);
-long long pass2r_smem(int warps, int G, int bcap);
-
+cudaError_t launch_pass2c(const P2GParams<T>& P, int warps_per_block, int blocks, cudaStream_t st);
 
 }  // namespace dexel

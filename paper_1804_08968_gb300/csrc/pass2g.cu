@@ -1,262 +1,316 @@
-// Pass 2 as a gather over the window (gather2.cuh).  A block takes a tile of consecutive
-// output columns of one column line, stages the pieces of the tile's window (float
-// approximations of the heights and dx) in shared memory with coalesced loads, and its warps
-// compute one output column at a time.  A window too large for the staging area is read
-// straight from global memory by the same code.
+// Pass 2 as a gather over the window (gather2.cuh): k_pass2t (tiles of a line staged in
+// shared memory, the main kernel) and k_pass2c (columns read from global memory with one
+// bucket for the whole window, for the columns k_pass2t hands back).
 #include "launch.h"
 
 namespace dexel {
 
-long long pass2g_smem(int warps, int stcap, int bcap, int tile, int R, int stage_cap) {
-  const long long win = (long long)tile + 2LL * R + 1;
-  long long b = 0;
-  b += (win + 1) * sizeof(int);                          // source offsets
-  b += (long long)stage_cap * (2 * sizeof(float) + 1);  // staged pieces
-  b = (b + 15) & ~15LL;
-  b += warps * ((gather_warp_bytes(stcap, bcap) + 15) & ~15LL);
-  return b;
+// Balanced gather (cover_range): one warp per output column, the window's pieces split
+// evenly over the lanes.  Per-warp shared memory: the window's piece offsets, the bucket (left
+// and right keys), the union's flags and outputs.  A column whose bucket overflows is marked
+// (count -1) for a second launch of the same kernel with a larger bucket (redo mode).
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pass2c(P2GParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwb = blockDim.x >> 5;
+  const Lanes L{lane, 32};
+  const int R = P.R, bcap = P.bcap;
+  unsigned char* wb = smem + (long long)warp * pass2c_warp_bytes(R, bcap);
+  int* srcoff = (int*)wb;
+  ukey* bl = (ukey*)(wb + (((2LL * R + 2) * sizeof(int) + 15) & ~15LL));
+  ukey* br = bl + bcap;
+  ukey* ul = br + bcap;
+  ukey* ur = ul + bcap;
+  int* f0 = (int*)(ur + bcap);
+  int* f1 = f0 + bcap;
+  int* bcount = f1 + bcap;
+  const float wmax2 = 2.0f * P.wtabf[0];
+  const long long ncols = (long long)P.nx * P.ny;
+  const long long nw = (long long)gridDim.x * nwb;
+  ArenaCursor cur{0, 0};
+  for (long long item = (long long)blockIdx.x * nwb + warp; item < ncols; item += nw) {
+    const int i = (int)(item / P.ny), j = (int)(item % P.ny);
+    const long long c = (long long)j * P.nx + i;
+    if (P.redo && P.o_cnt[c] != -1) continue;
+    PHASE_BEGIN();
+    const long long qb = (long long)i * P.ny;
+    const int s0 = max(0, j - R), s1 = min(P.ny - 1, j + R);
+    const int ns = s1 - s0 + 1;
+    int carry = 0;
+    for (int base = 0; base < ns; base += 32) {
+      const int t = base + lane;
+      const int v = t < ns ? P.m_cnt[qb + s0 + t] : 0;
+      const int inc = w_incl_add(v, lane);
+      if (t < ns) srcoff[t] = carry + inc - v;
+      carry += w_bcast(inc, 31);
+    }
+    if (lane == 0) { srcoff[ns] = carry; *bcount = 0; }
+    wsync();
+    PHASE(0);
+    const int per = (carry + 31) >> 5;
+    const int g0 = min(carry, lane * per), g1 = min(carry, g0 + per);
+    cover_range<T>(P, qb, j, s0, ns, srcoff, g0, g1, wmax2, bl, br, bcount, bcap);
+    wsync();
+    PHASE(1);
+    const int total = *bcount;
+    PHASE_COUNT(8, total);
+    PHASE_COUNT(9, carry);
+    PHASE_COUNT(10, 1);
+    if (total > bcap) {
+      if (lane == 0) {
+        P.o_cnt[c] = -1;
+        note_max(&P.ctr->max_state, total);
+        set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
+        atomicAdd(&P.ctr->redo_cols, 1);
+      }
+      wsync();
+      continue;
+    }
+    const int n2 = pow2_at_least(total);
+    for (int t = total + lane; t < n2; t += 32) { bl[t] = ~0ULL; br[t] = ~0ULL; }
+    wsync();
+    if (n2 > 1) warp_bitonic(L, bl, br, n2);
+    PHASE(2);
+    PHASE_COUNT(11, n2);
+    const int no = total > 0 ? union_runs(L, bl, br, total, true, f0, f1, ul, ur, br, nullptr) : 0;
+    const long long s = arena_take(L, &P.ctr->arena_top[3], P.blk, cur, no);
+    const bool fits = s + no <= P.o_cap;
+    if (!fits) {
+      if (lane == 0) set_status(&P.ctr->status, ST_OVERFLOW_ARENA);
+    } else {
+      for (int q = lane; q < no; q += 32) { P.o_l[s + q] = ul[q]; P.o_r[s + q] = ur[q]; }
+    }
+    if (lane == 0) {
+      P.o_start[c] = fits ? s : 0;
+      P.o_cnt[c] = no;
+      note_max(&P.ctr->max_out, no);
+      add_total(&P.ctr->out_total, no);
+    }
+    wsync();
+    PHASE(3);
+  }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_pass2g(P2GParams<T> P) {
-  typedef typename H<T>::K Key;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const Lanes L{lane, 32};
-  const int R = P.R, T_ = P.tile;
-  const int win = T_ + 2 * R + 1;
-  int* soff = (int*)smem;
-  float* saf = (float*)(soff + win + 1);
-  float* sbf = saf + P.stage_cap;
-  unsigned char* sd8 = (unsigned char*)(sbf + P.stage_cap);
-  unsigned char* wbase = smem + ((((long long)(win + 1) * sizeof(int) +
-                                   (long long)P.stage_cap * (2 * sizeof(float) + 1)) + 15) & ~15LL);
-  const GatherWarp G =
-      gather_warp(wbase + (long long)warp * ((gather_warp_bytes(P.stcap, P.bcap) + 15) & ~15LL), P.stcap, P.bcap);
-  const float wmax2 = 2.0f * P.wtabf[0];
-  ArenaCursor cur{0, 0};
-  if (P.redo) {
-    // only the columns the register-stack kernel marked (count -1), read from global memory
-    const long long ncols = (long long)P.nx * P.ny;
-    const long long nw = (long long)gridDim.x * P.warps_per_block;
-    for (long long c = (long long)blockIdx.x * P.warps_per_block + warp; c < ncols; c += nw) {
-      if (P.o_cnt[c] != -1) continue;
-      const int i = (int)(c % P.nx), j = (int)(c / P.nx);
-      const long long qb = (long long)i * P.ny;
-      auto src = [&](int jj) {
-        Src<Key> S;
-        const long long ms = P.m_start[qb + jj];
-        S.a = P.m_a + ms; S.b = P.m_b + ms; S.dx = P.m_l + ms; S.np = P.m_cnt[qb + jj];
-        S.af = nullptr; S.bf = nullptr; S.d8 = nullptr;
-        return S;
-      };
-      gather_column<T>(L, P, i, j, G, P.stcap, P.bcap, wmax2, src, cur);
+cudaError_t launch_pass2c(const P2GParams<T>& P, int warps_per_block, int blocks, cudaStream_t st) {
+  const size_t smem = (size_t)(warps_per_block * pass2c_warp_bytes(P.R, P.bcap));
+  cudaError_t e = cudaFuncSetAttribute(k_pass2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_pass2c<T><<<blocks, warps_per_block * 32, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_pass2c<float>(const P2GParams<float>&, int, int, cudaStream_t);
+template cudaError_t launch_pass2c<double>(const P2GParams<double>&, int, int, cudaStream_t);
+
+}  // namespace dexel
+
+namespace dexel {
+
+// Cover of output column j from the staged pieces [ga, gz) of its window (af/bf/dxs indexed
+// by the window's piece index): the pieces are split evenly over the lanes, and in rounds
+// every lane takes at most M pieces and appends at most Q intervals, after which the warp
+// unites the bucket into its front (acc runs, carried in and out so that a window can be
+// covered in several chunks).  Returns false when the union outgrows bcap - 32 Q runs.
+template <typename T>
+DXI bool column_cover(const P2GParams<T>& P, const Lanes& L, int j, int s0, const int* soff,
+                      const long long* sbase, int qlo, int qhi, int ga, int gz, const float* af,
+                      const float* bf, const short* dxs, const float* wt, float E, int Q, int M,
+                      ukey* bl, ukey* br, int* f0, int* f1, int* bcount, int bcap, int& acc) {
+  const int pc = gz - ga;
+  int per = (pc + 31) >> 5;
+  if (per > 1 && !(per & 1)) ++per;  // odd stride: no bank conflicts
+  const int g0 = ga + min(pc, L.lane * per), g1 = ga + min(pc, L.lane * per + per);
+  LaneWalk w;
+  walk_init<T>(w, j, s0, soff, sbase, qlo, qhi, g0, g1);
+  for (;;) {
+    if (L.lane == 0) *bcount = acc;
+    wsync();
+    cover_round<T>(P, w, j, s0, soff, sbase, af, bf, dxs, wt, g1, E, Q, M, bl, br, bcount, bcap);
+    wsync();
+    const int n = *bcount;
+    const bool fin = !w_any(!w.done);
+    if (n > acc) {
+      const int n2 = pow2_at_least(n);
+      for (int t = n + L.lane; t < n2; t += 32) { bl[t] = ~0ULL; br[t] = ~0ULL; }
+      wsync();
+      if (n2 > 1) warp_bitonic(L, bl, br, n2);
+      acc = union_count(L, bl, br, n, f0, f1);
+      union_write_inplace(L, bl, br, n, f0, f1);
     }
+    if (fin) return true;
+    if (acc > bcap - 32 * Q) return false;
+  }
+}
+
+// Writes the acc runs at the front of the bucket as output column (i, j), or marks the column
+// (count -1) for the redo launch.
+template <typename T>
+DXI void column_out(const P2GParams<T>& P, const Lanes& L, int j, int i, bool ok, int acc,
+                    const ukey* bl, const ukey* br, int bcap, ArenaCursor& cur) {
+  const long long c = (long long)j * P.nx + i;
+  if (!ok) {
+    if (L.lane == 0) {
+      P.o_cnt[c] = -1;
+      note_max(&P.ctr->max_state, 2 * bcap);
+      set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
+      atomicAdd(&P.ctr->redo_cols, 1);
+    }
+    wsync();
     return;
   }
-  const int tiles_per_line = (P.ny + T_ - 1) / T_;
-  const long long ntiles = (long long)P.nx * tiles_per_line;
+  const long long s = arena_take(L, &P.ctr->arena_top[3], P.blk, cur, acc);
+  const bool fits = s + acc <= P.o_cap;
+  if (!fits) {
+    if (L.lane == 0) set_status(&P.ctr->status, ST_OVERFLOW_ARENA);
+  } else {
+    for (int q = L.lane; q < acc; q += 32) { P.o_l[s + q] = bl[q]; P.o_r[s + q] = br[q]; }
+  }
+  if (L.lane == 0) {
+    P.o_start[c] = fits ? s : 0;
+    P.o_cnt[c] = acc;
+    note_max(&P.ctr->max_out, acc);
+    add_total(&P.ctr->out_total, acc);
+  }
+  wsync();
+}
+
+// Tiled balanced gather: a block takes tc consecutive output columns of one line, stages the
+// pieces of their common window (float ends and dx) in shared memory with coalesced loads,
+// and its warps take the tile's columns, each splitting its window's pieces evenly over the
+// lanes (column_cover).  A tile whose window holds more pieces than the staging area is cut
+// into the longest runs of columns whose windows fit; a single column whose window does not
+// fit is covered in chunks.  Columns whose union outgrows the bucket are marked (count -1)
+// for the redo launch of k_pass2c.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(512, MINB) k_pass2t(P2GParams<T> P, int tc, int ntab, int stage_cap, int Q, int M) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwb = blockDim.x >> 5;
+  const Lanes L{lane, 32};
+  const int R = P.R, bcap = P.bcap;
+  const P2TLayout Lo = p2t_layout(R, tc, ntab, stage_cap, nwb, bcap);
+  int* soff = (int*)(smem + Lo.soff);
+  long long* sbase = (long long*)(smem + Lo.sbase);
+  float* swt = (float*)(smem + Lo.swt);
+  float* saf = (float*)(smem + Lo.saf);
+  float* sbf = (float*)(smem + Lo.sbf);
+  short* sdx = (short*)(smem + Lo.sdx);
+  unsigned char* wb = smem + Lo.warps + (long long)warp * Lo.warp_bytes;
+  ukey* bl = (ukey*)wb;
+  ukey* br = bl + bcap;
+  int* f0 = (int*)(br + bcap);
+  int* f1 = f0 + bcap;
+  int* bcount = f1 + bcap;
+  for (int q = threadIdx.x; q < ntab; q += blockDim.x) swt[q] = P.wtabf[q];
+  const float* wt = ntab > 0 ? swt : P.wtabf;
+  const float wmax2 = 2.0f * P.wtabf[0];
+  const float E = 9.5367432e-7f * (__uint_as_float(P.ctr->zmax_bits) + P.wtabf[0]);  // 2^-20
+  long long* sgb = sbase + tc + 2 * R + 1;  // the tile's first piece in the packed copy
+  const int tpl = (P.ny + tc - 1) / tc;
+  const long long ntiles = (long long)P.nx * tpl;
+  ArenaCursor cur{0, 0};
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int i = (int)(tile / tiles_per_line);
-    const int j0 = (int)(tile % tiles_per_line) * T_;
-    const int j1 = min(P.ny, j0 + T_);
+    const int i = (int)(tile / tpl);
+    const int j0 = (int)(tile % tpl) * tc;
+    const int j1 = min(P.ny, j0 + tc);
     const int s0 = max(0, j0 - R), s1 = min(P.ny, j1 + R);
     const int ns = s1 - s0;
     const long long qb = (long long)i * P.ny;
-    // piece counts of the window's sources -> offsets (block-wide, one warp)
+    __syncthreads();  // the previous tile's readers are done
+    PHASE_BEGIN();
     if (warp == 0) {
       int carry = 0;
       for (int base = 0; base < ns; base += 32) {
         const int t = base + lane;
         const int v = t < ns ? P.m_cnt[qb + s0 + t] : 0;
         const int inc = w_incl_add(v, lane);
-        if (t < ns) soff[t] = carry + inc - v;
+        if (t < ns) {
+          soff[t] = carry + inc - v;
+          sbase[t] = P.m_start[qb + s0 + t] - (carry + inc - v);
+        }
         carry += w_bcast(inc, 31);
       }
-      if (lane == 0) soff[ns] = carry;
-    }
-    __syncthreads();
-    const int total = soff[ns];
-    const bool staged = total <= P.stage_cap && R < 256;
-    if (staged) {
-      // warps take sources round-robin; lanes copy pieces (coalesced)
-      for (int q = warp; q < ns; q += P.warps_per_block) {
-        const long long ms = P.m_start[qb + s0 + q];
-        const int n = soff[q + 1] - soff[q];
-        const int o = soff[q];
-        for (int p = lane; p < n; p += 32) {
-          saf[o + p] = keyf(P.m_a[ms + p]);
-          sbf[o + p] = keyf(P.m_b[ms + p]);
-          sd8[o + p] = (unsigned char)P.m_l[ms + p];
-        }
-      }
-    }
-    __syncthreads();
-    auto src = [&](int jj) {
-      Src<Key> S;
-      const long long q = qb + jj;
-      const long long ms = P.m_start[q];
-      S.a = P.m_a + ms;
-      S.b = P.m_b + ms;
-      S.dx = P.m_l + ms;
-      S.np = P.m_cnt[q];
-      if (staged) {
-        const int o = soff[jj - s0];
-        S.af = saf + o;
-        S.bf = sbf + o;
-        S.d8 = sd8 + o;
-      } else {
-        S.af = nullptr;
-        S.bf = nullptr;
-        S.d8 = nullptr;
-      }
-      return S;
-    };
-    for (int j = j0 + warp; j < j1; j += P.warps_per_block)
-      gather_column<T>(L, P, i, j, G, P.stcap, P.bcap, wmax2, src, cur);
-    __syncthreads();
-  }
-}
-
-template <typename T>
-cudaError_t launch_pass2g(const P2GParams<T>& P, int blocks, cudaStream_t st) {
-  const size_t smem = (size_t)pass2g_smem(P.warps_per_block, P.stcap, P.bcap, P.tile, P.R, P.stage_cap);
-  cudaError_t e = cudaFuncSetAttribute(k_pass2g<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_pass2g<T><<<blocks, P.warps_per_block * 32, smem, st>>>(P);
-  return cudaGetLastError();
-}
-
-template cudaError_t launch_pass2g<float>(const P2GParams<float>&, int, cudaStream_t);
-template cudaError_t launch_pass2g<double>(const P2GParams<double>&, int, cudaStream_t);
-
-}  // namespace dexel
-
-namespace dexel {
-
-// Register-stack gather: a warp covers G consecutive output columns at once when the window
-// is short (lane -> (column, dy)), otherwise one column with the lanes looping over dy.
-// Each column collects its sources' intervals in a shared-memory bucket, which is then
-// sorted and united by the whole warp.
-long long pass2r_smem(int warps, int G, int bcap) {
-  const long long per = (long long)G * bcap * 2 * sizeof(ukey) + 2LL * bcap * sizeof(ukey) +
-                        2LL * bcap * sizeof(int) + 16LL * G + 16;
-  return warps * ((per + 15) & ~15LL);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(128) k_pass2r(P2GParams<T> P, int G) {
-  typedef typename H<T>::K Key;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const Lanes L{lane, 32};
-  const int bcap = P.bcap;
-  const long long per = (long long)G * bcap * 2 * sizeof(ukey) + 2LL * bcap * sizeof(ukey) +
-                        2LL * bcap * sizeof(int) + 16LL * G + 16;
-  unsigned char* wb = smem + (long long)warp * ((per + 15) & ~15LL);
-  ukey* bkl = (ukey*)wb;                   // G buckets of bcap left keys
-  ukey* bkr = bkl + (long long)G * bcap;   // ... right keys
-  ukey* ul = bkr + (long long)G * bcap;
-  ukey* ur = ul + bcap;
-  int* f0 = (int*)(ur + bcap);
-  int* f1 = f0 + bcap;
-  int* cnt = f1 + bcap;                    // G counters
-  const float wmaxf = P.wtabf[0];
-  const int W = 2 * P.R + 1;
-  const long long ncols = (long long)P.nx * P.ny;
-  ArenaCursor cur{0, 0};
-  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long c0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * G; c0 < ncols; c0 += nwarps * G) {
-    const int g_n = (int)min((long long)G, ncols - c0);
-    if (lane < G) cnt[lane] = 0;
-    wsync();
-    bool ok = true;
-    if (G > 1) {
-      const int g = lane / W, d = lane % W;
-      if (g < g_n) {
-        const long long item = c0 + g;
-        const int i = (int)(item / P.ny), j = (int)(item % P.ny);
-        const int dy = d - P.R, jj = j + dy;
-        if (jj >= 0 && jj < P.ny) {
-          const long long q = (long long)i * P.ny + jj;
-          const long long ms = P.m_start[q];
-          Src<Key> S;
-          S.a = P.m_a + ms; S.b = P.m_b + ms; S.dx = P.m_l + ms; S.np = P.m_cnt[q];
-          S.af = nullptr; S.bf = nullptr; S.d8 = nullptr;
-          ok = source_cover_reg<Key, true>(S, dy < 0 ? -dy : dy, P.reach, P.wtab, P.wtabf, wmaxf,
-                                     bkl + (long long)g * bcap, bkr + (long long)g * bcap, cnt + g, bcap);
-        }
-      }
-    } else {
-      const int i = (int)(c0 / P.ny), j = (int)(c0 % P.ny);
-      for (int dy = -P.R + lane; dy <= P.R && ok; dy += 32) {
-        const int jj = j + dy;
-        if (jj < 0 || jj >= P.ny) continue;
-        const long long q = (long long)i * P.ny + jj;
-        const long long ms = P.m_start[q];
-        Src<Key> S;
-        S.a = P.m_a + ms; S.b = P.m_b + ms; S.dx = P.m_l + ms; S.np = P.m_cnt[q];
-        S.af = nullptr; S.bf = nullptr; S.d8 = nullptr;
-        ok = source_cover_reg<Key, true>(S, dy < 0 ? -dy : dy, P.reach, P.wtab, P.wtabf, wmaxf, bkl, bkr,
-                                   cnt, bcap);
-      }
-    }
-    wsync();
-    if (w_any(!ok)) {
-      // too deep a stack or too many intervals: mark the columns for the fallback pass
-      if (lane < g_n) {
-        const long long item = c0 + lane;
-        const int i = (int)(item / P.ny), j = (int)(item % P.ny);
-        P.o_cnt[(long long)j * P.nx + i] = -1;
-        note_max(&P.ctr->max_state, cnt[lane]);  // intervals the column needs (when counted)
-      }
       if (lane == 0) {
-        set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
-        atomicAdd(&P.ctr->redo_cols, g_n);
+        soff[ns] = carry;
+        *sgb = P.c_start[qb + s0];
       }
-      wsync();
-      continue;
     }
-    for (int g = 0; g < g_n; ++g) {
-      const long long item = c0 + g;
-      const int i = (int)(item / P.ny), j = (int)(item % P.ny);
-      ukey* kl = bkl + (long long)g * bcap;
-      ukey* kr = bkr + (long long)g * bcap;
-      const int total = cnt[g];
-      const int n2 = pow2_at_least(total);
-      for (int t = total + lane; t < n2; t += 32) { kl[t] = ~0ULL; kr[t] = ~0ULL; }
-      wsync();
-      if (n2 > 1) warp_bitonic(L, kl, kr, n2);
-      const int no = total > 0 ? union_runs(L, kl, kr, total, true, f0, f1, ul, ur, kr, nullptr) : 0;
-      const long long s = arena_take(L, &P.ctr->arena_top[3], P.blk, cur, no);
-      const bool fits = s + no <= P.o_cap;
-      if (!fits) {
-        if (lane == 0) set_status(&P.ctr->status, ST_OVERFLOW_ARENA);
+    __syncthreads();
+    // runs of columns [ja, jb) whose window [ja - R, jb + R) fits the staging area; a single
+    // column whose window does not fit is covered by warp 0 in chunks of the staging size
+    for (int ja = j0; ja < j1;) {
+      const int qa = max(0, ja - R) - s0;
+      int jb = j1;
+      while (jb > ja + 1 && soff[min(P.ny, jb + R) - s0] - soff[qa] > stage_cap) --jb;
+      const int qe = min(P.ny, jb + R) - s0;
+      const int gofs = soff[qa];
+      const int tot = soff[qe] - gofs;
+      PHASE_COUNT(12, tot <= stage_cap ? 1 : 0);
+      PHASE_COUNT(13, 1);
+      if (tot <= stage_cap) {
+        const long long src = *sgb + gofs;
+        for (int g = threadIdx.x; g < tot; g += blockDim.x) {
+          saf[g] = P.c_af[src + g];
+          sbf[g] = P.c_bf[src + g];
+          sdx[g] = P.c_dx[src + g];
+        }
+        __syncthreads();
+        PHASE(0);
+        for (int j = ja + warp; j < jb; j += nwb) {
+          const int qlo = max(0, j - R) - s0, qhi = min(P.ny - 1, j + R) - s0;
+          int acc = 0;
+          const bool ok = column_cover<T>(P, L, j, s0, soff, sbase, qlo, qhi, soff[qlo],
+                                          soff[qhi + 1], saf - gofs, sbf - gofs, sdx - gofs, wt,
+                                          E, Q, M, bl, br, f0, f1, bcount, bcap, acc);
+          PHASE(1);
+          column_out<T>(P, L, j, i, ok, acc, bl, br, bcap, cur);
+          PHASE(3);
+        }
+        __syncthreads();  // the run's staged pieces are no longer read
       } else {
-        for (int q = lane; q < no; q += 32) { P.o_l[s + q] = ul[q]; P.o_r[s + q] = ur[q]; }
+        const int j = ja;
+        const int qlo = max(0, j - R) - s0, qhi = min(P.ny - 1, j + R) - s0;
+        const int gb = soff[qlo], ge = soff[qhi + 1];
+        int acc = 0;
+        bool ok = true;
+        for (int ga = gb; ga < ge; ga += stage_cap) {
+          const int gz = min(ge, ga + stage_cap);
+          const long long src = *sgb + ga;
+          for (int g = threadIdx.x; g < gz - ga; g += blockDim.x) {
+            saf[g] = P.c_af[src + g];
+            sbf[g] = P.c_bf[src + g];
+            sdx[g] = P.c_dx[src + g];
+          }
+          __syncthreads();
+          if (warp == 0 && ok)
+            ok = column_cover<T>(P, L, j, s0, soff, sbase, qlo, qhi, ga, gz, saf - ga, sbf - ga,
+                                 sdx - ga, wt, E, Q, M, bl, br, f0, f1, bcount, bcap, acc);
+          __syncthreads();
+        }
+        if (warp == 0) column_out<T>(P, L, j, i, ok, acc, bl, br, bcap, cur);
+        PHASE(1);
       }
-      if (lane == 0) {
-        const long long c = (long long)j * P.nx + i;
-        P.o_start[c] = fits ? s : 0;
-        P.o_cnt[c] = no;
-        note_max(&P.ctr->max_out, no);
-        add_total(&P.ctr->out_total, no);
-      }
-      wsync();
+      ja = jb;
     }
   }
 }
 
+// minb: blocks an SM the kernel is compiled for (2 caps its registers at 64)
 template <typename T>
-cudaError_t launch_pass2r(const P2GParams<T>& P, int G, int blocks, cudaStream_t st) {
-  const size_t smem = (size_t)pass2r_smem(4, G, P.bcap);
-  cudaError_t e = cudaFuncSetAttribute(k_pass2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_pass2t(const P2GParams<T>& P, int warps_per_block, int tc, int ntab,
+                          int stage_cap, int Q, int M, int minb, int blocks, cudaStream_t st) {
+  const P2TLayout Lo = p2t_layout(P.R, tc, ntab, stage_cap, warps_per_block, P.bcap);
+  auto kern = minb >= 2 ? k_pass2t<T, 2> : k_pass2t<T, 1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lo.total);
   if (e != cudaSuccess) return e;
-  k_pass2r<T><<<blocks, 128, smem, st>>>(P, G);
+  kern<<<blocks, warps_per_block * 32, (size_t)Lo.total, st>>>(P, tc, ntab, stage_cap, Q, M);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_pass2r<float>(const P2GParams<float>&, int, int, cudaStream_t);
-template cudaError_t launch_pass2r<double>(const P2GParams<double>&, int, int, cudaStream_t);
+template cudaError_t launch_pass2t<float>(const P2GParams<float>&, int, int, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_pass2t<double>(const P2GParams<double>&, int, int, int, int, int, int, int, int, cudaStream_t);
 
 }  // namespace dexel

@@ -48,6 +48,9 @@ struct Counters {
   int redo_cols;      // gather: output columns handed to the fallback kernel
   unsigned long long mid_total;   // S_mid pieces written
   unsigned long long out_total;   // pass-2 intervals written
+  unsigned long long bucket_sum;  // gather: intervals collected over all columns (sizing)
+  unsigned zmax_bits;             // gather: bits of max |finite height| of S_mid (float >= 0)
+  int pad2;
   unsigned long long phase[16];   // optional per-phase clock totals (DEXEL_PHASES builds)
 };
 

@@ -165,3 +165,73 @@ def test_output_capacity_retry(dx):
     out = ctx.run(dx.DILATE, dg, 4.0, capacity=3)
     ref = oracle.dilate(g, 4.0)
     assert out.nseg == ref.nseg
+
+
+def _stack_column(n, lo, hi, gap_frac):
+    """n equal segments in [lo, hi] separated by gaps of gap_frac of the pitch."""
+    pitch = (hi - lo) / n
+    return [(lo + q * pitch, lo + q * pitch + pitch * (1 - gap_frac)) for q in range(n)]
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_dense_windows_chunked(dx, op):
+    """Windows holding more pieces than one staging area (a band of columns with 2500 close
+    segments each): the tiled kernel covers such a column in several chunks."""
+    cols = {(i, j): _stack_column(2500, 0.1, 0.9, 0.3) for i in range(6, 9) for j in range(0, 16)}
+    g = shapes.from_columns(16, 16, 1 / 16, cols)
+    for k in (3.0, 6.5):
+        gg, off, z = _gpu(dx, g, op, k)
+        _compare_full(off, z, _ref(gg, op, k), False, f"dense {op} k={k}")
+
+
+def _runs_grid(op, n, nx, h, gap):
+    """Many disjoint runs in the result: for dilation a 3 x 3 block of columns of n thin
+    segments; for erosion every column holds n thick segments, so the dilated complement
+    keeps n runs."""
+    c = nx // 2
+    if op == "dilate":
+        cols = {(i, j): _stack_column(n, 0.05, 0.95, gap) for i in range(c - 1, c + 2)
+                for j in range(c - 1, c + 2)}
+    else:
+        cols = {(i, j): _stack_column(n, 0.05, 0.95, 1 - gap) for i in range(nx) for j in range(nx)}
+    return shapes.from_columns(nx, nx, h, cols)
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_many_runs_redo(dx, op):
+    """Output columns with ~700 disjoint runs, whose windows take several rounds: the union
+    outgrows the round bucket, the columns go to the second gather kernel (k_pass2c), and the
+    result is still exact."""
+    import torch
+    g = _runs_grid(op, 700, 8, 1 / 4096, 0.8)
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    ctx = dx.Context(0)
+    k = 1.0
+    out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
+    off, z = out.to_host()
+    ref = _ref(g, op, k)
+    assert np.diff(ref.col_off).max() > 600
+    _compare_full(off, z.astype(np.float64), ref, False, f"runs {op} k={k}")
+    assert ctx.stats()[5] > 0  # some columns were redone
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_per_line_sweep_path(dx, op, monkeypatch):
+    """The per-line sweep (used when a column's union outgrows every gather bucket, or on
+    request) against the oracle, and a case that needs it: 3000 runs in a column."""
+    import torch
+    monkeypatch.setenv("DEXEL_PASS2", "sweep")
+    rng = np.random.default_rng(11)
+    g = shapes.random_grid(rng, 23, 31, 6, fill=0.8, point_frac=0.05, h=1 / 32)
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    ctx = dx.Context(0)
+    for k in (1.0, 3.7, 9.0):
+        out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
+        off, z = out.to_host()
+        _compare_full(off, z.astype(np.float64), _ref(g, op, k), False, f"sweep {op} k={k}")
+    monkeypatch.delenv("DEXEL_PASS2")
+    g = _runs_grid(op, 3000, 6, 1 / 32768, 0.8)
+    gg, off, z = _gpu(dx, g, op, 1.0)
+    ref = _ref(gg, op, 1.0)
+    assert np.diff(ref.col_off).max() > 2500
+    _compare_full(off, z, ref, False, f"3000 runs {op}")
