@@ -31,6 +31,7 @@ struct dexel_ctx {
   long long launches = 0;
   // capacities learnt from earlier calls (grown on overflow)
   int capA = 1024, capR = 1024, capS = 4096;
+  bool sweep1 = false;  // pass 1 as the per-row sweep instead of the window gather
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
   // needed the redo launch
@@ -462,11 +463,42 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       continue;
     }
     mark(ctx, 2, st);
-    CK(launch_pass1<T>(p1, nw1 / kWarpsPerBlock, st));
+    bool sweep1 = ctx->sweep1 || K > kGatherMaxReach1;
+    if (!sweep1) {
+      // gather: tiles of tc columns whose window's events (two per segment, two more per
+      // column for a complement) fit ecap; a window beyond ecap hands the call to the sweep
+      const double ev_col = 2.0 * (double)in->nseg / (double)std::max<long long>(ncols, 1) + (erode ? 2.0 : 0.0);
+      // (a tile of about 2K columns: a column's window then covers about half the tile's)
+      int ecap = 2048, tc = 8;
+      while (tc < 64 && tc < 2 * K) tc <<= 1;
+      while (tc > 8 && (tc + 2.0 * K + 1) * ev_col * 1.5 > 16384) tc >>= 1;
+      while (ecap < 16384 && (tc + 2.0 * K + 1) * ev_col * 1.5 > ecap) ecap <<= 1;
+      int obuf = 256;
+      while (obuf > 32 && pass1g_smem<T>(tc, K, ecap, obuf) > (220LL << 10)) obuf >>= 1;
+      while (ecap > 1024 && pass1g_smem<T>(tc, K, ecap, obuf) > (220LL << 10)) ecap >>= 1;
+      const long long sm1 = pass1g_smem<T>(tc, K, ecap, obuf);
+      const int per_sm = (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / sm1));
+      const long long ntiles = (long long)ny * ((nx + tc - 1) / tc);
+      const int b1 = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, ntiles));
+      CK(launch_pass1g<T>(p1, tc, ecap, obuf, b1, st));
+      ++ctx->launches;
+      CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
+        CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(&ctr->arena_top[1], 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(&ctr->mid_total, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(&ctr->max_pieces, 0, sizeof(int), st));
+        sweep1 = true;
+      }
+    }
+    if (sweep1) {
+      CK(launch_pass1<T>(p1, nw1 / kWarpsPerBlock, st));
+      ++ctx->launches;
+      CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
     mark(ctx, 3, st);
-    ++ctx->launches;
-    CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
     ctx->needF = std::max<long long>(ctx->needF, (long long)hc.arena_top[0]);
     ctx->needM = std::max<long long>(ctx->needM, (long long)hc.arena_top[1]);
     ctx->stats[6] = hc.status;
@@ -902,6 +934,8 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   const char* mode = getenv("DEXEL_PASS2");
   c->sweep2 = mode && strcmp(mode, "sweep") == 0;
+  const char* mode1 = getenv("DEXEL_PASS1");
+  c->sweep1 = mode1 && strcmp(mode1, "sweep") == 0;
   *ctx = c;
   return DEXEL_OK;
 }

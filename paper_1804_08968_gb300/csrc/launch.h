@@ -9,11 +9,18 @@ constexpr int kWarpsPerBlock = 4;
 // window gather (pass 2): largest reach it takes (beyond it the per-line sweep runs), and the
 // per-round limits of a lane in k_pass2t (appended intervals, pieces taken)
 constexpr int kGatherMaxReach = 1024;
+// pass-1 gather: the open sources of a window are a 128-bit mask, so 2R + 1 <= 127
+constexpr int kGatherMaxReach1 = 63;
 constexpr int kRoundAppends = 2;
 constexpr int kRoundPieces = 32;
 
 template <typename T>
 cudaError_t launch_pass1(const P1Params<T>& P, int blocks, cudaStream_t st);
+template <typename T>
+cudaError_t launch_pass1g(const P1Params<T>& P, int tc, int ecap, int obuf, int blocks,
+                          cudaStream_t st);
+template <typename T>
+long long pass1g_smem(int tc, int R, int ecap, int obuf);
 template <typename T>
 cudaError_t launch_pass2(const P2Params<T>& P, int blocks, cudaStream_t st);
 template <typename T>
