@@ -158,9 +158,10 @@ int64_t dexel_last_launches(const dexel_ctx* ctx);
 /* Turn per-stage timing on or off (off by default).  When on, each call brackets its
  * stages with CUDA events on the call's stream; dexel_last_stage_ms then reports the
  * device time of each stage of the last call (summed over both offsets of a closing or
- * opening): [0] validation + tables, [1] pass 1 (x-extrusion sweep), [2] pass 2 (y dilation
- * with per-piece radius), [3] output count + scan, [4] output write.  Returns the number of entries written
- * (at most max). */
+ * opening): [0] validation + tables, [1] pass 1 (x extrusion), [2] pass 2 (y dilation with
+ * per-piece radius: the gather kernels, or the sweep; the float copy of S_mid made before
+ * the gather is in no stage), [3] output count + scan, [4] output write.  Returns the number
+ * of entries written (at most max). */
 void dexel_set_profiling(dexel_ctx* ctx, int on);
 int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max);
 

@@ -523,7 +523,6 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       pg.o_start = (long long*)postart; pg.o_cnt = (int*)pocnt;
       pg.blk = 256;
       pg.ctr = ctr;
-      mark(ctx, 4, st);
       // line-contiguous float copy of S_mid in the (now free) pass-1 forward arena
       {
         const long long capC = (long long)(bF / 10);
@@ -571,6 +570,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         if (stage_cap < 256) return DEXEL_ERR_CAPACITY;  // not reached for K <= kGatherMaxReach
         const int ntiles_cap = nx * ((ny + tc - 1) / tc);
         const int tblocks = std::max(1, std::min(sms * per_sm, ntiles_cap));
+        mark(ctx, 4, st);  // the stage covers the pass-2 kernels only (not the copy above)
         CK(launch_pass2t<T>(pg, tw, tc, ntab, stage_cap, kRoundAppends, kRoundPieces, per_sm,
                             tblocks, st));
         ++ctx->launches;
