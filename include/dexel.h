@@ -123,14 +123,26 @@ dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
                          dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
                          void* stream);
 
-/* Batched offsets: nshapes independent grids, each with its own radius and operation.
- * ins / k / ops / outs are HOST arrays of nshapes entries whose grid pointers are device
- * pointers.  d_status (device, nshapes int32) receives each shape's dexel_status.  The
- * return value is the first failing status (or DEXEL_OK). */
+/* Batched offsets: nshapes independent grids, each with its own radius and operation
+ * (Sec. 3.3 applied to a table of shapes; no counterpart in the paper, which offsets one
+ * model at a time).  ins / k / ops / outs are HOST arrays of nshapes entries whose grid
+ * pointers are device pointers; outs[s].nseg receives each shape's segment count (the
+ * needed count when its status is DEXEL_ERR_CAPACITY).  All shapes run together, one launch
+ * per stage; the sequence is recorded as a CUDA graph and replayed when the next call has
+ * the same shapes (sizes, radii, operations); tile shapes are autotuned on the first call of
+ * such a signature (see dexel_set_batch_autotune).  Scratch is library-owned (ws is used
+ * only by shapes that fall back to the single-shape path: reach above 63 spacings, or a
+ * window beyond the batch kernels' limits).  d_status (device, nshapes int32, may be NULL)
+ * receives each shape's dexel_status.  Returns the first failing status (or DEXEL_OK);
+ * DEXEL_ERR_INVALID_ARG when any argument is invalid (nothing runs).  Synchronises the
+ * stream before returning. */
 dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_in* ins,
                                   const double* k, const dexel_op* ops, dexel_mode mode,
                                   dexel_grid_out* outs, void* ws, size_t ws_bytes,
                                   int32_t* d_status, void* stream);
+
+/* Turn the tile autotuning of dexel_offset_batched on (default) or off. */
+void dexel_set_batch_autotune(dexel_ctx* ctx, int on);
 
 /* Allocation-free dilation or erosion for small grids (the paper has no counterpart; this is
  * a deployment variant).  For callers that cannot allocate device memory when they need an

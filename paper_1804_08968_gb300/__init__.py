@@ -72,6 +72,8 @@ def lib():
                                            ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                            ctypes.POINTER(_Out), P, ctypes.c_size_t, P, P]
+        L.dexel_set_batch_autotune.argtypes = [P, ctypes.c_int]
+        L.dexel_set_batch_autotune.restype = None
         L.dexel_workspace_size.argtypes = [ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int]
         L.dexel_workspace_size.restype = ctypes.c_size_t
         L.dexel_last_required.argtypes = [P]
@@ -201,6 +203,55 @@ class Context:
             self._cap_hint[key] = cap
             return Grid(g.nx, g.ny, g.h, off, z[: out.nseg])
         raise DexelError(-3, "dexel offset (output capacity)")
+
+    def run_batched(self, ops, grids, ks, stream=None, capacities=None):
+        """Offsets of many grids in one batched call (dexel_offset_batched): ops[s] in
+        DILATE / ERODE / CLOSE / OPEN, grids all FP64 or all FP32.  Returns the output grids;
+        a shape whose output did not fit is run again with the size the library reported."""
+        torch = _torch()
+        n = len(grids)
+        if n == 0:
+            return []
+        mode = grids[0].mode
+        if any(g.mode != mode for g in grids):
+            raise ValueError("all grids of a batch share one precision")
+        caps = list(capacities) if capacities else [max(2 * g.nseg + g.nx * g.ny // 4, 1024) for g in grids]
+        st = self._stream(stream)
+        todo = list(range(n))
+        res = [None] * n
+        for _ in range(3):
+            ins = (_In * len(todo))(*[grids[s]._in() for s in todo])
+            outs_t = []
+            outs = (_Out * len(todo))()
+            for q, s in enumerate(todo):
+                g = grids[s]
+                off = torch.empty(g.nx * g.ny + 1, dtype=torch.int32, device=g.col_off.device)
+                z = torch.empty((caps[s], 2), dtype=g.z.dtype, device=g.z.device)
+                outs_t.append((off, z))
+                outs[q] = _Out(off.data_ptr(), z.data_ptr(), caps[s], 0)
+            kk = (ctypes.c_double * len(todo))(*[float(ks[s]) for s in todo])
+            oo = (ctypes.c_int * len(todo))(*[int(ops[s]) for s in todo])
+            dst = torch.zeros(len(todo), dtype=torch.int32, device=grids[todo[0]].col_off.device)
+            rc = lib().dexel_offset_batched(self.ptr, len(todo), ins, kk, oo, mode, outs, None, 0,
+                                            ctypes.c_void_p(dst.data_ptr()), st)
+            stat = dst.cpu().numpy()
+            again = []
+            for q, s in enumerate(todo):
+                if stat[q] == 0:
+                    off, z = outs_t[q]
+                    res[s] = Grid(grids[s].nx, grids[s].ny, grids[s].h, off, z[: outs[q].nseg])
+                elif stat[q] == -3 and outs[q].nseg > caps[s]:
+                    caps[s] = int(outs[q].nseg) + 16
+                    again.append(s)
+                else:
+                    raise DexelError(int(stat[q]), f"dexel_offset_batched shape {s} (rc {rc})")
+            if not again:
+                return res
+            todo = again
+        raise DexelError(-3, "dexel_offset_batched (output capacity)")
+
+    def set_batch_autotune(self, on: bool) -> None:
+        lib().dexel_set_batch_autotune(self.ptr, 1 if on else 0)
 
     def validate(self, g: Grid, stream=None) -> int:
         gin = g._in()

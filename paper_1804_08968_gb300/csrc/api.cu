@@ -15,6 +15,7 @@
 
 #include "../../include/dexel.h"
 #include "launch.h"
+#include "emit.cuh"
 
 using namespace dexel;
 
@@ -36,6 +37,8 @@ struct dexel_ctx {
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
   // needed the redo launch
   std::map<int, int> ccap;
+  BatchEngine* batch = nullptr;  // batched offsets (created on first use)
+  bool batch_autotune = true;
   long long needF = 0, needM = 0, needO = 0;  // arena entries
   Counters host_ctr{};
   // optional per-stage timing with CUDA events on the call's stream
@@ -99,46 +102,6 @@ __global__ void k_tables(double kk, double h, int nmax, int K, double* wtab, int
   }
 }
 
-// One output column: optional complement (erosion), rounding to T, and re-merge of pieces
-// that touch after rounding.  Returns the count; writes pieces when out != nullptr.
-template <typename T>
-__device__ int finalize_column(const ukey* lk, const ukey* rk, int m, bool erode, T* out) {
-  int cnt = 0;
-  T ca = 0, cb = 0;
-  bool have = false;
-  auto push = [&](double a, double b) {
-    const T ta = (T)a, tb = (T)b;
-    if (erode && !(ta < tb)) return;
-    if (have && ta <= cb) {
-      if (tb > cb) cb = tb;
-      return;
-    }
-    if (have) {
-      if (out) { out[2 * cnt] = ca; out[2 * cnt + 1] = cb; }
-      ++cnt;
-    }
-    ca = ta;
-    cb = tb;
-    have = true;
-  };
-  auto l = [&](int t) { return dval(lk[t]); };
-  auto r = [&](int t) { return dval(rk[t]); };
-  if (!erode) {
-    for (int t = 0; t < m; ++t) push(l(t), r(t));
-  } else if (m == 0) {
-    push(-INFINITY, INFINITY);
-  } else {
-    if (l(0) > -INFINITY) push(-INFINITY, l(0));
-    for (int t = 0; t + 1 < m; ++t) push(r(t), l(t + 1));
-    if (r(m - 1) < INFINITY) push(r(m - 1), INFINITY);
-  }
-  if (have) {
-    if (out) { out[2 * cnt] = ca; out[2 * cnt + 1] = cb; }
-    ++cnt;
-  }
-  return cnt;
-}
-
 template <typename T>
 __global__ void k_count(int ncols, const long long* ostart, const int* ocnt, const ukey* ol,
                         const ukey* orr, int erode, long long* cnt) {
@@ -155,87 +118,6 @@ __global__ void k_write(int ncols, const long long* ostart, const int* ocnt, con
   if (c >= ncols) return;
   const long long s = ostart[c];
   finalize_column<T>(ol + s, orr + s, ocnt[c], erode != 0, z + 2 * pos[c]);
-}
-
-// exclusive scan of cnt[0..n) (int64) in three launches; writes pos (int64) and col_off
-constexpr int kScanThreads = 256, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
-
-template <typename C>
-__global__ void k_scan1(long long n, const C* cnt, long long* pos, long long* sums) {
-  __shared__ long long sh[kScanThreads];
-  const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
-  long long v[kScanPer];
-  long long s = 0;
-  for (int q = 0; q < kScanPer; ++q) {
-    v[q] = base + q < n ? (long long)cnt[base + q] : 0;
-    s += v[q];
-  }
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < kScanThreads; o <<= 1) {
-    const long long u = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-    __syncthreads();
-    sh[threadIdx.x] += u;
-    __syncthreads();
-  }
-  long long run = sh[threadIdx.x] - s;
-  for (int q = 0; q < kScanPer; ++q) {
-    if (base + q < n) pos[base + q] = run;
-    run += v[q];
-  }
-  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = sh[threadIdx.x];
-}
-
-// Line-contiguous float copy of S_mid for the gather: column q = i*ny + j gets the range
-// c_start[q] = pos[q] + sums[q / kScanTile] (exclusive scan of the piece counts in q order), so
-// that the pieces of any run of sources of a line are one contiguous range; ends as float
-// approximations (keyf), dx as short.  Also records max |finite end| for the float filter.
-template <typename Key>
-__global__ void k_mid_pack(long long ncols, const long long* m_start, const int* m_cnt,
-                           const Key* m_a, const Key* m_b, const short* m_l,
-                           const long long* pos, const long long* sums, long long* c_start,
-                           float* c_af, float* c_bf, short* c_dx, Counters* ctr) {
-  const int lane = threadIdx.x & 31;
-  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-  float zm = 0.0f;
-  for (long long q = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < ncols; q += nw) {
-    const long long c = pos[q] + sums[q / kScanTile];
-    if (lane == 0) c_start[q] = c;
-    const long long ms = m_start[q];
-    const int n = m_cnt[q];
-    for (int p = lane; p < n; p += 32) {
-      const float a = keyf(m_a[ms + p]), b = keyf(m_b[ms + p]);
-      c_af[c + p] = a;
-      c_bf[c + p] = b;
-      c_dx[c + p] = m_l[ms + p];
-      if (fabsf(a) < __builtin_huge_valf()) zm = fmaxf(zm, fabsf(a));
-      if (fabsf(b) < __builtin_huge_valf()) zm = fmaxf(zm, fabsf(b));
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) zm = fmaxf(zm, __shfl_xor_sync(0xffffffffu, zm, o));
-  if (lane == 0 && zm > 0.0f) atomicMax(&ctr->zmax_bits, __float_as_uint(zm));
-}
-
-__global__ void k_scan2(long long nb, long long* sums) {
-  __shared__ long long sh[kScanThreads];
-  long long carry = 0;
-  for (long long b0 = 0; b0 < nb; b0 += kScanThreads) {
-    const long long b = b0 + threadIdx.x;
-    const long long v = b < nb ? sums[b] : 0;
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-      const long long u = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-      __syncthreads();
-      sh[threadIdx.x] += u;
-      __syncthreads();
-    }
-    if (b < nb) sums[b] = carry + sh[threadIdx.x] - v;
-    const long long tot = sh[kScanThreads - 1];
-    __syncthreads();
-    carry += tot;
-  }
-  if (threadIdx.x == 0) sums[nb] = carry;
 }
 
 __global__ void k_scan3(long long n, long long* pos, const long long* sums, int* col_off,
@@ -945,6 +827,7 @@ void dexel_ctx_destroy(dexel_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->own) cudaFree(ctx->own);
   if (ctx->mid) cudaFree(ctx->mid);
+  batch_engine_destroy(ctx->batch);
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
   delete ctx;
@@ -1075,12 +958,64 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
                                   dexel_grid_out* outs, void* ws, size_t ws_bytes,
                                   int32_t* d_status, void* stream) {
   if (!ctx || nshapes < 0 || (nshapes > 0 && (!ins || !k || !ops || !outs))) return DEXEL_ERR_INVALID_ARG;
-  dexel_status first = DEXEL_OK;
-  std::vector<int32_t> st(nshapes > 0 ? nshapes : 1, 0);
-  long long launches = 0;
-  double stage[5] = {0, 0, 0, 0, 0};
-  long long stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (mode != DEXEL_FP64 && mode != DEXEL_FP32_PRED64) return DEXEL_ERR_INVALID_ARG;
   for (int s = 0; s < nshapes; ++s) {
+    if (check_in(&ins[s], k[s]) != DEXEL_OK) return DEXEL_ERR_INVALID_ARG;
+    if (ops[s] < DEXEL_DILATE || ops[s] > DEXEL_OPEN) return DEXEL_ERR_INVALID_ARG;
+    const dexel_grid_out& o = outs[s];
+    if (!o.col_off || o.capacity_seg < 0 || (o.capacity_seg > 0 && !o.z)) return DEXEL_ERR_INVALID_ARG;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DEXEL_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!ctx->batch) {
+    ctx->batch = batch_engine_create(ctx->device, ctx->sm_count);
+    if (!ctx->batch) return DEXEL_ERR_NOMEM;
+    batch_set_autotune(ctx->batch, ctx->batch_autotune ? 1 : 0);
+  }
+  const int fp32 = mode == DEXEL_FP32_PRED64 ? 1 : 0;
+  long long launches = 0;
+  // first offset of every shape (the dilation of a closing, the erosion of an opening); the
+  // result of a closing / opening goes to engine memory, the others straight to the caller
+  std::vector<BatchItem> A(nshapes);
+  for (int s = 0; s < nshapes; ++s) {
+    const dexel_op op = ops[s];
+    A[s] = BatchItem{ins[s].nx, ins[s].ny, ins[s].h, ins[s].col_off, ins[s].z, ins[s].nseg, k[s],
+                     (op == DEXEL_ERODE || op == DEXEL_OPEN) ? 1 : 0, nullptr, nullptr, 0};
+    if (op == DEXEL_DILATE || op == DEXEL_ERODE) {
+      A[s].out_col_off = outs[s].col_off;
+      A[s].out_z = outs[s].z;
+      A[s].out_cap = outs[s].capacity_seg;
+    }
+  }
+  std::vector<int> stA, stB;
+  std::vector<long long> nA, nB;
+  int rc = batch_run(ctx->batch, fp32, A, st, stA, nA, &launches);
+  if (rc != DEXEL_OK) return (dexel_status)rc;
+  // second offset of closings / openings, from the engine-held first results
+  std::vector<BatchItem> B;
+  std::vector<int> which;
+  for (int s = 0; s < nshapes; ++s) {
+    if ((ops[s] == DEXEL_CLOSE || ops[s] == DEXEL_OPEN) && stA[s] == DEXEL_OK) {
+      B.push_back(BatchItem{ins[s].nx, ins[s].ny, ins[s].h, A[s].out_col_off, A[s].out_z, nA[s],
+                            k[s], ops[s] == DEXEL_CLOSE ? 1 : 0, outs[s].col_off, outs[s].z,
+                            outs[s].capacity_seg});
+      which.push_back(s);
+    }
+  }
+  std::vector<int> fin(nshapes);
+  std::vector<long long> fseg(nshapes);
+  for (int s = 0; s < nshapes; ++s) { fin[s] = stA[s]; fseg[s] = nA[s]; }
+  if (!B.empty()) {
+    rc = batch_run(ctx->batch, fp32, B, st, stB, nB, &launches);
+    if (rc != DEXEL_OK) return (dexel_status)rc;
+    for (size_t q = 0; q < which.size(); ++q) {
+      fin[which[q]] = stB[q];
+      fseg[which[q]] = nB[q];
+    }
+  }
+  // shapes beyond the batch kernels' limits: the single-shape path
+  for (int s = 0; s < nshapes; ++s) {
+    if (fin[s] != 1) continue;
     dexel_status r;
     switch (ops[s]) {
       case DEXEL_DILATE: r = dexel_dilate(ctx, &ins[s], k[s], mode, &outs[s], ws, ws_bytes, stream); break;
@@ -1088,22 +1023,30 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
       default: r = dexel_morph(ctx, &ins[s], k[s], ops[s], mode, &outs[s], ws, ws_bytes, stream); break;
     }
     launches += ctx->launches;
-    for (int q = 0; q < 5; ++q) stage[q] += ctx->stage_ms[q];
-    for (int q = 0; q < 4; ++q) stats[q] += ctx->stats[q];
-    for (int q = 4; q < 8; ++q) stats[q] = std::max(stats[q], ctx->stats[q]);
-    st[s] = (int32_t)r;
-    if (r != DEXEL_OK && first == DEXEL_OK) first = r;
+    fin[s] = r;
+    fseg[s] = outs[s].nseg;
+  }
+  dexel_status first = DEXEL_OK;
+  std::vector<int32_t> hst(nshapes > 0 ? nshapes : 1, 0);
+  for (int s = 0; s < nshapes; ++s) {
+    outs[s].nseg = fseg[s];
+    hst[s] = (int32_t)fin[s];
+    if (fin[s] != DEXEL_OK && first == DEXEL_OK) first = (dexel_status)fin[s];
   }
   ctx->launches = launches;
-  for (int q = 0; q < 5; ++q) ctx->stage_ms[q] = stage[q];
-  for (int q = 0; q < 8; ++q) ctx->stats[q] = stats[q];
   if (d_status && nshapes > 0) {
-    if (cudaMemcpyAsync(d_status, st.data(), sizeof(int32_t) * nshapes, cudaMemcpyHostToDevice,
-                        (cudaStream_t)stream) != cudaSuccess ||
-        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+    if (cudaMemcpyAsync(d_status, hst.data(), sizeof(int32_t) * nshapes, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
       return DEXEL_ERR_CUDA;
   }
   return first;
+}
+
+void dexel_set_batch_autotune(dexel_ctx* ctx, int on) {
+  if (!ctx) return;
+  ctx->batch_autotune = on != 0;
+  if (ctx->batch) batch_set_autotune(ctx->batch, on);
 }
 
 dexel_status dexel_offset_noalloc(const dexel_grid_in* in, double k, dexel_op op, dexel_mode mode,

@@ -1,6 +1,8 @@
 // Internal launch wrappers shared by the translation units of libdexel.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <vector>
 #include "gather2.cuh"
 
 namespace dexel {
@@ -28,5 +30,29 @@ cudaError_t launch_pass2t(const P2GParams<T>& P, int warps_per_block, int tc, in
                           int stage_cap, int Q, int M, int minb, int blocks, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pass2c(const P2GParams<T>& P, int warps_per_block, int blocks, cudaStream_t st);
+
+// Batched offsets (batch.cu): one launch per stage over many shapes.  An item's status after
+// batch_run: DEXEL_OK, DEXEL_ERR_BAD_CSR, DEXEL_ERR_CAPACITY (nseg holds the need), or 1 when
+// the item needs the single-shape path (a window beyond the batch kernels' limits).  An item
+// with out_z == nullptr gets its output in engine-owned memory (pointers set in the item,
+// valid until the engine's next run).
+struct BatchItem {
+  int nx, ny;
+  double h;
+  const int* col_off;
+  const void* z;
+  long long nseg;
+  double k;
+  int erode;
+  int* out_col_off;
+  void* out_z;
+  long long out_cap;
+};
+struct BatchEngine;
+BatchEngine* batch_engine_create(int device, int sms);
+void batch_engine_destroy(BatchEngine* e);
+void batch_set_autotune(BatchEngine* e, int on);
+int batch_run(BatchEngine* e, int fp32, std::vector<BatchItem>& items, cudaStream_t st,
+              std::vector<int>& status, std::vector<long long>& nseg, long long* launches);
 
 }  // namespace dexel

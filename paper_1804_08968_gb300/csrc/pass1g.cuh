@@ -233,7 +233,11 @@ __device__ __forceinline__ void pass1g_tile(const P1Params<T>& P, long long tile
     const int e0 = eoff[qa];
     const int E = eoff[qe] - e0;
     if (E > ecap) {  // one column's window holds more events than fit: the sweep takes over
-      if (threadIdx.x == 0) set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
+      if (threadIdx.x == 0) {
+        set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
+        P.m_start[(long long)ia * P.ny + j] = -1;  // marks the column (count 0)
+        P.m_cnt[(long long)ia * P.ny + j] = 0;
+      }
       ia = ib;
       continue;
     }
