@@ -97,7 +97,7 @@ __global__ void k_b_tables(const BShape<T>* S, const long long* tabb, int ns, lo
   }
 }
 
-template <typename T>
+template <typename T, int NW>
 __global__ void __launch_bounds__(256) k_b_pass1(const BShape<T>* S, const long long* t1b,
                                                  int ns, long long ntiles, int ecap, int obuf,
                                                  const int* sst) {
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) k_b_pass1(const BShape<T>* S, const long 
     const int s = find_base(t1b, ns, gt);
     if (sst[s] & BS_BAD) continue;
     const P1Params<T> P = S[s].p1;
-    pass1g_tile<T>(P, gt - t1b[s], S[s].tc1, ecap, obuf, smem, cur);
+    pass1g_tile<T, NW>(P, gt - t1b[s], S[s].tc1, ecap, obuf, smem, cur);
   }
 }
 
@@ -327,6 +327,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     base2 = std::max(base2, p2t_layout(K[s], 128, nt, 0, wpb2, bcap).total);
   }
   const int minb = maxK <= 12 ? 2 : 1;
+  const int nw1 = mask_words(maxK);  // pass-1 mask width (every shape's reach fits)
   const long long budget2 = minb == 2 ? (108LL << 10) : (220LL << 10);
   const int stage_cap = (int)std::max<long long>(512, (budget2 - base2 - 64) / 10);
   long long sm2 = 0;
@@ -472,7 +473,11 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
         k_b_tables<T><<<(unsigned)((ntab + thr - 1) / thr), thr, 0, s_>>>(dS, d_tabb, ns, ntab, wtab, wtabf);
       const int per1 = (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / sm1));
       const unsigned b1 = (unsigned)std::max<long long>(1, std::min<long long>((long long)E->sms * per1, nt1));
-      if (nt1 > 0) k_b_pass1<T><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
+      if (nt1 > 0) {
+        if (nw1 == 1) k_b_pass1<T, 1><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
+        else if (nw1 == 2) k_b_pass1<T, 2><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
+        else k_b_pass1<T, 4><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
+      }
       const long long nb = (ncols + kScanTile - 1) / kScanTile;
       if (ncols > 0) {
         k_scan1<int><<<(unsigned)nb, kScanThreads, 0, s_>>>(ncols, m_cnt, pos, sums);
@@ -498,7 +503,9 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       if (nl) *nl += 12;
       return cudaGetLastError();
     };
-    BK(cudaFuncSetAttribute(k_b_pass1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    BK(cudaFuncSetAttribute(k_b_pass1<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    BK(cudaFuncSetAttribute(k_b_pass1<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    BK(cudaFuncSetAttribute(k_b_pass1<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     BK(cudaFuncSetAttribute(k_b_pass2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     BK(cudaFuncSetAttribute(k_b_pass2<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     std::vector<long long> fullsig = sig;

@@ -11,8 +11,8 @@ constexpr int kWarpsPerBlock = 4;
 // window gather (pass 2): largest reach it takes (beyond it the per-line sweep runs), and the
 // per-round limits of a lane in k_pass2t (appended intervals, pieces taken)
 constexpr int kGatherMaxReach = 1024;
-// pass-1 gather: the open sources of a window are a 128-bit mask, so 2R + 1 <= 127
-constexpr int kGatherMaxReach1 = 63;
+// pass-1 gather: the open sources of a window are a mask of up to 256 bits, 2R + 1 <= 255
+constexpr int kGatherMaxReach1 = 127;
 constexpr int kRoundAppends = 2;
 constexpr int kRoundPieces = 32;
 

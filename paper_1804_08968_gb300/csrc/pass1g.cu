@@ -4,22 +4,24 @@
 
 namespace dexel {
 
-template <typename T>
+template <typename T, int NW>
 __global__ void __launch_bounds__(256) k_pass1g(P1Params<T> P, int tc, int ecap, int obuf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const long long ntiles = (long long)P.ny * ((P.nx + tc - 1) / tc);
   ArenaCursor cur{0, 0};
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-    pass1g_tile<T>(P, tile, tc, ecap, obuf, smem, cur);
+    pass1g_tile<T, NW>(P, tile, tc, ecap, obuf, smem, cur);
 }
 
 template <typename T>
 cudaError_t launch_pass1g(const P1Params<T>& P, int tc, int ecap, int obuf, int blocks,
                           cudaStream_t st) {
   const size_t smem = (size_t)pass1g_smem<T>(tc, P.K, ecap, obuf);
-  cudaError_t e = cudaFuncSetAttribute(k_pass1g<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int nw = mask_words(P.K);
+  auto kern = nw == 1 ? k_pass1g<T, 1> : (nw == 2 ? k_pass1g<T, 2> : k_pass1g<T, 4>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_pass1g<T><<<blocks, 256, smem, st>>>(P, tc, ecap, obuf);
+  kern<<<blocks, 256, smem, st>>>(P, tc, ecap, obuf);
   return cudaGetLastError();
 }
 

@@ -13,9 +13,10 @@
 // events of the tile's window (tc + 2R source columns, contiguous in the row-major input) are
 // staged in shared memory and sorted once by (height, open before close).  A warp then walks
 // the sorted events for one output column: the set of open sources is a bit mask (bit
-// i' - i + R; one 64-bit word for R < 32, two up to R = 63) kept by an XOR scan over the
-// lanes, the nearest open source is found from the mask with find-first-set, and the group
-// values O, P and the run starts follow from segmented scans.  The pieces go to a per-warp
+// i' - i + R; one 64-bit word for R < 32, two up to R = 63, four up to 127) kept by an XOR
+// scan over the lanes, the nearest open source is found from the mask with find-first-set,
+// and the group values O, P and the run starts follow from segmented scans.  The pieces go
+// to a per-warp
 // buffer in shared memory and are copied out once the column's count has reserved its place
 // (a column with more pieces than the buffer is walked a second time, straight into place).
 #pragma once
@@ -37,17 +38,36 @@ DXI ukey key_out<ukey>(ukey u) { return u; }
 template <>
 DXI float key_out<float>(ukey u) { return (float)dval(u); }
 
-// min |b - R| over the set bits b of the 128-bit mask (lo: bits 0..63, hi: 64..127), R <= 63
-DXI int nearest_label(ukey lo, ukey hi, int R) {
+// The open sources of a window as a bit mask of NW 64-bit words (bit b = source i - R + b).
+template <int NW>
+struct Mask {
+  ukey w[NW];
+};
+
+// min |b - R| over the set bits b of the mask (the nearest open source), R < 64 NW / 2
+template <int NW>
+DXI int nearest_label(const Mask<NW>& m, int R) {
   int best = kNoLabel;
-  const ukey up = lo & (~0ULL << R);
 #if defined(__CUDA_ARCH__)
-  if (up) best = (__ffsll((long long)up) - 1) - R;
-  else if (hi) best = 64 + (__ffsll((long long)hi) - 1) - R;
-  const ukey down = lo & (R >= 63 ? ~0ULL : ((2ULL << R) - 1));
-  if (down) {
-    const int d = R - (63 - __clzll((long long)down));
-    best = d < best ? d : best;
+  const int wr = R >> 6, br = R & 63;
+  // upwards: the lowest set bit >= R
+#pragma unroll
+  for (int q = 0; q < NW; ++q) {
+    if (q < wr || best != kNoLabel) continue;
+    const ukey v = q == wr ? (m.w[q] & (~0ULL << br)) : m.w[q];
+    if (v) best = 64 * q + (__ffsll((long long)v) - 1) - R;
+  }
+  // downwards: the highest set bit <= R
+  bool found = false;
+#pragma unroll
+  for (int q = NW - 1; q >= 0; --q) {
+    if (q > wr || found) continue;
+    const ukey v = q == wr ? (m.w[q] & (br >= 63 ? ~0ULL : ((2ULL << br) - 1))) : m.w[q];
+    if (v) {
+      const int d = R - (64 * q + 63 - __clzll((long long)v));
+      best = d < best ? d : best;
+      found = true;
+    }
   }
 #endif
   return best;
@@ -56,12 +76,14 @@ DXI int nearest_label(ukey lo, ukey hi, int R) {
 // Walks the sorted events ek/ep[0, E) for output column i (sources s0 + q, payload
 // (close << 16) | q); returns the number of S_mid pieces.  With oa != null the pieces with
 // index < cap are written at oa, ob, ol (a, b, dx).
-template <typename T, bool WIDE>
+template <typename T, int NW>
 DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int E, int s0,
                          int i, int R, typename H<T>::K* oa, typename H<T>::K* ob, short* ol,
                          int cap) {
   typedef typename H<T>::K Key;
-  ukey mlo = 0, mhi = 0;             // open sources before the chunk
+  Mask<NW> m;  // open sources before the chunk
+#pragma unroll
+  for (int q = 0; q < NW; ++q) m.w[q] = 0;
   int carry_p = kNoLabel, carry_ob = kNoLabel;  // segmented values of a group that continues
   ukey carry_key = 0;
   int cum = 0;
@@ -74,24 +96,28 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
     const int b = (int)(pay & 0xFFFFu) + s0 - i + R;
     const bool close = (pay >> 16) & 1u;
     const bool inwin = ev && b >= 0 && b <= 2 * R;
-    const ukey tlo = inwin && b < 64 ? (1ULL << b) : 0ULL;
-    const ukey thi = WIDE && inwin && b >= 64 ? (1ULL << (b - 64)) : 0ULL;
-    ukey xlo = tlo, xhi = thi;
+    Mask<NW> tg, M;  // this event's toggle; the open sources after it
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      tg.w[q] = inwin && (b >> 6) == q ? (1ULL << (b & 63)) : 0ULL;
+      ukey x = tg.w[q];
 #if defined(__CUDA_ARCH__)
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const ukey ylo = __shfl_up_sync(0xffffffffu, xlo, o);
-      if (L.lane >= o) xlo ^= ylo;
-      if (WIDE) {
-        const ukey yhi = __shfl_up_sync(0xffffffffu, xhi, o);
-        if (L.lane >= o) xhi ^= yhi;
+      for (int o = 1; o < 32; o <<= 1) {
+        const ukey y = __shfl_up_sync(0xffffffffu, x, o);
+        if (L.lane >= o) x ^= y;
       }
-    }
 #endif
-    const ukey Mlo = mlo ^ xlo, Mhi = mhi ^ xhi;  // open sources after event t
+      M.w[q] = m.w[q] ^ x;
+    }
     // candidate label of the height itself: after an open, before a close
     int pl = kNoLabel;
-    if (inwin) pl = close ? nearest_label(Mlo | tlo, Mhi | thi, R) : nearest_label(Mlo, Mhi, R);
+    if (inwin) {
+      Mask<NW> pm;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) pm.w[q] = close ? (M.w[q] | tg.w[q]) : M.w[q];
+      pl = nearest_label<NW>(pm, R);
+    }
     // groups of equal height
     ukey prevk = 0;
 #if defined(__CUDA_ARCH__)
@@ -103,7 +129,13 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
     // label of the open interval below the group (first value of the group) and the group's
     // point label (minimum): segmented scans, carried into the chunk when the group continues
     int vp = pl;
-    int vob = head ? nearest_label(Mlo ^ tlo, Mhi ^ thi, R) : kNoLabel;
+    int vob = kNoLabel;
+    if (head) {
+      Mask<NW> bm;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) bm.w[q] = M.w[q] ^ tg.w[q];
+      vob = nearest_label<NW>(bm, R);
+    }
     bool hd = head;
     if (L.lane == 0 && !head && valid) {
       vp = vp < carry_p ? vp : carry_p;
@@ -127,7 +159,7 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
     bool pt = false, endrun = false, strun = false;
     int Ok = kNoLabel;
     if (last) {
-      Ok = nearest_label(Mlo, Mhi, R);
+      Ok = nearest_label<NW>(M, R);
       const int Om = vob;
       pt = vp < (Om < Ok ? Om : Ok);
       endrun = Om < kNoLabel && (Ok != Om || pt);
@@ -151,8 +183,8 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
     }
     cum += w_bcast(inc, 31);
 #if defined(__CUDA_ARCH__)
-    mlo = __shfl_sync(0xffffffffu, Mlo, 31);
-    if (WIDE) mhi = __shfl_sync(0xffffffffu, Mhi, 31);
+#pragma unroll
+    for (int q = 0; q < NW; ++q) m.w[q] = __shfl_sync(0xffffffffu, M.w[q], 31);
     carry_p = __shfl_sync(0xffffffffu, vp, 31);
     carry_ob = __shfl_sync(0xffffffffu, vob, 31);
     carry_key = __shfl_sync(0xffffffffu, key, 31);
@@ -161,11 +193,8 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
   return cum;
 }
 
-template <typename T, bool WIDE>
-DXI int column_count(const Lanes& L, const ukey* ek, const unsigned* ep, int E, int s0, int i,
-                     int R, typename H<T>::K* oa, typename H<T>::K* ob, short* ol, int cap) {
-  return column_partition<T, WIDE>(L, ek, ep, E, s0, i, R, oa, ob, ol, cap);
-}
+// mask words for a reach: 2R + 1 bits
+DXI int mask_words(int R) { return R < 32 ? 1 : (R < 64 ? 2 : 4); }
 
 // Shared memory: sorted events (key, payload), the window's event offsets and per warp a
 // buffer of obuf output pieces.
@@ -184,7 +213,7 @@ DXI long long p1g_layout(int tc, int R, int ecap, int obuf, int nwarps, long lon
 
 // One tile of k_pass1g: columns i0 .. i0 + tc - 1 of row j (tile = j * tiles_per_row +
 // i0 / tc); smem holds the layout p1g_layout(tc, K, ecap, obuf, warps).
-template <typename T>
+template <typename T, int NW>
 __device__ __forceinline__ void pass1g_tile(const P1Params<T>& P, long long tile, int tc,
                                             int ecap, int obuf, unsigned char* smem,
                                             ArenaCursor& cur) {
@@ -304,17 +333,14 @@ __device__ __forceinline__ void pass1g_tile(const P1Params<T>& P, long long tile
       Key* ba = wbuf_a + (long long)warp * obuf;
       Key* bb = wbuf_b + (long long)warp * obuf;
       short* bl = wbuf_l + (long long)warp * obuf;
-      int n = R < 32 ? column_count<T, false>(L, ek, ep, E, s0, i, R, ba, bb, bl, obuf)
-                     : column_count<T, true>(L, ek, ep, E, s0, i, R, ba, bb, bl, obuf);
+      const int n = column_partition<T, NW>(L, ek, ep, E, s0, i, R, ba, bb, bl, obuf);
       const long long s = arena_take(L, &P.ctr->arena_top[1], P.blk, cur, n);
       const bool fits = s + n <= P.m_cap;
       if (fits && n > 0) {
         if (n <= obuf) {
           for (int q = lane; q < n; q += 32) { P.m_a[s + q] = ba[q]; P.m_b[s + q] = bb[q]; P.m_l[s + q] = bl[q]; }
-        } else if (R < 32) {
-          column_partition<T, false>(L, ek, ep, E, s0, i, R, P.m_a + s, P.m_b + s, P.m_l + s, 1 << 30);
         } else {
-          column_partition<T, true>(L, ek, ep, E, s0, i, R, P.m_a + s, P.m_b + s, P.m_l + s, 1 << 30);
+          column_partition<T, NW>(L, ek, ep, E, s0, i, R, P.m_a + s, P.m_b + s, P.m_l + s, 1 << 30);
         }
       }
       if (lane == 0) {

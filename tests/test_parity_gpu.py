@@ -235,3 +235,33 @@ def test_per_line_sweep_path(dx, op, monkeypatch):
     ref = _ref(gg, op, 1.0)
     assert np.diff(ref.col_off).max() > 2500
     _compare_full(off, z, ref, False, f"3000 runs {op}")
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+@pytest.mark.parametrize("k", [40.0, 90.5])
+def test_wide_reach(dx, op, k):
+    """Reaches beyond 31 and 63 spacings (pass-1 source masks of two and four words), on a
+    grid long enough in x for the windows to be full; the xy spacing is small against the
+    depth (h = 1/4000) so that the results keep their gaps."""
+    if op == "dilate":
+        prims = shapes.config2_prims(40, seed=9)
+        g = shapes.raycast(prims, 200)
+        cols = {(i, j): [tuple(s) for s in g.column(i, j + 88)]
+                for i in range(200) for j in range(24) if g.column(i, j + 88).size}
+    else:
+        # a solid slab with holes of several depths in a few patches of columns
+        rng = np.random.default_rng(4)
+        holes = [(int(rng.integers(0, 200)), int(rng.integers(0, 24)), int(rng.integers(2, 12)),
+                  float(rng.uniform(0.2, 0.7))) for _ in range(10)]
+        cols = {}
+        for i in range(200):
+            for j in range(24):
+                zs = [0.1, 0.9]
+                for (hi, hj, hr, hz) in holes:
+                    if (i - hi) ** 2 + (j - hj) ** 2 <= hr * hr:
+                        zs = [0.1, hz, hz + 0.05, 0.9]
+                        break
+                cols[(i, j)] = [(zs[q], zs[q + 1]) for q in range(0, len(zs), 2)]
+    sub = shapes.from_columns(200, 24, 1 / 4000, cols)
+    gg, off, z = _gpu(dx, sub, op, k)
+    _compare_full(off, z, _ref(gg, op, k), False, f"wide {op} k={k}")
