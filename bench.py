@@ -417,6 +417,88 @@ def run_batched_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_precision_workload(args):
+    """The precision configuration: the 2048 x 2048 grid of 1000 primitives (nested shells,
+    thin plates thinner than r, spheres, boxes, shells; up to 58 segments per column),
+    dilated by k = 64 spacings, in FP64 and in FP32 endpoints with FP64 decisions.  Reports
+    both times and each result's max endpoint error and count mismatches against the FP64
+    oracle on sampled columns (FP32: the oracle reads the same float32 input).  One JSON
+    line."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1804_08968_gb300 as dx
+    from synth import shapes
+
+    torch.cuda.set_device(0)
+    k = 64.0
+    t0 = time.perf_counter()
+    g64 = shapes.config3()
+    g32 = shapes.to_float32(g64)
+    gen_s = time.perf_counter() - t0
+    ctx = dx.Context(0)
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    res = {}
+    with ClockSampler(0) as clk:
+        for name, g, dt in (("fp64", g64, torch.float64), ("fp32", g32, torch.float32)):
+            d = dx.Grid.from_synth(g, dtype=dt)
+            out = ctx.run(dx.DILATE, d, k)  # warm-up (sizes the scratch)
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(max(1, min(args.steps, 3))):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                out = ctx.run(dx.DILATE, d, k)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            off, z = out.to_host()
+            res[name] = {"ms": statistics.median(times), "stage_ms": ctx.stage_ms(),
+                         "stats": ctx.stats(), "off": off, "z": z}
+            del d, out
+            torch.cuda.empty_cache()
+    rng = np.random.default_rng(1)
+    cols = np.concatenate([rng.choice(g64.nx * g64.ny, 2000, replace=False),
+                           np.arange(2048) + 1024 * 2048])
+    errs = {}
+    for name, g in (("fp64", g64), ("fp32", g32)):
+        ref = oracle.dilate(g, k, cols=cols)
+        off, z = res[name]["off"], res[name]["z"]
+        mx, mism = 0.0, 0
+        for t, c in enumerate(cols):
+            got = z[off[c]:off[c + 1]].astype(np.float64)
+            exp = ref.column(t)
+            if got.shape != exp.shape:
+                mism += 1
+            elif exp.size:
+                mx = max(mx, float(np.max(np.abs(got - exp))))
+        errs[name] = {"max_endpoint_error": mx, "count_mismatches": mism, "columns_checked": len(cols)}
+    cols_n = g64.nx * g64.ny
+    line = {
+        "metric": "output dexel columns/s", "value": cols_n / (res["fp32"]["ms"] / 1e3),
+        "unit": "columns/s", "n_gpus": 1, "steps": max(1, min(args.steps, 3)), "warmup": 1,
+        "ms_per_step": res["fp32"]["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "2048x2048 grid, 1000 primitives (nested shells, thin plates, "
+                               "spheres, boxes, shells), dilation k=64, FP32 endpoints with FP64 "
+                               "decisions vs FP64", "nseg_in": g64.nseg,
+                   "max_segs_per_col": int(np.diff(g64.col_off).max()),
+                   "l2": "inputs larger than L2", "parallelism": "replica x1"},
+        "fp64": {"ms_per_step": res["fp64"]["ms"], "value": cols_n / (res["fp64"]["ms"] / 1e3),
+                 "stage_ms": res["fp64"]["stage_ms"], "mid_pieces": res["fp64"]["stats"][1],
+                 "error_vs_oracle": errs["fp64"]},
+        "fp32": {"stage_ms": res["fp32"]["stage_ms"], "mid_pieces": res["fp32"]["stats"][1],
+                 "error_vs_oracle": errs["fp32"],
+                 "speedup_over_fp64": res["fp64"]["ms"] / res["fp32"]["ms"]},
+        "clocks": clk.summary(),
+        "generate_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -430,8 +512,9 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one offset of the workload and exit (for ncu captures)")
     ap.add_argument("--profile-k", type=float, default=8.0)
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
-                    help="batched: the 256-shape batched configuration (one JSON line)")
+    ap.add_argument("--workload", choices=["single", "batched", "precision"], default="single",
+                    help="batched: the 256-shape batched configuration; precision: the 2048^2 "
+                         "k = 64 FP32 vs FP64 configuration (one JSON line each)")
     ap.add_argument("--profile-op", choices=["dilate", "erode"], default="dilate")
     args = ap.parse_args()
     rank, ws = dist_init(args)
@@ -445,6 +528,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched_workload(args)
+        return
+    if args.workload == "precision":
+        run_precision_workload(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, ws)

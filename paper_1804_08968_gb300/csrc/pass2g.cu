@@ -114,9 +114,9 @@ namespace dexel {
 // pieces of their common window (float ends and dx) in shared memory with coalesced loads,
 // and its warps take the tile's columns, each splitting its window's pieces evenly over the
 // lanes (column_cover).  A tile whose window holds more pieces than the staging area is cut
-// into the longest runs of columns whose windows fit; a single column whose window does not
-// fit is covered in chunks.  Columns whose union outgrows the bucket are marked (count -1)
-// for the redo launch of k_pass2c.
+// into the longest runs of columns whose windows fit; columns whose single window does not
+// fit are covered a warp each, their joint window staged in chunks.  Columns whose union
+// outgrows the bucket are marked (count -1) for the redo launch of k_pass2c.
 template <typename T, int MINB>
 __global__ void __launch_bounds__(512, MINB) k_pass2t(P2GParams<T> P, int tc, int ntab, int stage_cap, int Q, int M) {
   extern __shared__ __align__(16) unsigned char smem[];

@@ -124,8 +124,8 @@ __device__ __forceinline__ void pass2t_tile(const P2GParams<T>& P, long long til
     }
   }
   __syncthreads();
-  // runs of columns [ja, jb) whose window [ja - R, jb + R) fits the staging area; a single
-  // column whose window does not fit is covered by warp 0 in chunks of the staging size
+  // runs of columns [ja, jb) whose window [ja - R, jb + R) fits the staging area; columns
+  // whose single window does not fit are covered by the warps together, in chunks
   for (int ja = j0; ja < j1;) {
     const int qa = max(0, ja - R) - s0;
     int jb = j1;
@@ -156,13 +156,19 @@ __device__ __forceinline__ void pass2t_tile(const P2GParams<T>& P, long long til
       }
       __syncthreads();  // the run's staged pieces are no longer read
     } else {
-      const int j = ja;
-      const int qlo = max(0, j - R) - s0, qhi = min(P.ny - 1, j + R) - s0;
-      const int gb = soff[qlo], ge = soff[qhi + 1];
+      // a single column's window is larger than the staging area: the next nwb columns (one
+      // a warp) are covered together, their joint window staged in chunks; each warp takes the
+      // part of a chunk inside its column's window and carries its runs across chunks
+      jb = min(j1, ja + nwb);
+      const int j = ja + warp;
+      const bool mine = j < jb;
+      const int qlo = mine ? max(0, j - R) - s0 : 0, qhi = mine ? min(P.ny - 1, j + R) - s0 : 0;
+      const int gb = mine ? soff[qlo] : 0, ge = mine ? soff[qhi + 1] : 0;
+      const int ua = soff[qa], ue = soff[min(P.ny, jb + R) - s0];  // joint window
       int acc = 0;
       bool ok = true;
-      for (int ga = gb; ga < ge; ga += stage_cap) {
-        const int gz = min(ge, ga + stage_cap);
+      for (int ga = ua; ga < ue; ga += stage_cap) {
+        const int gz = min(ue, ga + stage_cap);
         const long long src = *sgb + ga;
         for (int g = threadIdx.x; g < gz - ga; g += blockDim.x) {
           saf[g] = P.c_af[src + g];
@@ -170,12 +176,13 @@ __device__ __forceinline__ void pass2t_tile(const P2GParams<T>& P, long long til
           sdx[g] = P.c_dx[src + g];
         }
         __syncthreads();
-        if (warp == 0 && ok)
-          ok = column_cover<T>(P, L, j, s0, soff, sbase, qlo, qhi, ga, gz, saf - ga, sbf - ga,
+        const int ca = max(ga, gb), cz = min(gz, ge);
+        if (mine && ok && ca < cz)
+          ok = column_cover<T>(P, L, j, s0, soff, sbase, qlo, qhi, ca, cz, saf - ga, sbf - ga,
                                sdx - ga, wt, E, Q, M, bl, br, f0, f1, bcount, bcap, acc);
         __syncthreads();
       }
-      if (warp == 0) column_out<T>(P, L, j, i, ok, acc, bl, br, bcap, cur);
+      if (mine) column_out<T>(P, L, j, i, ok, acc, bl, br, bcap, cur);
       PHASE(1);
     }
     ja = jb;
