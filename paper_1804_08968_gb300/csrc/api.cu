@@ -85,6 +85,12 @@ __global__ void k_validate(int ncols, const int* off, const T* z, long long nseg
   if (bad) atomicOr(&ctr->status, ST_BAD_CSR);
 }
 
+// rows of the grid with a column marked for the pass-1 sweep (line-2 index q = i * ny + j)
+__global__ void k_mark_rows(long long ncols, int ny, const long long* m_start, int* rowflag) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < ncols && m_start[q] < 0) rowflag[q % ny] = 1;
+}
+
 __global__ void k_tables(double kk, double h, int nmax, int K, double* wtab, int* reach,
                          float* wtabf) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -350,11 +356,15 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       // gather: tiles of tc columns whose window's events (two per segment, two more per
       // column for a complement) fit ecap; a window beyond ecap hands the call to the sweep
       const double ev_col = 2.0 * (double)in->nseg / (double)std::max<long long>(ncols, 1) + (erode ? 2.0 : 0.0);
-      // (a tile of about 2K columns: a column's window then covers about half the tile's)
+      // (a tile of about K/2 columns: a column's window then covers ~80 % of the tile's;
+      // measured best of K/4 .. 2K on the 512^2 and 2048^2 workloads)
       int ecap = 2048, tc = 8;
-      while (tc < 64 && tc < 2 * K) tc <<= 1;
+      while (tc < 64 && tc < K / 2) tc <<= 1;
       while (tc > 8 && (tc + 2.0 * K + 1) * ev_col * 1.5 > 16384) tc >>= 1;
       while (ecap < 16384 && (tc + 2.0 * K + 1) * ev_col * 1.5 > ecap) ecap <<= 1;
+      // room for the densest single column's window, so that no row needs the sweep
+      const double ev_win_max = (2.0 * K + 1) * 2.0 * (hc.max_segs_in + 1);
+      while (ecap < 16384 && ev_win_max > ecap) ecap <<= 1;
       int obuf = 256;
       while (obuf > 32 && pass1g_smem<T>(tc, K, ecap, obuf) > (220LL << 10)) obuf >>= 1;
       while (ecap > 1024 && pass1g_smem<T>(tc, K, ecap, obuf) > (220LL << 10)) ecap >>= 1;
@@ -367,11 +377,26 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
+        // columns whose window had more events than fit (marked m_start = -1): the sweep
+        // redoes their rows
+        int* rowflag = (int*)ppos;  // free until pass 2
+        CK(cudaMemsetAsync(rowflag, 0, sizeof(int) * ny, st));
+        k_mark_rows<<<(unsigned)((ncols + 255) / 256), 256, 0, st>>>(ncols, ny, p1.m_start, rowflag);
+        std::vector<int> hf(ny);
+        CK(cudaMemcpyAsync(hf.data(), rowflag, sizeof(int) * ny, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<int> rows;
+        for (int j = 0; j < ny; ++j)
+          if (hf[j]) rows.push_back(j);
+        CK(cudaMemcpyAsync(rowflag, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
-        CK(cudaMemsetAsync(&ctr->arena_top[1], 0, sizeof(unsigned long long), st));
-        CK(cudaMemsetAsync(&ctr->mid_total, 0, sizeof(unsigned long long), st));
-        CK(cudaMemsetAsync(&ctr->max_pieces, 0, sizeof(int), st));
-        sweep1 = true;
+        P1Params<T> pr = p1;
+        pr.rows = rowflag;
+        pr.nrows = (int)rows.size();
+        CK(launch_pass1<T>(pr, nw1 / kWarpsPerBlock, st));
+        ++ctx->launches;
+        CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
       }
     }
     if (sweep1) {

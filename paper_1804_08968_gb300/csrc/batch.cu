@@ -238,10 +238,11 @@ int reach_of_kk(double kk) {
   return (int)R;
 }
 
-// tile rules: pass 1 about 2K columns, pass 2 about 2K + 16 columns, scaled by 2^(scale - 1)
+// tile rules: pass 1 about K/2 columns, pass 2 about 2K + 16 columns, scaled by
+// 2^(scale - 1)
 int tile1(int K, int scale) {
   int tc = 8;
-  const int want = std::max(8, (2 * K) << scale >> 1);
+  const int want = std::max(8, (K / 2) << scale >> 1);
   while (tc < 64 && tc < want) tc <<= 1;
   return tc;
 }

@@ -11,13 +11,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_pass1(P1Params<T> P) {
   typedef typename H<T>::K Key;
   const P1Slot<Key> W = p1_slot<Key>(P.slots + gw * P.slot_bytes, P.capF, P.capS, P.chunk);
   ArenaCursor cf{0, 0}, cm{0, 0};
-  const int nitems = P.ny * P.nchunks;
+  const int nitems = (P.rows ? P.nrows : P.ny) * P.nchunks;
   for (;;) {
     int item = 0;
     if (L.lane == 0) item = (int)atomicAdd(&P.ctr->work_next[0], 1ULL);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= nitems) break;
-    const int j = item / P.nchunks;
+    const int j = P.rows ? P.rows[item / P.nchunks] : item / P.nchunks;
     const int c = item % P.nchunks;
     const int c0 = c * P.chunk;
     const int c1 = min(P.nx, c0 + P.chunk);

@@ -231,6 +231,8 @@ struct P1Params {
   // per-warp slot
   char* slots; long long slot_bytes;
   int capF, capS;  // capacities of state arrays and of one column's segments
+  const int* rows;  // the sweep: only these rows (null: all rows)
+  int nrows;
   // local index of forward states for the current chunk: per warp, chunk entries
 };
 
