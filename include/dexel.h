@@ -164,6 +164,14 @@ dexel_status dexel_offset_noalloc(const dexel_grid_in* in, double k, dexel_op op
 /* Static description of a status code. */
 const char* dexel_status_string(dexel_status s);
 
+/* Device status bits after the last pass-2 level step (diagnostics; 16: a level list beyond
+ * its buffer, the tiled gather took over; 32: a self-check found an index out of range). */
+int dexel_last_levels_status(const dexel_ctx* ctx);
+
+/* Detail of the last DEXEL_ERR_CUDA / DEXEL_ERR_NOMEM of the calling thread: the CUDA error
+ * code and name and the library source line ("" when none). */
+const char* dexel_last_error_detail(void);
+
 /* Kernel launches issued by the last call on ctx (for launch accounting). */
 int64_t dexel_last_launches(const dexel_ctx* ctx);
 

@@ -72,6 +72,8 @@ def lib():
                                            ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                            ctypes.POINTER(_Out), P, ctypes.c_size_t, P, P]
+        L.dexel_last_error_detail.argtypes = []
+        L.dexel_last_error_detail.restype = ctypes.c_char_p
         L.dexel_set_batch_autotune.argtypes = [P, ctypes.c_int]
         L.dexel_set_batch_autotune.restype = None
         L.dexel_workspace_size.argtypes = [ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int]
@@ -198,8 +200,9 @@ class Context:
                 cap = int(out.nseg) + 16
                 continue
             if rc != 0:
+                detail = lib().dexel_last_error_detail().decode()
                 raise DexelError(rc, f"dexel offset (stats {self.stats()}, "
-                                     f"required {lib().dexel_last_required(self.ptr)} B)")
+                                     f"required {lib().dexel_last_required(self.ptr)} B{', ' + detail if detail else ''})")
             self._cap_hint[key] = cap
             return Grid(g.nx, g.ny, g.h, off, z[: out.nseg])
         raise DexelError(-3, "dexel offset (output capacity)")

@@ -39,7 +39,9 @@ struct dexel_ctx {
   std::map<int, int> ccap;
   BatchEngine* batch = nullptr;  // batched offsets (created on first use)
   bool batch_autotune = true;
-  long long needF = 0, needM = 0, needO = 0;  // arena entries
+  long long needF = 0, needM = 0, needO = 0, needL = 0;  // arena entries
+  bool levels = true;   // pass 2 by per-source level unions (else the tiled gather)
+  int levels_status = 0;  // device status after the last level pass (diagnostics)
   Counters host_ctr{};
   // optional per-stage timing with CUDA events on the call's stream
   bool profiling = false;
@@ -178,15 +180,19 @@ void reset_call(dexel_ctx* ctx) {
   for (long long& x : ctx->stats) x = 0;
 }
 
-dexel_status cuda_status(cudaError_t e) {
+thread_local char g_err_detail[192] = "";
+
+dexel_status cuda_status(cudaError_t e, int line = 0) {
   if (e == cudaSuccess) return DEXEL_OK;
+  snprintf(g_err_detail, sizeof(g_err_detail), "CUDA error %d (%s) at api.cu:%d", (int)e,
+           cudaGetErrorName(e), line);
   return e == cudaErrorMemoryAllocation ? DEXEL_ERR_NOMEM : DEXEL_ERR_CUDA;
 }
 
-#define CK(call)                                         \
-  do {                                                   \
-    cudaError_t e_ = (call);                             \
-    if (e_ != cudaSuccess) return cuda_status(e_);       \
+#define CK(call)                                                 \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return cuda_status(e_, __LINE__);     \
   } while (0)
 
 dexel_status ensure_owned(dexel_ctx* ctx, size_t bytes) {
@@ -303,7 +309,12 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     // pass-2 slot estimate from the remembered capacities
     const long long sb2_est =
         p2_slot_bytes<Key>(std::max(capS * 4, 64), ctx->capR, ctx->capA, ctx->capS, 1024);
-    const size_t slots = std::max((size_t)sb1, (size_t)sb2_est) * nwarps;
+    const size_t slots_sw = std::max((size_t)sb1, (size_t)sb2_est) * nwarps;
+    // the pass-2 level lists use the same room as the sweeps' slots (never both at once)
+    const long long nlev = ncols * (long long)(K + 1);
+    const long long eL = std::max<long long>(ctx->needL + ctx->needL / 8, 2 * nlev);
+    const size_t bL = K <= kGatherMaxReach ? align_up((size_t)nlev * 12 + 512, 256) + (size_t)eL * 16 : 0;
+    const size_t slots = std::max(slots_sw, bL);
     const size_t total = fixed + bF + bM + bO + slots + 4096;
     if (ws_user && total > ws_user_bytes) {
       ctx->last_required = total;
@@ -431,8 +442,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       pg.blk = 256;
       pg.ctr = ctr;
       // line-contiguous float copy of S_mid in the (now free) pass-1 forward arena
+      const long long capC = (long long)(bF / 10);
       {
-        const long long capC = (long long)(bF / 10);
         if ((long long)hc.mid_total > capC) return DEXEL_ERR_CAPACITY;  // not reached: bF >= 16 eM
         float* c_af = (float*)aF;
         float* c_bf = c_af + capC;
@@ -478,9 +489,58 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         const int ntiles_cap = nx * ((ny + tc - 1) / tc);
         const int tblocks = std::max(1, std::min(sms * per_sm, ntiles_cap));
         mark(ctx, 4, st);  // the stage covers the pass-2 kernels only (not the copy above)
-        CK(launch_pass2t<T>(pg, tw, tc, ntab, stage_cap, kRoundAppends, kRoundPieces, per_sm,
-                            tblocks, st));
-        ++ctx->launches;
+        bool done = false;
+        if (ctx->levels && slot_room >= bL && bL > 0) {
+          // per-source level unions in the sweeps' slot room, then the per-column gather
+          LvlParamsHost<T> H;
+          H.P = pg;
+          H.l_start = (long long*)pslots;
+          H.l_cnt = (int*)(H.l_start + nlev);
+          const size_t ib = align_up((size_t)nlev * 12 + 512, 256);
+          H.l_cap = (long long)((slot_room - ib) / 16);
+          H.l_l = (ukey*)(pslots + ib);
+          H.l_r = H.l_l + H.l_cap;
+          int& lb = ctx->ccap[2 * K + (erode ? 1 : 0)];
+          if (lb < 256) lb = 256;
+          H.bcap = lb;
+          H.m_cap = p1.m_cap;
+          H.c_cap = capC;
+          CK(launch_levels<T>(H, st, sms));
+          ctx->launches += 2;
+          CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          ctx->needL = std::max<long long>(ctx->needL, (long long)hc.arena_top[2]);
+          ctx->levels_status = hc.status;
+          if (hc.status & ST_LEVELS_OVER) {
+            // a list beyond its buffer or the arena: the tiled gather redoes pass 2
+            CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+            CK(cudaMemsetAsync(&ctr->arena_top[3], 0, sizeof(unsigned long long), st));
+            CK(cudaMemsetAsync(&ctr->out_total, 0, sizeof(unsigned long long), st));
+            CK(cudaMemsetAsync(&ctr->max_state, 0, sizeof(int), st));
+            CK(cudaMemsetAsync(&ctr->redo_cols, 0, sizeof(int), st));
+          } else {
+            done = true;
+            if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
+              // columns whose lists outgrew the bucket: the gather again, those columns only,
+              // with a bucket for their need
+              int b = 2 * H.bcap;
+              while (b < hc.max_state && b < 8192) b <<= 1;
+              if (hc.redo_cols * 64LL > ncols) lb = std::min(2 * lb, 2048);  // next calls
+              if (b >= hc.max_state) {
+                CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+                CK(launch_lgather<T>(H, b, 1, st, sms));
+                ++ctx->launches;
+                CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+              }
+            }
+          }
+        }
+        if (!done) {
+          CK(launch_pass2t<T>(pg, tw, tc, ntab, stage_cap, kRoundAppends, kRoundPieces, per_sm,
+                              tblocks, st));
+          ++ctx->launches;
+        }
       }
       CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -841,6 +901,7 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   const char* mode = getenv("DEXEL_PASS2");
   c->sweep2 = mode && strcmp(mode, "sweep") == 0;
+  if (mode && strcmp(mode, "tiled") == 0) c->levels = false;
   const char* mode1 = getenv("DEXEL_PASS1");
   c->sweep1 = mode1 && strcmp(mode1, "sweep") == 0;
   *ctx = c;
@@ -883,6 +944,8 @@ int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max) {
   for (int q = 0; q < n; ++q) ms[q] = ctx->stage_ms[q];
   return n;
 }
+
+int dexel_last_levels_status(const dexel_ctx* ctx) { return ctx ? ctx->levels_status : 0; }
 
 int dexel_last_phases(const dexel_ctx* ctx, uint64_t* ph, int max) {
   if (!ctx || !ph) return 0;
@@ -1088,6 +1151,8 @@ dexel_status dexel_offset_noalloc(const dexel_grid_in* in, double k, dexel_op op
   if (mode == DEXEL_FP64) return noalloc_offset<double>(in, k, erode, out, st);
   return noalloc_offset<float>(in, k, erode, out, st);
 }
+
+const char* dexel_last_error_detail(void) { return g_err_detail; }
 
 const char* dexel_status_string(dexel_status s) {
   switch (s) {

@@ -28,6 +28,23 @@ cudaError_t launch_pass2(const P2Params<T>& P, int blocks, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pass2t(const P2GParams<T>& P, int warps_per_block, int tc, int ntab,
                           int stage_cap, int Q, int M, int minb, int blocks, cudaStream_t st);
+// Pass 2 by levels (pass2l.cu): per-source level unions into l_l / l_r (index l_start /
+// l_cnt, [q * (R + 1) + t]) then the per-column gather with buckets of bcap intervals.
+template <typename T>
+struct LvlParamsHost {
+  P2GParams<T> P;
+  ukey* l_l;
+  ukey* l_r;
+  long long l_cap;
+  long long* l_start;
+  int* l_cnt;
+  int bcap;
+  long long m_cap, c_cap;  // entries of the S_mid arena and of its packed copy (self-checks)
+};
+template <typename T>
+cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms);
+template <typename T>
+cudaError_t launch_lgather(const LvlParamsHost<T>& H, int bcap, int redo, cudaStream_t st, int sms);
 template <typename T>
 cudaError_t launch_pass2c(const P2GParams<T>& P, int warps_per_block, int blocks, cudaStream_t st);
 

@@ -35,6 +35,8 @@ enum : int {
   ST_OVERFLOW_ARENA = 2,   // an output arena is full
   ST_BAD_CSR = 4,
   ST_TOO_MANY_OUT = 8,     // output does not fit int32 offsets
+  ST_LEVELS_OVER = 16,     // a level list outgrew its buffer (pass 2 by levels)
+  ST_BOUNDS = 32,          // a self-check found an index out of its array (access skipped)
 };
 
 struct Counters {
