@@ -28,9 +28,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 RADII = (2.0, 8.0, 32.0)
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_pass2t launch of the
-# k = 32 dilation, from an ncu capture of the current kernel (None once the kernel changes)
-TRAFFIC_K32_DILATE = 709_942_784
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the pass-2 kernels of the k = 32
+# dilation (k_levels + k_lgather), from an ncu capture of the current kernels (None once they
+# change)
+TRAFFIC_K32_DILATE = 1_505_701_632
 OPS = ("dilate", "erode")
 N = 512
 HBM_PEAK = None
@@ -191,10 +192,10 @@ def run_ours(args, rank, ws):
     ms_step = allmax(sum(times) / len(times), ws, device="cuda")
     value = units * ws / (ms_step / 1e3)
 
-    # roofline of the dominant launch: k_pass2t, the pass-2 gather of the k = 32 dilation
-    # (stage 2 of that call brackets exactly its pass-2 kernels).  Algorithmic bytes per
-    # launch: S_mid read once (two FP64 keys + int16 dx = 18 B a piece), pass-2 intervals
-    # written (16 B each), per-column start + count (12 B).
+    # roofline of the dominant stage: pass 2 of the k = 32 dilation (k_levels + k_lgather;
+    # stage 2 of that call brackets exactly its pass-2 kernels).  Algorithmic bytes: S_mid
+    # read once (two FP64 keys + int16 dx = 18 B a piece), pass-2 intervals written (16 B
+    # each), per-column start + count (12 B).
     dom = [r for r in rec if r[0] == "dilate" and r[1] == 32.0]
     dom_ms = sum(r[2][2] for r in dom) / len(dom)
     dom_bytes = 18 * dom[0][3][1] + 16 * dom[0][3][2] + 12 * g.nx * g.ny
@@ -241,8 +242,8 @@ def run_ours(args, rank, ws):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": TRAFFIC_K32_DILATE,
-                     "kernel": "k_pass2t (y dilation with per-piece radius, tiled window "
-                               "gather), dilation k=32",
+                     "kernel": "pass-2 stage: k_levels + k_lgather (y dilation with per-piece "
+                               "radius), dilation k=32",
                      "algorithmic_bytes": dom_bytes, "ms_per_launch": dom_ms,
                      "peak_source": peak_kind},
         "stage_ms_per_step": {"validate+tables": stages[0] / args.steps,
