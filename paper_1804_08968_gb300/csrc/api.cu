@@ -1102,6 +1102,8 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
     }
   }
   // shapes beyond the batch kernels' limits: the single-shape path
+  long long singles = 0;
+  for (int s = 0; s < nshapes; ++s) singles += fin[s] == 1;
   for (int s = 0; s < nshapes; ++s) {
     if (fin[s] != 1) continue;
     dexel_status r;
@@ -1122,6 +1124,7 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
     if (fin[s] != DEXEL_OK && first == DEXEL_OK) first = (dexel_status)fin[s];
   }
   ctx->launches = launches;
+  ctx->stats[5] = singles;  // shapes that took the single-shape path
   if (d_status && nshapes > 0) {
     if (cudaMemcpyAsync(d_status, hst.data(), sizeof(int32_t) * nshapes, cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||

@@ -22,6 +22,7 @@
 #include "emit.cuh"
 #include "launch.h"
 #include "pass1g.cuh"
+#include "pass2l.cuh"
 #include "pass2t.cuh"
 
 namespace dexel {
@@ -32,6 +33,7 @@ template <typename T>
 struct BShape {
   P1Params<T> p1;   // pass 1 (m_start / m_cnt point at the shape's columns)
   P2GParams<T> p2;  // pass 2 (o_start / o_cnt / c_start likewise, tables at the shape's)
+  LvlParams<T> lv;  // pass 2 by levels (p2 plus the shape's level lists)
   long long col_base, ncols;
   int tc1, tc2, ntab2, nmax;
   double kk, h;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(256) k_b_pass1(const BShape<T>* S, const long 
   ArenaCursor cur{0, 0};
   for (long long gt = blockIdx.x; gt < ntiles; gt += gridDim.x) {
     const int s = find_base(t1b, ns, gt);
-    if (sst[s] & BS_BAD) continue;
+    if ((sst[s] & BS_BAD) || mask_words(S[s].p1.K) != NW) continue;  // another launch's class
     const P1Params<T> P = S[s].p1;
     pass1g_tile<T, NW>(P, gt - t1b[s], S[s].tc1, ecap, obuf, smem, cur);
   }
@@ -127,6 +129,58 @@ __global__ void __launch_bounds__(512, MINB) k_b_pass2(const BShape<T>* S, const
     __syncthreads();  // the previous tile no longer reads the table
     for (int q = threadIdx.x; q < ntab; q += blockDim.x) swt[q] = P.wtabf[q];
     pass2t_tile<T>(P, gt - t2b[s], tc, ntab, stage_cap, Q, M, smem, ntab > 0 ? swt : P.wtabf, cur);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_levels(const BShape<T>* S, const long long* lvb,
+                                                  int ns, long long nitems, const int* sst) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ukey* bl = (ukey*)smem + (long long)warp * 64 * kLvlSlots + lane * kLvlSlots;
+  ukey* br = bl + 32 * kLvlSlots;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  ArenaCursor cur{0, 0};
+  for (long long gi = (long long)blockIdx.x * (blockDim.x >> 5) + warp; gi < nitems; gi += nw) {
+    const int s = find_base(lvb, ns, gi);
+    if (sst[s] & BS_BAD) continue;
+    const LvlParams<T>& A = S[s].lv;
+    const float E = 9.5367432e-7f * (__uint_as_float(A.P.ctr->zmax_bits) + A.P.wtabf[0]);
+    levels_item<T>(A, gi - lvb[s], lane, bl, br, E, cur);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_lgather(const BShape<T>* S, const long long* colb,
+                                                   int ns, long long ncols, int bcap,
+                                                   const int* sst, const Counters* ctr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wb = smem + (long long)warp * (bcap * (2 * sizeof(ukey) + 2 * sizeof(int)) + 16);
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  if (*(const volatile int*)&ctr->status & ST_LEVELS_OVER) return;  // the lists are incomplete
+  ArenaCursor cur{0, 0};
+  for (long long gi = (long long)blockIdx.x * (blockDim.x >> 5) + warp; gi < ncols; gi += nw) {
+    const int s = find_base(colb, ns, gi);
+    if (sst[s] & BS_BAD) continue;
+    lgather_column<T>(S[s].lv, gi - colb[s], bcap, 0, lane, wb, cur);
+  }
+}
+
+// the columns marked -1 by k_b_lgather, with a larger bucket
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_lgather_redo(const BShape<T>* S, const long long* colb,
+                                                        int ns, long long ncols, int bcap,
+                                                        const int* sst) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wb = smem + (long long)warp * (bcap * (2 * sizeof(ukey) + 2 * sizeof(int)) + 16);
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  ArenaCursor cur{0, 0};
+  for (long long gi = (long long)blockIdx.x * (blockDim.x >> 5) + warp; gi < ncols; gi += nw) {
+    const int s = find_base(colb, ns, gi);
+    if (sst[s] & BS_BAD) continue;
+    lgather_column<T>(S[s].lv, gi - colb[s], bcap, 1, lane, wb, cur);
   }
 }
 
@@ -198,7 +252,8 @@ struct BatchEngine {
   size_t host_bytes = 0;
   void* mid = nullptr;  // internal outputs
   size_t mid_bytes = 0;
-  long long needM = 0, needO = 0;  // arena entries learnt
+  long long needM = 0, needO = 0, needL = 0;  // arena entries learnt
+  std::map<std::vector<long long>, bool> no_levels;  // signatures whose level lists overflowed
   // recorded launch sequences by signature (shapes, scratch, tile scales)
   std::map<std::vector<long long>, cudaGraphExec_t> graphs;
   // autotuned tile scales per signature (x 1/2: 0 = half, 1 = default, 2 = double)
@@ -256,8 +311,8 @@ int tile2(int K, int scale) {
 struct Plan {
   size_t total = 0;
   size_t o_ctr, o_shapes, o_bases, o_sst, o_tot, o_colll, o_colint, o_cnt, o_pos, o_sums, o_cst,
-      o_tab, o_tabf, o_M, o_F, o_O;
-  long long capM = 0, capO = 0, capF = 0;
+      o_tab, o_tabf, o_M, o_F, o_O, o_lst, o_lcnt, o_L;
+  long long capM = 0, capO = 0, capF = 0, capL = 0;
 };
 
 }  // namespace
@@ -276,6 +331,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
   // ---- per-shape geometry
   std::vector<int> K(ns), nmax(ns);
   std::vector<long long> colb(ns + 1, 0), tabb(ns + 1, 0), t1b(ns + 1, 0), t2b(ns + 1, 0);
+  std::vector<long long> lvb(ns + 1, 0), nlb(ns + 1, 0);  // level items, level-list entries
   std::vector<long long> sig;
   sig.push_back(ns);
   sig.push_back(sizeof(T));
@@ -289,6 +345,12 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     maxK = std::max(maxK, K[s]);
     const long long nc = (long long)it.nx * it.ny;
     colb[s + 1] = colb[s] + nc;
+    {
+      const int L = K[s] + 1;
+      const long long items = L <= 32 ? (nc + (32 / L) - 1) / (32 / L) : nc * ((K[s] + 31) / 32);
+      lvb[s + 1] = lvb[s] + items;
+      nlb[s + 1] = nlb[s] + nc * L;
+    }
     tabb[s + 1] = tabb[s] + nmax[s] + 2;
     nseg_all += it.nseg;
     estM += (it.nseg + nc) * std::min(K[s] + 2, 64);
@@ -318,7 +380,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
   };
   tiles(sc1, sc2);
   // kernel geometry: pass-1 events and pass-2 staging sized for the largest shape parameters
-  const int ecap = 4096, obuf = 128;
+  const int ecap = 4096, obuf = 256;
   long long sm1 = 0;
   for (int s = 0; s < ns; ++s) sm1 = std::max(sm1, pass1g_smem<T>(64, K[s], ecap, obuf));
   const int bcap = 128, wpb2 = 16;
@@ -328,7 +390,8 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     base2 = std::max(base2, p2t_layout(K[s], 128, nt, 0, wpb2, bcap).total);
   }
   const int minb = maxK <= 12 ? 2 : 1;
-  const int nw1 = mask_words(maxK);  // pass-1 mask width (every shape's reach fits)
+  bool has_nw[3] = {false, false, false};  // pass-1 mask widths present (1, 2, 4 words)
+  for (int s = 0; s < ns; ++s) has_nw[mask_words(K[s]) == 1 ? 0 : (mask_words(K[s]) == 2 ? 1 : 2)] = true;
   const long long budget2 = minb == 2 ? (108LL << 10) : (220LL << 10);
   const int stage_cap = (int)std::max<long long>(512, (budget2 - base2 - 64) / 10);
   long long sm2 = 0;
@@ -348,7 +411,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     auto take = [&](size_t bytes) { const size_t o = x; x = bal(x + bytes); return o; };
     pl.o_ctr = take(sizeof(Counters));
     pl.o_shapes = take(sizeof(BShape<T>) * ns);
-    pl.o_bases = take(sizeof(long long) * 4 * (ns + 1));
+    pl.o_bases = take(sizeof(long long) * 5 * (ns + 1));
     pl.o_sst = take(sizeof(int) * ns);
     pl.o_tot = take(sizeof(long long) * ns);
     pl.o_colll = take(sizeof(long long) * 2 * ncols);  // m_start, o_start
@@ -365,6 +428,12 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     pl.o_M = take((size_t)pl.capM * (2 * sizeof(Key) + 2));
     pl.o_F = take((size_t)pl.capF * 10);
     pl.o_O = take((size_t)pl.capO * 16);
+    const bool levels = !E->no_levels.count(sig);
+    const long long nlev_all = nlb[ns];
+    pl.capL = levels ? std::max<long long>(std::max(E->needL + E->needL / 8, 2 * nlev_all), 1024) : 0;
+    pl.o_lst = take(levels ? sizeof(long long) * nlev_all : 0);
+    pl.o_lcnt = take(levels ? sizeof(int) * nlev_all : 0);
+    pl.o_L = take((size_t)pl.capL * 16);
     pl.total = x + 256;
     if (pl.total > E->ws_bytes) {
       if (E->ws) cudaFree(E->ws);
@@ -381,6 +450,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     BShape<T>* dS = (BShape<T>*)(W + pl.o_shapes);
     long long* dB = (long long*)(W + pl.o_bases);
     long long *d_colb = dB, *d_tabb = dB + (ns + 1), *d_t1b = dB + 2 * (ns + 1), *d_t2b = dB + 3 * (ns + 1);
+    long long* d_lvb = dB + 4 * (ns + 1);
     int* d_sst = (int*)(W + pl.o_sst);
     long long* d_tot = (long long*)(W + pl.o_tot);
     long long* m_start = (long long*)(W + pl.o_colll);
@@ -401,6 +471,10 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     short* c_dx = (short*)(c_bf + pl.capF);
     ukey* o_l = (ukey*)(W + pl.o_O);
     ukey* o_r = o_l + pl.capO;
+    long long* l_start = (long long*)(W + pl.o_lst);
+    int* l_cnt = (int*)(W + pl.o_lcnt);
+    ukey* l_l = (ukey*)(W + pl.o_L);
+    ukey* l_r = l_l + pl.capL;
 
     // ---- shape table
     std::vector<BShape<T>> hs(ns);
@@ -439,8 +513,19 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       q.ctr = ctr;
       q.bcap = bcap;
       q.c_start = cst + colb[s]; q.c_af = c_af; q.c_bf = c_bf; q.c_dx = c_dx;
+      LvlParams<T>& v = B.lv;
+      v.P = q;
+      v.l_l = l_l; v.l_r = l_r; v.l_cap = pl.capL;
+      v.l_start = l_start + nlb[s]; v.l_cnt = l_cnt + nlb[s];
+      v.L = K[s] + 1;
+      v.G = v.L <= 32 ? 32 / v.L : 1;
+      v.NG = v.L <= 32 ? 0 : (K[s] + 31) / 32;
+      v.nsrc = colb[s + 1] - colb[s];
+      v.nlev = nlb[s + 1] - nlb[s];
+      v.m_cap = pl.capM;
+      v.c_cap = pl.capF;
     }
-    const size_t up_bytes = sizeof(BShape<T>) * ns + sizeof(long long) * 4 * (ns + 1);
+    const size_t up_bytes = sizeof(BShape<T>) * ns + sizeof(long long) * 5 * (ns + 1);
     if (up_bytes > E->host_bytes) {
       if (E->host) cudaFreeHost(E->host);
       E->host = nullptr;
@@ -457,10 +542,18 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       hb[(ns + 1) + s] = tabb[s];
       hb[2 * (ns + 1) + s] = t1b[s];
       hb[3 * (ns + 1) + s] = t2b[s];
+      hb[4 * (ns + 1) + s] = lvb[s];
     }
     BK(cudaMemcpyAsync(dS, E->host, sizeof(BShape<T>) * ns, cudaMemcpyHostToDevice, st));
-    BK(cudaMemcpyAsync(dB, hb, sizeof(long long) * 4 * (ns + 1), cudaMemcpyHostToDevice, st));
+    BK(cudaMemcpyAsync(dB, hb, sizeof(long long) * 5 * (ns + 1), cudaMemcpyHostToDevice, st));
 
+    // level kernels' geometry
+    const size_t smL = (size_t)8 * 64 * kLvlSlots * sizeof(ukey);
+    const int bcapG = 256;
+    const size_t smG = (size_t)lgather_smem(8, bcapG);
+    const int perG = (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / (long long)smG));
+    BK(cudaFuncSetAttribute(k_b_levels<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smL));
+    BK(cudaFuncSetAttribute(k_b_lgather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smG));
     // ---- the launch sequence (recorded as a graph for a repeated signature)
     const long long nt1 = t1b[ns], nt2 = t2b[ns];
     const int thr = 256;
@@ -475,9 +568,10 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       const int per1 = (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / sm1));
       const unsigned b1 = (unsigned)std::max<long long>(1, std::min<long long>((long long)E->sms * per1, nt1));
       if (nt1 > 0) {
-        if (nw1 == 1) k_b_pass1<T, 1><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
-        else if (nw1 == 2) k_b_pass1<T, 2><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
-        else k_b_pass1<T, 4><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
+        // one launch per mask width, each taking the shapes of its class
+        if (has_nw[0]) k_b_pass1<T, 1><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
+        if (has_nw[1]) k_b_pass1<T, 2><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
+        if (has_nw[2]) k_b_pass1<T, 4><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
       }
       const long long nb = (ncols + kScanTile - 1) / kScanTile;
       if (ncols > 0) {
@@ -487,7 +581,11 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
                                                    cst, c_af, c_bf, c_dx, ctr);
       }
       const unsigned b2 = (unsigned)std::max<long long>(1, std::min<long long>((long long)E->sms * minb, nt2));
-      if (nt2 > 0) {
+      if (levels && ncols > 0) {
+        if ((e = cudaMemsetAsync(l_cnt, 0, sizeof(int) * nlev_all, s_)) != cudaSuccess) return e;
+        k_b_levels<T><<<E->sms * 6, 256, smL, s_>>>(dS, d_lvb, ns, lvb[ns], d_sst);
+        k_b_lgather<T><<<E->sms * perG, 256, smG, s_>>>(dS, d_colb, ns, ncols, bcapG, d_sst, ctr);
+      } else if (nt2 > 0) {
         if (minb == 2)
           k_b_pass2<T, 2><<<b2, wpb2 * 32, (size_t)sm2, s_>>>(dS, d_t2b, ns, nt2, stage_cap,
                                                              kRoundAppends, kRoundPieces, d_sst);
@@ -515,6 +613,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     fullsig.push_back(pl.capO);
     fullsig.push_back(sc1);
     fullsig.push_back(sc2);
+    fullsig.push_back(levels ? 1 : 0);
     auto gi = E->graphs.find(fullsig);
     const bool replay = gi != E->graphs.end();
     if (replay) {
@@ -532,8 +631,43 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     BK(cudaStreamSynchronize(st));
     E->needM = std::max<long long>(E->needM, (long long)hc.arena_top[1]);
     E->needO = std::max<long long>(E->needO, (long long)hc.arena_top[3]);
+    if (levels) E->needL = std::max<long long>(E->needL, (long long)hc.arena_top[2]);
     if (hc.status & ST_OVERFLOW_ARENA) continue;  // grown plan, uncaptured rerun
+    if (hc.status & ST_LEVELS_OVER) {
+      // level lists beyond their arena (grown next time) or a self-check: this signature
+      // reruns with the tiled gather
+      if (hc.arena_top[2] <= (unsigned long long)pl.capL) E->no_levels[sig] = true;
+      continue;
+    }
 
+    if (levels && (hc.status & ST_OVERFLOW_SLOT)) {
+      // columns whose lists outgrew the bucket: gathered again with a bucket for their need
+      int b = 2 * bcapG;
+      while (b < hc.max_state && b < 8192) b <<= 1;
+      if (b >= hc.max_state) {
+        int warps = 8;
+        while (warps > 1 && warps * lgather_smem(1, b) > (110LL << 10)) warps >>= 1;
+        const size_t smR = (size_t)lgather_smem(warps, b);
+        BK(cudaFuncSetAttribute(k_b_lgather_redo<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smR));
+        k_b_lgather_redo<T><<<E->sms * 2, warps * 32, smR, st>>>(dS, d_colb, ns, ncols, b, d_sst);
+        BK(cudaGetLastError());
+        // count again (the first count saw the redone columns as marked)
+        for (int q = 0; q < ns; ++q) hsst[q] &= ~BS_REDO;
+        BK(cudaMemcpyAsync(d_sst, hsst.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+        const long long nb = (ncols + kScanTile - 1) / kScanTile;
+        k_b_count<T><<<(unsigned)((ncols + thr - 1) / thr), thr, 0, st>>>(dS, d_colb, ns, ncols, cnt, d_sst);
+        k_scan1<long long><<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, cnt, pos, sums);
+        k_scan2<<<1, kScanThreads, 0, st>>>(nb, sums);
+        k_b_totals<T><<<(ns + 127) / 128, 128, 0, st>>>(dS, d_colb, ns, ncols, pos, sums, d_tot, d_sst);
+        BK(cudaGetLastError());
+        if (launches) *launches += 5;
+        BK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        BK(cudaMemcpyAsync(hsst.data(), d_sst, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+        BK(cudaMemcpyAsync(htot.data(), d_tot, sizeof(long long) * ns, cudaMemcpyDeviceToHost, st));
+        BK(cudaStreamSynchronize(st));
+        if (hc.status & ST_OVERFLOW_ARENA) continue;
+      }
+    }
     // autotuning of the tile scales: the first call of a signature times both passes at the
     // three scales (a rerun of the whole sequence per candidate) and keeps the fastest
     if (E->autotune && sc_it == E->scales.end() && depth == 0) {
