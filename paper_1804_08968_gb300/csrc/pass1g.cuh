@@ -85,6 +85,7 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
 #pragma unroll
   for (int q = 0; q < NW; ++q) m.w[q] = 0;
   int carry_p = kNoLabel, carry_ob = kNoLabel;  // segmented values of a group that continues
+  int carry_o = kNoLabel;  // the label after the previous chunk's last event
   ukey carry_key = 0;
   int cum = 0;
   for (int base = 0; base < E; base += 32) {
@@ -110,56 +111,63 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
 #endif
       M.w[q] = m.w[q] ^ x;
     }
-    // candidate label of the height itself: after an open, before a close
-    int pl = kNoLabel;
-    if (inwin) {
-      Mask<NW> pm;
-#pragma unroll
-      for (int q = 0; q < NW; ++q) pm.w[q] = close ? (M.w[q] | tg.w[q]) : M.w[q];
-      pl = nearest_label<NW>(pm, R);
-    }
-    // groups of equal height
+    // the label after each event: at a group's last event, the label O of the open interval
+    // above the group; after the event before it, the label below the group
+    const int oab = valid ? nearest_label<NW>(M, R) : kNoLabel;
     ukey prevk = 0;
+    int obelow = kNoLabel;
 #if defined(__CUDA_ARCH__)
     prevk = __shfl_up_sync(0xffffffffu, key, 1);
+    obelow = __shfl_up_sync(0xffffffffu, oab, 1);
 #endif
-    if (L.lane == 0) prevk = carry_key;
+    if (L.lane == 0) {
+      prevk = carry_key;
+      obelow = carry_o;
+    }
+    // groups of equal height
     const bool head = valid && (t == 0 || key != prevk);
     const bool last = valid && (t + 1 >= E || ek[t + 1] != key);
-    // label of the open interval below the group (first value of the group) and the group's
-    // point label (minimum): segmented scans, carried into the chunk when the group continues
-    int vp = pl;
-    int vob = kNoLabel;
-    if (head) {
-      Mask<NW> bm;
+    int vp = kNoLabel;   // the group's point label (a single event: not below its neighbours)
+    int vob = obelow;    // the label below the group
+    if (w_any(valid && !(head && last))) {
+      // some group has several events (or continues across chunks): the point label is the
+      // minimum over the group of the label at the height itself (after an open, before a
+      // close), and the label below is the head's; segmented scans, carried into the chunk
+      // when the group continues
+      int pl = kNoLabel;
+      if (inwin) {
+        Mask<NW> pm;
 #pragma unroll
-      for (int q = 0; q < NW; ++q) bm.w[q] = M.w[q] ^ tg.w[q];
-      vob = nearest_label<NW>(bm, R);
-    }
-    bool hd = head;
-    if (L.lane == 0 && !head && valid) {
-      vp = vp < carry_p ? vp : carry_p;
-      vob = carry_ob;
-      hd = true;
-    }
+        for (int q = 0; q < NW; ++q) pm.w[q] = close ? (M.w[q] | tg.w[q]) : M.w[q];
+        pl = nearest_label<NW>(pm, R);
+      }
+      vp = pl;
+      vob = head ? obelow : kNoLabel;
+      bool hd = head;
+      if (L.lane == 0 && !head && valid) {
+        vp = vp < carry_p ? vp : carry_p;
+        vob = carry_ob;
+        hd = true;
+      }
 #if defined(__CUDA_ARCH__)
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int p2 = __shfl_up_sync(0xffffffffu, vp, o);
-      const int ob2 = __shfl_up_sync(0xffffffffu, vob, o);
-      const bool h2 = __shfl_up_sync(0xffffffffu, hd, o);
-      if (L.lane >= o && !hd) {
-        vp = p2 < vp ? p2 : vp;
-        vob = ob2;
-        hd = h2;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int p2 = __shfl_up_sync(0xffffffffu, vp, o);
+        const int ob2 = __shfl_up_sync(0xffffffffu, vob, o);
+        const bool h2 = __shfl_up_sync(0xffffffffu, hd, o);
+        if (L.lane >= o && !hd) {
+          vp = p2 < vp ? p2 : vp;
+          vob = ob2;
+          hd = h2;
+        }
       }
-    }
 #endif
+    }
     int here = 0;
     bool pt = false, endrun = false, strun = false;
     int Ok = kNoLabel;
     if (last) {
-      Ok = nearest_label<NW>(M, R);
+      Ok = oab;
       const int Om = vob;
       pt = vp < (Om < Ok ? Om : Ok);
       endrun = Om < kNoLabel && (Ok != Om || pt);
@@ -186,6 +194,7 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
 #pragma unroll
     for (int q = 0; q < NW; ++q) m.w[q] = __shfl_sync(0xffffffffu, M.w[q], 31);
     carry_p = __shfl_sync(0xffffffffu, vp, 31);
+    carry_o = __shfl_sync(0xffffffffu, oab, 31);
     carry_ob = __shfl_sync(0xffffffffu, vob, 31);
     carry_key = __shfl_sync(0xffffffffu, key, 31);
 #endif
