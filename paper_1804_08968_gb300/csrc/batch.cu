@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_b_levels(const BShape<T>* S, const long
     if (sst[s] & BS_BAD) continue;
     const LvlParams<T>& A = S[s].lv;
     const float E = 9.5367432e-7f * (__uint_as_float(A.P.ctr->zmax_bits) + A.P.wtabf[0]);
-    levels_item<T>(A, gi - lvb[s], lane, bl, br, E, cur);
+    levels_item<T>(A, gi - lvb[s], lane, bl, br, E, A.P.wtabf, cur);
   }
 }
 

@@ -25,7 +25,9 @@
 namespace dexel {
 
 // per-lane list buffer in shared memory (intervals)
-constexpr int kLvlSlots = 16;
+constexpr int kLvlSlots = 8;
+// w-table entries k_levels keeps in shared memory (n <= k^2: radii up to 64 spacings)
+constexpr int kLvlTable = 4097;
 
 template <typename T>
 struct LvlParams {
@@ -47,9 +49,12 @@ struct LvlParams {
 // one interval at a time; the first cap intervals are stored at bl / br; returns the count.
 template <typename T>
 DXI int level_walk(const P2GParams<T>& P, long long q, int p0, int p1, int tt, float E,
-                   ukey* bl, ukey* br, int cap) {
+                   const float* wt, ukey* bl, ukey* br, int cap) {
   const long long cs = P.c_start[q];
   const long long ms = P.m_start[q];
+  const short* dxp = P.c_dx + cs;
+  const float* afp = P.c_af + cs;
+  const float* bfp = P.c_bf + cs;
   int cnt = 0;
   bool have = false;
   float clf = 0.0f, crf = 0.0f;
@@ -61,13 +66,19 @@ DXI int level_walk(const P2GParams<T>& P, long long q, int p0, int p1, int tt, f
     }
     ++cnt;
   };
+  // the next piece is loaded while the current one is merged
+  int dxn = 0;
+  float afn = 0.0f, bfn = 0.0f;
+  if (p0 < p1) { dxn = dxp[p0]; afn = afp[p0]; bfn = bfp[p0]; }
   for (int p = p0; p < p1; ++p) {
-    const int dx = P.c_dx[cs + p];
+    const int dx = dxn;
+    const float af = afn, bf = bfn;
+    if (p + 1 < p1) { dxn = dxp[p + 1]; afn = afp[p + 1]; bfn = bfp[p + 1]; }
     const int n = dx * dx + tt;
     const bool in = n <= P.nmax;
-    const float wf = P.wtabf[in ? n : 0];
-    const float lf = P.c_af[cs + p] - wf;
-    const float rf = P.c_bf[cs + p] + wf;
+    const float wf = wt[in ? n : 0];
+    const float lf = af - wf;
+    const float rf = bf + wf;
     const float dl = lf - clf, dr = rf - crf;
     const bool ov = lf <= crf - E && rf >= clf + E;  // certain overlap
     const bool decided = !(fabsf(dl) < E) && !(fabsf(dr) < E);
@@ -92,7 +103,8 @@ DXI int level_walk(const P2GParams<T>& P, long long q, int p0, int p1, int tt, f
 // or (source, level group).  bl / br: the lane's buffer slots (br = bl + 32 slots).
 template <typename T>
 __device__ __forceinline__ void levels_item(const LvlParams<T>& A, long long item, int lane,
-                                            ukey* bl, ukey* br, float E, ArenaCursor& cur) {
+                                            ukey* bl, ukey* br, float E, const float* wt,
+                                            ArenaCursor& cur) {
   const Lanes Ln{lane, 32};
   const P2GParams<T>& P = A.P;
   long long q;
@@ -116,7 +128,7 @@ __device__ __forceinline__ void levels_item(const LvlParams<T>& A, long long ite
       set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
       act = false;
     } else {
-      cnt = level_walk<T>(P, q, 0, np, t * t, E, bl, br, kLvlSlots);
+      cnt = level_walk<T>(P, q, 0, np, t * t, E, wt, bl, br, kLvlSlots);
     }
   }
   // the lanes' lists, contiguous in the level arena; a list longer than its buffer is
@@ -133,7 +145,7 @@ __device__ __forceinline__ void levels_item(const LvlParams<T>& A, long long ite
     if (cnt <= kLvlSlots) {
       for (int k = 0; k < cnt; ++k) { A.l_l[o + k] = bl[k]; A.l_r[o + k] = br[k]; }
     } else {
-      level_walk<T>(P, q, 0, np, t * t, E, A.l_l + o, A.l_r + o, cnt);
+      level_walk<T>(P, q, 0, np, t * t, E, wt, A.l_l + o, A.l_r + o, cnt);
     }
     if (act) {
       A.l_start[q * A.L + t] = o;
@@ -150,7 +162,7 @@ __device__ __forceinline__ void levels_item(const LvlParams<T>& A, long long ite
     }
     const int per = (np0 + 31) >> 5;
     const int p0 = min(np0, lane * per), p1 = min(np0, p0 + per);
-    const int cnt0 = level_walk<T>(P, q, p0, p1, 0, E, bl, br, kLvlSlots);
+    const int cnt0 = level_walk<T>(P, q, p0, p1, 0, E, wt, bl, br, kLvlSlots);
     const int inc = w_incl_add(cnt0, lane);
     const int tot = w_bcast(inc, 31);
     const long long s = arena_take(Ln, &P.ctr->arena_top[2], P.blk, cur, tot);
@@ -162,7 +174,7 @@ __device__ __forceinline__ void levels_item(const LvlParams<T>& A, long long ite
     if (cnt0 <= kLvlSlots) {
       for (int k = 0; k < cnt0; ++k) { A.l_l[o + k] = bl[k]; A.l_r[o + k] = br[k]; }
     } else {
-      level_walk<T>(P, q, p0, p1, 0, E, A.l_l + o, A.l_r + o, cnt0);
+      level_walk<T>(P, q, p0, p1, 0, E, wt, A.l_l + o, A.l_r + o, cnt0);
     }
     if (lane == 0) {
       A.l_start[q * A.L] = s;
