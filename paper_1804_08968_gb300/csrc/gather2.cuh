@@ -75,6 +75,71 @@ DXI void warp_bitonic(const Lanes& L, ukey* key, ukey* val, int n) {
   }
 }
 
+// Bitonic sort of (key, val) pairs by key held in registers: PER pairs a lane, element
+// i = r * 32 + lane (so that the shared-memory loads and stores are conflict free); steps
+// with partner distance >= 32 swap within a lane, shorter ones exchange by shuffles.
+template <int PER>
+__device__ __forceinline__ void reg_sort_pairs(ukey* key, ukey* val, int n2, int lane) {
+#if defined(__CUDA_ARCH__)
+  ukey k[PER], v[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int i = r * 32 + lane;
+    k[r] = i < n2 ? key[i] : ~0ULL;
+    v[r] = i < n2 ? val[i] : ~0ULL;
+  }
+  const int n = 32 * PER;
+  for (int kk = 2; kk <= n; kk <<= 1) {
+#pragma unroll
+    for (int jr = PER / 2; jr > 0; jr >>= 1) {  // distance jr * 32: within the lane
+      if (jr * 32 > (kk >> 1)) continue;
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        const int rp = r ^ jr;
+        if (rp > r) {
+          const bool up = ((r * 32 + lane) & kk) == 0;
+          if ((k[r] > k[rp]) == up) {
+            const ukey tk = k[r]; k[r] = k[rp]; k[rp] = tk;
+            const ukey tv = v[r]; v[r] = v[rp]; v[rp] = tv;
+          }
+        }
+      }
+    }
+    for (int jj = (kk >> 1) < 16 ? (kk >> 1) : 16; jj > 0; jj >>= 1) {  // across lanes
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        const ukey ko = __shfl_xor_sync(0xffffffffu, k[r], jj);
+        const ukey vo = __shfl_xor_sync(0xffffffffu, v[r], jj);
+        const bool up = ((r * 32 + lane) & kk) == 0;
+        const bool lower = (lane & jj) == 0;
+        const bool take = lower ? ((k[r] > ko) == up) : ((ko > k[r]) == up);
+        if (take) { k[r] = ko; v[r] = vo; }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int i = r * 32 + lane;
+    if (i < n2) { key[i] = k[r]; val[i] = v[r]; }
+  }
+  __syncwarp();
+#endif
+}
+
+// Sort of n2 (a power of two) pairs in shared memory by key: in registers up to 256, else
+// the shared-memory network.
+DXI void warp_sort_pairs(const Lanes& L, ukey* key, ukey* val, int n2) {
+#if defined(__CUDA_ARCH__)
+  if (n2 <= 32) reg_sort_pairs<1>(key, val, n2, L.lane);
+  else if (n2 <= 64) reg_sort_pairs<2>(key, val, n2, L.lane);
+  else if (n2 <= 128) reg_sort_pairs<4>(key, val, n2, L.lane);
+  else if (n2 <= 256) reg_sort_pairs<8>(key, val, n2, L.lane);
+  else warp_bitonic(L, key, val, n2);
+#else
+  warp_bitonic(L, key, val, n2);
+#endif
+}
+
 DXI int pow2_at_least(int n) {
   int m = 1;
   while (m < n) m <<= 1;

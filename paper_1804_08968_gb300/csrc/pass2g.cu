@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_pass2c(P2GParams<T> P) {
     const int n2 = pow2_at_least(total);
     for (int t = total + lane; t < n2; t += 32) { bl[t] = ~0ULL; br[t] = ~0ULL; }
     wsync();
-    if (n2 > 1) warp_bitonic(L, bl, br, n2);
+    if (n2 > 1) warp_sort_pairs(L, bl, br, n2);
     PHASE(2);
     PHASE_COUNT(11, n2);
     const int no = total > 0 ? union_runs(L, bl, br, total, true, f0, f1, ul, ur, br, nullptr) : 0;

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) k_levels(LvlParams<T> A) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_lgather(LvlParams<T> A, int bcap, int redo) {
+__global__ void __launch_bounds__(256, 3) k_lgather(LvlParams<T> A, int bcap, int redo) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* wb = smem + (long long)warp * (bcap * (2 * sizeof(ukey) + 2 * sizeof(int)) + 16);

@@ -238,9 +238,12 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
     return;
   }
   const int n2 = pow2_at_least(total);
-  for (int t = total + lane; t < n2; t += 32) { bl[t] = ~0ULL; br[t] = ~0ULL; }
   wsync();
-  if (n2 > 1) warp_bitonic(L, bl, br, n2);
+  if (n2 > 1) {
+    for (int t = total + lane; t < n2; t += 32) { bl[t] = ~0ULL; br[t] = ~0ULL; }
+    wsync();
+    warp_sort_pairs(L, bl, br, n2);
+  }
   const int no = total > 0 ? union_count(L, bl, br, total, f0, f1) : 0;
   const long long s = arena_take(L, &P.ctr->arena_top[3], P.blk, cur, no);
   const bool fits = s + no <= P.o_cap;
