@@ -32,7 +32,7 @@ DXI bool column_cover(const P2GParams<T>& P, const Lanes& L, int j, int s0, cons
       const int n2 = pow2_at_least(n);
       for (int t = n + L.lane; t < n2; t += 32) { bl[t] = ~0ULL; br[t] = ~0ULL; }
       wsync();
-      if (n2 > 1) warp_sort_pairs(L, bl, br, n2);
+      if (n2 > 1) warp_bitonic(L, bl, br, n2);
       acc = union_count(L, bl, br, n, f0, f1);
       union_write_inplace(L, bl, br, n, f0, f1);
     }
