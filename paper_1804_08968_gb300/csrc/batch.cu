@@ -111,6 +111,10 @@ __global__ void __launch_bounds__(256) k_b_pass1(const BShape<T>* S, const long 
     const P1Params<T> P = S[s].p1;
     pass1g_tile<T, NW>(P, gt - t1b[s], S[s].tc1, ecap, obuf, smem, cur);
   }
+  if ((threadIdx.x & 31) == 0 && cur.tally > 0) {
+    add_total(&S[0].p1.ctr->mid_total, cur.tally);
+    note_max(&S[0].p1.ctr->max_pieces, cur.tmax);
+  }
 }
 
 template <typename T, int MINB>
@@ -164,6 +168,9 @@ __global__ void __launch_bounds__(256) k_b_lgather(const BShape<T>* S, const lon
     const int s = find_base(colb, ns, gi);
     if (sst[s] & BS_BAD) continue;
     lgather_column<T>(S[s].lv, gi - colb[s], bcap, 0, lane, wb, cur);
+  }  if (lane == 0 && cur.tally > 0) {
+    add_total(&S[0].p2.ctr->out_total, cur.tally);
+    note_max(&S[0].p2.ctr->max_out, cur.tmax);
   }
 }
 
@@ -181,6 +188,9 @@ __global__ void __launch_bounds__(256) k_b_lgather_redo(const BShape<T>* S, cons
     const int s = find_base(colb, ns, gi);
     if (sst[s] & BS_BAD) continue;
     lgather_column<T>(S[s].lv, gi - colb[s], bcap, 1, lane, wb, cur);
+  }  if (lane == 0 && cur.tally > 0) {
+    add_total(&S[0].p2.ctr->out_total, cur.tally);
+    note_max(&S[0].p2.ctr->max_out, cur.tmax);
   }
 }
 

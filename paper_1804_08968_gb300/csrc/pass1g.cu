@@ -11,6 +11,10 @@ __global__ void __launch_bounds__(256) k_pass1g(P1Params<T> P, int tc, int ecap,
   ArenaCursor cur{0, 0};
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
     pass1g_tile<T, NW>(P, tile, tc, ecap, obuf, smem, cur);
+  if ((threadIdx.x & 31) == 0 && cur.tally > 0) {
+    add_total(&P.ctr->mid_total, cur.tally);
+    note_max(&P.ctr->max_pieces, cur.tmax);
+  }
 }
 
 template <typename T>

@@ -79,7 +79,7 @@ DXI int nearest_label(const Mask<NW>& m, int R) {
 template <typename T, int NW>
 DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int E, int s0,
                          int i, int R, typename H<T>::K* oa, typename H<T>::K* ob, short* ol,
-                         int cap) {
+                         int cap, Counters* dctr = nullptr) {
   typedef typename H<T>::K Key;
   Mask<NW> m;  // open sources before the chunk
 #pragma unroll
@@ -129,7 +129,13 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
     const bool last = valid && (t + 1 >= E || ek[t + 1] != key);
     int vp = kNoLabel;   // the group's point label (a single event: not below its neighbours)
     int vob = obelow;    // the label below the group
+#if defined(DEXEL_PHASES) && defined(__CUDA_ARCH__)
+    if (dctr && L.lane == 0) atomicAdd(&dctr->phase[8], 1ULL);
+#endif
     if (w_any(valid && !(head && last))) {
+#if defined(DEXEL_PHASES) && defined(__CUDA_ARCH__)
+      if (dctr && L.lane == 0) atomicAdd(&dctr->phase[9], 1ULL);
+#endif
       // some group has several events (or continues across chunks): the point label is the
       // minimum over the group of the label at the height itself (after an open, before a
       // close), and the label below is the head's; segmented scans, carried into the chunk
@@ -141,25 +147,21 @@ DXI int column_partition(const Lanes& L, const ukey* ek, const unsigned* ep, int
         for (int q = 0; q < NW; ++q) pm.w[q] = close ? (M.w[q] | tg.w[q]) : M.w[q];
         pl = nearest_label<NW>(pm, R);
       }
-      vp = pl;
-      vob = head ? obelow : kNoLabel;
-      bool hd = head;
-      if (L.lane == 0 && !head && valid) {
-        vp = vp < carry_p ? vp : carry_p;
-        vob = carry_ob;
-        hd = true;
-      }
+      // the group's first lane in this chunk: the last head at or below this lane (none: the
+      // group continues from the previous chunk)
 #if defined(__CUDA_ARCH__)
+      const unsigned hm = __ballot_sync(0xffffffffu, head);
+      const unsigned below = hm & (0xffffffffu >> (31 - L.lane));
+      const int hl = below ? 31 - __clz((int)below) : -1;
+      const int ob_head = __shfl_sync(0xffffffffu, obelow, hl < 0 ? 0 : hl);
+      vob = hl >= 0 ? ob_head : carry_ob;
+      const int seg0 = hl >= 0 ? hl : 0;
+      vp = pl;
+      if (hl < 0) vp = vp < carry_p ? vp : carry_p;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int p2 = __shfl_up_sync(0xffffffffu, vp, o);
-        const int ob2 = __shfl_up_sync(0xffffffffu, vob, o);
-        const bool h2 = __shfl_up_sync(0xffffffffu, hd, o);
-        if (L.lane >= o && !hd) {
-          vp = p2 < vp ? p2 : vp;
-          vob = ob2;
-          hd = h2;
-        }
+        if (L.lane - o >= seg0) vp = p2 < vp ? p2 : vp;
       }
 #endif
     }
@@ -317,6 +319,7 @@ __device__ __forceinline__ void pass1g_tile(const P1Params<T>& P, long long tile
     }
     for (int t = E + threadIdx.x; t < n2; t += blockDim.x) { ek[t] = ~0ULL; ep[t] = kEvNone; }
     __syncthreads();
+    PHASE_BEGIN();
     // block bitonic sort by (height, open before close)
     for (int k = 2; k <= n2; k <<= 1) {
       for (int jj = k >> 1; jj > 0; jj >>= 1) {
@@ -336,13 +339,15 @@ __device__ __forceinline__ void pass1g_tile(const P1Params<T>& P, long long tile
         __syncthreads();
       }
     }
+    PHASE(0);
     // output columns of the run: pieces go to the warp's buffer, then to the arena; a column
     // with more pieces than the buffer holds is walked a second time straight into the arena
     for (int i = ia + warp; i < ib; i += nwb) {
       Key* ba = wbuf_a + (long long)warp * obuf;
       Key* bb = wbuf_b + (long long)warp * obuf;
       short* bl = wbuf_l + (long long)warp * obuf;
-      const int n = column_partition<T, NW>(L, ek, ep, E, s0, i, R, ba, bb, bl, obuf);
+      const int n = column_partition<T, NW>(L, ek, ep, E, s0, i, R, ba, bb, bl, obuf, P.ctr);
+      PHASE(1);
       const long long s = arena_take(L, &P.ctr->arena_top[1], P.blk, cur, n);
       const bool fits = s + n <= P.m_cap;
       if (fits && n > 0) {
@@ -357,12 +362,17 @@ __device__ __forceinline__ void pass1g_tile(const P1Params<T>& P, long long tile
         const long long q = (long long)i * P.ny + j;
         P.m_start[q] = fits ? s : 0;
         P.m_cnt[q] = n;
-        note_max(&P.ctr->max_pieces, n);
-        add_total(&P.ctr->mid_total, n);
+        cur.tally += n;
+        cur.tmax = n > cur.tmax ? n : cur.tmax;
+        PHASE_COUNT(10, 1);
+        PHASE_COUNT(11, E);
+        PHASE_COUNT(12, n > obuf ? 1 : 0);
       }
       wsync();
+      PHASE(2);
     }
     __syncthreads();
+    PHASE(3);
     ia = ib;
   }
 }

@@ -37,6 +37,10 @@ __global__ void __launch_bounds__(256, 3) k_lgather(LvlParams<T> A, int bcap, in
   ArenaCursor cur{0, 0};
   for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + warp; item < ncols; item += nw)
     lgather_column<T>(A, item, bcap, redo, lane, wb, cur);
+  if (lane == 0 && cur.tally > 0) {
+    add_total(&A.P.ctr->out_total, cur.tally);
+    note_max(&A.P.ctr->max_out, cur.tmax);
+  }
 }
 
 template <typename T>

@@ -255,8 +255,8 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
   if (lane == 0) {
     P.o_start[c] = fits ? s : 0;
     P.o_cnt[c] = no;
-    note_max(&P.ctr->max_out, no);
-    add_total(&P.ctr->out_total, no);
+    cur.tally += no;
+    cur.tmax = no > cur.tmax ? no : cur.tmax;
   }
   wsync();
 }

@@ -76,6 +76,8 @@ struct Counters {
 
 struct ArenaCursor {
   long long cur, end;
+  long long tally;  // entries written by this warp (lane 0), added to a counter at the end
+  int tmax;         // the largest column of this warp (lane 0)
 };
 
 // Reserve n consecutive entries of an arena for one column (warp-uniform result).
