@@ -141,8 +141,9 @@ __global__ void __launch_bounds__(256) k_b_levels(const BShape<T>* S, const long
                                                   int ns, long long nitems, const int* sst) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ukey* bl = (ukey*)smem + (long long)warp * 64 * kLvlSlots + lane * kLvlSlots;
-  ukey* br = bl + 32 * kLvlSlots;
+  const LvlLayout Lo = lvl_layout(blockDim.x >> 5, 0);
+  unsigned* ws = (unsigned*)(smem + Lo.slots) + warp * 2 * kLvlSlots * 32;
+  float4* stg = (float4*)(smem + Lo.stage) + warp * kLvlStage;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   ArenaCursor cur{0, 0};
   for (long long gi = (long long)blockIdx.x * (blockDim.x >> 5) + warp; gi < nitems; gi += nw) {
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) k_b_levels(const BShape<T>* S, const long
     if (sst[s] & BS_BAD) continue;
     const LvlParams<T>& A = S[s].lv;
     const float E = 9.5367432e-7f * (__uint_as_float(A.P.ctr->zmax_bits) + A.P.wtabf[0]);
-    levels_item<T>(A, gi - lvb[s], lane, bl, br, E, A.P.wtabf, cur);
+    levels_item<T, false>(A, gi - lvb[s], lane, ws, stg, E, A.P.wtabf, cur);
   }
 }
 
@@ -357,7 +358,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     colb[s + 1] = colb[s] + nc;
     {
       const int L = K[s] + 1;
-      const long long items = L <= 32 ? (nc + (32 / L) - 1) / (32 / L) : nc * ((K[s] + 31) / 32);
+      const long long items = lvl_items(nc, L);
       lvb[s + 1] = lvb[s] + items;
       nlb[s + 1] = nlb[s] + nc * L;
     }
@@ -558,7 +559,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     BK(cudaMemcpyAsync(dB, hb, sizeof(long long) * 5 * (ns + 1), cudaMemcpyHostToDevice, st));
 
     // level kernels' geometry
-    const size_t smL = (size_t)8 * 64 * kLvlSlots * sizeof(ukey);
+    const size_t smL = (size_t)lvl_layout(8, 0).total;
     const int bcapG = 256;
     const size_t smG = (size_t)lgather_smem(8, bcapG);
     const int perG = (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / (long long)smG));

@@ -6,24 +6,22 @@
 
 namespace dexel {
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_levels(LvlParams<T> A) {
+template <typename T, bool LTAB>
+__global__ void __launch_bounds__(256, 4) k_levels(LvlParams<T> A, int tab_floats) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ukey* bl = (ukey*)smem + (long long)warp * 64 * kLvlSlots + lane * kLvlSlots;
-  ukey* br = bl + 32 * kLvlSlots;
-  // the w table in shared memory when it is short
-  float* swt = (float*)((ukey*)smem + (long long)(blockDim.x >> 5) * 64 * kLvlSlots);
-  const int ntab = A.P.nmax + 1 <= kLvlTable ? A.P.nmax + 1 : 0;
-  for (int q = threadIdx.x; q < ntab; q += blockDim.x) swt[q] = A.P.wtabf[q];
+  const LvlLayout Lo = lvl_layout(blockDim.x >> 5, tab_floats);
+  unsigned* ws = (unsigned*)(smem + Lo.slots) + warp * 2 * kLvlSlots * 32;
+  float4* stg = (float4*)(smem + Lo.stage) + warp * kLvlStage;
+  const float* tab = lvl_tables<LTAB>((float*)(smem + Lo.tab), A.P.R, A.L, A.G, A.NG, A.P.nmax,
+                                      A.P.wtabf);
   __syncthreads();
-  const float* wt = ntab > 0 ? swt : A.P.wtabf;
   const float E = 9.5367432e-7f * (__uint_as_float(A.P.ctr->zmax_bits) + A.P.wtabf[0]);  // 2^-20
-  const long long nitems = A.NG == 0 ? (A.nsrc + A.G - 1) / A.G : A.nsrc * A.NG;
+  const long long nitems = lvl_items(A.nsrc, A.L);
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   ArenaCursor cur{0, 0};
   for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + warp; item < nitems; item += nw)
-    levels_item<T>(A, item, lane, bl, br, E, wt, cur);
+    levels_item<T, LTAB>(A, item, lane, ws, stg, E, tab, cur);
 }
 
 template <typename T>
@@ -73,10 +71,19 @@ cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms) {
   // lists a warp skips (an overflow) then read as empty
   cudaError_t e = cudaMemsetAsync(H.l_cnt, 0, sizeof(int) * A.nlev, st);
   if (e != cudaSuccess) return e;
-  const size_t sm1 = (size_t)8 * 64 * kLvlSlots * sizeof(ukey) + kLvlTable * sizeof(float);
-  e = cudaFuncSetAttribute(k_levels<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-  if (e != cudaSuccess) return e;
-  k_levels<T><<<sms * 6, 256, sm1, st>>>(A);
+  const long long lt = lvl_lane_tab(H.P.R);
+  const bool ltab = lt <= kLvlLaneTab;
+  const int tab_floats = ltab ? (int)lt : (H.P.nmax + 1 <= kLvlTable ? H.P.nmax + 1 : 0);
+  const size_t sm1 = (size_t)lvl_layout(8, tab_floats).total;
+  if (ltab) {
+    e = cudaFuncSetAttribute(k_levels<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e != cudaSuccess) return e;
+    k_levels<T, true><<<sms * 4, 256, sm1, st>>>(A, tab_floats);
+  } else {
+    e = cudaFuncSetAttribute(k_levels<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e != cudaSuccess) return e;
+    k_levels<T, false><<<sms * 4, 256, sm1, st>>>(A, tab_floats);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return launch_lgather<T>(H, H.bcap, 0, st, sms);
 }

@@ -7,27 +7,40 @@
 //
 //   k_levels   for every source column and every level t = 0 .. R, the union of its slices,
 //              appended as a short list of exact intervals (float-filtered merges, exact
-//              ends, as in gather2.cuh).  One lane a level: the lanes of a warp walk the same
-//              pieces in height order (broadcast loads), each with its own radius
-//              w(dx, t).  Short windows pack several sources into a warp (lane = (source,
-//              level)); long ones split the levels into groups of 32 and give level 0 to
-//              all 32 lanes, each a range of the pieces.
+//              ends, as in gather2.cuh).  One lane a level: short windows pack several
+//              sources into a warp (lane = (source, level)); long ones give a warp one source
+//              and 32 levels (the pieces staged in shared memory, broadcast reads), and level
+//              0 one lane per source.  Each lane's radius comes from its own column of a
+//              table indexed by |dx| (conflict-free shared-memory reads).  The walk records
+//              only which pieces set the ends; the exact ends are computed afterwards by all
+//              lanes together, so the double arithmetic stays out of the divergent loop.
 //   k_lgather  for every output column, the lists (j', |j - j'|) of its window gathered into
-//              a bucket, sorted by left end and united exactly.
+//              a bucket and united exactly: by jumps (a run's right end raised by warp
+//              reductions until it stops rising), or sorted when the runs are many.
 //
 // Every (source, level) union is computed once instead of twice, by a walk without range
-// splits or segment bookkeeping.  A list longer than its lane's buffer is walked a second
+// splits or segment bookkeeping.  A list longer than its lane's slots is walked a second
 // time straight into place; a column whose lists outgrow the bucket is gathered again with a
 // larger one.
 #pragma once
 #include "gather2.cuh"
 
+#define DXD __device__ __forceinline__
+
 namespace dexel {
 
-// per-lane list buffer in shared memory (intervals)
-constexpr int kLvlSlots = 8;
-// w-table entries k_levels keeps in shared memory (n <= k^2: radii up to 64 spacings)
+// per-lane interval slots in shared memory (a slot: the pieces and |dx| of the two ends)
+constexpr int kLvlSlots = 16;
+// pieces a warp stages in shared memory at a time (a level group walks one source)
+constexpr int kLvlStage = 64;
+// w-table entries kept in shared memory when the per-lane tables do not fit (n <= k^2:
+// radii up to 64 spacings)
 constexpr int kLvlTable = 4097;
+// shared memory for the per-lane tables (floats): (level groups) x (R + 1) x 32 lanes
+constexpr int kLvlLaneTab = 12288;
+// piece index and |dx| packed in one word: index < 2^21, |dx| < 2^11
+constexpr int kLvlDxBits = 11;
+constexpr int kLvlMaxPieces = 1 << (32 - kLvlDxBits);
 
 template <typename T>
 struct LvlParams {
@@ -45,144 +58,417 @@ struct LvlParams {
   long long m_cap, c_cap;  // entries of the S_mid arena and of its packed copy
 };
 
-// One lane's walk over source q's pieces [p0, p1) at level t (tt = t^2), uniting slices into
-// one interval at a time; the first cap intervals are stored at bl / br; returns the count.
+// Work items of k_levels: L <= 32, groups of G = 32 / L sources (lane = (source, level));
+// L > 32, first the level-0 items (32 sources, lane = source), then (source, level group).
+DXI long long lvl_level0_items(long long nsrc, int L) { return L <= 32 ? 0 : (nsrc + 31) / 32; }
+DXI long long lvl_items(long long nsrc, int L) {
+  if (L <= 32) return (nsrc + (32 / L) - 1) / (32 / L);
+  return lvl_level0_items(nsrc, L) + nsrc * ((L - 1 + 31) / 32);
+}
+
+// entries of the per-lane tables: (level groups) x (R + 1) x 32, then the level-0 row (R + 1)
+DXI long long lvl_lane_tab(int R) {
+  const int L = R + 1;
+  const int ng = L <= 32 ? 1 : (R + 31) / 32;
+  return (long long)ng * L * 32 + L;
+}
+
+// shared memory of k_levels: per warp the slots (2 x kLvlSlots x 32 words) and the staged
+// pieces (kLvlStage float4), then the table
+struct LvlLayout {
+  long long slots, stage, tab, total;
+};
+DXI LvlLayout lvl_layout(int warps, int tab_floats) {
+  LvlLayout o;
+  o.slots = 0;
+  o.stage = (long long)warps * 2 * kLvlSlots * 32 * sizeof(unsigned);
+  o.tab = o.stage + (long long)warps * kLvlStage * 16;
+  o.total = o.tab + (long long)tab_floats * sizeof(float);
+  return o;
+}
+
+// The float radius of a piece at |dx| for one lane's level (negative: dx^2 + t^2 > k^2).
+// STab: a table indexed by |dx| << sh (the per-lane tables: sh = 5, the lane's column;
+// level 0: sh = 0).  FlatTab: w[dx^2 + t^2].
+struct STab {
+  const float* p;
+  int sh;
+  DXD float operator()(int adx) const { return p[adx << sh]; }
+};
+struct FlatTab {
+  const float* w;
+  int tt;
+  int nmax;
+  DXD float operator()(int adx) const {
+    const int n = adx * adx + tt;
+    return n <= nmax ? w[n] : -1.0f;
+  }
+};
+
+// State of one lane's walk: the open interval (float ends) and the pieces that set its ends.
+struct LvlRun {
+  float clf, crf;
+  int gl, gr, al, ar;  // piece index and |dx| of the left / right end
+  bool have;
+  int cnt;  // intervals closed so far
+};
+DXD LvlRun lvl_run() { return LvlRun{0.0f, 0.0f, 0, 0, 0, 0, false, 0}; }
+
+// One step of a level walk (Sec. 3.3: the slice [a - w, b + w] of piece p at this lane's
+// level): merged into the open interval when the overlap is certain under the float error
+// bound E, else the open interval is closed (emit) and the slice opens the next one.
+template <typename Emit>
+DXD void lvl_step(LvlRun& s, float af, float bf, int adx, int p, float wf, float E,
+                  const Emit& emit) {
+  const bool in = wf >= 0.0f;
+  const float lf = af - wf;
+  const float rf = bf + wf;
+  const float dl = lf - s.clf, dr = rf - s.crf;
+  const bool ov = lf <= s.crf - E && rf >= s.clf + E;  // certain overlap
+  const bool decided = !(fabsf(dl) < E) && !(fabsf(dr) < E);
+  const bool merge = in && s.have && ov && decided;
+  if (in && s.have && !merge) {
+    emit(s);
+    ++s.cnt;
+  }
+  const bool fresh = in && !merge;
+  const bool tl = fresh || (merge && dl < 0.0f);
+  const bool tr = fresh || (merge && dr > 0.0f);
+  s.clf = tl ? lf : s.clf;
+  s.gl = tl ? p : s.gl;
+  s.al = tl ? adx : s.al;
+  s.crf = tr ? rf : s.crf;
+  s.gr = tr ? p : s.gr;
+  s.ar = tr ? adx : s.ar;
+  s.have = s.have || in;
+}
+template <typename Emit>
+DXD void lvl_close(LvlRun& s, const Emit& emit) {
+  if (s.have) {
+    emit(s);
+    ++s.cnt;
+  }
+}
+
+// emit into the lane's slots (the first cap intervals): slot k of lane x at ws[k * 32 + x],
+// its right end kLvlSlots * 32 words further
+struct PackEmit {
+  unsigned* sl;  // ws + lane
+  DXD void operator()(const LvlRun& s) const {
+    if (s.cnt < kLvlSlots) {
+      sl[s.cnt << 5] = ((unsigned)s.gl << kLvlDxBits) | (unsigned)s.al;
+      sl[(s.cnt << 5) + kLvlSlots * 32] = ((unsigned)s.gr << kLvlDxBits) | (unsigned)s.ar;
+    }
+  }
+};
+
+// the exact ends: a - w(dx^2 + t^2) and b + w(dx^2 + t^2) in double
 template <typename T>
-DXI int level_walk(const P2GParams<T>& P, long long q, int p0, int p1, int tt, float E,
-                   const float* wt, ukey* bl, ukey* br, int cap) {
-  const long long cs = P.c_start[q];
-  const long long ms = P.m_start[q];
+DXD ukey lvl_left(const P2GParams<T>& P, long long ms, int p, int adx, int tt) {
+  return dkey(keyd(P.m_a[ms + p]) - P.wtab[adx * adx + tt]);
+}
+template <typename T>
+DXD ukey lvl_right(const P2GParams<T>& P, long long ms, int p, int adx, int tt) {
+  return dkey(keyd(P.m_b[ms + p]) + P.wtab[adx * adx + tt]);
+}
+
+// emit exact ends straight into the level arena (a list longer than the slots)
+template <typename T>
+struct ExactEmit {
+  const P2GParams<T>* P;
+  long long ms;
+  int tt;
+  ukey* ol;
+  ukey* orr;
+  DXD void operator()(const LvlRun& s) const {
+    ol[s.cnt] = lvl_left<T>(*P, ms, s.gl, s.al, tt);
+    orr[s.cnt] = lvl_right<T>(*P, ms, s.gr, s.ar, tt);
+  }
+};
+
+// A lane's walk over pieces [p0, p1) of the source at c_start cs, loading from the packed
+// copy (the next piece is loaded while the current one is merged).
+template <typename T, typename W, typename Emit>
+DXD void walk_global(const P2GParams<T>& P, long long cs, int p0, int p1, float E, const W& wl,
+                     LvlRun& s, const Emit& emit) {
   const short* dxp = P.c_dx + cs;
   const float* afp = P.c_af + cs;
   const float* bfp = P.c_bf + cs;
-  int cnt = 0;
-  bool have = false;
-  float clf = 0.0f, crf = 0.0f;
-  int gl = 0, gr = 0, nl = 0, nr = 0;
-  auto emit = [&]() {
-    if (cnt < cap) {
-      bl[cnt] = dkey(keyd(P.m_a[ms + gl]) - P.wtab[nl]);
-      br[cnt] = dkey(keyd(P.m_b[ms + gr]) + P.wtab[nr]);
-    }
-    ++cnt;
-  };
-  // the next piece is loaded while the current one is merged
   int dxn = 0;
   float afn = 0.0f, bfn = 0.0f;
   if (p0 < p1) { dxn = dxp[p0]; afn = afp[p0]; bfn = bfp[p0]; }
   for (int p = p0; p < p1; ++p) {
-    const int dx = dxn;
+    const int adx = min(dxn < 0 ? -dxn : dxn, P.R);  // labels lie in [-R, R]
     const float af = afn, bf = bfn;
     if (p + 1 < p1) { dxn = dxp[p + 1]; afn = afp[p + 1]; bfn = bfp[p + 1]; }
-    const int n = dx * dx + tt;
-    const bool in = n <= P.nmax;
-    const float wf = wt[in ? n : 0];
-    const float lf = af - wf;
-    const float rf = bf + wf;
-    const float dl = lf - clf, dr = rf - crf;
-    const bool ov = lf <= crf - E && rf >= clf + E;  // certain overlap
-    const bool decided = !(fabsf(dl) < E) && !(fabsf(dr) < E);
-    const bool merge = in && have && ov && decided;
-    if (in && have && !merge) emit();
-    const bool fresh = in && !merge;
-    const bool tl = fresh || (merge && dl < 0.0f);
-    const bool tr = fresh || (merge && dr > 0.0f);
-    clf = tl ? lf : clf;
-    gl = tl ? p : gl;
-    nl = tl ? n : nl;
-    crf = tr ? rf : crf;
-    gr = tr ? p : gr;
-    nr = tr ? n : nr;
-    have = have || in;
+    lvl_step(s, af, bf, adx, p, wl(adx), E, emit);
   }
-  if (have) emit();
-  return cnt;
+  lvl_close(s, emit);
 }
 
-// One work item of k_levels (see the file comment): item = a group of G sources (L <= 32)
-// or (source, level group).  bl / br: the lane's buffer slots (br = bl + 32 slots).
-template <typename T>
-__device__ __forceinline__ void levels_item(const LvlParams<T>& A, long long item, int lane,
-                                            ukey* bl, ukey* br, float E, const float* wt,
-                                            ArenaCursor& cur) {
-  const Lanes Ln{lane, 32};
-  const P2GParams<T>& P = A.P;
-  long long q;
-  int t;
-  bool act;
-  if (A.NG == 0) {
-    const int g = lane / A.L;
-    q = item * A.G + g;
-    t = lane % A.L;
-    act = g < A.G && q < A.nsrc;
-  } else {
-    q = item / A.NG;
-    t = 1 + (int)(item % A.NG) * 32 + lane;
-    act = t < A.L;
-  }
-  int cnt = 0, np = 0;
-  if (act) {
-    np = P.m_cnt[q];
-    if (np < 0 || P.m_start[q] < 0 || P.m_start[q] + np > A.m_cap || P.c_start[q] < 0 ||
-        P.c_start[q] + np > A.c_cap || q * A.L + t >= A.nlev) {
-      set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
-      act = false;
-    } else {
-      cnt = level_walk<T>(P, q, 0, np, t * t, E, wt, bl, br, kLvlSlots);
+// The warp's walk over the np pieces of one source (all lanes, each its own level): the
+// pieces pass through shared memory in chunks (coalesced loads, broadcast reads).
+template <typename T, typename W, typename Emit>
+DXD void walk_staged(const P2GParams<T>& P, long long cs, int np, int lane, float4* stg, float E,
+                     const W& wl, LvlRun& s, const Emit& emit) {
+  for (int base = 0; base < np; base += kLvlStage) {
+    const int m = min(kLvlStage, np - base);
+    wsync();
+    for (int k = lane; k < m; k += 32) {
+      const int dx = P.c_dx[cs + base + k];
+      stg[k] = make_float4(P.c_af[cs + base + k], P.c_bf[cs + base + k],
+                           __int_as_float(min(dx < 0 ? -dx : dx, P.R)), 0.0f);
+    }
+    wsync();
+    for (int k = 0; k < m; ++k) {
+      const float4 v = stg[k];
+      const int adx = __float_as_int(v.z);
+      lvl_step(s, v.x, v.y, adx, base + k, wl(adx), E, emit);
     }
   }
-  // the lanes' lists, contiguous in the level arena; a list longer than its buffer is
-  // walked again straight into place
-  {
-    const int inc = w_incl_add(cnt, lane);
-    const int tot = w_bcast(inc, 31);
-    const long long s = arena_take(Ln, &P.ctr->arena_top[2], P.blk, cur, tot);
-    if (s + tot > A.l_cap) {
-      if (lane == 0) set_status(&P.ctr->status, ST_LEVELS_OVER);
-      return;
-    }
-    const long long o = s + inc - cnt;
-    if (cnt <= kLvlSlots) {
-      for (int k = 0; k < cnt; ++k) { A.l_l[o + k] = bl[k]; A.l_r[o + k] = br[k]; }
-    } else {
-      level_walk<T>(P, q, 0, np, t * t, E, wt, A.l_l + o, A.l_r + o, cnt);
-    }
-    if (act) {
-      A.l_start[q * A.L + t] = o;
-      A.l_cnt[q * A.L + t] = cnt;
-    }
-  }
-  // level 0 of a long window: all lanes, a range of the pieces each, one list
-  if (A.NG != 0 && item % A.NG == 0) {
-    const int np0 = P.m_cnt[q];
-    if (np0 < 0 || P.m_start[q] < 0 || P.m_start[q] + np0 > A.m_cap || P.c_start[q] < 0 ||
-        P.c_start[q] + np0 > A.c_cap) {
-      if (lane == 0) set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
-      return;
-    }
-    const int per = (np0 + 31) >> 5;
-    const int p0 = min(np0, lane * per), p1 = min(np0, p0 + per);
-    const int cnt0 = level_walk<T>(P, q, p0, p1, 0, E, wt, bl, br, kLvlSlots);
-    const int inc = w_incl_add(cnt0, lane);
-    const int tot = w_bcast(inc, 31);
-    const long long s = arena_take(Ln, &P.ctr->arena_top[2], P.blk, cur, tot);
-    if (s + tot > A.l_cap) {
-      if (lane == 0) set_status(&P.ctr->status, ST_LEVELS_OVER);
-      return;
-    }
-    const long long o = s + inc - cnt0;
-    if (cnt0 <= kLvlSlots) {
-      for (int k = 0; k < cnt0; ++k) { A.l_l[o + k] = bl[k]; A.l_r[o + k] = br[k]; }
-    } else {
-      level_walk<T>(P, q, p0, p1, 0, E, wt, A.l_l + o, A.l_r + o, cnt0);
-    }
-    if (lane == 0) {
-      A.l_start[q * A.L] = s;
-      A.l_cnt[q * A.L] = tot;
-    }
-  }
+  lvl_close(s, emit);
   wsync();
 }
+
+// The lanes' lists (cnt each, in the slots; lane x's at level t of source q) into the level
+// arena, contiguous per warp: the exact ends are computed by all lanes together, a list
+// longer than the slots is walked again by its lane straight into place (redo).  Returns
+// false when the arena is full (status set).
+template <typename T, typename Redo>
+DXD bool lvl_flush(const LvlParams<T>& A, int lane, const unsigned* ws, int cnt, bool act,
+                   long long q, int t, long long ms, ArenaCursor& cur, const Redo& redo) {
+  const Lanes Ln{lane, 32};
+  const P2GParams<T>& P = A.P;
+  const int inc = w_incl_add(cnt, lane);
+  const int tot = w_bcast(inc, 31);
+  const long long s = arena_take(Ln, &P.ctr->arena_top[2], P.blk, cur, tot);
+  if (s + tot > A.l_cap) {
+    if (lane == 0) set_status(&P.ctr->status, ST_LEVELS_OVER);
+    return false;
+  }
+  const int ex = inc - cnt;
+  const int tt = t * t;
+  wsync();
+  for (int b = 0; b < tot; b += 32) {
+    const int idx = b + lane;
+    int own = 0;  // the lane whose list holds entry idx: lanes with inc <= idx
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1) {
+      const int v = __shfl_sync(0xffffffffu, inc, own + st - 1);
+      own += v <= idx ? st : 0;
+    }
+    const int exo = __shfl_sync(0xffffffffu, ex, own);
+    const int cno = __shfl_sync(0xffffffffu, cnt, own);
+    const int tto = __shfl_sync(0xffffffffu, tt, own);
+    const long long mso = __shfl_sync(0xffffffffu, ms, own);
+    if (idx < tot && cno <= kLvlSlots) {
+      const int k = idx - exo;
+      const unsigned pl = ws[(k << 5) + own];
+      const unsigned pr = ws[(k << 5) + own + kLvlSlots * 32];
+      const unsigned m = (1u << kLvlDxBits) - 1;
+      A.l_l[s + idx] = lvl_left<T>(P, mso, (int)(pl >> kLvlDxBits), (int)(pl & m), tto);
+      A.l_r[s + idx] = lvl_right<T>(P, mso, (int)(pr >> kLvlDxBits), (int)(pr & m), tto);
+    }
+  }
+  if (cnt > kLvlSlots) redo(A.l_l + s + ex, A.l_r + s + ex);
+  if (act) {
+    A.l_start[q * A.L + t] = s + ex;
+    A.l_cnt[q * A.L + t] = cnt;
+  }
+  wsync();
+  return true;
+}
+
+// the bounds of source q's pieces (self-check against the arenas)
+template <typename T>
+DXD bool lvl_src_ok(const LvlParams<T>& A, long long q, int np) {
+  const P2GParams<T>& P = A.P;
+  return np >= 0 && np < kLvlMaxPieces && P.m_start[q] >= 0 && P.m_start[q] + np <= A.m_cap &&
+         P.c_start[q] >= 0 && P.c_start[q] + np <= A.c_cap;
+}
+
+// One work item of k_levels.  LTAB: the per-lane tables at tab (else tab is the flat w table).
+template <typename T, bool LTAB>
+DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* ws, float4* stg,
+                     float E, const float* tab, ArenaCursor& cur) {
+  const P2GParams<T>& P = A.P;
+  const int R1 = P.R + 1;
+  const long long n0 = lvl_level0_items(A.nsrc, A.L);
+  if (A.NG == 0 || item < n0) {
+    // lane = (source, level): a walk of its own
+    long long q;
+    int t;
+    bool act;
+    if (A.NG == 0) {
+      const int g = lane / A.L;
+      q = item * A.G + g;
+      t = lane % A.L;
+      act = g < A.G && q < A.nsrc;
+    } else {
+      q = item * 32 + lane;
+      t = 0;
+      act = q < A.nsrc;
+    }
+    int np = 0;
+    long long ms = 0, cs = 0;
+    if (act) {
+      np = P.m_cnt[q];
+      if (!lvl_src_ok(A, q, np) || q * A.L + t >= A.nlev) {
+        set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
+        act = false;
+        np = 0;
+      } else {
+        ms = P.m_start[q];
+        cs = P.c_start[q];
+      }
+    }
+    LvlRun s = lvl_run();
+    const PackEmit pe{ws + lane};
+    if (LTAB) {
+      const STab wl = A.NG == 0 ? STab{tab + lane, 5} : STab{tab + (long long)A.NG * R1 * 32, 0};
+      walk_global<T>(P, cs, 0, np, E, wl, s, pe);
+      lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
+        LvlRun s2 = lvl_run();
+        walk_global<T>(P, cs, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+      });
+    } else {
+      const FlatTab wl{tab, t * t, P.nmax};
+      walk_global<T>(P, cs, 0, np, E, wl, s, pe);
+      lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
+        LvlRun s2 = lvl_run();
+        walk_global<T>(P, cs, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+      });
+    }
+    return;
+  }
+  // (source, level group): the warp walks one source, lane = level
+  const long long it = item - n0;
+  const long long q = it / A.NG;
+  const int grp = (int)(it % A.NG);
+  const int t = 1 + grp * 32 + lane;
+  const bool act = t < A.L;
+  const int np = P.m_cnt[q];
+  if (!lvl_src_ok(A, q, np) || q * A.L + A.L > A.nlev) {
+    if (lane == 0) set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
+    return;
+  }
+  const long long ms = P.m_start[q], cs = P.c_start[q];
+  LvlRun s = lvl_run();
+  const PackEmit pe{ws + lane};
+  if (LTAB) {
+    const STab wl{tab + (long long)grp * R1 * 32 + lane, 5};
+    walk_staged<T>(P, cs, np, lane, stg, E, wl, s, pe);
+    lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
+      LvlRun s2 = lvl_run();
+      walk_global<T>(P, cs, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+    });
+  } else {
+    const FlatTab wl{tab, t * t, P.nmax};
+    walk_staged<T>(P, cs, np, lane, stg, E, wl, s, pe);
+    lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
+      LvlRun s2 = lvl_run();
+      walk_global<T>(P, cs, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+    });
+  }
+}
+
+// The tables of k_levels in shared memory.  LTAB: for every level group, |dx| and lane the
+// lane's float radius (or -1), then the level-0 row w[dx^2]; else the flat float table when
+// it fits (returns the table the walks read).
+template <bool LTAB>
+__device__ __forceinline__ const float* lvl_tables(float* tab, int R, int L, int G, int NG,
+                                                   int nmax, const float* wtabf) {
+  const int R1 = R + 1;
+  if (LTAB) {
+    const int ng = NG == 0 ? 1 : NG;
+    const int ne = ng * R1 * 32;
+    for (int e = threadIdx.x; e < ne + R1; e += blockDim.x) {
+      float v;
+      if (e < ne) {
+        const int ln = e & 31, adx = (e >> 5) % R1, grp = (e >> 5) / R1;
+        int t;
+        bool ok;
+        if (NG == 0) {
+          ok = ln < G * L;
+          t = ln % L;
+        } else {
+          t = 1 + grp * 32 + ln;
+          ok = t < L;
+        }
+        const int n = adx * adx + t * t;
+        v = ok && n <= nmax ? wtabf[n] : -1.0f;
+      } else {
+        const int adx = e - ne;
+        v = wtabf[adx * adx];
+      }
+      tab[e] = v;
+    }
+    return tab;
+  }
+  if (nmax + 1 <= kLvlTable) {
+    for (int n = threadIdx.x; n <= nmax; n += blockDim.x) tab[n] = wtabf[n];
+    return tab;
+  }
+  return wtabf;
+}
+
+// Union of a column's bucket by jumps (the union of closed intervals, Sec. 3.3): a run starts
+// at the least left end not yet covered, and its right end is raised to the largest right
+// end among the intervals that start at or below it until it no longer rises (touching
+// intervals join).  Each pass reads the bucket once and ends in warp reductions; run r is
+// kept by lane r.  Returns the run count, or -1 after kJumpPasses passes or 32 runs (the
+// caller then sorts the bucket).
+constexpr int kJumpPasses = 24;
+
+__device__ __forceinline__ ukey wmax_u64(ukey v) {
+  const unsigned h = __reduce_max_sync(0xffffffffu, (unsigned)(v >> 32));
+  const unsigned l = __reduce_max_sync(0xffffffffu, (unsigned)(v >> 32) == h ? (unsigned)v : 0u);
+  return ((ukey)h << 32) | l;
+}
+__device__ __forceinline__ ukey wmin_u64(ukey v) {
+  const unsigned h = __reduce_min_sync(0xffffffffu, (unsigned)(v >> 32));
+  const unsigned l = __reduce_min_sync(0xffffffffu, (unsigned)(v >> 32) == h ? (unsigned)v : ~0u);
+  return ((ukey)h << 32) | l;
+}
+
+// visit(f) calls f(l, pointer to r) for each interval this lane reads
+template <typename Visit>
+__device__ __forceinline__ int jump_union(const Visit& visit, int lane, ukey& run_l, ukey& run_r) {
+  ukey mn = ~0ULL;
+  visit([&](ukey l, const ukey*) { mn = l < mn ? l : mn; });
+  ukey lo = wmin_u64(mn), hi = lo;
+  int runs = 0;
+  for (int pass = 0; pass < kJumpPasses; ++pass) {
+    ukey mx = 0, nxt = ~0ULL;
+    bool more = false;
+    visit([&](ukey l, const ukey* rp) {
+      if (l <= hi) {
+        const ukey r = *rp;
+        mx = r > mx ? r : mx;
+      } else {
+        nxt = l < nxt ? l : nxt;
+        more = true;
+      }
+    });
+    mx = wmax_u64(mx);
+    if (mx > hi) {
+      hi = mx;
+      continue;
+    }
+    if (lane == runs) {
+      run_l = lo;
+      run_r = hi;
+    }
+    ++runs;
+    if (!__any_sync(0xffffffffu, more)) return runs;
+    if (runs == 32) return -1;
+    lo = hi = wmin_u64(nxt);
+  }
+  return -1;
+}
+
+// buckets up to this size are sorted (one register a lane), larger ones united by jumps
+constexpr int kJumpMin = 32;
 
 // One output column of k_lgather (item = i * ny + j); wb: the warp's bucket (bcap intervals
 // with their union flags).
@@ -227,24 +513,69 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
   }
   wsync();
   const int total = carry;
+  ukey run_l = 0, run_r = 0;
+  int nj = -1;
   if (total > bcap) {
+    // beyond the bucket: the union by jumps straight over the window's lists
+    nj = jump_union(
+        [&](auto f) {
+          for (int jj = s0 + lane; jj <= s1; jj += 32) {
+            const int t = jj > j ? jj - j : j - jj;
+            const long long li = (qb + jj) * A.L + t;
+            if (li >= A.nlev) continue;
+            const int n = A.l_cnt[li];
+            const long long st = A.l_start[li];
+            if (n < 0 || st < 0 || st + n > A.l_cap) continue;  // flagged by the gather above
+            for (int k = 0; k < n; ++k) f(A.l_l[st + k], A.l_r + st + k);
+          }
+        },
+        lane, run_l, run_r);
+    if (nj < 0) {
+      if (lane == 0) {
+        P.o_cnt[c] = -1;
+        note_max(&P.ctr->max_state, total);
+        set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
+        atomicAdd(&P.ctr->redo_cols, 1);
+      }
+      wsync();
+      return;
+    }
+  } else if (total > kJumpMin) {
+    nj = jump_union(
+        [&](auto f) {
+          for (int t = lane; t < total; t += 32) f(bl[t], br + t);
+        },
+        lane, run_l, run_r);
+  } else if (total == 0) {
+    nj = 0;
+  }
+  // the runs found by jumps; else (a small bucket, many runs, a long chain of overlaps) the
+  // bucket sorted and united
+  if (nj >= 0) {
+    const long long s = arena_take(L, &P.ctr->arena_top[3], P.blk, cur, nj);
+    const bool fits = s + nj <= P.o_cap;
+    if (!fits) {
+      if (lane == 0) set_status(&P.ctr->status, ST_OVERFLOW_ARENA);
+    } else if (lane < nj) {
+      P.o_l[s + lane] = run_l;
+      P.o_r[s + lane] = run_r;
+    }
     if (lane == 0) {
-      P.o_cnt[c] = -1;
-      note_max(&P.ctr->max_state, total);
-      set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
-      atomicAdd(&P.ctr->redo_cols, 1);
+      P.o_start[c] = fits ? s : 0;
+      P.o_cnt[c] = nj;
+      cur.tally += nj;
+      cur.tmax = nj > cur.tmax ? nj : cur.tmax;
     }
     wsync();
     return;
   }
   const int n2 = pow2_at_least(total);
-  wsync();
   if (n2 > 1) {
     for (int t = total + lane; t < n2; t += 32) { bl[t] = ~0ULL; br[t] = ~0ULL; }
     wsync();
     warp_sort_pairs(L, bl, br, n2);
   }
-  const int no = total > 0 ? union_count(L, bl, br, total, f0, f1) : 0;
+  const int no = union_count(L, bl, br, total, f0, f1);
   const long long s = arena_take(L, &P.ctr->arena_top[3], P.blk, cur, no);
   const bool fits = s + no <= P.o_cap;
   if (!fits) {
