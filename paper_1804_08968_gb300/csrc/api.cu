@@ -33,6 +33,9 @@ struct dexel_ctx {
   // capacities learnt from earlier calls (grown on overflow)
   int capA = 1024, capR = 1024, capS = 4096;
   bool sweep1 = false;  // pass 1 as the per-row sweep instead of the window gather
+  bool lane1 = true;    // pass 1 with one lane per column where the windows fit
+  int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
+  int p1l_gw = 0;       // its warps a tile (0: by the reach)
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
   // needed the redo launch
@@ -367,24 +370,40 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       // gather: tiles of tc columns whose window's events (two per segment, two more per
       // column for a complement) fit ecap; a window beyond ecap hands the call to the sweep
       const double ev_col = 2.0 * (double)in->nseg / (double)std::max<long long>(ncols, 1) + (erode ? 2.0 : 0.0);
-      // (a tile of about K/2 columns: a column's window then covers ~80 % of the tile's;
-      // measured best of K/4 .. 2K on the 512^2 and 2048^2 workloads)
-      int ecap = 2048, tc = 8;
-      while (tc < 64 && tc < K / 2) tc <<= 1;
-      while (tc > 8 && (tc + 2.0 * K + 1) * ev_col * 1.5 > 16384) tc >>= 1;
-      while (ecap < 16384 && (tc + 2.0 * K + 1) * ev_col * 1.5 > ecap) ecap <<= 1;
       // room for the densest single column's window, so that no row needs the sweep
       const double ev_win_max = (2.0 * K + 1) * 2.0 * (hc.max_segs_in + 1);
-      while (ecap < 16384 && ev_win_max > ecap) ecap <<= 1;
-      int obuf = 256;
-      while (obuf > 32 && pass1g_smem<T>(tc, K, ecap, obuf) > (220LL << 10)) obuf >>= 1;
-      while (ecap > 1024 && pass1g_smem<T>(tc, K, ecap, obuf) > (220LL << 10)) ecap >>= 1;
-      const long long sm1 = pass1g_smem<T>(tc, K, ecap, obuf);
-      const int per_sm = (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / sm1));
-      const long long ntiles = (long long)ny * ((nx + tc - 1) / tc);
-      const int b1 = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, ntiles));
-      CK(launch_pass1g<T>(p1, tc, ecap, obuf, b1, st));
-      ++ctx->launches;
+      // one lane per column: a tile of 32 columns, its window's events (32 + 2K columns) in
+      // ecap events of shared memory, room for the densest single column's window
+      const double ev_tile = (32.0 + 2.0 * K + 1) * ev_col * 2.0;
+      if (ctx->lane1 && K <= 127) {
+        int ecapL = 512;
+        while (ecapL < 16384 && (ecapL < ev_tile || ecapL < ev_win_max)) ecapL <<= 1;
+        if (ctx->p1l_ecap > 0) ecapL = ctx->p1l_ecap;
+        // warps a tile: more as the windows grow (a tile's walk is split over its warps, its
+        // sort shared); measured best on the 512^2 workload: 2 up to k = 8, 4 at k = 32
+        int gw = K <= 12 ? 2 : (K <= 48 ? 4 : 8);
+        if (ctx->p1l_gw > 0) gw = ctx->p1l_gw;
+        while (gw < 8 && pass1l_smem(K, ecapL, gw) > (220LL << 10)) gw <<= 1;
+        CK(launch_pass1l<T>(p1, ecapL, gw, sms, st));
+        ++ctx->launches;
+      } else {
+        // (a tile of about K/2 columns: a column's window then covers ~80 % of the tile's;
+        // measured best of K/4 .. 2K on the 512^2 and 2048^2 workloads)
+        int ecap = 2048, tc = 8;
+        while (tc < 64 && tc < K / 2) tc <<= 1;
+        while (tc > 8 && (tc + 2.0 * K + 1) * ev_col * 1.5 > 16384) tc >>= 1;
+        while (ecap < 16384 && (tc + 2.0 * K + 1) * ev_col * 1.5 > ecap) ecap <<= 1;
+        while (ecap < 16384 && ev_win_max > ecap) ecap <<= 1;
+        int obuf = 256;
+        while (obuf > 32 && pass1g_smem<T>(tc, K, ecap, obuf) > (220LL << 10)) obuf >>= 1;
+        while (ecap > 1024 && pass1g_smem<T>(tc, K, ecap, obuf) > (220LL << 10)) ecap >>= 1;
+        const long long sm1 = pass1g_smem<T>(tc, K, ecap, obuf);
+        const int per_sm = (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / sm1));
+        const long long ntiles = (long long)ny * ((nx + tc - 1) / tc);
+        const int b1 = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, ntiles));
+        CK(launch_pass1g<T>(p1, tc, ecap, obuf, b1, st));
+        ++ctx->launches;
+      }
       CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
@@ -904,6 +923,15 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   if (mode && strcmp(mode, "tiled") == 0) c->levels = false;
   const char* mode1 = getenv("DEXEL_PASS1");
   c->sweep1 = mode1 && strcmp(mode1, "sweep") == 0;
+  if (mode1 && strcmp(mode1, "gather") == 0) c->lane1 = false;
+  if (const char* e = getenv("DEXEL_PASS1_ECAP")) {
+    const int v = atoi(e);
+    if (v >= 256 && v <= 16384 && (v & (v - 1)) == 0) c->p1l_ecap = v;
+  }
+  if (const char* e = getenv("DEXEL_PASS1_GW")) {
+    const int v = atoi(e);
+    if (v == 1 || v == 2 || v == 4 || v == 8) c->p1l_gw = v;
+  }
   *ctx = c;
   return DEXEL_OK;
 }

@@ -23,6 +23,11 @@ cudaError_t launch_pass1g(const P1Params<T>& P, int tc, int ecap, int obuf, int 
                           cudaStream_t st);
 template <typename T>
 long long pass1g_smem(int tc, int R, int ecap, int obuf);
+// pass 1 with one lane per output column (pass1l.cu); ecap (a power of two) events a tile,
+// gw (1, 2, 4, 8) warps a tile
+template <typename T>
+cudaError_t launch_pass1l(const P1Params<T>& P, int ecap, int gw, int sms, cudaStream_t st);
+long long pass1l_smem(int R, int ecap, int gw);
 template <typename T>
 cudaError_t launch_pass2(const P2Params<T>& P, int blocks, cudaStream_t st);
 template <typename T>

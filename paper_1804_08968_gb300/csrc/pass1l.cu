@@ -1,0 +1,55 @@
+// Pass-1 kernel with one lane per output column (the formulation and the per-tile body are
+// in pass1l.cuh).
+#include <algorithm>
+
+#include "launch.h"
+#include "pass1l.cuh"
+
+namespace dexel {
+
+constexpr int kP1LWarps = 8;
+
+// the block's warps in groups of gw (1, 2, 4, 8), each group its own tiles and shared memory
+template <typename T, int NH>
+__global__ void __launch_bounds__(256, 3) k_pass1l(P1Params<T> P, int ecap, int gw) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5;
+  const int groups = (blockDim.x >> 5) / gw;
+  const TGroup G{gw, warp / gw, warp % gw, (int)threadIdx.x % (gw * 32)};
+  unsigned char* gsm = smem + (long long)G.gid * p1l_layout(P.K, ecap, gw).total;
+  const long long ntiles = (long long)P.ny * ((P.nx + 31) >> 5);
+  ArenaCursor cur{0, 0};
+  for (long long tile = (long long)blockIdx.x * groups + G.gid; tile < ntiles;
+       tile += (long long)gridDim.x * groups)
+    pass1l_tile<T, NH>(P, tile, ecap, gsm, G, cur);
+  if (G.gtid == 0 && cur.tally > 0) {
+    add_total(&P.ctr->mid_total, cur.tally);
+    note_max(&P.ctr->max_pieces, cur.tmax);
+  }
+}
+
+long long pass1l_smem(int R, int ecap, int gw) {
+  return p1l_layout(R, ecap, gw).total * (kP1LWarps / gw);
+}
+
+template <typename T>
+cudaError_t launch_pass1l(const P1Params<T>& P, int ecap, int gw, int sms, cudaStream_t st) {
+  if (gw != 1 && gw != 2 && gw != 4 && gw != 8) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)pass1l_smem(P.K, ecap, gw);
+  if (smem > (220u << 10) || P.K > 127) return cudaErrorInvalidValue;
+  auto kern = P.K <= 64 ? k_pass1l<T, 1> : k_pass1l<T, 2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (long long)P.ny * ((P.nx + 31) >> 5);
+  const int groups = kP1LWarps / gw;
+  const int per_sm = (int)std::max<long long>(1, std::min<long long>(3, (220LL << 10) / (long long)smem));
+  const long long want = (ntiles + groups - 1) / groups;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, want));
+  kern<<<blocks, kP1LWarps * 32, smem, st>>>(P, ecap, gw);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_pass1l<float>(const P1Params<float>&, int, int, int, cudaStream_t);
+template cudaError_t launch_pass1l<double>(const P1Params<double>&, int, int, int, cudaStream_t);
+
+}  // namespace dexel

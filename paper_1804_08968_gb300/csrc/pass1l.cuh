@@ -1,0 +1,393 @@
+// Pass 1 of the dexel offset (Sec. 3.3, the extrusion along x) with one lane per output
+// column.
+//
+// The partition is the one of pass1g.cuh: between consecutive distinct endpoint heights the
+// open interval carries the label O = min |i - i'| over the sources i' open there, and the
+// height v itself the label P <= min(O_below, O_above); the pieces are the maximal runs of
+// equal O (closed) and the points [v, v] with P below both neighbours.  Every source that
+// contains v is open below it, open above it, or has an event at v, so P = min(O_below,
+// O_above, g) with g the least |i - i'| over the sources with an event at v: a point exists
+// exactly when g < min(O_below, O_above), and it does not matter in which order the events of
+// one height are applied.
+//
+// GB300 mapping: a block takes 32 consecutive output columns of row j, one lane each.  The
+// events of their window (32 + 2R source columns, contiguous in the row-major input) are
+// staged in shared memory and sorted by height once.  The sorted events are cut at group
+// boundaries into one chunk per warp; a warp walks its chunk for all 32 columns (broadcast
+// reads, a warp-uniform loop: no divergence, no shuffles), each lane starting from the sources
+// open at the chunk's start (the XOR of the earlier chunks' toggles) and keeping them as two
+// bit masks centred on its column, so that the nearest open source is two find-first-set
+// operations.  A first walk counts each column's pieces and notes where its runs start; the
+// counts place every (column, chunk) in the S_mid arena, and a second walk writes the pieces
+// there, a run that began in an earlier chunk taking its start from the last one noted.  A
+// window with more events than fit is split into narrower runs of columns.
+#pragma once
+#include "pass1g.cuh"
+
+#define DXD __device__ __forceinline__
+
+namespace dexel {
+
+// words of the tile-relative source masks (32 + 2R + 1 <= 287 sources)
+constexpr int kP1TileWords = 5;
+
+// Shared memory of k_pass1l: sorted events (key, source), the window's event offsets, chunk
+// bounds, chunk toggle masks, per (chunk, lane) counts and last run starts, tile base.
+struct P1LLayout {
+  long long ek, ep, eoff, cb, cm, ccnt, cst, misc, total;
+};
+DXI long long p1l_align(long long x) { return (x + 15) & ~15LL; }
+DXI P1LLayout p1l_layout(int R, int ecap, int warps) {
+  P1LLayout o;
+  long long x = 0;
+  o.ek = x; x = p1l_align(x + (long long)ecap * sizeof(ukey));
+  o.ep = x; x = p1l_align(x + (long long)ecap * sizeof(unsigned short));
+  o.eoff = x; x = p1l_align(x + (long long)(32 + 2 * R + 2) * sizeof(int));
+  o.cb = x; x = p1l_align(x + (long long)(warps + 1) * sizeof(int));
+  o.cm = x; x = p1l_align(x + (long long)warps * kP1TileWords * sizeof(ukey));
+  o.ccnt = x; x = p1l_align(x + (long long)warps * 32 * sizeof(int));
+  o.cst = x; x = p1l_align(x + (long long)warps * 32 * sizeof(ukey));
+  o.misc = x; x = p1l_align(x + 2 * sizeof(long long));
+  o.total = x;
+  return o;
+}
+
+// The open sources of one column as seen from it: bit d - 1 of `up` (`dn`) for the source d
+// columns above (below) it, `cen` for the column itself; NH words each (R <= 64 NH).
+template <int NH>
+struct CMask {
+  ukey up[NH], dn[NH];
+  int cen;
+};
+
+// least distance of an open source (kNoLabel if none)
+template <int NH>
+DXD int cnearest(const CMask<NH>& m) {
+  if (m.cen) return 0;
+  int a = kNoLabel, b = kNoLabel;
+#pragma unroll
+  for (int q = NH - 1; q >= 0; --q) {
+    if (m.up[q]) a = 64 * q + __ffsll((long long)m.up[q]);
+    if (m.dn[q]) b = 64 * q + __ffsll((long long)m.dn[q]);
+  }
+  return a < b ? a : b;
+}
+
+// 64 bits of the multiword mask T starting at bit position p (zeros outside)
+DXD ukey bits64(const ukey* T, int p) {
+  const int w = p >> 6, off = p & 63;  // floor division (p may be negative)
+  const ukey lo = (w >= 0 && w < kP1TileWords) ? T[w] : 0ULL;
+  const ukey hi = (w + 1 >= 0 && w + 1 < kP1TileWords) ? T[w + 1] : 0ULL;
+  return off ? (lo >> off) | (hi << (64 - off)) : lo;
+}
+
+// The column at tile position pc: its open sources from the tile-relative mask T (bit q:
+// source s0 + q), within reach R.
+template <int NH>
+DXD CMask<NH> cmask_from(const ukey* T, int pc, int R) {
+  CMask<NH> m;
+  m.cen = (int)(bits64(T, pc) & 1ULL);
+#pragma unroll
+  for (int q = 0; q < NH; ++q) {
+    const int keep = R - 64 * q;  // bits of this word within reach
+    const ukey mk = keep >= 64 ? ~0ULL : (keep <= 0 ? 0ULL : ((1ULL << keep) - 1));
+    m.up[q] = bits64(T, pc + 1 + 64 * q) & mk;
+    // below: bit d - 1 is source pc - d, i.e. the 64 bits ending at pc - 1 - 64 q reversed
+    m.dn[q] = __brevll(bits64(T, pc - 64 - 64 * q)) & mk;
+  }
+  return m;
+}
+
+// One lane's walk over the sorted events [c0, c1) (a chunk that starts at a group boundary)
+// for the column at tile position pc.  m / Om: the open sources and the label just below the
+// chunk; run_a: the start of the run open there.  WRITE: the pieces go to oa, ob, ol.
+// last_start: the last run start in the chunk (~0 if none).  Returns the pieces.
+template <typename T, int NH, bool WRITE>
+DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int pc, int R,
+                   bool act, CMask<NH> m, int Om, ukey run_a, ukey& last_start,
+                   typename H<T>::K* oa, typename H<T>::K* ob, short* ol) {
+  typedef typename H<T>::K Key;
+  int gmin = kNoLabel;
+  int cnt = 0;
+  last_start = ~0ULL;
+  if (c0 >= c1) return 0;
+  ukey gkey = ek[c0];
+  auto close_group = [&](ukey v) {
+    const int Ok = cnearest<NH>(m);
+    const bool pt = gmin < (Om < Ok ? Om : Ok);
+    const bool ch = Ok != Om || pt;
+    if (Om < kNoLabel && ch) {  // the run below v ends at v
+      if (WRITE) {
+        oa[cnt] = key_out<Key>(run_a);
+        ob[cnt] = key_out<Key>(v);
+        ol[cnt] = (short)Om;
+      }
+      ++cnt;
+    }
+    if (pt) {  // the point [v, v]
+      if (WRITE) {
+        oa[cnt] = key_out<Key>(v);
+        ob[cnt] = key_out<Key>(v);
+        ol[cnt] = (short)gmin;
+      }
+      ++cnt;
+    }
+    if (Ok < kNoLabel && ch) {  // a run starts at v
+      run_a = v;
+      last_start = v;
+    }
+    Om = Ok;
+    gmin = kNoLabel;
+  };
+  for (int t = c0; t < c1; ++t) {
+    const ukey key = ek[t];
+    const int src = ep[t];
+    if (key != gkey) {  // warp-uniform: every lane reads the same event
+      close_group(gkey);
+      gkey = key;
+    }
+    const int d = src - pc;
+    const int ad = d < 0 ? -d : d;
+    if (act && ad <= R) {
+      if (d == 0) {
+        m.cen ^= 1;
+      } else {
+        const int b = ad - 1;
+        const ukey bit = 1ULL << (b & 63);
+#pragma unroll
+        for (int q = 0; q < NH; ++q) {
+          const ukey x = (b >> 6) == q ? bit : 0ULL;
+          m.up[q] ^= d > 0 ? x : 0ULL;
+          m.dn[q] ^= d < 0 ? x : 0ULL;
+        }
+      }
+      gmin = ad < gmin ? ad : gmin;
+    }
+  }
+  close_group(gkey);
+  return cnt;
+}
+
+// The warps of one tile group: W warps (1, 2, 4 or 8) synchronised by named barrier gid + 1
+// (a single warp by __syncwarp).
+struct TGroup {
+  int W, gid, warp, gtid;  // warps, group index in the block, warp and thread within the group
+  DXD void sync() const {
+    if (W == 1) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(W * 32) : "memory");
+    }
+  }
+};
+
+// One tile of k_pass1l: columns i0 .. i0 + 31 of row j, the group's warps one chunk each.
+template <typename T, int NH>
+DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned char* smem,
+                     const TGroup& G, ArenaCursor& cur) {
+  const int lane = threadIdx.x & 31, warp = G.warp;
+  const int W = G.W;
+  const int gthreads = W * 32;
+  const P1LLayout Lo = p1l_layout(P.K, ecap, W);
+  ukey* ek = (ukey*)(smem + Lo.ek);
+  unsigned short* ep = (unsigned short*)(smem + Lo.ep);
+  int* eoff = (int*)(smem + Lo.eoff);
+  int* cb = (int*)(smem + Lo.cb);
+  ukey* cm = (ukey*)(smem + Lo.cm);
+  int* ccnt = (int*)(smem + Lo.ccnt);
+  ukey* cst = (ukey*)(smem + Lo.cst);
+  long long* misc = (long long*)(smem + Lo.misc);
+  const Lanes L{lane, 32};
+  const int R = P.K;
+  const int tpr = (P.nx + 31) >> 5;
+  const int j = (int)(tile / tpr);
+  const int i0 = (int)(tile % tpr) * 32;
+  const int i1 = min(P.nx, i0 + 32);
+  const int s0 = max(0, i0 - R), s1 = min(P.nx, i1 + R);
+  const int ns = s1 - s0;
+  const long long rb = (long long)j * P.nx;
+  G.sync();  // the previous tile is done with the shared memory
+  if (warp == 0) {  // event slots of the window's sources (exclusive prefix)
+    int carry = 0;
+    for (int base = 0; base < ns; base += 32) {
+      const int q = base + lane;
+      int v = 0;
+      if (q < ns) {
+        const int n = P.col_off[rb + s0 + q + 1] - P.col_off[rb + s0 + q];
+        v = P.erode ? 2 * (n + 1) : 2 * n;
+      }
+      const int inc = w_incl_add(v, lane);
+      if (q < ns) eoff[q] = carry + inc - v;
+      carry += w_bcast(inc, 31);
+    }
+    if (lane == 0) eoff[ns] = carry;
+  }
+  G.sync();
+  for (int ia = i0; ia < i1;) {
+    // the widest run of columns from ia whose window's events fit (block-uniform)
+    int ib = i1;
+    const int qa = max(0, ia - R) - s0;
+    while (ib > ia + 1 && eoff[min(P.nx, ib + R) - s0] - eoff[qa] > ecap) ib = ia + ((ib - ia) >> 1);
+    const int qe = min(P.nx, ib + R) - s0;
+    const int e0 = eoff[qa];
+    const int E = eoff[qe] - e0;
+    if (E > ecap) {  // one column's window holds more events than fit: the sweep takes over
+      if (G.gtid == 0) {
+        set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
+        P.m_start[(long long)ia * P.ny + j] = -1;  // marks the column (count 0)
+        P.m_cnt[(long long)ia * P.ny + j] = 0;
+      }
+      ia = ib;
+      continue;
+    }
+    const int n2 = pow2_at_least(E);  // <= ecap (a power of two)
+    // stage the events, one thread per source (payload: the source's tile position)
+    for (int q = qa + G.gtid; q < qe; q += gthreads) {
+      const long long c = rb + s0 + q;
+      const int g0 = P.col_off[c], g1 = P.col_off[c + 1];
+      int o = eoff[q] - e0;
+      const int oend = eoff[q + 1] - e0;
+      const unsigned short src = (unsigned short)q;
+      if (!P.erode) {
+        for (int g = g0; g < g1; ++g) {
+          ek[o] = event_key(P.z[2LL * g]);
+          ep[o++] = src;
+          ek[o] = event_key(P.z[2LL * g + 1]);
+          ep[o++] = src;
+        }
+      } else {
+        // closure of the complement: (-inf, a0], [b0, a1], ..., [b_last, +inf); zero-length
+        // segments leave no gap
+        ukey lo = KEY_NINF;
+        for (int g = g0; g < g1; ++g) {
+          const ukey a = event_key(P.z[2LL * g]), b = event_key(P.z[2LL * g + 1]);
+          if (a == b) continue;
+          ek[o] = lo;
+          ep[o++] = src;
+          ek[o] = a;
+          ep[o++] = src;
+          lo = b;
+        }
+        ek[o] = lo;
+        ep[o++] = src;
+        ek[o] = KEY_PINF;
+        ep[o++] = src;
+      }
+      for (; o < oend; ++o) { ek[o] = ~0ULL; ep[o] = 0xFFFFu; }
+    }
+    for (int t = E + G.gtid; t < n2; t += gthreads) { ek[t] = ~0ULL; ep[t] = 0xFFFFu; }
+    G.sync();
+    // block bitonic sort by height (the order within a height does not matter)
+    for (int k = 2; k <= n2; k <<= 1) {
+      for (int jj = k >> 1; jj > 0; jj >>= 1) {
+        for (int p = G.gtid; p < (n2 >> 1); p += gthreads) {
+          const int t = ((p & ~(jj - 1)) << 1) | (p & (jj - 1));
+          const int x = t | jj;
+          const bool up = (t & k) == 0;
+          const ukey kt = ek[t], kx = ek[x];
+          if ((kt > kx) == up) {
+            ek[t] = kx; ek[x] = kt;
+            const unsigned short vt = ep[t]; ep[t] = ep[x]; ep[x] = vt;
+          }
+        }
+        G.sync();
+      }
+    }
+    // real events (the padding sorts last); chunk bounds at group boundaries
+    const int Er = lower_bound(ek, n2, ~0ULL);
+    if (warp == 0 && lane <= W) {
+      int b = (int)((long long)lane * Er / W);
+      while (b > 0 && b < Er && ek[b] == ek[b - 1]) ++b;
+      cb[lane] = b;
+    }
+    G.sync();
+    const int c0 = cb[warp], c1 = cb[warp + 1];
+    // the chunk's toggles as a tile-relative mask
+    {
+      ukey lm[kP1TileWords];
+#pragma unroll
+      for (int q = 0; q < kP1TileWords; ++q) lm[q] = 0;
+      for (int t = c0 + lane; t < c1; t += 32) {
+        const int src = ep[t];
+        const ukey bit = 1ULL << (src & 63);
+#pragma unroll
+        for (int q = 0; q < kP1TileWords; ++q) lm[q] ^= (src >> 6) == q ? bit : 0ULL;
+      }
+#pragma unroll
+      for (int q = 0; q < kP1TileWords; ++q) {
+        const unsigned h = __reduce_xor_sync(0xffffffffu, (unsigned)(lm[q] >> 32));
+        const unsigned l = __reduce_xor_sync(0xffffffffu, (unsigned)lm[q]);
+        if (lane == 0) cm[warp * kP1TileWords + q] = ((ukey)h << 32) | l;
+      }
+    }
+    G.sync();
+    ukey Tm[kP1TileWords];  // sources open at the chunk's start
+#pragma unroll
+    for (int q = 0; q < kP1TileWords; ++q) Tm[q] = 0;
+    for (int c = 0; c < warp; ++c) {
+#pragma unroll
+      for (int q = 0; q < kP1TileWords; ++q) Tm[q] ^= cm[c * kP1TileWords + q];
+    }
+    const int i = ia + lane;
+    const bool act = i < ib;
+    const int pc = i - s0;
+    CMask<NH> m0 = cmask_from<NH>(Tm, pc, R);
+    if (!act) {
+      m0.cen = 0;
+#pragma unroll
+      for (int q = 0; q < NH; ++q) { m0.up[q] = 0; m0.dn[q] = 0; }
+    }
+    const int Om0 = cnearest<NH>(m0);
+    ukey last = ~0ULL;
+    const int n = chunk_walk<T, NH, false>(ek, ep, c0, c1, pc, R, act, m0, Om0, 0ULL, last,
+                                           nullptr, nullptr, nullptr);
+    ccnt[warp * 32 + lane] = n;
+    cst[warp * 32 + lane] = last;
+    G.sync();
+    // the column's pieces before this chunk, its total, and the start of the run open at the
+    // chunk's start
+    int before = 0, tot_col = 0;
+    ukey run_a = 0ULL;
+    for (int c = 0; c < W; ++c) {
+      const int v = ccnt[c * 32 + lane];
+      if (c < warp) {
+        before += v;
+        const ukey st = cst[c * 32 + lane];
+        if (st != ~0ULL) run_a = st;
+      }
+      tot_col += v;
+    }
+    const int inc = w_incl_add(tot_col, lane);
+    const int tot = w_bcast(inc, 31);
+    if (warp == 0) {
+      const long long s = arena_take(L, &P.ctr->arena_top[1], P.blk, cur, tot);
+      if (lane == 0) misc[0] = s;
+      const int mx = __reduce_max_sync(0xffffffffu, tot_col);
+      if (lane == 0) {
+        cur.tally += tot;
+        cur.tmax = mx > cur.tmax ? mx : cur.tmax;
+      }
+    }
+    G.sync();
+    const long long s = misc[0];
+    const bool fits = s + tot <= P.m_cap;
+    if (fits && n > 0) {
+      const long long o = s + (inc - tot_col) + before;
+      ukey dummy;
+      chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, run_a, dummy, P.m_a + o,
+                              P.m_b + o, P.m_l + o);
+    }
+    if (warp == 0) {
+      if (act) {
+        const long long q = (long long)i * P.ny + j;
+        P.m_start[q] = fits ? s + (inc - tot_col) : 0;
+        P.m_cnt[q] = tot_col;
+      }
+      if (lane == 0 && !fits) set_status(&P.ctr->status, ST_OVERFLOW_ARENA);
+    }
+    G.sync();
+    ia = ib;
+  }
+}
+
+}  // namespace dexel
