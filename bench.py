@@ -28,10 +28,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 RADII = (2.0, 8.0, 32.0)
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the pass-2 kernels of the k = 32
-# dilation (k_levels + k_lgather), from an ncu capture of the current kernels (None once they
-# change)
-TRAFFIC_K32_DILATE = 1_515_418_624
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the k = 32
+# dilation's kernels, from an ncu capture of the current kernels (None once they change):
+# the pass-1 window kernel, and the pass-2 pair k_levels + k_lgather
+TRAFFIC_K32_DILATE_PASS1 = 469_825_792
+TRAFFIC_K32_DILATE_PASS2 = 1_554_365_696
 OPS = ("dilate", "erode")
 N = 512
 HBM_PEAK = None
@@ -159,7 +160,7 @@ def run_ours(args, rank, ws):
                 out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, grid, k, stream)
                 launches += ctx.last_launches
                 if record is not None:
-                    record.append((op, k, ctx.stage_ms(), ctx.stats()))
+                    record.append((op, k, ctx.stage_ms(), ctx.stats(), ctx.kernel_ms()))
                 outs.append(out)
         return launches, outs
 
@@ -192,15 +193,21 @@ def run_ours(args, rank, ws):
     ms_step = allmax(sum(times) / len(times), ws, device="cuda")
     value = units * ws / (ms_step / 1e3)
 
-    # roofline of the dominant stage: pass 2 of the k = 32 dilation (k_levels + k_lgather;
-    # stage 2 of that call brackets exactly its pass-2 kernels).  Algorithmic bytes: S_mid
-    # read once (two FP64 keys + int16 dx = 18 B a piece), pass-2 intervals written (16 B
-    # each), per-column start + count (12 B).
+    # roofline of the dominant kernel: the pass-1 window kernel of the k = 32 dilation (its
+    # own event pair on the call's stream).  Algorithmic bytes: the input read once (16 B a
+    # segment, 4 B a column offset), S_mid written (two FP64 keys + int16 dx = 18 B a piece)
+    # with its per-column start + count (12 B).
     dom = [r for r in rec if r[0] == "dilate" and r[1] == 32.0]
-    dom_ms = sum(r[2][2] for r in dom) / len(dom)
-    dom_bytes = 18 * dom[0][3][1] + 16 * dom[0][3][2] + 12 * g.nx * g.ny
+    ncol = g.nx * g.ny
+    dom_ms = sum(r[4][0] for r in dom) / len(dom)
+    dom_bytes = 16 * g.nseg + 4 * (ncol + 1) + 18 * dom[0][3][1] + 12 * ncol
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
+    # the pass-2 pair of the same offset (k_levels + k_lgather): S_mid read once (18 B a
+    # piece), pass-2 intervals written (16 B each), per-column start + count (12 B)
+    p2_ms = sum(r[4][1] + r[4][2] for r in dom) / len(dom)
+    p2_bytes = 18 * dom[0][3][1] + 16 * dom[0][3][2] + 12 * ncol
+    p2_achieved = p2_bytes / (p2_ms / 1e3) / 1e9
     stages = [sum(r[2][q] for r in rec) for q in range(5)]
 
     # end to end through the public API with host buffers (pinned), copies timed
@@ -241,17 +248,27 @@ def run_ours(args, rank, ws):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC_K32_DILATE,
-                     "kernel": "pass-2 stage: k_levels + k_lgather (y dilation with per-piece "
-                               "radius), dilation k=32",
+                     "frac": achieved / peak, "traffic": TRAFFIC_K32_DILATE_PASS1,
+                     "kernel": "k_pass1l (pass 1, x extrusion, one lane per output column), "
+                               "dilation k=32",
                      "algorithmic_bytes": dom_bytes, "ms_per_launch": dom_ms,
                      "peak_source": peak_kind},
+        "roofline_pass2": {"bound": "hbm", "achieved": p2_achieved, "peak": peak, "unit": "GB/s",
+                           "frac": p2_achieved / peak, "traffic": TRAFFIC_K32_DILATE_PASS2,
+                           "kernel": "k_levels + k_lgather (pass 2, y dilation with per-piece "
+                                     "radius), dilation k=32",
+                           "algorithmic_bytes": p2_bytes, "ms_per_launch": p2_ms,
+                           "peak_source": peak_kind},
+        "kernel_ms_per_step": {"pass1_window": sum(r[4][0] for r in rec) / args.steps,
+                               "k_levels": sum(r[4][1] for r in rec) / args.steps,
+                               "k_lgather": sum(r[4][2] for r in rec) / args.steps,
+                               "smid_pack": sum(r[4][3] for r in rec) / args.steps},
         "stage_ms_per_step": {"validate+tables": stages[0] / args.steps,
                               "pass1": stages[1] / args.steps, "pass2": stages[2] / args.steps,
                               "count+scan": stages[3] / args.steps, "write": stages[4] / args.steps},
         "stats": {f"{op}_k{int(k)}": {"mid_pieces": st[1], "out_segs": st[3],
                                       "max_pieces_col": st[4], "redo_cols": st[5]}
-                  for (op, k, _, st) in rec[: len(OPS) * len(RADII)]},
+                  for (op, k, _, st, _k) in rec[: len(OPS) * len(RADII)]},
         "wall_s_timed": t_wall,
     }
     if rank == 0:

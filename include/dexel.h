@@ -185,6 +185,14 @@ int64_t dexel_last_launches(const dexel_ctx* ctx);
 void dexel_set_profiling(dexel_ctx* ctx, int on);
 int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max);
 
+/* With profiling on, the device time of single kernels of the last call, each bracketed by
+ * its own CUDA events on the call's stream (0 when the kernel did not run): [0] the pass-1
+ * window kernel (one lane per output column), [1] k_levels (per-source level unions of
+ * pass 2), [2] k_lgather (their per-column union), [3] the packed float copy of S_mid (scan
+ * + pack).  Summed over both offsets of a closing or opening.  Returns the number of entries
+ * written (at most max, 4 in all). */
+int dexel_last_kernel_ms(const dexel_ctx* ctx, double* ms, int max);
+
 /* Sizes seen by the last call (summed over both offsets of a closing or opening):
  * [0] input segments, [1] S_mid pieces (pass-1 output), [2] pass-2 intervals before the final
  * complement/rounding, [3] output segments, [4] max pieces in one S_mid column, [5] window

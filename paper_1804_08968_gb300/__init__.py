@@ -87,6 +87,7 @@ def lib():
         L.dexel_set_profiling.argtypes = [P, ctypes.c_int]
         L.dexel_set_profiling.restype = None
         L.dexel_last_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.dexel_last_kernel_ms.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.dexel_last_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
         _lib = L
     return _lib
@@ -165,6 +166,13 @@ class Context:
         """Device ms of [validate+tables, pass 1, pass 2, count+scan, write] of the last call."""
         a = (ctypes.c_double * 5)()
         n = lib().dexel_last_stage_ms(self.ptr, a, 5)
+        return [a[i] for i in range(n)]
+
+    def kernel_ms(self):
+        """Device ms of [pass-1 window kernel, k_levels, k_lgather, S_mid float copy] of the
+        last call (profiling on; 0 for a kernel that did not run)."""
+        a = (ctypes.c_double * 4)()
+        n = lib().dexel_last_kernel_ms(self.ptr, a, 4)
         return [a[i] for i in range(n)]
 
     def stats(self):

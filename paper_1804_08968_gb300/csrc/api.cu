@@ -48,8 +48,10 @@ struct dexel_ctx {
   Counters host_ctr{};
   // optional per-stage timing with CUDA events on the call's stream
   bool profiling = false;
-  cudaEvent_t ev[10] = {};
+  cudaEvent_t ev[18] = {};  // stage pairs 0-9, kernel pairs 10-17
   double stage_ms[5] = {0, 0, 0, 0, 0};
+  double kernel_ms[4] = {0, 0, 0, 0};  // pass-1 kernel, k_levels, k_lgather, S_mid pack
+  bool kernel_rec[4] = {false, false, false, false};
   long long stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long phase[16] = {};
 };
@@ -176,8 +178,19 @@ void mark(dexel_ctx* ctx, int e, cudaStream_t st) {
   cudaEventRecord(ctx->ev[e], st);
 }
 
+// a kernel's own event pair (10 + 2 q, 11 + 2 q)
+void kmark(dexel_ctx* ctx, int q, bool end, cudaStream_t st) {
+  if (!ctx->profiling) return;
+  mark(ctx, 10 + 2 * q + (end ? 1 : 0), st);
+  if (end) ctx->kernel_rec[q] = true;
+}
+
 void reset_call(dexel_ctx* ctx) {
   ctx->launches = 0;
+  for (int q = 0; q < 4; ++q) {
+    ctx->kernel_ms[q] = 0;
+    ctx->kernel_rec[q] = false;
+  }
   for (unsigned long long& x : ctx->phase) x = 0;
   for (double& m : ctx->stage_ms) m = 0;
   for (long long& x : ctx->stats) x = 0;
@@ -384,7 +397,9 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         int gw = K <= 12 ? 2 : (K <= 48 ? 4 : 8);
         if (ctx->p1l_gw > 0) gw = ctx->p1l_gw;
         while (gw < 8 && pass1l_smem(K, ecapL, gw) > (220LL << 10)) gw <<= 1;
+        kmark(ctx, 0, false, st);
         CK(launch_pass1l<T>(p1, ecapL, gw, sms, st));
+        kmark(ctx, 0, true, st);
         ++ctx->launches;
       } else {
         // (a tile of about K/2 columns: a column's window then covers ~80 % of the tile's;
@@ -467,6 +482,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         float* c_af = (float*)aF;
         float* c_bf = c_af + capC;
         short* c_dx = (short*)(c_bf + capC);
+        kmark(ctx, 3, false, st);
         const long long nb = (ncols + kScanTile - 1) / kScanTile;
         k_scan1<int><<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, (const int*)pmcnt, (long long*)ppos,
                                                         (long long*)psums);
@@ -474,6 +490,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         k_mid_pack<Key><<<sms * 8, 256, 0, st>>>(ncols, p1.m_start, p1.m_cnt, p1.m_a, p1.m_b, p1.m_l,
                                                  (const long long*)ppos, (const long long*)psums,
                                                  (long long*)pcnt, c_af, c_bf, c_dx, ctr);
+        kmark(ctx, 3, true, st);
         ctx->launches += 3;
         CK(cudaGetLastError());
         pg.c_start = (const long long*)pcnt;
@@ -524,7 +541,12 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           H.bcap = lb;
           H.m_cap = p1.m_cap;
           H.c_cap = capC;
+          kmark(ctx, 1, false, st);
           CK(launch_levels<T>(H, st, sms));
+          kmark(ctx, 1, true, st);
+          kmark(ctx, 2, false, st);
+          CK(launch_lgather<T>(H, H.bcap, 0, st, sms));
+          kmark(ctx, 2, true, st);
           ctx->launches += 2;
           CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
           CK(cudaStreamSynchronize(st));
@@ -702,6 +724,12 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         float ms = 0;
         if (cudaEventElapsedTime(&ms, ctx->ev[2 * q], ctx->ev[2 * q + 1]) == cudaSuccess)
           ctx->stage_ms[q] += ms;
+      }
+      for (int q = 0; q < 4; ++q) {
+        float ms = 0;
+        if (ctx->kernel_rec[q] &&
+            cudaEventElapsedTime(&ms, ctx->ev[10 + 2 * q], ctx->ev[11 + 2 * q]) == cudaSuccess)
+          ctx->kernel_ms[q] += ms;
       }
     }
     for (int q = 0; q < 16; ++q) ctx->phase[q] += hc.phase[q];
@@ -970,6 +998,13 @@ int dexel_last_stage_ms(const dexel_ctx* ctx, double* ms, int max) {
   if (!ctx || !ms) return 0;
   int n = max < 5 ? max : 5;
   for (int q = 0; q < n; ++q) ms[q] = ctx->stage_ms[q];
+  return n;
+}
+
+int dexel_last_kernel_ms(const dexel_ctx* ctx, double* ms, int max) {
+  if (!ctx || !ms) return 0;
+  int n = max < 4 ? max : 4;
+  for (int q = 0; q < n; ++q) ms[q] = ctx->kernel_ms[q];
   return n;
 }
 

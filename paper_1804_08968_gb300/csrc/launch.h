@@ -46,6 +46,7 @@ struct LvlParamsHost {
   int bcap;
   long long m_cap, c_cap;  // entries of the S_mid arena and of its packed copy (self-checks)
 };
+// k_levels (the per-source level lists); launch_lgather then unites them per column
 template <typename T>
 cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms);
 template <typename T>

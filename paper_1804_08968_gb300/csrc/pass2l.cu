@@ -84,8 +84,7 @@ cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms) {
     if (e != cudaSuccess) return e;
     k_levels<T, false><<<sms * 4, 256, sm1, st>>>(A, tab_floats);
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return launch_lgather<T>(H, H.bcap, 0, st, sms);
+  return cudaGetLastError();
 }
 
 // the per-column gather with buckets of bcap intervals (redo: only the columns marked -1)
