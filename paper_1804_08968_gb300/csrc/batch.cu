@@ -1,14 +1,16 @@
 // Batched offsets: many shapes, each with its own grid, radius and operation, computed with
 // one launch per stage over a table of shapes (validation, tables, pass-1 gather, packing,
 // pass-2 gather, output count, scan, output write).  Tiles of all shapes are numbered
-// globally; a block finds the shape of its tile by binary search over the tile bases and
-// runs the same tile bodies as the single-shape kernels (pass1g.cuh, pass2t.cuh).
+// globally; a block (or a warp group) finds the shape of its tile by binary search over the
+// tile bases and runs the same tile bodies as the single-shape kernels (pass1l.cuh,
+// pass2l.cuh, pass2t.cuh).
 //
 // Once a batch of a given shape signature has run without growing its scratch, the launch
 // sequence up to the output count is recorded as a CUDA graph and replayed by the next call
 // with the same signature (the kernels read every per-shape pointer from the shape table, so
-// only the table is uploaded again).  Tile shapes are chosen per shape from its radius by a
-// rule with one scale per pass; with autotuning on, the first call of a signature times the
+// only the table is uploaded again).  Pass-1 tiles are 32 columns, taken by groups of warps
+// whose size follows the largest radius; pass-2 tiles are chosen per shape from its radius.
+// Each rule has one scale; with autotuning on, the first call of a signature times the
 // scales {1/2, 1, 2} x the default for each pass and keeps the fastest.
 #include <cuda_runtime.h>
 
@@ -21,7 +23,7 @@
 #include "../../include/dexel.h"
 #include "emit.cuh"
 #include "launch.h"
-#include "pass1g.cuh"
+#include "pass1l.cuh"
 #include "pass2l.cuh"
 #include "pass2t.cuh"
 
@@ -35,7 +37,7 @@ struct BShape {
   P2GParams<T> p2;  // pass 2 (o_start / o_cnt / c_start likewise, tables at the shape's)
   LvlParams<T> lv;  // pass 2 by levels (p2 plus the shape's level lists)
   long long col_base, ncols;
-  int tc1, tc2, ntab2, nmax;
+  int tc2, ntab2, nmax;
   double kk, h;
   int erode;
   int* out_col_off;
@@ -99,19 +101,25 @@ __global__ void k_b_tables(const BShape<T>* S, const long long* tabb, int ns, lo
   }
 }
 
-template <typename T, int NW>
-__global__ void __launch_bounds__(256) k_b_pass1(const BShape<T>* S, const long long* t1b,
-                                                 int ns, long long ntiles, int ecap, int obuf,
-                                                 const int* sst) {
+// pass 1, one lane per output column: groups of gw warps, each a tile of 32 columns of one
+// shape (the shapes of one mask width NH; the other launch takes the rest)
+template <typename T, int NH>
+__global__ void __launch_bounds__(256, 3) k_b_pass1(const BShape<T>* S, const long long* t1b,
+                                                    int ns, long long ntiles, int ecap, int gw,
+                                                    long long gstride, const int* sst) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5;
+  const int groups = (blockDim.x >> 5) / gw;
+  const TGroup G{gw, warp / gw, warp % gw, (int)threadIdx.x % (gw * 32)};
   ArenaCursor cur{0, 0};
-  for (long long gt = blockIdx.x; gt < ntiles; gt += gridDim.x) {
+  for (long long gt = (long long)blockIdx.x * groups + G.gid; gt < ntiles;
+       gt += (long long)gridDim.x * groups) {
     const int s = find_base(t1b, ns, gt);
-    if ((sst[s] & BS_BAD) || mask_words(S[s].p1.K) != NW) continue;  // another launch's class
-    const P1Params<T> P = S[s].p1;
-    pass1g_tile<T, NW>(P, gt - t1b[s], S[s].tc1, ecap, obuf, smem, cur);
+    if ((sst[s] & BS_BAD) || (S[s].p1.K <= 64 ? 1 : 2) != NH) continue;  // another launch's class
+    unsigned char* gsm = smem + (long long)G.gid * gstride;  // the largest shape's layout
+    pass1l_tile<T, NH>(S[s].p1, gt - t1b[s], ecap, gsm, G, cur);
   }
-  if ((threadIdx.x & 31) == 0 && cur.tally > 0) {
+  if (G.gtid == 0 && cur.tally > 0) {
     add_total(&S[0].p1.ctr->mid_total, cur.tally);
     note_max(&S[0].p1.ctr->max_pieces, cur.tmax);
   }
@@ -136,22 +144,27 @@ __global__ void __launch_bounds__(512, MINB) k_b_pass2(const BShape<T>* S, const
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_b_levels(const BShape<T>* S, const long long* lvb,
-                                                  int ns, long long nitems, const int* sst) {
+// TABM: kTabWarp (each warp builds its lanes' radius table per item, tstride floats a warp
+// after the level layout) or kTabFlat (the shape's flat table in global memory)
+template <typename T, int TABM>
+__global__ void __launch_bounds__(256) k_b_levels(const BShape<T>* __restrict__ S,
+                                                  const long long* lvb, int ns, long long nitems,
+                                                  int tstride, const int* sst) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const LvlLayout Lo = lvl_layout(blockDim.x >> 5, 0);
   unsigned* ws = (unsigned*)(smem + Lo.slots) + warp * 2 * kLvlSlots * 32;
   float4* stg = (float4*)(smem + Lo.stage) + warp * kLvlStage;
+  float* wt = (float*)(smem + Lo.total) + (long long)warp * tstride;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   ArenaCursor cur{0, 0};
   for (long long gi = (long long)blockIdx.x * (blockDim.x >> 5) + warp; gi < nitems; gi += nw) {
     const int s = find_base(lvb, ns, gi);
     if (sst[s] & BS_BAD) continue;
-    const LvlParams<T>& A = S[s].lv;
+    const LvlParams<T> A = S[s].lv;
     const float E = 9.5367432e-7f * (__uint_as_float(A.P.ctr->zmax_bits) + A.P.wtabf[0]);
-    levels_item<T, false>(A, gi - lvb[s], lane, ws, stg, E, A.P.wtabf, cur);
+    levels_item<T, TABM>(A, gi - lvb[s], lane, ws, stg, E,
+                         TABM == kTabWarp ? wt : (float*)A.P.wtabf, cur);
   }
 }
 
@@ -168,7 +181,8 @@ __global__ void __launch_bounds__(256) k_b_lgather(const BShape<T>* S, const lon
   for (long long gi = (long long)blockIdx.x * (blockDim.x >> 5) + warp; gi < ncols; gi += nw) {
     const int s = find_base(colb, ns, gi);
     if (sst[s] & BS_BAD) continue;
-    lgather_column<T>(S[s].lv, gi - colb[s], bcap, 0, lane, wb, cur);
+    const LvlParams<T> A = S[s].lv;
+    lgather_column<T>(A, gi - colb[s], bcap, 0, lane, wb, cur);
   }  if (lane == 0 && cur.tally > 0) {
     add_total(&S[0].p2.ctr->out_total, cur.tally);
     note_max(&S[0].p2.ctr->max_out, cur.tmax);
@@ -188,7 +202,8 @@ __global__ void __launch_bounds__(256) k_b_lgather_redo(const BShape<T>* S, cons
   for (long long gi = (long long)blockIdx.x * (blockDim.x >> 5) + warp; gi < ncols; gi += nw) {
     const int s = find_base(colb, ns, gi);
     if (sst[s] & BS_BAD) continue;
-    lgather_column<T>(S[s].lv, gi - colb[s], bcap, 1, lane, wb, cur);
+    const LvlParams<T> A = S[s].lv;
+    lgather_column<T>(A, gi - colb[s], bcap, 1, lane, wb, cur);
   }  if (lane == 0 && cur.tally > 0) {
     add_total(&S[0].p2.ctr->out_total, cur.tally);
     note_max(&S[0].p2.ctr->max_out, cur.tmax);
@@ -304,14 +319,8 @@ int reach_of_kk(double kk) {
   return (int)R;
 }
 
-// tile rules: pass 1 about K/2 columns, pass 2 about 2K + 16 columns, scaled by
-// 2^(scale - 1)
-int tile1(int K, int scale) {
-  int tc = 8;
-  const int want = std::max(8, (K / 2) << scale >> 1);
-  while (tc < 64 && tc < want) tc <<= 1;
-  return tc;
-}
+// tile rule of pass 2: about 2K + 16 columns, scaled by 2^(scale - 1) (the pass-1 scale
+// scales the warps a pass-1 tile instead)
 int tile2(int K, int scale) {
   int tc = 16;
   const int want = std::max(16, (2 * K + 16) << scale >> 1);
@@ -380,20 +389,34 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
   auto sc_it = E->scales.find(sig);
   int sc1 = 1, sc2 = 1;
   if (sc_it != E->scales.end()) { sc1 = sc_it->second.first; sc2 = sc_it->second.second; }
-  std::vector<int> tc1(ns), tc2(ns);
+  std::vector<int> tc2(ns);
   auto tiles = [&](int a1, int a2) {
     for (int s = 0; s < ns; ++s) {
-      tc1[s] = tile1(K[s], a1);
       tc2[s] = tile2(K[s], a2);
-      t1b[s + 1] = t1b[s] + (long long)items[s].ny * ((items[s].nx + tc1[s] - 1) / tc1[s]);
+      t1b[s + 1] = t1b[s] + (long long)items[s].ny * ((items[s].nx + 31) / 32);
       t2b[s + 1] = t2b[s] + (long long)items[s].nx * ((items[s].ny + tc2[s] - 1) / tc2[s]);
     }
   };
   tiles(sc1, sc2);
-  // kernel geometry: pass-1 events and pass-2 staging sized for the largest shape parameters
-  const int ecap = 4096, obuf = 256;
+  // kernel geometry: pass-1 events and pass-2 staging sized for the largest shape parameters.
+  // Pass 1: a tile's window events (twice the mean density of its shape, at least 1024; a
+  // shape with a denser window takes the single-shape path), warps a tile by the largest
+  // reach, scaled by the pass-1 scale
+  int ecap = 1024;
+  for (int s = 0; s < ns; ++s) {
+    const long long nc = (long long)items[s].nx * items[s].ny;
+    const double ev_col = 2.0 * (double)items[s].nseg / (double)std::max<long long>(nc, 1) + 2.0;
+    const double ev_tile = (32.0 + 2.0 * K[s] + 1) * ev_col * 2.0;
+    while (ecap < 16384 && ecap < ev_tile) ecap <<= 1;
+  }
+  int gw1 = std::min(8, std::max(1, ((maxK <= 12 ? 2 : (maxK <= 48 ? 4 : 8)) << sc1) >> 1));
   long long sm1 = 0;
-  for (int s = 0; s < ns; ++s) sm1 = std::max(sm1, pass1g_smem<T>(64, K[s], ecap, obuf));
+  for (;;) {  // fewer tile groups a block when their shared memory does not fit
+    sm1 = 0;
+    for (int s = 0; s < ns; ++s) sm1 = std::max(sm1, pass1l_smem(K[s], ecap, gw1));
+    if (sm1 <= (220LL << 10) || gw1 == 8) break;
+    gw1 <<= 1;
+  }
   const int bcap = 128, wpb2 = 16;
   long long base2 = 0;
   for (int s = 0; s < ns; ++s) {
@@ -401,8 +424,8 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     base2 = std::max(base2, p2t_layout(K[s], 128, nt, 0, wpb2, bcap).total);
   }
   const int minb = maxK <= 12 ? 2 : 1;
-  bool has_nw[3] = {false, false, false};  // pass-1 mask widths present (1, 2, 4 words)
-  for (int s = 0; s < ns; ++s) has_nw[mask_words(K[s]) == 1 ? 0 : (mask_words(K[s]) == 2 ? 1 : 2)] = true;
+  bool has_nh[2] = {false, false};  // pass-1 centred mask widths present (1, 2 words)
+  for (int s = 0; s < ns; ++s) has_nh[K[s] <= 64 ? 0 : 1] = true;
   const long long budget2 = minb == 2 ? (108LL << 10) : (220LL << 10);
   const int stage_cap = (int)std::max<long long>(512, (budget2 - base2 - 64) / 10);
   long long sm2 = 0;
@@ -495,7 +518,6 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       memset(&B, 0, sizeof(B));
       B.col_base = colb[s];
       B.ncols = colb[s + 1] - colb[s];
-      B.tc1 = tc1[s];
       B.tc2 = tc2[s];
       B.nmax = nmax[s];
       B.ntab2 = nmax[s] + 1 <= 4096 ? nmax[s] + 1 : 0;
@@ -559,11 +581,15 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     BK(cudaMemcpyAsync(dB, hb, sizeof(long long) * 5 * (ns + 1), cudaMemcpyHostToDevice, st));
 
     // level kernels' geometry
-    const size_t smL = (size_t)lvl_layout(8, 0).total;
+    // per-warp radius tables when the largest reach allows ((R + 1) x 32 floats a warp)
+    const bool warp_tab = (long long)(maxK + 1) * 32 * 4 * 8 <= (64LL << 10);
+    const int tstride = warp_tab ? (maxK + 1) * 32 : 0;
+    const size_t smL = (size_t)lvl_layout(8, 0).total + (size_t)8 * tstride * sizeof(float);
     const int bcapG = 256;
     const size_t smG = (size_t)lgather_smem(8, bcapG);
     const int perG = (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / (long long)smG));
-    BK(cudaFuncSetAttribute(k_b_levels<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smL));
+    BK(cudaFuncSetAttribute(k_b_levels<T, kTabWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smL));
+    BK(cudaFuncSetAttribute(k_b_levels<T, kTabFlat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smL));
     BK(cudaFuncSetAttribute(k_b_lgather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smG));
     // ---- the launch sequence (recorded as a graph for a repeated signature)
     const long long nt1 = t1b[ns], nt2 = t2b[ns];
@@ -576,13 +602,16 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
         k_b_validate<T><<<(unsigned)((ncols + thr - 1) / thr), thr, 0, s_>>>(dS, d_colb, ns, ncols, d_sst);
       if (ntab > 0)
         k_b_tables<T><<<(unsigned)((ntab + thr - 1) / thr), thr, 0, s_>>>(dS, d_tabb, ns, ntab, wtab, wtabf);
-      const int per1 = (int)std::max<long long>(1, std::min<long long>(8, (220LL << 10) / sm1));
-      const unsigned b1 = (unsigned)std::max<long long>(1, std::min<long long>((long long)E->sms * per1, nt1));
+      const int per1 = (int)std::max<long long>(1, std::min<long long>(3, (220LL << 10) / sm1));
+      const long long want1 = (nt1 + (8 / gw1) - 1) / (8 / gw1);
+      const unsigned b1 = (unsigned)std::max<long long>(1, std::min<long long>((long long)E->sms * per1, want1));
       if (nt1 > 0) {
         // one launch per mask width, each taking the shapes of its class
-        if (has_nw[0]) k_b_pass1<T, 1><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
-        if (has_nw[1]) k_b_pass1<T, 2><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
-        if (has_nw[2]) k_b_pass1<T, 4><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, obuf, d_sst);
+        const long long gstride = sm1 / (8 / gw1);
+        if (has_nh[0])
+          k_b_pass1<T, 1><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, gw1, gstride, d_sst);
+        if (has_nh[1])
+          k_b_pass1<T, 2><<<b1, 256, (size_t)sm1, s_>>>(dS, d_t1b, ns, nt1, ecap, gw1, gstride, d_sst);
       }
       const long long nb = (ncols + kScanTile - 1) / kScanTile;
       if (ncols > 0) {
@@ -594,7 +623,10 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       const unsigned b2 = (unsigned)std::max<long long>(1, std::min<long long>((long long)E->sms * minb, nt2));
       if (levels && ncols > 0) {
         if ((e = cudaMemsetAsync(l_cnt, 0, sizeof(int) * nlev_all, s_)) != cudaSuccess) return e;
-        k_b_levels<T><<<E->sms * 6, 256, smL, s_>>>(dS, d_lvb, ns, lvb[ns], d_sst);
+        if (warp_tab)
+          k_b_levels<T, kTabWarp><<<E->sms * 4, 256, smL, s_>>>(dS, d_lvb, ns, lvb[ns], tstride, d_sst);
+        else
+          k_b_levels<T, kTabFlat><<<E->sms * 4, 256, smL, s_>>>(dS, d_lvb, ns, lvb[ns], 0, d_sst);
         k_b_lgather<T><<<E->sms * perG, 256, smG, s_>>>(dS, d_colb, ns, ncols, bcapG, d_sst, ctr);
       } else if (nt2 > 0) {
         if (minb == 2)
@@ -615,7 +647,6 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     };
     BK(cudaFuncSetAttribute(k_b_pass1<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     BK(cudaFuncSetAttribute(k_b_pass1<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-    BK(cudaFuncSetAttribute(k_b_pass1<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
     BK(cudaFuncSetAttribute(k_b_pass2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     BK(cudaFuncSetAttribute(k_b_pass2<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     std::vector<long long> fullsig = sig;

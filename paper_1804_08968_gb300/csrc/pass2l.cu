@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(256, 4) k_levels(LvlParams<T> A, int tab_float
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   ArenaCursor cur{0, 0};
   for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + warp; item < nitems; item += nw)
-    levels_item<T, LTAB>(A, item, lane, ws, stg, E, tab, cur);
+    levels_item<T, LTAB ? kTabBlock : kTabFlat>(A, item, lane, ws, stg, E, (float*)tab, cur);
 }
 
 template <typename T>

@@ -287,10 +287,27 @@ DXD bool lvl_src_ok(const LvlParams<T>& A, long long q, int np) {
          P.c_start[q] >= 0 && P.c_start[q] + np <= A.c_cap;
 }
 
-// One work item of k_levels.  LTAB: the per-lane tables at tab (else tab is the flat w table).
-template <typename T, bool LTAB>
+// Table modes of a level walk: the flat float table w[dx^2 + t^2] (global or shared), the
+// block's per-lane tables (lvl_tables), or the warp's own per-lane table built per item
+// ((R + 1) x 32 floats: lane x's radius at |dx| at tab[|dx| * 32 + x]).
+constexpr int kTabFlat = 0, kTabBlock = 1, kTabWarp = 2;
+
+// the warp's own table for this item: lane's level t (act false: no level)
+DXD void lvl_warp_table(float* tab, int R, int nmax, const float* wtabf, int lane, int t,
+                        bool act) {
+  __syncwarp();  // the previous item no longer reads it
+  for (int adx = 0; adx <= R; ++adx) {
+    const int n = adx * adx + t * t;
+    tab[(adx << 5) + lane] = act && n <= nmax ? wtabf[n] : -1.0f;
+  }
+  __syncwarp();
+}
+
+// One work item of k_levels.  TABM: the table mode; tab: the block's tables (kTabBlock), the
+// flat table (kTabFlat) or the warp's table space (kTabWarp).
+template <typename T, int TABM>
 DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* ws, float4* stg,
-                     float E, const float* tab, ArenaCursor& cur) {
+                     float E, float* tab, ArenaCursor& cur) {
   const P2GParams<T>& P = A.P;
   const int R1 = P.R + 1;
   const long long n0 = lvl_level0_items(A.nsrc, A.L);
@@ -324,8 +341,14 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     }
     LvlRun s = lvl_run();
     const PackEmit pe{ws + lane};
-    if (LTAB) {
-      const STab wl = A.NG == 0 ? STab{tab + lane, 5} : STab{tab + (long long)A.NG * R1 * 32, 0};
+    if (TABM != kTabFlat) {
+      STab wl;
+      if (TABM == kTabWarp) {
+        lvl_warp_table(tab, P.R, P.nmax, P.wtabf, lane, t, act);
+        wl = STab{tab + lane, 5};
+      } else {
+        wl = A.NG == 0 ? STab{tab + lane, 5} : STab{tab + (long long)A.NG * R1 * 32, 0};
+      }
       walk_global<T>(P, cs, 0, np, E, wl, s, pe);
       lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
         LvlRun s2 = lvl_run();
@@ -355,8 +378,14 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
   const long long ms = P.m_start[q], cs = P.c_start[q];
   LvlRun s = lvl_run();
   const PackEmit pe{ws + lane};
-  if (LTAB) {
-    const STab wl{tab + (long long)grp * R1 * 32 + lane, 5};
+  if (TABM != kTabFlat) {
+    STab wl;
+    if (TABM == kTabWarp) {
+      lvl_warp_table(tab, P.R, P.nmax, P.wtabf, lane, t, act);
+      wl = STab{tab + lane, 5};
+    } else {
+      wl = STab{tab + (long long)grp * R1 * 32 + lane, 5};
+    }
     walk_staged<T>(P, cs, np, lane, stg, E, wl, s, pe);
     lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
       LvlRun s2 = lvl_run();
