@@ -241,6 +241,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       continue;
     }
     const int n2 = pow2_at_least(E);  // <= ecap (a power of two)
+    PHASE_BEGIN();
     // stage the events, one thread per source (payload: the source's tile position)
     for (int q = qa + G.gtid; q < qe; q += gthreads) {
       const long long c = rb + s0 + q;
@@ -277,6 +278,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     }
     for (int t = E + G.gtid; t < n2; t += gthreads) { ek[t] = ~0ULL; ep[t] = 0xFFFFu; }
     G.sync();
+    PHASE(0);
     // block bitonic sort by height (the order within a height does not matter)
     for (int k = 2; k <= n2; k <<= 1) {
       for (int jj = k >> 1; jj > 0; jj >>= 1) {
@@ -293,6 +295,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
         G.sync();
       }
     }
+    PHASE(1);
     // real events (the padding sorts last); chunk bounds at group boundaries
     const int Er = lower_bound(ek, n2, ~0ULL);
     if (warp == 0 && lane <= W) {
@@ -343,7 +346,9 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
                                            nullptr, nullptr, nullptr);
     ccnt[warp * 32 + lane] = n;
     cst[warp * 32 + lane] = last;
+    PHASE(2);
     G.sync();
+    PHASE(3);
     // the column's pieces before this chunk, its total, and the start of the run open at the
     // chunk's start
     int before = 0, tot_col = 0;
@@ -385,7 +390,11 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       }
       if (lane == 0 && !fits) set_status(&P.ctr->status, ST_OVERFLOW_ARENA);
     }
+    PHASE(4);
     G.sync();
+    PHASE(5);
+    PHASE_COUNT(10, 1);
+    PHASE_COUNT(11, Er);
     ia = ib;
   }
 }

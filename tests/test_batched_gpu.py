@@ -153,3 +153,22 @@ def test_batched_capacity_and_bad_shape(dx):
     assert outs[0].nseg == ref.nseg and outs[2].nseg == ref.nseg
     off, z = keep[0]
     _same(off.cpu().numpy().astype(np.int64), z[: outs[0].nseg].cpu().numpy(), ref, TOL64, "good shape")
+
+
+def test_batched_wide_reach(dx):
+    """Reaches beyond 31 and 63 spacings in one batch with a small one (pass-1 masks of two
+    words, level groups, and the level walk's flat table once a reach passes 63)."""
+    import torch
+    rng = np.random.default_rng(21)
+    items = []
+    for n, k, op in ((96, 66.0, "dilate"), (80, 40.0, "erode"), (30, 3.0, "dilate"),
+                     (64, 33.5, "close")):
+        g = shapes.random_grid(rng, n, n, 4, fill=0.5, point_frac=0.05, h=1 / 4000)
+        items.append((g, op, k))
+    code = {"dilate": dx.DILATE, "erode": dx.ERODE, "close": dx.CLOSE, "open": dx.OPEN}
+    grids = [dx.Grid.from_synth(g, dtype=torch.float64) for g, _, _ in items]
+    ctx = dx.Context(0)
+    outs = ctx.run_batched([code[op] for _, op, _ in items], grids, [k for _, _, k in items])
+    for (g, op, k), o in zip(items, outs):
+        off, z = o.to_host()
+        _same(off, z, _ref(g, op, k), TOL64, f"{op} k={k} {g.nx}x{g.ny}")

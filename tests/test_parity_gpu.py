@@ -265,3 +265,41 @@ def test_wide_reach(dx, op, k):
     sub = shapes.from_columns(200, 24, 1 / 4000, cols)
     gg, off, z = _gpu(dx, sub, op, k)
     _compare_full(off, z, _ref(gg, op, k), False, f"wide {op} k={k}")
+
+
+@pytest.mark.parametrize("gw", ["1", "2", "4", "8"])
+def test_pass1_lane_groups(dx, gw, monkeypatch):
+    """The pass-1 window kernel with every warp-group size (chunked walks of 1 to 8 warps),
+    and with a small event room (256 events a tile) that splits tiles into narrower runs of
+    columns and hands the densest columns' rows to the sweep."""
+    import torch
+    rng = np.random.default_rng(31)
+    g = shapes.random_grid(rng, 45, 37, 12, fill=0.7, point_frac=0.05, h=1 / 64)
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    for ecap in (None, "256"):
+        monkeypatch.setenv("DEXEL_PASS1_GW", gw)
+        if ecap:
+            monkeypatch.setenv("DEXEL_PASS1_ECAP", ecap)
+        ctx = dx.Context(0)
+        for op in ("dilate", "erode"):
+            for k in (1.0, 4.5, 9.0):
+                out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
+                off, z = out.to_host()
+                _compare_full(off, z.astype(np.float64), _ref(g, op, k), False,
+                              f"gw={gw} ecap={ecap} {op} k={k}")
+        monkeypatch.delenv("DEXEL_PASS1_ECAP", raising=False)
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_pass1_gather_variant(dx, op, monkeypatch):
+    """The per-column pass-1 kernel (DEXEL_PASS1=gather) against the oracle."""
+    import torch
+    monkeypatch.setenv("DEXEL_PASS1", "gather")
+    rng = np.random.default_rng(32)
+    g = shapes.random_grid(rng, 29, 41, 8, fill=0.75, point_frac=0.05, h=1 / 48)
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    ctx = dx.Context(0)
+    for k in (1.0, 3.7, 12.0):
+        out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
+        off, z = out.to_host()
+        _compare_full(off, z.astype(np.float64), _ref(g, op, k), False, f"gather {op} k={k}")
