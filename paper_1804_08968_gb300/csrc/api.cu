@@ -36,6 +36,7 @@ struct dexel_ctx {
   bool lane1 = true;    // pass 1 with one lane per column where the windows fit
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
+  bool p1l_ring = true; // one walk into a ring (else a counting walk and a writing walk)
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
   // needed the redo launch
@@ -397,6 +398,20 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         int gw = K <= 12 ? 2 : (K <= 48 ? 4 : 8);
         if (ctx->p1l_gw > 0) gw = ctx->p1l_gw;
         while (gw < 8 && pass1l_smem(K, ecapL, gw) > (220LL << 10)) gw <<= 1;
+        // the ring of the one-walk variant in the (free) forward arena: up to 128 pieces a
+        // thread of the grid
+        {
+          const long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms) * 256;
+          const long long esz = 2 * (long long)sizeof(Key) + 2;
+          const long long rc = std::min<long long>(128, (long long)bF / (thr * esz)) & ~7LL;
+          if (rc >= 16 && ctx->p1l_ring) {
+            const long long n = thr * rc;
+            p1.r_a = (Key*)aF;
+            p1.r_b = p1.r_a + n;
+            p1.r_l = (short*)(p1.r_b + n);
+            p1.r_cap = (int)rc;
+          }
+        }
         kmark(ctx, 0, false, st);
         CK(launch_pass1l<T>(p1, ecapL, gw, sms, st));
         kmark(ctx, 0, true, st);
@@ -956,6 +971,7 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
     const int v = atoi(e);
     if (v >= 256 && v <= 16384 && (v & (v - 1)) == 0) c->p1l_ecap = v;
   }
+  if (const char* e = getenv("DEXEL_PASS1_RING")) c->p1l_ring = atoi(e) != 0;
   if (const char* e = getenv("DEXEL_PASS1_GW")) {
     const int v = atoi(e);
     if (v == 1 || v == 2 || v == 4 || v == 8) c->p1l_gw = v;

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256, 3) k_b_pass1(const BShape<T>* S, const lo
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
   const int groups = (blockDim.x >> 5) / gw;
-  const TGroup G{gw, warp / gw, warp % gw, (int)threadIdx.x % (gw * 32)};
+  const TGroup G{gw, warp / gw, warp % gw, (int)threadIdx.x % (gw * 32), 0};  // no ring
   ArenaCursor cur{0, 0};
   for (long long gt = (long long)blockIdx.x * groups + G.gid; gt < ntiles;
        gt += (long long)gridDim.x * groups) {

@@ -15,7 +15,8 @@ __global__ void __launch_bounds__(256, 3) k_pass1l(P1Params<T> P, int ecap, int 
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
   const int groups = (blockDim.x >> 5) / gw;
-  const TGroup G{gw, warp / gw, warp % gw, (int)threadIdx.x % (gw * 32)};
+  const TGroup G{gw, warp / gw, warp % gw, (int)threadIdx.x % (gw * 32),
+                 (long long)blockIdx.x * groups + warp / gw};
   unsigned char* gsm = smem + (long long)G.gid * p1l_layout(P.K, ecap, gw).total;
   const long long ntiles = (long long)P.ny * ((P.nx + 31) >> 5);
   ArenaCursor cur{0, 0};
@@ -32,6 +33,15 @@ long long pass1l_smem(int R, int ecap, int gw) {
   return p1l_layout(R, ecap, gw).total * (kP1LWarps / gw);
 }
 
+int pass1l_blocks(int nx, int ny, int R, int ecap, int gw, int sms) {
+  const long long smem = pass1l_smem(R, ecap, gw);
+  const long long ntiles = (long long)ny * ((nx + 31) >> 5);
+  const int groups = kP1LWarps / gw;
+  const int per_sm = (int)std::max<long long>(1, std::min<long long>(3, (220LL << 10) / smem));
+  const long long want = (ntiles + groups - 1) / groups;
+  return (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, want));
+}
+
 template <typename T>
 cudaError_t launch_pass1l(const P1Params<T>& P, int ecap, int gw, int sms, cudaStream_t st) {
   if (gw != 1 && gw != 2 && gw != 4 && gw != 8) return cudaErrorInvalidValue;
@@ -40,11 +50,8 @@ cudaError_t launch_pass1l(const P1Params<T>& P, int ecap, int gw, int sms, cudaS
   auto kern = P.K <= 64 ? k_pass1l<T, 1> : k_pass1l<T, 2>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long ntiles = (long long)P.ny * ((P.nx + 31) >> 5);
-  const int groups = kP1LWarps / gw;
-  const int per_sm = (int)std::max<long long>(1, std::min<long long>(3, (220LL << 10) / (long long)smem));
-  const long long want = (ntiles + groups - 1) / groups;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, want));
+  // the grid the ring (when given) was sized for: pass1l_blocks threads x r_cap pieces
+  const int blocks = pass1l_blocks(P.nx, P.ny, P.K, ecap, gw, sms);
   kern<<<blocks, kP1LWarps * 32, smem, st>>>(P, ecap, gw);
   return cudaGetLastError();
 }

@@ -32,9 +32,10 @@ namespace dexel {
 constexpr int kP1TileWords = 5;
 
 // Shared memory of k_pass1l: sorted events (key, source), the window's event offsets, chunk
-// bounds, chunk toggle masks, per (chunk, lane) counts and last run starts, tile base.
+// bounds, chunk toggle masks, per (chunk, lane) counts, last run starts and open-run flags,
+// the columns' offsets in the tile, tile base and ring-overflow flag.
 struct P1LLayout {
-  long long ek, ep, eoff, cb, cm, ccnt, cst, misc, total;
+  long long ek, ep, eoff, cb, cm, ccnt, cst, cco, cex, misc, total;
 };
 DXI long long p1l_align(long long x) { return (x + 15) & ~15LL; }
 DXI P1LLayout p1l_layout(int R, int ecap, int warps) {
@@ -47,6 +48,8 @@ DXI P1LLayout p1l_layout(int R, int ecap, int warps) {
   o.cm = x; x = p1l_align(x + (long long)warps * kP1TileWords * sizeof(ukey));
   o.ccnt = x; x = p1l_align(x + (long long)warps * 32 * sizeof(int));
   o.cst = x; x = p1l_align(x + (long long)warps * 32 * sizeof(ukey));
+  o.cco = x; x = p1l_align(x + (long long)warps * 32 * sizeof(int));
+  o.cex = x; x = p1l_align(x + 32 * sizeof(int));
   o.misc = x; x = p1l_align(x + 2 * sizeof(long long));
   o.total = x;
   return o;
@@ -100,12 +103,12 @@ DXD CMask<NH> cmask_from(const ukey* T, int pc, int R) {
 
 // One lane's walk over the sorted events [c0, c1) (a chunk that starts at a group boundary)
 // for the column at tile position pc.  m / Om: the open sources and the label just below the
-// chunk; run_a: the start of the run open there.  WRITE: the pieces go to oa, ob, ol.
-// last_start: the last run start in the chunk (~0 if none).  Returns the pieces.
+// chunk; run_a: the start of the run open there.  WRITE: the first cap pieces go to oa, ob,
+// ol.  last_start: the last run start in the chunk (~0 if none).  Returns the pieces.
 template <typename T, int NH, bool WRITE>
 DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int pc, int R,
                    bool act, CMask<NH> m, int Om, ukey run_a, ukey& last_start,
-                   typename H<T>::K* oa, typename H<T>::K* ob, short* ol) {
+                   typename H<T>::K* oa, typename H<T>::K* ob, short* ol, int cap) {
   typedef typename H<T>::K Key;
   int gmin = kNoLabel;
   int cnt = 0;
@@ -117,7 +120,7 @@ DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int
     const bool pt = gmin < (Om < Ok ? Om : Ok);
     const bool ch = Ok != Om || pt;
     if (Om < kNoLabel && ch) {  // the run below v ends at v
-      if (WRITE) {
+      if (WRITE && cnt < cap) {
         oa[cnt] = key_out<Key>(run_a);
         ob[cnt] = key_out<Key>(v);
         ol[cnt] = (short)Om;
@@ -125,7 +128,7 @@ DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int
       ++cnt;
     }
     if (pt) {  // the point [v, v]
-      if (WRITE) {
+      if (WRITE && cnt < cap) {
         oa[cnt] = key_out<Key>(v);
         ob[cnt] = key_out<Key>(v);
         ol[cnt] = (short)gmin;
@@ -172,6 +175,7 @@ DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int
 // (a single warp by __syncwarp).
 struct TGroup {
   int W, gid, warp, gtid;  // warps, group index in the block, warp and thread within the group
+  long long ring;          // the group's index in the grid (its ring region)
   DXD void sync() const {
     if (W == 1) {
       __syncwarp();
@@ -196,7 +200,15 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
   ukey* cm = (ukey*)(smem + Lo.cm);
   int* ccnt = (int*)(smem + Lo.ccnt);
   ukey* cst = (ukey*)(smem + Lo.cst);
+  int* cco = (int*)(smem + Lo.cco);
+  int* cex = (int*)(smem + Lo.cex);
   long long* misc = (long long*)(smem + Lo.misc);
+  typedef typename H<T>::K Key;
+  // the group's ring: W x 32 regions of r_cap pieces
+  const long long rg0 = (long long)G.ring * W * 32 * P.r_cap;
+  Key* rg_a = P.r_a ? P.r_a + rg0 : nullptr;
+  Key* rg_b = P.r_b ? P.r_b + rg0 : nullptr;
+  short* rg_l = P.r_l ? P.r_l + rg0 : nullptr;
   const Lanes L{lane, 32};
   const int R = P.K;
   const int tpr = (P.nx + 31) >> 5;
@@ -298,6 +310,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     PHASE(1);
     // real events (the padding sorts last); chunk bounds at group boundaries
     const int Er = lower_bound(ek, n2, ~0ULL);
+    if (G.gtid == 0) ((int*)misc)[2] = 0;  // no ring region overflowed yet
     if (warp == 0 && lane <= W) {
       int b = (int)((long long)lane * Er / W);
       while (b > 0 && b < Er && ek[b] == ek[b - 1]) ++b;
@@ -342,10 +355,21 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     }
     const int Om0 = cnearest<NH>(m0);
     ukey last = ~0ULL;
-    const int n = chunk_walk<T, NH, false>(ek, ep, c0, c1, pc, R, act, m0, Om0, 0ULL, last,
-                                           nullptr, nullptr, nullptr);
+    // one walk into the lane's ring region (the start of a run open at the chunk's start is
+    // patched when the pieces are copied), or a counting walk without a ring
+    const bool ring = P.r_a != nullptr;
+    const long long rbase = ring ? (long long)(warp * 32 + lane) * P.r_cap : 0;
+    int n;
+    if (ring)
+      n = chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, 0ULL, last, rg_a + rbase,
+                                  rg_b + rbase, rg_l + rbase, P.r_cap);
+    else
+      n = chunk_walk<T, NH, false>(ek, ep, c0, c1, pc, R, act, m0, Om0, 0ULL, last, nullptr,
+                                   nullptr, nullptr, 0);
     ccnt[warp * 32 + lane] = n;
     cst[warp * 32 + lane] = last;
+    cco[warp * 32 + lane] = Om0 < kNoLabel ? 1 : 0;
+    if (ring && __any_sync(0xffffffffu, n > P.r_cap) && lane == 0) ((int*)misc)[2] = 1;
     PHASE(2);
     G.sync();
     PHASE(3);
@@ -365,6 +389,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     const int inc = w_incl_add(tot_col, lane);
     const int tot = w_bcast(inc, 31);
     if (warp == 0) {
+      cex[lane] = inc - tot_col;
       const long long s = arena_take(L, &P.ctr->arena_top[1], P.blk, cur, tot);
       if (lane == 0) misc[0] = s;
       const int mx = __reduce_max_sync(0xffffffffu, tot_col);
@@ -376,11 +401,31 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     G.sync();
     const long long s = misc[0];
     const bool fits = s + tot <= P.m_cap;
-    if (fits && n > 0) {
+    const bool spilled = ((const int*)misc)[2] != 0;
+    if (fits && ring && !spilled) {
+      // the ring regions into the arena: a warp a column, lanes over its pieces (coalesced)
+      for (int x = warp; x < 32; x += W) {
+        long long d = s + cex[x];
+        ukey carry = ~0ULL;
+        for (int c = 0; c < W; ++c) {
+          const int cn = ccnt[c * 32 + x];
+          const long long sb = (long long)(c * 32 + x) * P.r_cap;
+          const bool patch = cco[c * 32 + x] != 0 && carry != ~0ULL;
+          for (int k = lane; k < cn; k += 32) {
+            P.m_a[d + k] = (k == 0 && patch) ? key_out<Key>(carry) : rg_a[sb + k];
+            P.m_b[d + k] = rg_b[sb + k];
+            P.m_l[d + k] = rg_l[sb + k];
+          }
+          d += cn;
+          const ukey st = cst[c * 32 + x];
+          if (st != ~0ULL) carry = st;
+        }
+      }
+    } else if (fits && n > 0) {
       const long long o = s + (inc - tot_col) + before;
       ukey dummy;
       chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, run_a, dummy, P.m_a + o,
-                              P.m_b + o, P.m_l + o);
+                              P.m_b + o, P.m_l + o, 1 << 30);
     }
     if (warp == 0) {
       if (act) {

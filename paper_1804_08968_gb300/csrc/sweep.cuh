@@ -237,6 +237,8 @@ struct P1Params {
   int capF, capS;  // capacities of state arrays and of one column's segments
   const int* rows;  // the sweep: only these rows (null: all rows)
   int nrows;
+  // the window kernel's ring: per thread of the grid r_cap pieces (null: two walks)
+  Key* r_a; Key* r_b; short* r_l; int r_cap;
   // local index of forward states for the current chunk: per warp, chunk entries
 };
 
