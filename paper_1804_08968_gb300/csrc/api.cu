@@ -37,6 +37,7 @@ struct dexel_ctx {
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
   bool p1l_ring = true; // one walk into a ring (else a counting walk and a writing walk)
+  int lane_gather_max = 4;  // pass-2 gather with one lane a column up to this reach
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
   // needed the redo launch
@@ -560,7 +561,10 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           CK(launch_levels<T>(H, st, sms));
           kmark(ctx, 1, true, st);
           kmark(ctx, 2, false, st);
-          CK(launch_lgather<T>(H, H.bcap, 0, st, sms));
+          if (K <= ctx->lane_gather_max)
+            CK(launch_lgather_lanes<T>(H, st, sms));
+          else
+            CK(launch_lgather<T>(H, H.bcap, 0, st, sms));
           kmark(ctx, 2, true, st);
           ctx->launches += 2;
           CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
@@ -972,6 +976,7 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
     if (v >= 256 && v <= 16384 && (v & (v - 1)) == 0) c->p1l_ecap = v;
   }
   if (const char* e = getenv("DEXEL_PASS1_RING")) c->p1l_ring = atoi(e) != 0;
+  if (const char* e = getenv("DEXEL_LANE_GATHER_MAX")) c->lane_gather_max = atoi(e);
   if (const char* e = getenv("DEXEL_PASS1_GW")) {
     const int v = atoi(e);
     if (v == 1 || v == 2 || v == 4 || v == 8) c->p1l_gw = v;

@@ -54,6 +54,10 @@ template <typename T>
 cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms);
 template <typename T>
 cudaError_t launch_lgather(const LvlParamsHost<T>& H, int bcap, int redo, cudaStream_t st, int sms);
+// the same gather with one lane an output column (short windows; columns it cannot finish
+// are marked for launch_lgather's redo)
+template <typename T>
+cudaError_t launch_lgather_lanes(const LvlParamsHost<T>& H, cudaStream_t st, int sms);
 template <typename T>
 cudaError_t launch_pass2c(const P2GParams<T>& P, int warps_per_block, int blocks, cudaStream_t st);
 

@@ -42,6 +42,22 @@ __global__ void __launch_bounds__(256, 3) k_lgather(LvlParams<T> A, int bcap, in
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_lgather_lanes(LvlParams<T> A) {
+  const int lane = threadIdx.x & 31;
+  const long long ncols = (long long)A.P.nx * A.P.ny;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (*(volatile int*)&A.P.ctr->status & ST_LEVELS_OVER) return;  // the lists are incomplete
+  ArenaCursor cur{0, 0};
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ncols;
+       base += stride)
+    lgather_lane<T>(A, base + lane, base + lane < ncols, lane, cur);
+  if (lane == 0 && cur.tally > 0) {
+    add_total(&A.P.ctr->out_total, cur.tally);
+    note_max(&A.P.ctr->max_out, cur.tmax);
+  }
+}
+
+template <typename T>
 cudaError_t launch_lgather(const LvlParamsHost<T>& H, int bcap, int redo, cudaStream_t st, int sms);
 
 template <typename T>
@@ -103,6 +119,17 @@ cudaError_t launch_lgather(const LvlParamsHost<T>& H, int bcap, int redo, cudaSt
   return cudaGetLastError();
 }
 
+// the per-column gather with one lane a column (short windows); marked columns are left for
+// launch_lgather's redo
+template <typename T>
+cudaError_t launch_lgather_lanes(const LvlParamsHost<T>& H, cudaStream_t st, int sms) {
+  const LvlParams<T> A = lvl_params(H);
+  k_lgather_lanes<T><<<sms * 8, 256, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_lgather_lanes<float>(const LvlParamsHost<float>&, cudaStream_t, int);
+template cudaError_t launch_lgather_lanes<double>(const LvlParamsHost<double>&, cudaStream_t, int);
 template cudaError_t launch_levels<float>(const LvlParamsHost<float>&, cudaStream_t, int);
 template cudaError_t launch_levels<double>(const LvlParamsHost<double>&, cudaStream_t, int);
 template cudaError_t launch_lgather<float>(const LvlParamsHost<float>&, int, int, cudaStream_t, int);

@@ -621,6 +621,109 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
   wsync();
 }
 
+// One output column a lane (short windows): the window's lists united by jumps straight from
+// global memory, no bucket and no sort.  A column with more than kLaneRuns runs, or whose runs
+// need more than kLanePasses passes, is marked (o_cnt = -1, with its interval count as the
+// bucket it needs) for the warp-per-column gather.  Call with all 32 lanes; act false: a lane
+// without a column.
+constexpr int kLaneRuns = 32;   // a lane's runs (local memory)
+constexpr int kLanePasses = 64;
+
+template <typename T>
+DXD void lgather_lane(const LvlParams<T>& A, long long item, bool act, int lane, ArenaCursor& cur) {
+  const Lanes L{lane, 32};
+  const P2GParams<T>& P = A.P;
+  const int R = P.R;
+  int i = 0, j = 0, s0 = 0, s1 = -1;
+  long long c = 0, qb = 0;
+  if (act) {
+    i = (int)(item / P.ny);
+    j = (int)(item % P.ny);
+    c = (long long)j * P.nx + i;
+    s0 = max(0, j - R);
+    s1 = min(P.ny - 1, j + R);
+    qb = (long long)i * P.ny;
+  }
+  // f(l, pointer to r) over the column's intervals
+  auto visit = [&](auto f) {
+    for (int jj = s0; jj <= s1; ++jj) {
+      const int t = jj > j ? jj - j : j - jj;
+      const long long li = (qb + jj) * A.L + t;
+      if (li >= A.nlev) continue;
+      const int n = A.l_cnt[li];
+      const long long st = A.l_start[li];
+      if (n < 0 || st < 0 || st + n > A.l_cap) {
+        set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
+        continue;
+      }
+      for (int k = 0; k < n; ++k) f(A.l_l[st + k], A.l_r + st + k);
+    }
+  };
+  ukey rl[kLaneRuns], rr[kLaneRuns];
+  int nr = 0, total = 0;
+  bool ok = true;
+  if (act) {
+    ukey lo = ~0ULL;
+    visit([&](ukey l, const ukey*) {
+      lo = l < lo ? l : lo;
+      ++total;
+    });
+    ukey hi = lo;
+    bool more = total > 0;
+    for (int pass = 0; more && pass < kLanePasses; ++pass) {
+      ukey mx = 0, nxt = ~0ULL;
+      bool later = false;
+      visit([&](ukey l, const ukey* rp) {
+        if (l <= hi) {
+          const ukey r = *rp;
+          mx = r > mx ? r : mx;
+        } else {
+          nxt = l < nxt ? l : nxt;
+          later = true;
+        }
+      });
+      if (mx > hi) {
+        hi = mx;
+        continue;
+      }
+      rl[nr] = lo;
+      rr[nr] = hi;
+      ++nr;
+      more = later;
+      if (more && nr == kLaneRuns) break;
+      lo = hi = nxt;
+    }
+    ok = !more;
+  }
+  const bool mark = act && !ok;
+  const int n = act && ok ? nr : 0;
+  const int inc = w_incl_add(n, lane);
+  const int tot = w_bcast(inc, 31);
+  const long long s = arena_take(L, &P.ctr->arena_top[3], P.blk, cur, tot);
+  const bool fits = s + tot <= P.o_cap;
+  if (act) {
+    if (mark) {
+      P.o_cnt[c] = -1;
+      note_max(&P.ctr->max_state, total);
+      set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
+      atomicAdd(&P.ctr->redo_cols, 1);
+    } else {
+      const long long o = s + inc - n;
+      if (fits) {
+        for (int q = 0; q < n; ++q) { P.o_l[o + q] = rl[q]; P.o_r[o + q] = rr[q]; }
+      }
+      P.o_start[c] = fits ? o : 0;
+      P.o_cnt[c] = n;
+    }
+  }
+  if (lane == 0 && !fits) set_status(&P.ctr->status, ST_OVERFLOW_ARENA);
+  const int mx = __reduce_max_sync(0xffffffffu, n);
+  if (lane == 0) {
+    cur.tally += tot;
+    cur.tmax = mx > cur.tmax ? mx : cur.tmax;
+  }
+}
+
 DXI long long lgather_smem(int warps, int bcap) {
   return (long long)warps * (bcap * (2 * sizeof(ukey) + 2 * sizeof(int)) + 16);
 }
