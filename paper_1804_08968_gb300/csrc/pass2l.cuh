@@ -105,20 +105,22 @@ struct FlatTab {
   }
 };
 
-// State of one lane's walk: the open interval (float ends) and the pieces that set its ends.
+// State of one lane's walk: the open interval (float ends) and the pieces that set its ends
+// (piece index << kLvlDxBits | |dx|).
 struct LvlRun {
   float clf, crf;
-  int gl, gr, al, ar;  // piece index and |dx| of the left / right end
+  unsigned pl, pr;
   bool have;
   int cnt;  // intervals closed so far
 };
-DXD LvlRun lvl_run() { return LvlRun{0.0f, 0.0f, 0, 0, 0, 0, false, 0}; }
+DXD LvlRun lvl_run() { return LvlRun{0.0f, 0.0f, 0u, 0u, false, 0}; }
+DXD unsigned lvl_pack(int p, int adx) { return ((unsigned)p << kLvlDxBits) | (unsigned)adx; }
 
 // One step of a level walk (Sec. 3.3: the slice [a - w, b + w] of piece p at this lane's
 // level): merged into the open interval when the overlap is certain under the float error
 // bound E, else the open interval is closed (emit) and the slice opens the next one.
 template <typename Emit>
-DXD void lvl_step(LvlRun& s, float af, float bf, int adx, int p, float wf, float E,
+DXD void lvl_step(LvlRun& s, float af, float bf, unsigned pk, float wf, float E,
                   const Emit& emit) {
   const bool in = wf >= 0.0f;
   const float lf = af - wf;
@@ -135,11 +137,9 @@ DXD void lvl_step(LvlRun& s, float af, float bf, int adx, int p, float wf, float
   const bool tl = fresh || (merge && dl < 0.0f);
   const bool tr = fresh || (merge && dr > 0.0f);
   s.clf = tl ? lf : s.clf;
-  s.gl = tl ? p : s.gl;
-  s.al = tl ? adx : s.al;
+  s.pl = tl ? pk : s.pl;
   s.crf = tr ? rf : s.crf;
-  s.gr = tr ? p : s.gr;
-  s.ar = tr ? adx : s.ar;
+  s.pr = tr ? pk : s.pr;
   s.have = s.have || in;
 }
 template <typename Emit>
@@ -156,8 +156,8 @@ struct PackEmit {
   unsigned* sl;  // ws + lane
   DXD void operator()(const LvlRun& s) const {
     if (s.cnt < kLvlSlots) {
-      sl[s.cnt << 5] = ((unsigned)s.gl << kLvlDxBits) | (unsigned)s.al;
-      sl[(s.cnt << 5) + kLvlSlots * 32] = ((unsigned)s.gr << kLvlDxBits) | (unsigned)s.ar;
+      sl[s.cnt << 5] = s.pl;
+      sl[(s.cnt << 5) + kLvlSlots * 32] = s.pr;
     }
   }
 };
@@ -181,8 +181,9 @@ struct ExactEmit {
   ukey* ol;
   ukey* orr;
   DXD void operator()(const LvlRun& s) const {
-    ol[s.cnt] = lvl_left<T>(*P, ms, s.gl, s.al, tt);
-    orr[s.cnt] = lvl_right<T>(*P, ms, s.gr, s.ar, tt);
+    const unsigned m = (1u << kLvlDxBits) - 1;
+    ol[s.cnt] = lvl_left<T>(*P, ms, (int)(s.pl >> kLvlDxBits), (int)(s.pl & m), tt);
+    orr[s.cnt] = lvl_right<T>(*P, ms, (int)(s.pr >> kLvlDxBits), (int)(s.pr & m), tt);
   }
 };
 
@@ -201,7 +202,7 @@ DXD void walk_global(const P2GParams<T>& P, long long cs, int p0, int p1, float 
     const int adx = min(dxn < 0 ? -dxn : dxn, P.R);  // labels lie in [-R, R]
     const float af = afn, bf = bfn;
     if (p + 1 < p1) { dxn = dxp[p + 1]; afn = afp[p + 1]; bfn = bfp[p + 1]; }
-    lvl_step(s, af, bf, adx, p, wl(adx), E, emit);
+    lvl_step(s, af, bf, lvl_pack(p, adx), wl(adx), E, emit);
   }
   lvl_close(s, emit);
 }
@@ -216,14 +217,15 @@ DXD void walk_staged(const P2GParams<T>& P, long long cs, int np, int lane, floa
     wsync();
     for (int k = lane; k < m; k += 32) {
       const int dx = P.c_dx[cs + base + k];
-      stg[k] = make_float4(P.c_af[cs + base + k], P.c_bf[cs + base + k],
-                           __int_as_float(min(dx < 0 ? -dx : dx, P.R)), 0.0f);
+      const int adx = min(dx < 0 ? -dx : dx, P.R);  // labels lie in [-R, R]
+      stg[k] = make_float4(P.c_af[cs + base + k], P.c_bf[cs + base + k], __int_as_float(adx),
+                           __uint_as_float(lvl_pack(base + k, adx)));
     }
     wsync();
+#pragma unroll 2
     for (int k = 0; k < m; ++k) {
       const float4 v = stg[k];
-      const int adx = __float_as_int(v.z);
-      lvl_step(s, v.x, v.y, adx, base + k, wl(adx), E, emit);
+      lvl_step(s, v.x, v.y, __float_as_uint(v.w), wl(__float_as_int(v.z)), E, emit);
     }
   }
   lvl_close(s, emit);
