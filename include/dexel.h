@@ -130,9 +130,11 @@ dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
  * needed count when its status is DEXEL_ERR_CAPACITY).  All shapes run together, one launch
  * per stage; the sequence is recorded as a CUDA graph and replayed when the next call has
  * the same shapes (sizes, radii, operations); tile shapes are autotuned on the first call of
- * such a signature (see dexel_set_batch_autotune).  Scratch is library-owned (ws is used
- * only by shapes that fall back to the single-shape path: reach above 63 spacings, or a
- * window beyond the batch kernels' limits).  d_status (device, nshapes int32, may be NULL)
+ * such a signature (see dexel_set_batch_autotune).  Shapes of more than 131072 columns
+ * (environment DEXEL_BATCH_MAX_COLS at context creation) take the single-shape path, one
+ * call each: their kernels are sized for them, and batching pays off for the small shapes.
+ * Scratch is library-owned (ws is used only by shapes on the single-shape path: the large
+ * ones, reach above 127 spacings, or a window beyond the batch kernels' limits).  d_status (device, nshapes int32, may be NULL)
  * receives each shape's dexel_status.  Returns the first failing status (or DEXEL_OK);
  * DEXEL_ERR_INVALID_ARG when any argument is invalid (nothing runs).  Synchronises the
  * stream before returning. */

@@ -37,6 +37,7 @@ struct dexel_ctx {
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
   bool p1l_ring = true; // one walk into a ring (else a counting walk and a writing walk)
+  long long batch_max_cols = 131072;  // larger shapes of a batch take the single-shape path
   int lane_gather_max = 4;  // pass-2 gather with one lane a column up to this reach
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
@@ -976,6 +977,7 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
     if (v >= 256 && v <= 16384 && (v & (v - 1)) == 0) c->p1l_ecap = v;
   }
   if (const char* e = getenv("DEXEL_PASS1_RING")) c->p1l_ring = atoi(e) != 0;
+  if (const char* e = getenv("DEXEL_BATCH_MAX_COLS")) c->batch_max_cols = atoll(e);
   if (const char* e = getenv("DEXEL_LANE_GATHER_MAX")) c->lane_gather_max = atoi(e);
   if (const char* e = getenv("DEXEL_PASS1_GW")) {
     const int v = atoi(e);
@@ -1146,43 +1148,55 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
   }
   const int fp32 = mode == DEXEL_FP32_PRED64 ? 1 : 0;
   long long launches = 0;
-  // first offset of every shape (the dilation of a closing, the erosion of an opening); the
-  // result of a closing / opening goes to engine memory, the others straight to the caller
-  std::vector<BatchItem> A(nshapes);
-  for (int s = 0; s < nshapes; ++s) {
+  // Shapes of more than batch_max_cols columns take the single-shape path (their own
+  // kernel geometry; batching pays off for the many small shapes, whose launches it shares).
+  // First offset of every other shape (the dilation of a closing, the erosion of an opening);
+  // the result of a closing / opening goes to engine memory, the others straight to the caller.
+  std::vector<int> inb;
+  for (int s = 0; s < nshapes; ++s)
+    if ((long long)ins[s].nx * ins[s].ny <= ctx->batch_max_cols) inb.push_back(s);
+  std::vector<BatchItem> A(inb.size());
+  for (size_t q = 0; q < inb.size(); ++q) {
+    const int s = inb[q];
     const dexel_op op = ops[s];
-    A[s] = BatchItem{ins[s].nx, ins[s].ny, ins[s].h, ins[s].col_off, ins[s].z, ins[s].nseg, k[s],
+    A[q] = BatchItem{ins[s].nx, ins[s].ny, ins[s].h, ins[s].col_off, ins[s].z, ins[s].nseg, k[s],
                      (op == DEXEL_ERODE || op == DEXEL_OPEN) ? 1 : 0, nullptr, nullptr, 0};
     if (op == DEXEL_DILATE || op == DEXEL_ERODE) {
-      A[s].out_col_off = outs[s].col_off;
-      A[s].out_z = outs[s].z;
-      A[s].out_cap = outs[s].capacity_seg;
+      A[q].out_col_off = outs[s].col_off;
+      A[q].out_z = outs[s].z;
+      A[q].out_cap = outs[s].capacity_seg;
     }
   }
   std::vector<int> stA, stB;
   std::vector<long long> nA, nB;
-  int rc = batch_run(ctx->batch, fp32, A, st, stA, nA, &launches);
-  if (rc != DEXEL_OK) return (dexel_status)rc;
-  // second offset of closings / openings, from the engine-held first results
-  std::vector<BatchItem> B;
-  std::vector<int> which;
-  for (int s = 0; s < nshapes; ++s) {
-    if ((ops[s] == DEXEL_CLOSE || ops[s] == DEXEL_OPEN) && stA[s] == DEXEL_OK) {
-      B.push_back(BatchItem{ins[s].nx, ins[s].ny, ins[s].h, A[s].out_col_off, A[s].out_z, nA[s],
-                            k[s], ops[s] == DEXEL_CLOSE ? 1 : 0, outs[s].col_off, outs[s].z,
-                            outs[s].capacity_seg});
-      which.push_back(s);
-    }
-  }
-  std::vector<int> fin(nshapes);
-  std::vector<long long> fseg(nshapes);
-  for (int s = 0; s < nshapes; ++s) { fin[s] = stA[s]; fseg[s] = nA[s]; }
-  if (!B.empty()) {
-    rc = batch_run(ctx->batch, fp32, B, st, stB, nB, &launches);
+  std::vector<int> fin(nshapes, 1);  // 1: the single-shape path
+  std::vector<long long> fseg(nshapes, 0);
+  if (!A.empty()) {
+    int rc = batch_run(ctx->batch, fp32, A, st, stA, nA, &launches);
     if (rc != DEXEL_OK) return (dexel_status)rc;
-    for (size_t q = 0; q < which.size(); ++q) {
-      fin[which[q]] = stB[q];
-      fseg[which[q]] = nB[q];
+    // second offset of closings / openings, from the engine-held first results
+    std::vector<BatchItem> B;
+    std::vector<int> which;
+    for (size_t q = 0; q < inb.size(); ++q) {
+      const int s = inb[q];
+      if ((ops[s] == DEXEL_CLOSE || ops[s] == DEXEL_OPEN) && stA[q] == DEXEL_OK) {
+        B.push_back(BatchItem{ins[s].nx, ins[s].ny, ins[s].h, A[q].out_col_off, A[q].out_z, nA[q],
+                              k[s], ops[s] == DEXEL_CLOSE ? 1 : 0, outs[s].col_off, outs[s].z,
+                              outs[s].capacity_seg});
+        which.push_back(s);
+      }
+    }
+    for (size_t q = 0; q < inb.size(); ++q) {
+      fin[inb[q]] = stA[q];
+      fseg[inb[q]] = nA[q];
+    }
+    if (!B.empty()) {
+      rc = batch_run(ctx->batch, fp32, B, st, stB, nB, &launches);
+      if (rc != DEXEL_OK) return (dexel_status)rc;
+      for (size_t q = 0; q < which.size(); ++q) {
+        fin[which[q]] = stB[q];
+        fseg[which[q]] = nB[q];
+      }
     }
   }
   // shapes beyond the batch kernels' limits: the single-shape path

@@ -172,3 +172,21 @@ def test_batched_wide_reach(dx):
     for (g, op, k), o in zip(items, outs):
         off, z = o.to_host()
         _same(off, z, _ref(g, op, k), TOL64, f"{op} k={k} {g.nx}x{g.ny}")
+
+
+def test_batched_large_shapes_single_path(dx, monkeypatch):
+    """Shapes above the batch size limit (here 600 columns) take the single-shape path inside
+    the batched call, closings and openings included; every result matches the oracle."""
+    import torch
+    monkeypatch.setenv("DEXEL_BATCH_MAX_COLS", "600")
+    items = _batch(7, 12, False)
+    code = {"dilate": dx.DILATE, "erode": dx.ERODE, "close": dx.CLOSE, "open": dx.OPEN}
+    grids = [dx.Grid.from_synth(g, dtype=torch.float64) for g, _, _ in items]
+    ctx = dx.Context(0)
+    outs = ctx.run_batched([code[op] for _, op, _ in items], grids, [k for _, _, k in items])
+    big = sum(g.nx * g.ny > 600 for g, _, _ in items)
+    assert 0 < big < len(items)
+    assert ctx.stats()[5] == big
+    for (g, op, k), o in zip(items, outs):
+        off, z = o.to_host()
+        _same(off, z, _ref(g, op, k), TOL64, f"{op} k={k} {g.nx}x{g.ny}")
