@@ -38,6 +38,7 @@ struct dexel_ctx {
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
   bool p1l_ring = true; // one walk into a ring (else a counting walk and a writing walk)
   long long batch_max_cols = 131072;  // larger shapes of a batch take the single-shape path
+  bool levels_exact = true;  // reach >= 32: the level walks read S_mid (no packed copy)
   int lane_gather_max = 4;  // pass-2 gather with one lane a column up to this reach
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
@@ -77,22 +78,27 @@ int reach_of(double kk) {
 template <typename T>
 __global__ void k_validate(int ncols, const int* off, const T* z, long long nseg, Counters* ctr) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncols) return;
-  const int s0 = off[c], s1 = off[c + 1];
-  bool bad = false;
-  if (c == 0 && s0 != 0) bad = true;
-  if (c == ncols - 1 && (long long)s1 != nseg) bad = true;
-  if (s1 < s0 || s0 < 0 || (long long)s1 > nseg) bad = true;
-  if (!bad) {
-    for (int s = s0; s < s1; ++s) {
-      const T a = z[2LL * s], b = z[2LL * s + 1];
-      if (!(a <= b)) { bad = true; break; }  // also catches NaN
-      if (!(a > -(T)INFINITY) || !(b < (T)INFINITY)) { bad = true; break; }
-      if (s + 1 < s1 && !(b < z[2LL * (s + 1)])) { bad = true; break; }
+  float zm = 0.0f;  // max |z|: the scale of pass 2's float filter
+  if (c < ncols) {
+    const int s0 = off[c], s1 = off[c + 1];
+    bool bad = false;
+    if (c == 0 && s0 != 0) bad = true;
+    if (c == ncols - 1 && (long long)s1 != nseg) bad = true;
+    if (s1 < s0 || s0 < 0 || (long long)s1 > nseg) bad = true;
+    if (!bad) {
+      for (int s = s0; s < s1; ++s) {
+        const T a = z[2LL * s], b = z[2LL * s + 1];
+        if (!(a <= b)) { bad = true; break; }  // also catches NaN
+        if (!(a > -(T)INFINITY) || !(b < (T)INFINITY)) { bad = true; break; }
+        if (s + 1 < s1 && !(b < z[2LL * (s + 1)])) { bad = true; break; }
+        zm = fmaxf(zm, fmaxf(fabsf((float)a), fabsf((float)b)));
+      }
+      atomicMax(&ctr->max_segs_in, s1 - s0);
     }
-    atomicMax(&ctr->max_segs_in, s1 - s0);
+    if (bad) atomicOr(&ctr->status, ST_BAD_CSR);
   }
-  if (bad) atomicOr(&ctr->status, ST_BAD_CSR);
+  const unsigned zb = __reduce_max_sync(0xffffffffu, __float_as_uint(zm));  // zm >= 0
+  if ((threadIdx.x & 31) == 0 && zb > 0) atomicMax(&ctr->zmax_bits, zb);
 }
 
 // rows of the grid with a column marked for the pass-1 sweep (line-2 index q = i * ny + j)
@@ -492,13 +498,16 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       pg.o_start = (long long*)postart; pg.o_cnt = (int*)pocnt;
       pg.blk = 256;
       pg.ctr = ctr;
-      // line-contiguous float copy of S_mid in the (now free) pass-1 forward arena
+      // line-contiguous float copy of S_mid in the (now free) pass-1 forward arena: made here
+      // unless the level walks read S_mid itself (reach >= 32: each piece is read by a whole
+      // warp and rounded once as it is staged); the tiled gather always needs it
       const long long capC = (long long)(bF / 10);
-      {
-        if ((long long)hc.mid_total > capC) return DEXEL_ERR_CAPACITY;  // not reached: bF >= 16 eM
-        float* c_af = (float*)aF;
-        float* c_bf = c_af + capC;
-        short* c_dx = (short*)(c_bf + capC);
+      if ((long long)hc.mid_total > capC) return DEXEL_ERR_CAPACITY;  // not reached: bF >= 16 eM
+      float* c_af = (float*)aF;
+      float* c_bf = c_af + capC;
+      short* c_dx = (short*)(c_bf + capC);
+      bool packed = false;
+      auto pack_lines = [&]() -> cudaError_t {
         kmark(ctx, 3, false, st);
         const long long nb = (ncols + kScanTile - 1) / kScanTile;
         k_scan1<int><<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, (const int*)pmcnt, (long long*)ppos,
@@ -509,10 +518,13 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
                                                  (long long*)pcnt, c_af, c_bf, c_dx, ctr);
         kmark(ctx, 3, true, st);
         ctx->launches += 3;
-        CK(cudaGetLastError());
         pg.c_start = (const long long*)pcnt;
         pg.c_af = c_af; pg.c_bf = c_bf; pg.c_dx = c_dx;
-      }
+        packed = true;
+        return cudaGetLastError();
+      };
+      const bool levels_exact = ctx->levels && K >= 32 && ctx->levels_exact;
+      if (!levels_exact) CK(pack_lines());
       int& cc = ctx->ccap[2 * K + (erode ? 1 : 0)];
       if (cc < 128) cc = 128;
       pg.bcap = cc;
@@ -558,6 +570,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           H.bcap = lb;
           H.m_cap = p1.m_cap;
           H.c_cap = capC;
+          H.exact = !packed;
           kmark(ctx, 1, false, st);
           CK(launch_levels<T>(H, st, sms));
           kmark(ctx, 1, true, st);
@@ -598,6 +611,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           }
         }
         if (!done) {
+          if (!packed) CK(pack_lines());  // the tiled gather stages line-contiguous sources
           CK(launch_pass2t<T>(pg, tw, tc, ntab, stage_cap, kRoundAppends, kRoundPieces, per_sm,
                               tblocks, st));
           ++ctx->launches;
@@ -978,6 +992,7 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   }
   if (const char* e = getenv("DEXEL_PASS1_RING")) c->p1l_ring = atoi(e) != 0;
   if (const char* e = getenv("DEXEL_BATCH_MAX_COLS")) c->batch_max_cols = atoll(e);
+  if (const char* e = getenv("DEXEL_LEVELS_EXACT")) c->levels_exact = atoi(e) != 0;
   if (const char* e = getenv("DEXEL_LANE_GATHER_MAX")) c->lane_gather_max = atoi(e);
   if (const char* e = getenv("DEXEL_PASS1_GW")) {
     const int v = atoi(e);

@@ -48,6 +48,7 @@ struct LvlParamsHost {
   int* l_cnt;
   int bcap;
   long long m_cap, c_cap;  // entries of the S_mid arena and of its packed copy (self-checks)
+  bool exact;  // k_levels reads S_mid itself (no packed copy; c_start unused)
 };
 // k_levels (the per-source level lists); launch_lgather then unites them per column
 template <typename T>

@@ -6,7 +6,7 @@
 
 namespace dexel {
 
-template <typename T, bool LTAB>
+template <typename T, bool LTAB, bool EXACT>
 __global__ void __launch_bounds__(256, 4) k_levels(LvlParams<T> A, int tab_floats) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(256, 4) k_levels(LvlParams<T> A, int tab_float
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   ArenaCursor cur{0, 0};
   for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + warp; item < nitems; item += nw)
-    levels_item<T, LTAB ? kTabBlock : kTabFlat>(A, item, lane, ws, stg, E, (float*)tab, cur);
+    levels_item<T, LTAB ? kTabBlock : kTabFlat, EXACT>(A, item, lane, ws, stg, E, (float*)tab, cur);
 }
 
 template <typename T>
@@ -91,15 +91,11 @@ cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms) {
   const bool ltab = lt <= kLvlLaneTab;
   const int tab_floats = ltab ? (int)lt : (H.P.nmax + 1 <= kLvlTable ? H.P.nmax + 1 : 0);
   const size_t sm1 = (size_t)lvl_layout(8, tab_floats).total;
-  if (ltab) {
-    e = cudaFuncSetAttribute(k_levels<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-    if (e != cudaSuccess) return e;
-    k_levels<T, true><<<sms * 4, 256, sm1, st>>>(A, tab_floats);
-  } else {
-    e = cudaFuncSetAttribute(k_levels<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-    if (e != cudaSuccess) return e;
-    k_levels<T, false><<<sms * 4, 256, sm1, st>>>(A, tab_floats);
-  }
+  auto kern = ltab ? (H.exact ? k_levels<T, true, true> : k_levels<T, true, false>)
+                   : (H.exact ? k_levels<T, false, true> : k_levels<T, false, false>);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  if (e != cudaSuccess) return e;
+  kern<<<sms * 4, 256, sm1, st>>>(A, tab_floats);
   return cudaGetLastError();
 }
 

@@ -187,21 +187,39 @@ struct ExactEmit {
   }
 };
 
-// A lane's walk over pieces [p0, p1) of the source at c_start cs, loading from the packed
-// copy (the next piece is loaded while the current one is merged).
-template <typename T, typename W, typename Emit>
-DXD void walk_global(const P2GParams<T>& P, long long cs, int p0, int p1, float E, const W& wl,
+// The pieces of one source as the walks read them: float ends and dx.  PackSrc: the packed
+// float copy; ExactSrc: S_mid itself, each end rounded to float (by truncation, within the
+// filter's error bound) as it is read.
+struct PackSrc {
+  const float* a;
+  const float* b;
+  const short* d;
+  DXD float af(int p) const { return a[p]; }
+  DXD float bf(int p) const { return b[p]; }
+  DXD int dx(int p) const { return d[p]; }
+};
+template <typename Key>
+struct ExactSrc {
+  const Key* a;
+  const Key* b;
+  const short* d;
+  DXD float af(int p) const { return keyf(a[p]); }
+  DXD float bf(int p) const { return keyf(b[p]); }
+  DXD int dx(int p) const { return d[p]; }
+};
+
+// A lane's walk over pieces [p0, p1) of one source (the next piece is loaded while the
+// current one is merged).
+template <typename T, typename W, typename Emit, typename Src>
+DXD void walk_global(const P2GParams<T>& P, const Src& src, int p0, int p1, float E, const W& wl,
                      LvlRun& s, const Emit& emit) {
-  const short* dxp = P.c_dx + cs;
-  const float* afp = P.c_af + cs;
-  const float* bfp = P.c_bf + cs;
   int dxn = 0;
   float afn = 0.0f, bfn = 0.0f;
-  if (p0 < p1) { dxn = dxp[p0]; afn = afp[p0]; bfn = bfp[p0]; }
+  if (p0 < p1) { dxn = src.dx(p0); afn = src.af(p0); bfn = src.bf(p0); }
   for (int p = p0; p < p1; ++p) {
     const int adx = min(dxn < 0 ? -dxn : dxn, P.R);  // labels lie in [-R, R]
     const float af = afn, bf = bfn;
-    if (p + 1 < p1) { dxn = dxp[p + 1]; afn = afp[p + 1]; bfn = bfp[p + 1]; }
+    if (p + 1 < p1) { dxn = src.dx(p + 1); afn = src.af(p + 1); bfn = src.bf(p + 1); }
     lvl_step(s, af, bf, lvl_pack(p, adx), wl(adx), E, emit);
   }
   lvl_close(s, emit);
@@ -209,16 +227,16 @@ DXD void walk_global(const P2GParams<T>& P, long long cs, int p0, int p1, float 
 
 // The warp's walk over the np pieces of one source (all lanes, each its own level): the
 // pieces pass through shared memory in chunks (coalesced loads, broadcast reads).
-template <typename T, typename W, typename Emit>
-DXD void walk_staged(const P2GParams<T>& P, long long cs, int np, int lane, float4* stg, float E,
+template <typename T, typename W, typename Emit, typename Src>
+DXD void walk_staged(const P2GParams<T>& P, const Src& src, int np, int lane, float4* stg, float E,
                      const W& wl, LvlRun& s, const Emit& emit) {
   for (int base = 0; base < np; base += kLvlStage) {
     const int m = min(kLvlStage, np - base);
     wsync();
     for (int k = lane; k < m; k += 32) {
-      const int dx = P.c_dx[cs + base + k];
+      const int dx = src.dx(base + k);
       const int adx = min(dx < 0 ? -dx : dx, P.R);  // labels lie in [-R, R]
-      stg[k] = make_float4(P.c_af[cs + base + k], P.c_bf[cs + base + k], __int_as_float(adx),
+      stg[k] = make_float4(src.af(base + k), src.bf(base + k), __int_as_float(adx),
                            __uint_as_float(lvl_pack(base + k, adx)));
     }
     wsync();
@@ -282,11 +300,21 @@ DXD bool lvl_flush(const LvlParams<T>& A, int lane, const unsigned* ws, int cnt,
 }
 
 // the bounds of source q's pieces (self-check against the arenas)
-template <typename T>
+template <typename T, bool EXACT>
 DXD bool lvl_src_ok(const LvlParams<T>& A, long long q, int np) {
   const P2GParams<T>& P = A.P;
-  return np >= 0 && np < kLvlMaxPieces && P.m_start[q] >= 0 && P.m_start[q] + np <= A.m_cap &&
-         P.c_start[q] >= 0 && P.c_start[q] + np <= A.c_cap;
+  const bool m_ok = np >= 0 && np < kLvlMaxPieces && P.m_start[q] >= 0 && P.m_start[q] + np <= A.m_cap;
+  if (EXACT) return m_ok;
+  return m_ok && P.c_start[q] >= 0 && P.c_start[q] + np <= A.c_cap;
+}
+
+// the pieces of source q (m_start ms, packed copy at cs)
+template <typename T, bool EXACT>
+DXD auto lvl_src(const P2GParams<T>& P, long long ms, long long cs) {
+  if constexpr (EXACT)
+    return ExactSrc<typename H<T>::K>{P.m_a + ms, P.m_b + ms, P.m_l + ms};
+  else
+    return PackSrc{P.c_af + cs, P.c_bf + cs, P.c_dx + cs};
 }
 
 // Table modes of a level walk: the flat float table w[dx^2 + t^2] (global or shared), the
@@ -306,8 +334,9 @@ DXD void lvl_warp_table(float* tab, int R, int nmax, const float* wtabf, int lan
 }
 
 // One work item of k_levels.  TABM: the table mode; tab: the block's tables (kTabBlock), the
-// flat table (kTabFlat) or the warp's table space (kTabWarp).
-template <typename T, int TABM>
+// flat table (kTabFlat) or the warp's table space (kTabWarp).  EXACT: the walks read S_mid
+// itself (no packed copy).
+template <typename T, int TABM, bool EXACT = false>
 DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* ws, float4* stg,
                      float E, float* tab, ArenaCursor& cur) {
   const P2GParams<T>& P = A.P;
@@ -332,15 +361,16 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     long long ms = 0, cs = 0;
     if (act) {
       np = P.m_cnt[q];
-      if (!lvl_src_ok(A, q, np) || q * A.L + t >= A.nlev) {
+      if (!lvl_src_ok<T, EXACT>(A, q, np) || q * A.L + t >= A.nlev) {
         set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
         act = false;
         np = 0;
       } else {
         ms = P.m_start[q];
-        cs = P.c_start[q];
+        cs = EXACT ? 0 : P.c_start[q];
       }
     }
+    const auto src = lvl_src<T, EXACT>(P, ms, cs);
     LvlRun s = lvl_run();
     const PackEmit pe{ws + lane};
     if (TABM != kTabFlat) {
@@ -351,17 +381,17 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
       } else {
         wl = A.NG == 0 ? STab{tab + lane, 5} : STab{tab + (long long)A.NG * R1 * 32, 0};
       }
-      walk_global<T>(P, cs, 0, np, E, wl, s, pe);
+      walk_global<T>(P, src, 0, np, E, wl, s, pe);
       lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
         LvlRun s2 = lvl_run();
-        walk_global<T>(P, cs, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+        walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
       });
     } else {
       const FlatTab wl{tab, t * t, P.nmax};
-      walk_global<T>(P, cs, 0, np, E, wl, s, pe);
+      walk_global<T>(P, src, 0, np, E, wl, s, pe);
       lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
         LvlRun s2 = lvl_run();
-        walk_global<T>(P, cs, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+        walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
       });
     }
     return;
@@ -373,11 +403,12 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
   const int t = 1 + grp * 32 + lane;
   const bool act = t < A.L;
   const int np = P.m_cnt[q];
-  if (!lvl_src_ok(A, q, np) || q * A.L + A.L > A.nlev) {
+  if (!lvl_src_ok<T, EXACT>(A, q, np) || q * A.L + A.L > A.nlev) {
     if (lane == 0) set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
     return;
   }
-  const long long ms = P.m_start[q], cs = P.c_start[q];
+  const long long ms = P.m_start[q], cs = EXACT ? 0 : P.c_start[q];
+  const auto src = lvl_src<T, EXACT>(P, ms, cs);
   LvlRun s = lvl_run();
   const PackEmit pe{ws + lane};
   if (TABM != kTabFlat) {
@@ -388,17 +419,17 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     } else {
       wl = STab{tab + (long long)grp * R1 * 32 + lane, 5};
     }
-    walk_staged<T>(P, cs, np, lane, stg, E, wl, s, pe);
+    walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe);
     lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
       LvlRun s2 = lvl_run();
-      walk_global<T>(P, cs, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+      walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
     });
   } else {
     const FlatTab wl{tab, t * t, P.nmax};
-    walk_staged<T>(P, cs, np, lane, stg, E, wl, s, pe);
+    walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe);
     lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
       LvlRun s2 = lvl_run();
-      walk_global<T>(P, cs, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+      walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
     });
   }
 }
