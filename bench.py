@@ -137,9 +137,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def offset_plan(nstreams):
+    """The six offsets of a step split over nstreams host threads (each its own context and
+    stream), the most expensive first, each to the least loaded stream (cost: reach)."""
+    order = sorted(((op, k) for op in OPS for k in RADII), key=lambda x: -x[1])
+    plan = [[] for _ in range(nstreams)]
+    load = [0.0] * nstreams
+    for op, k in order:
+        w = min(range(nstreams), key=lambda q: load[q])
+        plan[w].append((op, k))
+        load[w] += 1.0 + k / 8.0
+    return plan
+
+
 def run_ours(args, rank, ws):
     import numpy as np
     import torch
+    from concurrent.futures import ThreadPoolExecutor
 
     import paper_1804_08968_gb300 as dx
 
@@ -147,29 +161,58 @@ def run_ours(args, rank, ws):
     torch.cuda.set_device(dev)
     g = workload()
     grid = dx.Grid.from_synth(g, dtype=torch.float64)
-    ctx = dx.Context(dev)
-    stream = torch.cuda.current_stream()
+    ns = max(1, args.streams)
+    ctxs = [dx.Context(dev) for _ in range(ns)]
+    streams = [torch.cuda.Stream() for _ in range(ns)]
+    plan = offset_plan(ns)
+    pool = ThreadPoolExecutor(ns)
+    main = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     units = len(OPS) * len(RADII) * g.nx * g.ny
 
-    def step(record=None):
-        launches = 0
-        outs = []
-        for op in OPS:
-            for k in RADII:
-                out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, grid, k, stream)
-                launches += ctx.last_launches
-                if record is not None:
-                    record.append((op, k, ctx.stage_ms(), ctx.stats(), ctx.kernel_ms()))
-                outs.append(out)
-        return launches, outs
+    pinned = {}  # (stream, offset) -> pinned host buffers for the results, reused
+
+    def host_buf(key, t):
+        b = pinned.get(key)
+        if b is None or b.numel() < t.numel():
+            b = torch.empty(t.numel() + t.numel() // 8 + 64, dtype=t.dtype, pin_memory=True)
+            pinned[key] = b
+        return b[: t.numel()].view(t.shape)
+
+    def worker(w, gd, fetch):
+        """Stream w's offsets through the public API (each call synchronises its stream);
+        fetch: copy every result to pinned host memory (asynchronous on the stream, waited
+        for at the end)."""
+        launches, nbytes = 0, 0
+        with torch.cuda.stream(streams[w]):
+            for q, (op, k) in enumerate(plan[w]):
+                out = ctxs[w].run(dx.DILATE if op == "dilate" else dx.ERODE, gd, k, streams[w])
+                launches += ctxs[w].last_launches
+                if fetch:
+                    h_off = host_buf((w, q, 0), out.col_off)
+                    h_z = host_buf((w, q, 1), out.z)
+                    h_off.copy_(out.col_off, non_blocking=True)
+                    h_z.copy_(out.z, non_blocking=True)
+                    nbytes += out.col_off.numel() * 4 + out.z.numel() * 8
+            streams[w].synchronize()
+        return launches, nbytes
+
+    def step(gd, fetch=False):
+        """One step: the six offsets, the streams started after everything queued on the main
+        stream, the main stream waiting for all of them."""
+        ev = torch.cuda.Event()
+        ev.record(main)
+        for st in streams:
+            st.wait_event(ev)
+        res = list(pool.map(lambda w: worker(w, gd, fetch), range(ns)))
+        for st in streams:
+            main.wait_stream(st)
+        return sum(r[0] for r in res), sum(r[1] for r in res)
 
     for _ in range(args.warmup):
-        step()
+        step(grid)
     torch.cuda.synchronize()
 
-    ctx.set_profiling(True)
-    rec = []
     times = []
     launches = 0
     barrier(ws)
@@ -180,18 +223,32 @@ def run_ours(args, rank, ws):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            n, _ = step(rec)
-            e1.record(stream)
+            e0.record(main)
+            n, _ = step(grid)
+            e1.record(main)
             launches += n
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     barrier(ws)
-    ctx.set_profiling(False)
     ms_step = allmax(sum(times) / len(times), ws, device="cuda")
     value = units * ws / (ms_step / 1e3)
+
+    # kernel and stage times from a serial pass (one context, one offset at a time, each
+    # kernel bracketed by its own events; concurrent streams would stretch them)
+    ctx = ctxs[0]
+    ctx.set_profiling(True)
+    rec = []
+    for _ in range(2):
+        rec = []
+        for op in OPS:
+            for k in RADII:
+                flush.zero_()
+                ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, grid, k, main)
+                rec.append((op, k, ctx.stage_ms(), ctx.stats(), ctx.kernel_ms()))
+    ctx.set_profiling(False)
+    torch.cuda.synchronize()
 
     # roofline of the dominant kernel: the pass-1 window kernel of the k = 32 dilation (its
     # own event pair on the call's stream).  Algorithmic bytes: the input read once (16 B a
@@ -209,8 +266,10 @@ def run_ours(args, rank, ws):
     p2_bytes = 18 * dom[0][3][1] + 16 * dom[0][3][2] + 12 * ncol
     p2_achieved = p2_bytes / (p2_ms / 1e3) / 1e9
     stages = [sum(r[2][q] for r in rec) for q in range(5)]
+    kms = [sum(r[4][q] for r in rec) for q in range(4)]
 
-    # end to end through the public API with host buffers (pinned), copies timed
+    # end to end through the public API with host buffers (pinned), copies timed: each step
+    # copies the input to the device and reads every result back
     off_h = torch.from_numpy(np.asarray(g.col_off, np.int32)).pin_memory()
     z_h = torch.from_numpy(np.asarray(g.z, np.float64)).pin_memory()
     e2e_times = []
@@ -223,17 +282,12 @@ def run_ours(args, rank, ws):
         z_d = z_h.to("cuda", non_blocking=True)
         gd = dx.Grid(g.nx, g.ny, g.h, off_d, z_d)
         b_in = off_h.numel() * 4 + z_h.numel() * 8
-        b_out = 0
-        for op in OPS:
-            for k in RADII:
-                out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, gd, k, stream)
-                o_off = out.col_off.to("cpu")
-                o_z = out.z.to("cpu")
-                b_out += o_off.numel() * 4 + o_z.numel() * 8
+        _, b_out = step(gd, fetch=True)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         h2d, d2h = b_in, b_out
     e2e_s = allmax(statistics.median(e2e_times), ws, device="cuda")
+    pool.shutdown()
 
     line = {
         "metric": "output dexel columns/s", "value": value, "unit": "columns/s",
@@ -243,7 +297,9 @@ def run_ours(args, rank, ws):
         "config": {"workload": "512x512 grid, 200 seeded primitives (spheres/boxes/hollow shells, "
                                "<=16 segs/col), dilation+erosion at k=2,8,32 spacings, FP64",
                    "columns_per_step": units, "nseg_in": g.nseg, "l2": "flushed (256 MiB write) "
-                   "before every timed step", "parallelism": f"replica x{ws}"},
+                   "before every timed step", "parallelism": f"replica x{ws}",
+                   "streams": f"{ns} (the six offsets of a step on {ns} host threads, each its "
+                              f"own context and stream: {plan})"},
         "e2e": {"value": units * ws / e2e_s, "unit": "columns/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -259,16 +315,13 @@ def run_ours(args, rank, ws):
                                      "radius), dilation k=32",
                            "algorithmic_bytes": p2_bytes, "ms_per_launch": p2_ms,
                            "peak_source": peak_kind},
-        "kernel_ms_per_step": {"pass1_window": sum(r[4][0] for r in rec) / args.steps,
-                               "k_levels": sum(r[4][1] for r in rec) / args.steps,
-                               "k_lgather": sum(r[4][2] for r in rec) / args.steps,
-                               "smid_pack": sum(r[4][3] for r in rec) / args.steps},
-        "stage_ms_per_step": {"validate+tables": stages[0] / args.steps,
-                              "pass1": stages[1] / args.steps, "pass2": stages[2] / args.steps,
-                              "count+scan": stages[3] / args.steps, "write": stages[4] / args.steps},
+        "serial_ms_per_step": {"validate+tables": stages[0], "pass1": stages[1], "pass2": stages[2],
+                               "count+scan": stages[3], "write": stages[4],
+                               "kernels": {"pass1_window": kms[0], "k_levels": kms[1],
+                                           "k_lgather": kms[2], "smid_pack": kms[3]}},
         "stats": {f"{op}_k{int(k)}": {"mid_pieces": st[1], "out_segs": st[3],
                                       "max_pieces_col": st[4], "redo_cols": st[5]}
-                  for (op, k, _, st, _k) in rec[: len(OPS) * len(RADII)]},
+                  for (op, k, _, st, _k) in rec},
         "wall_s_timed": t_wall,
     }
     if rank == 0:
@@ -520,6 +573,9 @@ def run_precision_workload(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--streams", type=int, default=2,
+                    help="host threads (each its own context and stream) the six offsets of a "
+                         "step are split over")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
