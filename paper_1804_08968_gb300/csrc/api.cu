@@ -38,7 +38,10 @@ struct dexel_ctx {
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
   bool p1l_ring = true; // one walk into a ring (else a counting walk and a writing walk)
   long long batch_max_cols = 131072;  // larger shapes of a batch take the single-shape path
-  bool levels_exact = true;  // reach >= 32: the level walks read S_mid (no packed copy)
+  // the level walks read S_mid itself (no packed copy) at reach >= 32: off by default
+  // (measured: 0.04 ms a k = 32 offset faster on the 512^2 workload, 20 % slower at k = 64
+  // on the 2048^2 one, where each source is staged three times)
+  bool levels_exact = false;
   int lane_gather_max = 4;  // pass-2 gather with one lane a column up to this reach
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
@@ -499,8 +502,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       pg.blk = 256;
       pg.ctr = ctr;
       // line-contiguous float copy of S_mid in the (now free) pass-1 forward arena: made here
-      // unless the level walks read S_mid itself (reach >= 32: each piece is read by a whole
-      // warp and rounded once as it is staged); the tiled gather always needs it
+      // unless the level walks read S_mid itself (DEXEL_LEVELS_EXACT=1, reach >= 32: each
+      // piece is then rounded once as it is staged); the tiled gather always needs it
       const long long capC = (long long)(bF / 10);
       if ((long long)hc.mid_total > capC) return DEXEL_ERR_CAPACITY;  // not reached: bF >= 16 eM
       float* c_af = (float*)aF;
