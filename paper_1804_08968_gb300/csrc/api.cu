@@ -34,6 +34,7 @@ struct dexel_ctx {
   int capA = 1024, capR = 1024, capS = 4096;
   bool sweep1 = false;  // pass 1 as the per-row sweep instead of the window gather
   bool lane1 = true;    // pass 1 with one lane per column where the windows fit
+  bool merge1 = true;   // short reaches: the per-lane merge instead
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
   bool p1l_ring = true; // one walk into a ring (else a counting walk and a writing walk)
@@ -400,7 +401,13 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       // one lane per column: a tile of 32 columns, its window's events (32 + 2K columns) in
       // ecap events of shared memory, room for the densest single column's window
       const double ev_tile = (32.0 + 2.0 * K + 1) * ev_col * 2.0;
-      if (ctx->lane1 && K <= 127) {
+      if (ctx->merge1 && K <= kMergeMaxReach) {
+        // short reaches: one lane a column, merging its own window's sources
+        kmark(ctx, 0, false, st);
+        CK(launch_pass1m<T>(p1, sms, st));
+        kmark(ctx, 0, true, st);
+        ++ctx->launches;
+      } else if (ctx->lane1 && K <= 127) {
         int ecapL = 512;
         while (ecapL < 16384 && (ecapL < ev_tile || ecapL < ev_win_max)) ecapL <<= 1;
         if (ctx->p1l_ecap > 0) ecapL = ctx->p1l_ecap;
@@ -989,6 +996,7 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   const char* mode1 = getenv("DEXEL_PASS1");
   c->sweep1 = mode1 && strcmp(mode1, "sweep") == 0;
   if (mode1 && strcmp(mode1, "gather") == 0) c->lane1 = false;
+  if (mode1 && (strcmp(mode1, "gather") == 0 || strcmp(mode1, "lane") == 0)) c->merge1 = false;
   if (const char* e = getenv("DEXEL_PASS1_ECAP")) {
     const int v = atoi(e);
     if (v >= 256 && v <= 16384 && (v & (v - 1)) == 0) c->p1l_ecap = v;

@@ -28,6 +28,11 @@ long long pass1g_smem(int tc, int R, int ecap, int obuf);
 template <typename T>
 cudaError_t launch_pass1l(const P1Params<T>& P, int ecap, int gw, int sms, cudaStream_t st);
 long long pass1l_smem(int R, int ecap, int gw);
+// pass 1 for reaches up to kMergeMaxReach, one lane a column merging its window's sources
+// (pass1m.cu)
+constexpr int kMergeMaxReach = 4;
+template <typename T>
+cudaError_t launch_pass1m(const P1Params<T>& P, int sms, cudaStream_t st);
 // blocks of 256 threads launch_pass1l starts (its ring, when given, holds r_cap pieces for
 // each of their threads)
 int pass1l_blocks(int nx, int ny, int R, int ecap, int gw, int sms);

@@ -276,6 +276,7 @@ def test_pass1_lane_groups(dx, gw, monkeypatch):
     rng = np.random.default_rng(31)
     g = shapes.random_grid(rng, 45, 37, 12, fill=0.7, point_frac=0.05, h=1 / 64)
     dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    monkeypatch.setenv("DEXEL_PASS1", "lane")  # also at the short reaches (not the merge)
     for ecap in (None, "256"):
         monkeypatch.setenv("DEXEL_PASS1_GW", gw)
         if ecap:
