@@ -29,8 +29,10 @@ template <typename T>
 cudaError_t launch_pass1l(const P1Params<T>& P, int ecap, int gw, int sms, cudaStream_t st);
 long long pass1l_smem(int R, int ecap, int gw);
 // pass 1 for reaches up to kMergeMaxReach, one lane a column merging its window's sources
-// (pass1m.cu)
-constexpr int kMergeMaxReach = 4;
+// (pass1m.cu); measured faster than the window kernel at reach 2 (0.35 against 0.57 ms on
+// the 512^2 workload), much slower at reach 8 (each step advances one of 17 slots
+// predicated over all of them)
+constexpr int kMergeMaxReach = 2;
 template <typename T>
 cudaError_t launch_pass1m(const P1Params<T>& P, int sms, cudaStream_t st);
 // blocks of 256 threads launch_pass1l starts (its ring, when given, holds r_cap pieces for

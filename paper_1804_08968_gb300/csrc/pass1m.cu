@@ -51,10 +51,8 @@ cudaError_t launch_pass1m(const P1Params<T>& P, int sms, cudaStream_t st) {
   const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8, (ncols + 255) / 256));
   if (P.K <= 1)
     k_pass1m<T, 3><<<blocks, 256, 0, st>>>(P);
-  else if (P.K <= 2)
-    k_pass1m<T, 5><<<blocks, 256, 0, st>>>(P);
   else
-    k_pass1m<T, 9><<<blocks, 256, 0, st>>>(P);
+    k_pass1m<T, 5><<<blocks, 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 
