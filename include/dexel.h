@@ -83,7 +83,26 @@ typedef struct {
 typedef struct dexel_ctx dexel_ctx;
 
 /* Create / destroy a context bound to CUDA device `device`.  The context owns only small
- * tables (the half-width table w[n] = h sqrt(k^2 - n), reach table) and status words. */
+ * tables (the half-width table w[n] = h sqrt(k^2 - n), reach table) and status words.
+ *
+ * Kernel choices are read from the environment when the context is created (for testing
+ * and tuning; every choice gives the same result):
+ *   DEXEL_PASS1=sweep|gather|lane   pass 1 as the per-row sweep, the per-column window
+ *                                   kernel, or the lane-per-column window kernel at every
+ *                                   reach (default: per-lane merges up to reach 2, the
+ *                                   lane-per-column window kernel up to 127, the sweep beyond)
+ *   DEXEL_PASS1_GW=1|2|4|8          warps a pass-1 tile (default by reach)
+ *   DEXEL_PASS1_ECAP=256..16384     events a pass-1 tile holds (a power of two; default by
+ *                                   density)
+ *   DEXEL_PASS1_RING=0|1            pass 1 in one walk through per-lane ring regions (1,
+ *                                   default) or in a counting and a writing walk
+ *   DEXEL_PASS2=sweep|tiled         pass 2 as the per-line sweep or the tiled gather instead
+ *                                   of the level unions
+ *   DEXEL_LANE_GATHER_MAX=R         the pass-2 gather with one lane a column up to reach R
+ *                                   (default 4)
+ *   DEXEL_LEVELS_EXACT=0|1          level walks at reach >= 32 read S_mid itself (default 0)
+ *   DEXEL_BATCH_MAX_COLS=n          batched calls: shapes above n columns take the
+ *                                   single-shape path (default 131072) */
 dexel_status dexel_ctx_create(dexel_ctx** ctx, int device);
 void dexel_ctx_destroy(dexel_ctx* ctx);
 
