@@ -24,8 +24,10 @@ __global__ void __launch_bounds__(256, 4) k_levels(LvlParams<T> A, int tab_float
     levels_item<T, LTAB ? kTabBlock : kTabFlat, EXACT>(A, item, lane, ws, stg, E, (float*)tab, cur);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 3) k_lgather(LvlParams<T> A, int bcap, int redo) {
+// MINB blocks an SM: 4 (64 registers, some spilled) pays at short windows (k = 8: 0.47 ->
+// 0.34 ms on the 512^2 workload), 3 (80 registers) at long ones (k = 32: 0.62 against 0.76)
+template <typename T, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_lgather(LvlParams<T> A, int bcap, int redo) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* wb = smem + (long long)warp * (bcap * (2 * sizeof(ukey) + 2 * sizeof(int)) + 16);
@@ -108,10 +110,11 @@ cudaError_t launch_lgather(const LvlParamsHost<T>& H, int bcap, int redo, cudaSt
   while (warps > 1 && warps * per_warp > (110LL << 10)) warps >>= 1;
   const size_t sm2 = (size_t)lgather_smem(warps, bcap);
   if (sm2 > (220u << 10)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_lgather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  auto kern = H.P.R <= 12 ? k_lgather<T, 4> : k_lgather<T, 3>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   if (e != cudaSuccess) return e;
   const int per_sm = (int)std::max<long long>(1, std::min<long long>(64 / warps, (220LL << 10) / (long long)sm2));
-  k_lgather<T><<<sms * per_sm, warps * 32, sm2, st>>>(A, bcap, redo);
+  kern<<<sms * per_sm, warps * 32, sm2, st>>>(A, bcap, redo);
   return cudaGetLastError();
 }
 
