@@ -17,10 +17,12 @@
 // reads, a warp-uniform loop: no divergence, no shuffles), each lane starting from the sources
 // open at the chunk's start (the XOR of the earlier chunks' toggles) and keeping them as two
 // bit masks centred on its column, so that the nearest open source is two find-first-set
-// operations.  A first walk counts each column's pieces and notes where its runs start; the
-// counts place every (column, chunk) in the S_mid arena, and a second walk writes the pieces
-// there, a run that began in an earlier chunk taking its start from the last one noted.  A
-// window with more events than fit is split into narrower runs of columns.
+// operations.  One walk writes each lane's pieces of its chunk to the lane's ring region and
+// notes where its runs start; the counts then place every (column, chunk) in the S_mid arena
+// and the warps copy the regions there (coalesced), a run that began in an earlier chunk taking
+// its start from the last one noted.  Without a ring (or when a lane outgrows its region) a
+// counting walk and a writing walk do the same.  A window with more events than fit is split
+// into narrower runs of columns.
 #pragma once
 #include "pass1g.cuh"
 

@@ -43,8 +43,9 @@ __global__ void __launch_bounds__(256, MINB) k_lgather(LvlParams<T> A, int bcap,
   }
 }
 
+// 6 blocks an SM (40 registers; the runs live in local memory): load-latency-bound
 template <typename T>
-__global__ void __launch_bounds__(256) k_lgather_lanes(LvlParams<T> A) {
+__global__ void __launch_bounds__(256, 6) k_lgather_lanes(LvlParams<T> A) {
   const int lane = threadIdx.x & 31;
   const long long ncols = (long long)A.P.nx * A.P.ny;
   const long long stride = (long long)gridDim.x * blockDim.x;
