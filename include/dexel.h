@@ -96,6 +96,8 @@ typedef struct dexel_ctx dexel_ctx;
  *                                   density)
  *   DEXEL_PASS1_RING=0|1            pass 1 in one walk through per-lane ring regions (1,
  *                                   default) or in a counting and a writing walk
+ *   DEXEL_PASS1_RING_CAP=16..128    pieces a lane's ring region holds (a tile with a lane
+ *                                   beyond it is walked again into place)
  *   DEXEL_PASS2=sweep|tiled         pass 2 as the per-line sweep or the tiled gather instead
  *                                   of the level unions
  *   DEXEL_LANE_GATHER_MAX=R         the pass-2 gather with one lane a column up to reach R

@@ -38,6 +38,7 @@ struct dexel_ctx {
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
   bool p1l_ring = true; // one walk into a ring (else a counting walk and a writing walk)
+  int p1l_ring_cap = 0; // pieces a lane's ring region holds at most (0: up to 128)
   long long batch_max_cols = 131072;  // larger shapes of a batch take the single-shape path
   // the level walks read S_mid itself (no packed copy) at reach >= 32: off by default
   // (measured: 0.04 ms a k = 32 offset faster on the 512^2 workload, 20 % slower at k = 64
@@ -421,7 +422,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         {
           const long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms) * 256;
           const long long esz = 2 * (long long)sizeof(Key) + 2;
-          const long long rc = std::min<long long>(128, (long long)bF / (thr * esz)) & ~7LL;
+          long long rc = std::min<long long>(128, (long long)bF / (thr * esz)) & ~7LL;
+          if (ctx->p1l_ring_cap > 0) rc = std::min<long long>(rc, ctx->p1l_ring_cap);
           if (rc >= 16 && ctx->p1l_ring) {
             const long long n = thr * rc;
             p1.r_a = (Key*)aF;
@@ -1002,6 +1004,10 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
     if (v >= 256 && v <= 16384 && (v & (v - 1)) == 0) c->p1l_ecap = v;
   }
   if (const char* e = getenv("DEXEL_PASS1_RING")) c->p1l_ring = atoi(e) != 0;
+  if (const char* e = getenv("DEXEL_PASS1_RING_CAP")) {
+    const int v = atoi(e);
+    if (v >= 16 && v <= 128) c->p1l_ring_cap = v & ~7;
+  }
   if (const char* e = getenv("DEXEL_BATCH_MAX_COLS")) c->batch_max_cols = atoll(e);
   if (const char* e = getenv("DEXEL_LEVELS_EXACT")) c->levels_exact = atoi(e) != 0;
   if (const char* e = getenv("DEXEL_LANE_GATHER_MAX")) c->lane_gather_max = atoi(e);

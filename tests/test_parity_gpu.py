@@ -304,3 +304,22 @@ def test_pass1_gather_variant(dx, op, monkeypatch):
         out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
         off, z = out.to_host()
         _compare_full(off, z.astype(np.float64), _ref(g, op, k), False, f"gather {op} k={k}")
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_pass1_ring_spill(dx, op, monkeypatch):
+    """Ring regions of 16 pieces (DEXEL_PASS1_RING_CAP): lanes of dense columns outgrow them,
+    their tiles are walked again straight into the arena, and the result is unchanged."""
+    import torch
+    monkeypatch.setenv("DEXEL_PASS1", "lane")
+    monkeypatch.setenv("DEXEL_PASS1_RING_CAP", "16")
+    rng = np.random.default_rng(33)
+    g = shapes.random_grid(rng, 41, 35, 12, fill=0.8, point_frac=0.05, h=1 / 64)
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    ctx = dx.Context(0)
+    for k in (2.5, 9.0, 20.0):
+        out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
+        off, z = out.to_host()
+        ref = _ref(g, op, k)
+        assert ctx.stats()[4] > 16  # some column has more pieces than a region holds
+        _compare_full(off, z.astype(np.float64), ref, False, f"ring 16 {op} k={k}")
