@@ -597,6 +597,13 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           CK(cudaStreamSynchronize(st));
           ctx->needL = std::max<long long>(ctx->needL, (long long)hc.arena_top[2]);
           ctx->levels_status = hc.status;
+          if (hc.over_cols * 64LL > ncols) {
+            // many columns outgrew the bucket (united straight from the lists, slower): a
+            // bucket for their need in the next calls of this reach and operation
+            int b = lb;
+            while (b < hc.over_max && b < 2048) b <<= 1;
+            lb = b;
+          }
           if (hc.status & ST_LEVELS_OVER) {
             // a list beyond its buffer or the arena: the tiled gather redoes pass 2
             CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));

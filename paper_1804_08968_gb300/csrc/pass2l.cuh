@@ -602,6 +602,10 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
       wsync();
       return;
     }
+    if (lane == 0) {  // done from the lists; the host sizes the next call's bucket by these
+      atomicAdd(&P.ctr->over_cols, 1);
+      note_max(&P.ctr->over_max, total);
+    }
   } else if (total > kJumpMin) {
     nj = jump_union(
         [&](auto f) {

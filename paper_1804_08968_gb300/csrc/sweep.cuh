@@ -52,7 +52,8 @@ struct Counters {
   unsigned long long out_total;   // pass-2 intervals written
   unsigned long long bucket_sum;  // gather: intervals collected over all columns (sizing)
   unsigned zmax_bits;             // gather: bits of max |finite height| of S_mid (float >= 0)
-  int pad2;
+  int over_cols;                  // level gather: columns whose lists outgrew the bucket
+  int over_max;                   //   and the most intervals one of them collected
   unsigned long long phase[16];   // optional per-phase clock totals (DEXEL_PHASES builds)
 };
 
