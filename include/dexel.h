@@ -171,16 +171,28 @@ void dexel_set_batch_autotune(dexel_ctx* ctx, int on);
  * a deployment variant).  For callers that cannot allocate device memory when they need an
  * offset -- an application whose own pool owns the GPU's memory, a real-time loop that must
  * not pay cudaMalloc's implicit synchronisation, code running where allocation is
- * forbidden.  It runs the same kernels as dexel_dilate / dexel_erode, but every byte of
- * scratch comes from one static 64 MiB device array inside the library, held by every GPU
- * that loads it until the process exits; nothing is allocated or freed (no ctx either).
- *   in, out : as for dexel_dilate (device buffers owned by the caller; out->nseg written).
+ * forbidden.  It runs the per-line sweep kernels of dexel_dilate / dexel_erode, but every
+ * byte of scratch comes from one static 64 MiB device array inside the library; nothing is
+ * allocated or freed (no ctx either).  The array is committed when the library's module is
+ * loaded on a device (eagerly, or on first use under lazy loading) and is held by every GPU
+ * that loads it until the process exits; a failure to load it is reported as DEXEL_ERR_CUDA.
+ *   in, out : as for dexel_dilate (device buffers owned by the caller).
  *   op      : DEXEL_DILATE or DEXEL_ERODE.
- * Limits: nx*ny <= 65536 and k <= 32; beyond them, or when the data need more scratch than
- * the array holds, the call returns DEXEL_ERR_CAPACITY and writes no partial CSR.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the array: calls that
- * overlap on the GPU (other streams or threads) race.  The call synchronises `stream`. */
+ * out->nseg on return:
+ *   >= 0 and <= capacity_seg   success (DEXEL_OK): the number of output segments;
+ *   > capacity_seg             DEXEL_ERR_CAPACITY: the caller's output is too small, nseg is
+ *                              the size it needs (retry with a larger buffer);
+ *   -1                         DEXEL_ERR_CAPACITY: the grid is beyond the static scratch
+ *                              (nx*ny > 65536, k > 32, or data needing more scratch than the
+ *                              array holds); retrying cannot help.
+ * On DEXEL_ERR_CAPACITY out->z is not written; with nseg = -1 out->col_off is not written
+ * either.
+ * Every call looks up the array's device address in the current device's context
+ * (cudaGetSymbolAddress) and reads status words back with synchronous copies, so the call
+ * synchronises `stream` several times and must not be made while `stream` (or a stream it
+ * joins) is being captured into a CUDA graph.  All calls share the array and the next call
+ * overwrites what the last one left: calls that overlap on the GPU (other streams or
+ * threads) race. */
 dexel_status dexel_offset_noalloc(const dexel_grid_in* in, double k, dexel_op op, dexel_mode mode,
                                   dexel_grid_out* out, void* stream);
 

@@ -10,7 +10,6 @@
 #include <cstring>
 #include <map>
 #include <new>
-#include <mutex>
 #include <vector>
 
 #include "../../include/dexel.h"
@@ -829,12 +828,12 @@ dexel_status offset(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erod
 // Some callers cannot allocate device memory at the moment they need an offset: a host
 // application that owns every byte of the GPU through its own pool, a real-time loop that
 // must not pay cudaMalloc's implicit synchronisation, or code running where allocation is
-// forbidden.  dexel_offset_noalloc serves them: it runs the same kernels as dexel_dilate /
-// dexel_erode with all of their scratch (counters, tables, indices, arenas, per-warp sweep
-// state) carved from one file-scope static device array.  Every GPU that loads the library
-// holds that array until the process exits.  All calls on a device share it, so calls that
-// overlap on the GPU (different streams or threads) race; the counters that must start at
-// zero are cleared at the start of every call.
+// forbidden.  dexel_offset_noalloc serves them: it runs the per-line sweep kernels of
+// dexel_dilate / dexel_erode with all of their scratch (counters, tables, indices, arenas,
+// per-warp sweep state) carved from one file-scope static device array.  Every GPU that loads
+// the library holds that array until the process exits.  All calls on a device share it, so
+// calls that overlap on the GPU (different streams or threads) race; the counters that must
+// start at zero are cleared at the start of every call.
 // ------------------------------------------------------------------------------------------
 constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // 64 MiB per device
 constexpr long long kNoAllocMaxColumns = 256 * 256;
@@ -845,23 +844,18 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
 
-std::mutex g_noalloc_lock;
-void* g_noalloc_ptr[256] = {};
-
-// Device address of the static scratch on the current device, looked up once per device.
+// Device address of the static scratch in the current device's context.  In host code the
+// array's name is only a host-side stand-in, so the address is asked of the runtime; it is
+// asked on every call (a host-side table lookup), never cached, because a context torn down
+// and created again (cudaDeviceReset) may load the module at another address.
 dexel_status noalloc_scratch(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return DEXEL_ERR_CUDA;
-  std::lock_guard<std::mutex> g(g_noalloc_lock);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return DEXEL_ERR_CUDA;
-    }
-    g_noalloc_ptr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e, __LINE__);
   }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return DEXEL_OK;
 }
 
@@ -872,6 +866,9 @@ dexel_status noalloc_offset(const dexel_grid_in* in, double k, bool erode, dexel
   void* base = nullptr;
   dexel_status s = noalloc_scratch(&base);
   if (s != DEXEL_OK) return s;
+  // nseg = -1 until the output count is known: a DEXEL_ERR_CAPACITY returned before that
+  // means the static scratch is too small, not the caller's output buffer
+  out->nseg = -1;
   const int nx = in->nx, ny = in->ny;
   const long long ncols = (long long)nx * ny;
   const double kk = k * k;
@@ -1285,6 +1282,7 @@ dexel_status dexel_offset_noalloc(const dexel_grid_in* in, double k, dexel_op op
   if (mode != DEXEL_FP64 && mode != DEXEL_FP32_PRED64) return DEXEL_ERR_INVALID_ARG;
   const dexel_status s = check_in(in, k);
   if (s != DEXEL_OK) return s;
+  out->nseg = -1;  // beyond the static scratch's limits (below): not an output-size problem
   if ((long long)in->nx * in->ny > kNoAllocMaxColumns || k > kNoAllocMaxK) return DEXEL_ERR_CAPACITY;
   cudaStream_t st = (cudaStream_t)stream;
   const bool erode = op == DEXEL_ERODE;

@@ -1,8 +1,13 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
-Tolerances: FP64 endpoints within 1e-10 of the depth extent (Z = 1), FP32
-mode within 4e-6; segment counts identical, except in FP32 mode where the oracle's gap at
-that place is below one float ulp (it cannot be represented and the two pieces merge).
+Tolerances, in units of the depth extent Z = 1: FP64 endpoints within 1e-10, FP32-endpoint
+mode within 4e-6.  Segment counts are identical column by column, with one excuse each:
+  * FP64: a column whose oracle result has a gap below 1e-9 Z (two runs the method may
+    legitimately join at that resolution);
+  * FP32: a column whose oracle result has a gap below one float32 ulp of its ends
+    (2^-23 max(|z|, 1)): rounding each end once to float moves a gap by up to one ulp, and
+    runs that touch after rounding are merged, so such a gap cannot survive in float32.
+Every column whose count matches has its endpoints compared, whatever happens elsewhere.
 """
 import math
 
@@ -46,21 +51,41 @@ def _ref(g, op, k, cols=None):
     return oracle.open_(g, k)
 
 
+GAP64 = 1e-9
+
+
+def _excused(ref, c, f32):
+    """True when the oracle's column c has a gap below the mode's threshold."""
+    segs = ref.z[ref.col_off[c]:ref.col_off[c + 1]]
+    if segs.shape[0] < 2:
+        return False
+    gaps = segs[1:, 0] - segs[:-1, 1]
+    if f32:
+        scale = np.maximum(np.maximum(np.abs(segs[1:, 0]), np.abs(segs[:-1, 1])), 1.0)
+        return bool(np.min(gaps / scale) < 2.0 ** -23)
+    return bool(np.min(gaps) < GAP64)
+
+
 def _compare_full(off, z, ref, f32, what):
+    """Counts per column (with the excuse above), then the endpoints of every column whose
+    count matches."""
+    off = np.asarray(off, np.int64)
     rc = np.diff(ref.col_off)
     gc = np.diff(off)
     bad = np.flatnonzero(rc != gc)
-    if f32:
-        # a count may differ only where the oracle has a gap below one float ulp
-        for c in bad:
-            segs = ref.z[ref.col_off[c]:ref.col_off[c + 1]]
-            gaps = segs[1:, 0] - segs[:-1, 1]
-            scale = np.maximum(np.abs(segs[1:, 0]), 1.0)
-            assert gaps.size and np.min(gaps / scale) < 2 ** -23, f"{what}: count mismatch col {c}"
-        bad = []
-    assert len(bad) == 0, f"{what}: count mismatch at {bad[:8]}"
-    if (rc == gc).all() and z.size:
-        err = np.max(np.abs(z - ref.z))
+    unexcused = [int(c) for c in bad if not _excused(ref, c, f32)]
+    assert not unexcused, f"{what}: count mismatch at columns {unexcused[:8]}"
+    same = rc == gc
+    if not same.any():
+        return
+    # segments of the matching columns, in the same order on both sides
+    sel_g = np.repeat(same, gc)
+    sel_r = np.repeat(same, rc)
+    zg = np.asarray(z, np.float64).reshape(-1, 2)[sel_g]
+    zr = np.asarray(ref.z, np.float64).reshape(-1, 2)[sel_r]
+    assert zg.shape == zr.shape, what
+    if zg.size:
+        err = float(np.max(np.abs(zg - zr)))
         assert err <= (TOL32 if f32 else TOL64), f"{what}: max endpoint error {err}"
 
 
@@ -323,3 +348,22 @@ def test_pass1_ring_spill(dx, op, monkeypatch):
         ref = _ref(g, op, k)
         assert ctx.stats()[4] > 16  # some column has more pieces than a region holds
         _compare_full(off, z.astype(np.float64), ref, False, f"ring 16 {op} k={k}")
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_levels_exact_reads(dx, op, monkeypatch):
+    """Level walks at reach >= 32 reading S_mid itself (DEXEL_LEVELS_EXACT=1, no packed float
+    copy) against the oracle, FP64 and FP32 endpoints."""
+    import torch
+    monkeypatch.setenv("DEXEL_LEVELS_EXACT", "1")
+    rng = np.random.default_rng(41)
+    g = shapes.random_grid(rng, 90, 80, 4, fill=0.6, point_frac=0.05, h=1 / 512)
+    for f32 in (False, True):
+        gg = shapes.to_float32(g) if f32 else g
+        dg = dx.Grid.from_synth(gg, dtype=torch.float32 if f32 else torch.float64)
+        ctx = dx.Context(0)
+        for k in (32.0, 40.5):
+            out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
+            off, z = out.to_host()
+            _compare_full(off, z.astype(np.float64), _ref(gg, op, k), f32,
+                          f"levels exact {op} k={k} f32={f32}")
