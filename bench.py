@@ -1,17 +1,21 @@
 """Benchmark of the GB300 dexel offset path (one JSON line on rank 0).
 
-Workload (one step): the 512 x 512 grid of 200 seeded primitives (spheres, boxes, hollow
-shells; up to 16 segments per column, FP64 endpoints), dilated and eroded by balls of
-radius 2, 8 and 32 grid spacings -- six offsets per step.  Metric: output dexel columns per
-second (6 * 512^2 columns per step).  Inputs are resident in HBM when the timed region
-starts; the L2 is flushed (a 256 MiB write) before every timed step.
+Default workload (one step): the 2048 x 2048 grid of 1000 seeded primitives (groups of
+nested hollow spheres, thin plates thinner than the radius, spheres, boxes, shells; up to 58
+segments per column, 44.8 M segments, FP64 endpoints), dilated by a ball of radius 64 grid
+spacings through the C ABI.  Metric: output dexel columns per second (2048^2 columns per
+step).  Inputs are resident in HBM when the timed region starts and are larger than the L2.
+The same step with FP32 endpoints (FP64 decisions) is timed beside it and both results are
+checked against the FP64 oracle on sampled columns; the 512 x 512 six-offset step (k = 2, 8,
+32, dilation and erosion) is reported under "offsets_512".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload single|offsets512|batched|morph4096]
 
 With --impl reference the FP64 CPU oracle is timed instead (on the host cores, on a bounded
-sample of columns of the same workload per step).  For N > 1 (torchrun) every rank runs its
-own replica of the workload (independent problems, no collective on the data path); the
-line reports the whole-job rate with the max time over ranks.
+sample of output columns of the same workload per step).  For N > 1 (torchrun) every rank
+runs its own replica of the workload (independent problems, no collective on the data path);
+the line reports the whole-job rate with the max time over ranks.
 """
 from __future__ import annotations
 
@@ -21,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -28,14 +33,17 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 RADII = (2.0, 8.0, 32.0)
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the k = 32
-# dilation's kernels, from an ncu capture of the current kernels (None once they change):
-# the pass-1 window kernel, and the pass-2 pair k_levels + k_lgather
-TRAFFIC_K32_DILATE_PASS1 = 1_006_439_936
-TRAFFIC_K32_DILATE_PASS2 = None  # k_lgather changed after its capture (1.55 GB then)
 OPS = ("dilate", "erode")
-N = 512
-HBM_PEAK = None
+K_MAIN = 64.0  # the 2048^2 workload's radius in grid spacings
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per S_mid piece of the 2048^2
+# k = 64 dilation's kernels, from an ncu capture of the current kernels on a 256-row strip of
+# the workload, scaled to a full launch by the pieces processed (None once a kernel changed
+# after its capture)
+TRAFFIC_PER_PIECE = {"k_pass1l": None, "k_levels": None}
+# instructions (smsp__inst_executed.sum) per S_mid piece from the same capture
+INST_PER_PIECE = {"k_pass1l": None, "k_levels": None}
+# issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock
+ISSUE_PER_CLK = 152 * 4
 
 
 def measured_peaks():
@@ -48,6 +56,12 @@ def measured_peaks():
 
 
 def workload():
+    """The 2048 x 2048 grid of 1000 seeded primitives (FP64 endpoints)."""
+    from synth import shapes
+    return shapes.config3()
+
+
+def workload512():
     from synth import shapes
     return shapes.config2()
 
@@ -89,11 +103,11 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="dexel_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -113,6 +127,15 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
+        try:
+            return self._summary()
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+
+    def _summary(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm, mx, reasons = [], [], set()
@@ -150,16 +173,20 @@ def offset_plan(nstreams):
     return plan
 
 
-def run_ours(args, rank, ws):
+def run_offsets512(args, rank, ws, steps=None, warmup=None, with_e2e=True):
+    """The 512 x 512 step: six offsets (dilation and erosion at k = 2, 8, 32), on two host
+    threads with their own contexts and streams.  Returns the line's fields."""
     import numpy as np
     import torch
     from concurrent.futures import ThreadPoolExecutor
 
     import paper_1804_08968_gb300 as dx
 
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    g = workload()
+    g = workload512()
     grid = dx.Grid.from_synth(g, dtype=torch.float64)
     ns = max(1, args.streams)
     ctxs = [dx.Context(dev) for _ in range(ns)]
@@ -209,187 +236,345 @@ def run_ours(args, rank, ws):
             main.wait_stream(st)
         return sum(r[0] for r in res), sum(r[1] for r in res)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(grid)
     torch.cuda.synchronize()
 
     times = []
     launches = 0
-    barrier(ws)
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        n, _ = step(grid)
+        e1.record(main)
+        launches += n
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
-    with ClockSampler(dev) as clk:
-        t_wall = time.perf_counter()
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(main)
-            n, _ = step(grid)
-            e1.record(main)
-            launches += n
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall
-    barrier(ws)
     ms_step = allmax(sum(times) / len(times), ws, device="cuda")
-    value = units * ws / (ms_step / 1e3)
 
-    # kernel and stage times from a serial pass (one context, one offset at a time, each
-    # kernel bracketed by its own events; concurrent streams would stretch them)
+    # kernel and stage times from a serial pass (one context, one offset at a time)
     ctx = ctxs[0]
     ctx.set_profiling(True)
     rec = []
-    for _ in range(2):
-        rec = []
-        for op in OPS:
-            for k in RADII:
-                flush.zero_()
-                ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, grid, k, main)
-                rec.append((op, k, ctx.stage_ms(), ctx.stats(), ctx.kernel_ms()))
+    for op in OPS:
+        for k in RADII:
+            flush.zero_()
+            ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, grid, k, main)
+            rec.append((op, k, ctx.stage_ms(), ctx.stats(), ctx.kernel_ms()))
     ctx.set_profiling(False)
     torch.cuda.synchronize()
 
-    # roofline of the dominant kernel: the pass-1 window kernel of the k = 32 dilation (its
-    # own event pair on the call's stream).  Algorithmic bytes: the input read once (16 B a
-    # segment, 4 B a column offset), S_mid written (two FP64 keys + int16 dx = 18 B a piece)
-    # with its per-column start + count (12 B).
-    dom = [r for r in rec if r[0] == "dilate" and r[1] == 32.0]
-    ncol = g.nx * g.ny
-    dom_ms = sum(r[4][0] for r in dom) / len(dom)
-    dom_bytes = 16 * g.nseg + 4 * (ncol + 1) + 18 * dom[0][3][1] + 12 * ncol
-    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-    peak, peak_kind = measured_peaks()
-    # the pass-2 pair of the same offset (k_levels + k_lgather): S_mid read once (18 B a
-    # piece), pass-2 intervals written (16 B each), per-column start + count (12 B)
-    p2_ms = sum(r[4][1] + r[4][2] for r in dom) / len(dom)
-    p2_bytes = 18 * dom[0][3][1] + 16 * dom[0][3][2] + 12 * ncol
-    p2_achieved = p2_bytes / (p2_ms / 1e3) / 1e9
-    stages = [sum(r[2][q] for r in rec) for q in range(5)]
-    kms = [sum(r[4][q] for r in rec) for q in range(4)]
+    res = {"value": units * ws / (ms_step / 1e3), "unit": "columns/s", "ms_per_step": ms_step,
+           "steps": steps, "warmup": warmup, "gpu_launches": launches,
+           "workload": "512x512 grid, 200 seeded primitives (spheres/boxes/hollow shells, <=16 "
+                       "segs/col), dilation+erosion at k=2,8,32 spacings, FP64",
+           "columns_per_step": units, "nseg_in": g.nseg,
+           "l2": "flushed (256 MiB write) before every timed step",
+           "streams": f"{ns} (the six offsets of a step on {ns} host threads, each its own "
+                      f"context and stream: {plan})",
+           "kernel_ms": {f"{op}_k{int(k)}": {"pass1_window": km[0], "k_levels": km[1],
+                                             "k_lgather": km[2], "smid_pack": km[3]}
+                         for (op, k, _, _s, km) in rec},
+           "stats": {f"{op}_k{int(k)}": {"mid_pieces": st[1], "out_segs": st[3],
+                                         "max_pieces_col": st[4]}
+                     for (op, k, _, st, _k) in rec}}
 
-    # end to end through the public API with host buffers (pinned), copies timed: each step
-    # copies the input to the device and reads every result back
-    off_h = torch.from_numpy(np.asarray(g.col_off, np.int32)).pin_memory()
-    z_h = torch.from_numpy(np.asarray(g.z, np.float64)).pin_memory()
-    e2e_times = []
+    if with_e2e:
+        # end to end through the public API with host buffers (pinned), copies timed
+        off_h = torch.from_numpy(np.asarray(g.col_off, np.int32)).pin_memory()
+        z_h = torch.from_numpy(np.asarray(g.z, np.float64)).pin_memory()
+        e2e_times = []
+        h2d = d2h = 0
+        for it in range(max(2, steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            off_d = off_h.to("cuda", non_blocking=True)
+            z_d = z_h.to("cuda", non_blocking=True)
+            gd = dx.Grid(g.nx, g.ny, g.h, off_d, z_d)
+            b_in = off_h.numel() * 4 + z_h.numel() * 8
+            _, b_out = step(gd, fetch=True)
+            torch.cuda.synchronize()
+            e2e_times.append(time.perf_counter() - t0)
+            h2d, d2h = b_in, b_out
+        e2e_s = allmax(statistics.median(e2e_times), ws, device="cuda")
+        res["e2e"] = {"value": units * ws / e2e_s, "unit": "columns/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h}
+    pool.shutdown()
+    return res
+
+
+def kernel_roofline(name, km_ms, g, stats, fp32, peak, peak_kind, clk_mhz):
+    """Roofline objects of one kernel of the 2048^2 call: HBM (algorithmic bytes over its
+    CUDA-event time) and instruction issue (instructions from the ncu capture, scaled by the
+    S_mid pieces, over the issue peak at the measured clock)."""
+    ncol = g.nx * g.ny
+    P = stats[1]
+    s = 8 if fp32 else 16              # an endpoint pair
+    sm = 10 if fp32 else 18            # an S_mid piece: two keys + int16 dx
+    if name == "k_pass1l":
+        # the input read once (pairs + column offsets), S_mid written with its per-column
+        # start and count
+        nbytes = s * g.nseg + 4 * (ncol + 1) + sm * P + 12 * ncol
+        what = "k_pass1l (pass 1, x extrusion, one lane per output column)"
+    else:
+        # S_mid read once with its index
+        nbytes = sm * P + 12 * ncol
+        what = "k_levels (pass 2, per-source level unions of the capsule slices)"
+    achieved = nbytes / (km_ms / 1e3) / 1e9
+    tp = TRAFFIC_PER_PIECE.get(name)
+    line = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None if tp is None else tp * P,
+            "kernel": what + (", FP32 endpoints" if fp32 else ", FP64"),
+            "algorithmic_bytes": nbytes, "ms_per_launch": km_ms, "peak_source": peak_kind}
+    ipp = INST_PER_PIECE.get(name)
+    issue = None
+    if ipp is not None and clk_mhz:
+        inst = ipp * P
+        ach = inst / (km_ms / 1e3) / 1e9
+        pk = ISSUE_PER_CLK * clk_mhz / 1e3
+        issue = {"bound": "issue", "achieved": ach, "peak": pk, "unit": "G warp-instr/s",
+                 "frac": ach / pk, "kernel": line["kernel"],
+                 "peak_source": "152 SMs x 4 schedulers x measured median SM clock"}
+    return line, issue
+
+
+def sample_columns(n, count, seed):
+    """Seeded output columns of an n x n grid: `count` random ones plus one full row."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    cols = rng.choice(n * n, min(count, n * n), replace=False)
+    return np.unique(np.concatenate([cols, np.arange(n) + (n // 2) * n]))
+
+
+def check_sampled(g, off, z, k, cols):
+    """Max endpoint error and count mismatches of a dilation against the FP64 oracle."""
+    import numpy as np
+
+    import oracle
+    ref = oracle.dilate(g, k, cols=cols)
+    mx, mism = 0.0, 0
+    for t, c in enumerate(cols):
+        got = np.asarray(z[off[c]:off[c + 1]], np.float64)
+        exp = ref.column(t)
+        if got.shape != exp.shape:
+            mism += 1
+        elif exp.size:
+            mx = max(mx, float(np.max(np.abs(got - exp))))
+    return {"max_endpoint_error": mx, "count_mismatches": mism, "columns_checked": int(len(cols))}
+
+
+def run_ours(args, rank, ws):
+    """The 2048^2 k = 64 dilation, FP64 (the line's value) and FP32 endpoints beside it."""
+    import numpy as np
+    import torch
+
+    import paper_1804_08968_gb300 as dx
+    from synth import shapes
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    g64 = workload()
+    g32 = shapes.to_float32(g64)
+    gen_s = time.perf_counter() - t0
+    n = g64.nx
+    units = n * n
+    k = K_MAIN
+    ctx = dx.Context(dev)
+    stream = torch.cuda.current_stream()
+    grids = {"fp64": dx.Grid.from_synth(g64, dtype=torch.float64),
+             "fp32": dx.Grid.from_synth(g32, dtype=torch.float32)}
+    res = {}
+    launches = 0
+    barrier(ws)
+    with ClockSampler(dev) as clk:
+        for name in ("fp64", "fp32"):
+            d = grids[name]
+            for _ in range(args.warmup):
+                out = ctx.run(dx.DILATE, d, k, stream)
+            torch.cuda.synchronize()
+            times = []
+            nl = 0
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                out = ctx.run(dx.DILATE, d, k, stream)
+                e1.record(stream)
+                nl += ctx.last_launches
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            torch.cuda.synchronize()
+            res[name] = {"ms": sum(times) / len(times), "launches": nl}
+            if name == "fp64":
+                launches = nl
+            del out
+    clocks = clk.summary()
+    barrier(ws)
+    ms64 = allmax(res["fp64"]["ms"], ws, device="cuda")
+    ms32 = allmax(res["fp32"]["ms"], ws, device="cuda")
+
+    # per-kernel device times from a serial profiled call of each mode, and the results
+    # checked against the FP64 oracle on sampled columns (FP32: the same float32 input)
+    ctx.set_profiling(True)
+    prof = {}
+    cols = sample_columns(n, args.check_cols, seed=11)
+    for name, g in (("fp64", g64), ("fp32", g32)):
+        out = ctx.run(dx.DILATE, grids[name], k, stream)
+        torch.cuda.synchronize()
+        prof[name] = {"stage_ms": ctx.stage_ms(), "kernel_ms": ctx.kernel_ms(), "stats": ctx.stats()}
+        off, z = out.to_host()
+        prof[name]["check"] = check_sampled(g, off, z, k, cols) if rank == 0 else None
+        del out
+    ctx.set_profiling(False)
+
+    peak, peak_kind = measured_peaks()
+    km = prof["fp64"]["kernel_ms"]
+    names = ["k_pass1l", "k_levels"]
+    dom = names[0] if km[0] >= km[1] else names[1]
+    roof, issue = kernel_roofline(dom, km[0] if dom == "k_pass1l" else km[1], g64,
+                                  prof["fp64"]["stats"], False, peak, peak_kind, clocks.get("sm_mhz"))
+    other = names[1] if dom == names[0] else names[0]
+    roof2, issue2 = kernel_roofline(other, km[0] if other == "k_pass1l" else km[1], g64,
+                                    prof["fp64"]["stats"], False, peak, peak_kind, clocks.get("sm_mhz"))
+    st = prof["fp64"]["stats"]
+    s = 16
+    call_bytes = 12 * (units + 1) + s * g64.nseg + 2 * 18 * st[1] + s * st[3]
+
+    # end to end through the public API with host buffers: every step copies the input from
+    # pinned host memory to the device, runs the call and reads the result back
+    off_h = torch.from_numpy(np.asarray(g64.col_off, np.int32)).pin_memory()
+    z_h = torch.from_numpy(np.asarray(g64.z, np.float64)).pin_memory()
+    zo_h = torch.empty((max(st[3], 1), 2), dtype=torch.float64, pin_memory=True)
+    oo_h = torch.empty(units + 1, dtype=torch.int32, pin_memory=True)
+    e2e = []
     h2d = d2h = 0
-    for it in range(max(2, args.steps)):
-        flush.zero_()
+    for _ in range(max(2, min(args.steps, 5))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        off_d = off_h.to("cuda", non_blocking=True)
-        z_d = z_h.to("cuda", non_blocking=True)
-        gd = dx.Grid(g.nx, g.ny, g.h, off_d, z_d)
-        b_in = off_h.numel() * 4 + z_h.numel() * 8
-        _, b_out = step(gd, fetch=True)
+        gd = dx.Grid(n, n, g64.h, off_h.to("cuda", non_blocking=True), z_h.to("cuda", non_blocking=True))
+        out = ctx.run(dx.DILATE, gd, k, stream)
+        oo_h.copy_(out.col_off, non_blocking=True)
+        zo = zo_h[: out.nseg] if out.nseg <= zo_h.shape[0] else torch.empty_like(out.z, device="cpu")
+        zo.copy_(out.z, non_blocking=True)
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
-        h2d, d2h = b_in, b_out
-    e2e_s = allmax(statistics.median(e2e_times), ws, device="cuda")
-    pool.shutdown()
+        e2e.append(time.perf_counter() - t0)
+        h2d = off_h.numel() * 4 + z_h.numel() * 8
+        d2h = oo_h.numel() * 4 + out.nseg * 16
+        del gd, out
+    e2e_s = allmax(statistics.median(e2e), ws, device="cuda")
 
     line = {
-        "metric": "output dexel columns/s", "value": value, "unit": "columns/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "metric": "output dexel columns/s", "value": units * ws / (ms64 / 1e3), "unit": "columns/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms64,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "512x512 grid, 200 seeded primitives (spheres/boxes/hollow shells, "
-                               "<=16 segs/col), dilation+erosion at k=2,8,32 spacings, FP64",
-                   "columns_per_step": units, "nseg_in": g.nseg, "l2": "flushed (256 MiB write) "
-                   "before every timed step", "parallelism": f"replica x{ws}",
-                   "streams": f"{ns} (the six offsets of a step on {ns} host threads, each its "
-                              f"own context and stream: {plan})"},
+        "config": {"workload": "2048x2048 grid, 1000 seeded primitives (nested hollow spheres, thin "
+                               "plates, spheres, boxes, shells; <=58 segs/col), dilation by a ball "
+                               "of radius k=64 spacings, FP64 endpoints",
+                   "columns_per_step": units, "nseg_in": g64.nseg,
+                   "max_segs_per_col": int(np.diff(g64.col_off).max()),
+                   "l2": "inputs larger than L2 (717 MB of endpoints)", "parallelism": f"replica x{ws}"},
         "e2e": {"value": units * ws / e2e_s, "unit": "columns/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC_K32_DILATE_PASS1,
-                     "kernel": "k_pass1l (pass 1, x extrusion, one lane per output column), "
-                               "dilation k=32",
-                     "algorithmic_bytes": dom_bytes, "ms_per_launch": dom_ms,
-                     "peak_source": peak_kind},
-        "roofline_pass2": {"bound": "hbm", "achieved": p2_achieved, "peak": peak, "unit": "GB/s",
-                           "frac": p2_achieved / peak, "traffic": TRAFFIC_K32_DILATE_PASS2,
-                           "kernel": "k_levels + k_lgather (pass 2, y dilation with per-piece "
-                                     "radius), dilation k=32",
-                           "algorithmic_bytes": p2_bytes, "ms_per_launch": p2_ms,
-                           "peak_source": peak_kind},
-        "serial_ms_per_step": {"validate+tables": stages[0], "pass1": stages[1], "pass2": stages[2],
-                               "count+scan": stages[3], "write": stages[4],
-                               "kernels": {"pass1_window": kms[0], "k_levels": kms[1],
-                                           "k_lgather": kms[2], "smid_pack": kms[3]}},
-        "stats": {f"{op}_k{int(k)}": {"mid_pieces": st[1], "out_segs": st[3],
-                                      "max_pieces_col": st[4], "redo_cols": st[5]}
-                  for (op, k, _, st, _k) in rec},
-        "wall_s_timed": t_wall,
+        "roofline": roof,
+        "roofline_issue": issue,
+        "roofline_other": {"hbm": roof2, "issue": issue2},
+        "hbm_call": {"algorithmic_bytes": call_bytes, "gbs": call_bytes / (ms64 / 1e3) / 1e9,
+                     "frac": call_bytes / (ms64 / 1e3) / 1e9 / peak,
+                     "formula": "12(N^2+1) + 16 nseg + 2*18 P + 16 M (FP64)"},
+        "fp64": {"ms_per_step": ms64, "stage_ms": prof["fp64"]["stage_ms"],
+                 "kernel_ms": dict(zip(["pass1_window", "k_levels", "k_lgather", "smid_pack"],
+                                       prof["fp64"]["kernel_ms"])),
+                 "mid_pieces": st[1], "out_segs": st[3], "error_vs_oracle": prof["fp64"]["check"]},
+        "fp32": {"ms_per_step": ms32, "value": units * ws / (ms32 / 1e3),
+                 "speedup_over_fp64": ms64 / ms32, "stage_ms": prof["fp32"]["stage_ms"],
+                 "kernel_ms": dict(zip(["pass1_window", "k_levels", "k_lgather", "smid_pack"],
+                                       prof["fp32"]["kernel_ms"])),
+                 "mid_pieces": prof["fp32"]["stats"][1], "error_vs_oracle": prof["fp32"]["check"]},
+        "clocks": clocks,
+        "generate_s": gen_s,
     }
+    del grids
+    torch.cuda.empty_cache()
+    if not args.no_512:
+        line["offsets_512"] = run_offsets512(args, rank, ws, steps=min(args.steps, 10),
+                                             warmup=max(3, min(args.warmup, 3)), with_e2e=False)
     if rank == 0:
-        line["clocks"] = clk.summary()
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(g, args)
+            line["cpu_baseline"] = cpu_baseline(g64, args)
         print(json.dumps(line), flush=True)
 
 
-def oracle_sample(g, cols_per_op, seed=0):
-    """Time the FP64 oracle on a bounded sample of columns of every offset of the step."""
+def oracle_sample(g, ncols, seed=0, k=K_MAIN):
+    """Time the FP64 oracle's dilation of the workload on `ncols` seeded random output
+    columns (a bounded sample of the step)."""
     import numpy as np
 
     import oracle
     rng = np.random.default_rng(seed)
-    n = 0
-    t = 0.0
-    for op in OPS:
-        for k in RADII:
-            cols = rng.choice(g.nx * g.ny, cols_per_op, replace=False)
-            t0 = time.perf_counter()
-            (oracle.dilate if op == "dilate" else oracle.erode)(g, k, cols=cols)
-            t += time.perf_counter() - t0
-            n += cols.size
-    return n, t
+    cols = rng.choice(g.nx * g.ny, min(ncols, g.nx * g.ny), replace=False)
+    t0 = time.perf_counter()
+    oracle.dilate(g, k, cols=cols)
+    return cols.size, time.perf_counter() - t0
+
+
+def calibrated_columns(g, seconds):
+    """Output columns the oracle takes about `seconds` for on this host."""
+    n0, t0 = oracle_sample(g, 200, seed=7)
+    return int(min(g.nx * g.ny, max(200, n0 * seconds / max(t0, 1e-3))))
 
 
 def cpu_baseline(g, args):
     import oracle
     oracle.build()
-    # size the sample for about args.cpu_seconds of oracle work (bounded, same workload)
-    n0, t0 = oracle_sample(g, 40, seed=7)
-    cols = int(min(g.nx * g.ny, max(40, 40 * args.cpu_seconds / max(t0, 1e-3))))
-    args.cpu_cols = cols
+    cols = args.ref_cols or calibrated_columns(g, args.cpu_seconds)
     n, t = oracle_sample(g, cols)
     return {"value": n / t, "unit": "columns/s", "cores": oracle.default_threads(), "kind": "oracle",
-            "sample": f"{args.cpu_cols} random output columns per offset (6 offsets), FP64 brute-force "
-                      f"gather, {t:.1f} s"}
+            "sample": f"{n} random output columns of the 2048^2 k=64 dilation, FP64 brute-force "
+                      f"gather over all columns within reach, {t:.1f} s"}
 
 
 def run_reference(args, rank, ws):
+    """The reference arm: the FP64 CPU oracle on the host cores, each step a bounded sample
+    of output columns of the same workload (sized like the GPU arm's cpu_baseline)."""
     if rank != 0:
         return
     import oracle
     oracle.build()
     g = workload()
-    for _ in range(args.warmup):
-        oracle_sample(g, 50, seed=1)
+    cols = args.ref_cols or calibrated_columns(g, args.ref_seconds)
+    for w in range(args.warmup):
+        oracle_sample(g, max(50, cols // 10), seed=1 + w)
     times = []
     n_tot = 0
     for s in range(args.steps):
-        n, t = oracle_sample(g, args.ref_cols, seed=100 + s)
+        n, t = oracle_sample(g, cols, seed=100 + s)
         times.append(t)
         n_tot += n
     per_col = sum(times) / n_tot
-    units = len(OPS) * len(RADII) * g.nx * g.ny
+    units = g.nx * g.ny
     value = 1.0 / per_col
     line = {
         "impl": "reference", "metric": "output dexel columns/s", "value": value, "unit": "columns/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": units * per_col * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "512x512 grid, 200 seeded primitives (spheres/boxes/hollow shells, "
-                               "<=16 segs/col), dilation+erosion at k=2,8,32 spacings, FP64",
+        "ms_per_step": units * per_col * 1e3, "ms_per_step_extrapolated": True,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "2048x2048 grid, 1000 seeded primitives (nested hollow spheres, thin "
+                               "plates, spheres, boxes, shells; <=58 segs/col), dilation by a ball "
+                               "of radius k=64 spacings, FP64 endpoints",
                    "columns_per_step": units, "nseg_in": g.nseg, "parallelism": "host threads"},
         "cpu_baseline": {"value": value, "unit": "columns/s", "cores": oracle.default_threads(),
                          "kind": "oracle",
-                         "sample": f"{args.ref_cols} random output columns per offset per step"},
+                         "sample": f"{cols} random output columns per step ({n_tot} in all, "
+                                   f"{sum(times):.1f} s); ms_per_step extrapolated to the "
+                                   f"{units} columns of a step"},
         "e2e": {"value": value, "unit": "columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -488,131 +673,87 @@ def run_batched_workload(args):
     print(json.dumps(line), flush=True)
 
 
-def run_precision_workload(args):
-    """The precision configuration: the 2048 x 2048 grid of 1000 primitives (nested shells,
-    thin plates thinner than r, spheres, boxes, shells; up to 58 segments per column),
-    dilated by k = 64 spacings, in FP64 and in FP32 endpoints with FP64 decisions.  Reports
-    both times and each result's max endpoint error and count mismatches against the FP64
-    oracle on sampled columns (FP32: the oracle reads the same float32 input).  One JSON
-    line."""
-    import numpy as np
-    import torch
-
-    import oracle
-    import paper_1804_08968_gb300 as dx
-    from synth import shapes
-
-    torch.cuda.set_device(0)
-    k = 64.0
-    t0 = time.perf_counter()
-    g64 = shapes.config3()
-    g32 = shapes.to_float32(g64)
-    gen_s = time.perf_counter() - t0
-    ctx = dx.Context(0)
-    ctx.set_profiling(True)
-    stream = torch.cuda.current_stream()
-    res = {}
-    with ClockSampler(0) as clk:
-        for name, g, dt in (("fp64", g64, torch.float64), ("fp32", g32, torch.float32)):
-            d = dx.Grid.from_synth(g, dtype=dt)
-            out = ctx.run(dx.DILATE, d, k)  # warm-up (sizes the scratch)
-            torch.cuda.synchronize()
-            times = []
-            for _ in range(max(1, min(args.steps, 3))):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                out = ctx.run(dx.DILATE, d, k)
-                e1.record(stream)
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
-            off, z = out.to_host()
-            res[name] = {"ms": statistics.median(times), "stage_ms": ctx.stage_ms(),
-                         "stats": ctx.stats(), "off": off, "z": z}
-            del d, out
-            torch.cuda.empty_cache()
-    rng = np.random.default_rng(1)
-    cols = np.concatenate([rng.choice(g64.nx * g64.ny, 2000, replace=False),
-                           np.arange(2048) + 1024 * 2048])
-    errs = {}
-    for name, g in (("fp64", g64), ("fp32", g32)):
-        ref = oracle.dilate(g, k, cols=cols)
-        off, z = res[name]["off"], res[name]["z"]
-        mx, mism = 0.0, 0
-        for t, c in enumerate(cols):
-            got = z[off[c]:off[c + 1]].astype(np.float64)
-            exp = ref.column(t)
-            if got.shape != exp.shape:
-                mism += 1
-            elif exp.size:
-                mx = max(mx, float(np.max(np.abs(got - exp))))
-        errs[name] = {"max_endpoint_error": mx, "count_mismatches": mism, "columns_checked": len(cols)}
-    cols_n = g64.nx * g64.ny
-    line = {
-        "metric": "output dexel columns/s", "value": cols_n / (res["fp32"]["ms"] / 1e3),
-        "unit": "columns/s", "n_gpus": 1, "steps": max(1, min(args.steps, 3)), "warmup": 1,
-        "ms_per_step": res["fp32"]["ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "2048x2048 grid, 1000 primitives (nested shells, thin plates, "
-                               "spheres, boxes, shells), dilation k=64, FP32 endpoints with FP64 "
-                               "decisions vs FP64", "nseg_in": g64.nseg,
-                   "max_segs_per_col": int(np.diff(g64.col_off).max()),
-                   "l2": "inputs larger than L2", "parallelism": "replica x1"},
-        "fp64": {"ms_per_step": res["fp64"]["ms"], "value": cols_n / (res["fp64"]["ms"] / 1e3),
-                 "stage_ms": res["fp64"]["stage_ms"], "mid_pieces": res["fp64"]["stats"][1],
-                 "error_vs_oracle": errs["fp64"]},
-        "fp32": {"stage_ms": res["fp32"]["stage_ms"], "mid_pieces": res["fp32"]["stats"][1],
-                 "error_vs_oracle": errs["fp32"],
-                 "speedup_over_fp64": res["fp64"]["ms"] / res["fp32"]["ms"]},
-        "clocks": clk.summary(),
-        "generate_s": gen_s,
-    }
-    print(json.dumps(line), flush=True)
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--streams", type=int, default=2,
-                    help="host threads (each its own context and stream) the six offsets of a "
-                         "step are split over")
+                    help="host threads (each its own context and stream) the six offsets of the "
+                         "512^2 step are split over")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-cols", type=int, default=300)
-    ap.add_argument("--ref-cols", type=int, default=100)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-cols", type=int, default=0,
+                    help="oracle columns per step of the reference arm / cpu_baseline "
+                         "(0: calibrated to --ref-seconds / --cpu-seconds)")
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--check-cols", type=int, default=2000,
+                    help="random output columns (plus one full row) checked against the oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-512", action="store_true", help="skip the 512^2 six-offset extra")
     ap.add_argument("--profile-case", action="store_true",
-                    help="run one offset of the workload and exit (for ncu captures)")
-    ap.add_argument("--profile-k", type=float, default=8.0)
-    ap.add_argument("--workload", choices=["single", "batched", "precision"], default="single",
-                    help="batched: the 256-shape batched configuration; precision: the 2048^2 "
-                         "k = 64 FP32 vs FP64 configuration (one JSON line each)")
+                    help="run one offset of a workload and exit (for ncu captures)")
+    ap.add_argument("--profile-k", type=float, default=64.0)
+    ap.add_argument("--profile-rows", type=int, default=0,
+                    help="--profile-case on a strip of this many rows of the 2048^2 workload")
+    ap.add_argument("--profile-mode", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--profile-op", choices=["dilate", "erode"], default="dilate")
+    ap.add_argument("--workload", choices=["single", "offsets512", "batched"], default="single",
+                    help="single: the 2048^2 k=64 dilation (default line); offsets512: the 512^2 "
+                         "six-offset step alone; batched: the 256-shape batched configuration")
     args = ap.parse_args()
     rank, ws = dist_init(args)
     if args.profile_case:
-        import torch
-        import paper_1804_08968_gb300 as dx
-        g = workload()
-        grid = dx.Grid.from_synth(g, dtype=torch.float64)
-        (dx.dilate if args.profile_op == "dilate" else dx.erode)(grid, args.profile_k)
-        torch.cuda.synchronize()
+        run_profile_case(args)
         return
     if args.workload == "batched":
         run_batched_workload(args)
         return
-    if args.workload == "precision":
-        run_precision_workload(args)
-        return
     if args.impl == "reference":
         run_reference(args, rank, ws)
+    elif args.workload == "offsets512":
+        res = run_offsets512(args, rank, ws)
+        if rank == 0:
+            line = {"metric": "output dexel columns/s", "value": res["value"], "unit": "columns/s",
+                    "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                    "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                    "config": {"workload": res["workload"], "columns_per_step": res["columns_per_step"],
+                               "l2": res["l2"], "streams": res["streams"],
+                               "parallelism": f"replica x{ws}"},
+                    "e2e": res.get("e2e"), "gpu_launches": res["gpu_launches"],
+                    "kernel_ms": res["kernel_ms"], "stats": res["stats"]}
+            print(json.dumps(line), flush=True)
     else:
         run_ours(args, rank, ws)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_profile_case(args):
+    """One offset of the 2048^2 workload (or a strip of its rows) for an ncu capture: a warm-up
+    call, then the captured one."""
+    import torch
+
+    import paper_1804_08968_gb300 as dx
+    from synth import shapes
+    g = workload()
+    if args.profile_rows:
+        r = args.profile_rows
+        j0 = (g.ny - r) // 2
+        c0, c1 = g.col_off[j0 * g.nx], g.col_off[(j0 + r) * g.nx]
+        g = shapes.DexelGrid(g.nx, r, g.h, g.col_off[j0 * g.nx:(j0 + r) * g.nx + 1] - c0, g.z[c0:c1])
+    if args.profile_mode == "fp32":
+        g = shapes.to_float32(g)
+    grid = dx.Grid.from_synth(g, dtype=torch.float32 if args.profile_mode == "fp32" else torch.float64)
+    ctx = dx.Context(0)
+    fn = dx.DILATE if args.profile_op == "dilate" else dx.ERODE
+    for _ in range(2):
+        ctx.run(fn, grid, args.profile_k)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": True, "rows": g.ny, "k": args.profile_k,
+                      "stats": ctx.stats()}), flush=True)
 
 
 if __name__ == "__main__":

@@ -257,7 +257,32 @@ def from_columns(nx: int, ny: int, h: float, columns: dict, dtype=np.float64) ->
 
 
 def to_float32(g: DexelGrid) -> DexelGrid:
-    """Round endpoints to float32 and re-merge segments that now touch or overlap."""
+    """Round endpoints to float32 and re-merge segments that now touch or overlap.
+
+    Rounding to nearest is monotone, so every column stays sorted; a segment joins the one
+    before it (same column) exactly when its rounded start is at or below that one's rounded
+    end, and the joined run ends at the rounded end of its last segment (ends stay ordered).
+    """
+    z32 = np.asarray(g.z, np.float64).reshape(-1, 2).astype(np.float32)
+    n = g.nx * g.ny
+    cnt = np.diff(g.col_off)
+    if z32.shape[0] == 0:
+        return DexelGrid(g.nx, g.ny, g.h, np.zeros(n + 1, np.int64), np.zeros((0, 2), np.float32))
+    col = np.repeat(np.arange(n, dtype=np.int64), cnt)
+    new = np.ones(z32.shape[0], bool)
+    new[1:] = (col[1:] != col[:-1]) | (z32[1:, 0] > z32[:-1, 1])
+    starts = np.flatnonzero(new)
+    ends = np.append(starts[1:], z32.shape[0]) - 1
+    za = z32[starts, 0]
+    zb = z32[ends, 1]
+    counts = np.bincount(col[starts], minlength=n)
+    off = np.zeros(n + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    return DexelGrid(g.nx, g.ny, g.h, off, np.stack([za, zb], axis=1).astype(np.float32))
+
+
+def to_float32_sorting(g: DexelGrid) -> DexelGrid:
+    """The same rounding and re-merge through a full per-column sort and closed union."""
     z32 = g.z.astype(np.float32)
     col = np.repeat(np.arange(g.nx * g.ny, dtype=np.int64), np.diff(g.col_off))
     off, z = union_merge(col, z32[:, 0].astype(np.float64), z32[:, 1].astype(np.float64), g.nx * g.ny)

@@ -60,3 +60,22 @@ def test_compare_full_checks_every_matching_column():
     # in FP64 a gap of 2e-9 is not below the 1e-9 threshold: the merge is not excused
     with pytest.raises(AssertionError):
         _compare_full(got.col_off, got.z, ref, False, "planted merge")
+
+
+def test_float32_rounding_merge_matches_sorting_union():
+    """The linear re-merge after rounding gives the sort-and-union result."""
+    rng = np.random.default_rng(3)
+    g = shapes.random_grid(rng, 30, 20, 8, fill=0.8, point_frac=0.1, h=1 / 32)
+    # squeeze some gaps below float resolution so that rounding makes segments touch
+    z = g.z.copy()
+    for c in range(g.nx * g.ny):
+        s0, s1 = g.col_off[c], g.col_off[c + 1]
+        for s in range(s0 + 1, s1):
+            if rng.random() < 0.3 and z[s - 1, 1] + 1e-9 < z[s, 1]:
+                z[s, 0] = z[s - 1, 1] + 1e-9
+    g2 = shapes.DexelGrid(g.nx, g.ny, g.h, g.col_off, z)
+    a = shapes.to_float32(g2)
+    b = shapes.to_float32_sorting(g2)
+    assert np.array_equal(a.col_off, b.col_off)
+    assert np.array_equal(a.z, b.z)
+    assert a.nseg < g2.nseg  # some segments did merge
