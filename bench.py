@@ -673,6 +673,133 @@ def run_batched_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def contained(inner, outer):
+    """Every segment of `inner` lies within one segment of `outer` (one column's arrays)."""
+    import numpy as np
+    if inner.shape[0] == 0:
+        return True
+    if outer.shape[0] == 0:
+        return False
+    q = np.searchsorted(outer[:, 0], inner[:, 0], side="right") - 1
+    ok = q >= 0
+    qq = np.maximum(q, 0)
+    return bool(np.all(ok & (outer[qq, 1] >= inner[:, 1])))
+
+
+def run_morph_workload(args):
+    """The large morphology configuration: the 4096 x 4096 grid of 550 seeded spheres, boxes
+    and hollow shells (61.6 M segments, <= 15 a column), closed and opened by a ball of radius
+    k = 128 spacings, with FP64 endpoints and with FP32 endpoints (FP64 decisions).  Each
+    offset runs in blocks of y lines so that its intermediate pieces fit the device.  Checks:
+    the first stage (the dilation of the closing, the erosion of the opening) against the FP64
+    oracle on sampled columns; closing extensive and opening anti-extensive on sampled
+    columns; FP32 against FP64 results.  One JSON line."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1804_08968_gb300 as dx
+    from synth import shapes
+
+    torch.cuda.set_device(0)
+    k = 128.0
+    t0 = time.perf_counter()
+    g64 = shapes.config5()
+    g32 = shapes.to_float32(g64)
+    gen_s = time.perf_counter() - t0
+    n = g64.nx
+    ctx = dx.Context(0)
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(17)
+    cols = rng.choice(n * n, args.check_cols, replace=False)
+    res = {}
+    with ClockSampler(0) as clk:
+        for name, g, dt in (("fp64", g64, torch.float64), ("fp32", g32, torch.float32)):
+            d = dx.Grid.from_synth(g, dtype=dt)
+            res[name] = {}
+            for opname, op, first in (("close", dx.CLOSE, dx.DILATE), ("open", dx.OPEN, dx.ERODE)):
+                out = ctx.run(op, d, k)  # warm-up (sizes the scratch)
+                torch.cuda.synchronize()
+                times = []
+                for _ in range(max(1, args.steps)):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    out = ctx.run(op, d, k)
+                    e1.record(stream)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                st = ctx.stats()
+                km = ctx.kernel_ms()
+                off, z = out.to_host()
+                del out
+                # the first stage alone, against the oracle on sampled columns
+                s1 = ctx.run(first, d, k)
+                o1, z1 = s1.to_host()
+                del s1
+                torch.cuda.empty_cache()
+                res[name][opname] = {"ms": statistics.median(times), "stats": st, "kernel_ms": km,
+                                     "off": off, "z": z, "stage1": (o1, z1)}
+            del d
+            torch.cuda.empty_cache()
+    out_line = {}
+    for name, g in (("fp64", g64), ("fp32", g32)):
+        for opname, first in (("close", "dilate"), ("open", "erode")):
+            r = res[name][opname]
+            o1, z1 = r["stage1"]
+            ref = (oracle.dilate if first == "dilate" else oracle.erode)(g, k, cols=cols)
+            mx, mism = 0.0, 0
+            for t, c in enumerate(cols):
+                got = np.asarray(z1[o1[c]:o1[c + 1]], np.float64)
+                exp = ref.column(t)
+                if got.shape != exp.shape:
+                    mism += 1
+                elif exp.size:
+                    mx = max(mx, float(np.max(np.abs(got - exp))))
+            ok = 0
+            for c in cols:
+                inp = np.asarray(g.z[g.col_off[c]:g.col_off[c + 1]], np.float64)
+                res_c = np.asarray(r["z"][r["off"][c]:r["off"][c + 1]], np.float64)
+                ok += contained(inp, res_c) if opname == "close" else contained(res_c, inp)
+            out_line[f"{name}_{opname}"] = {
+                "ms": r["ms"], "value": n * n / (r["ms"] / 1e3), "out_segs": int(r["off"][-1]),
+                "mid_pieces_last_stage": r["stats"][1], "blocks_of_lines": r["stats"][9],
+                "kernel_ms": dict(zip(["pass1_window", "k_levels", "k_lgather", "smid_pack"],
+                                      r["kernel_ms"])),
+                "first_stage_vs_oracle": {"stage": first, "max_endpoint_error": mx,
+                                          "count_mismatches": mism, "columns_checked": int(len(cols))},
+                ("extensive_columns" if opname == "close" else "anti_extensive_columns"): int(ok)}
+    # FP32 against FP64 (sampled columns)
+    for opname in ("close", "open"):
+        a, b = res["fp64"][opname], res["fp32"][opname]
+        mx, mism = 0.0, 0
+        for c in cols:
+            za = np.asarray(a["z"][a["off"][c]:a["off"][c + 1]], np.float64)
+            zb = np.asarray(b["z"][b["off"][c]:b["off"][c + 1]], np.float64)
+            if za.shape != zb.shape:
+                mism += 1
+            elif za.size:
+                mx = max(mx, float(np.max(np.abs(za - zb))))
+        out_line[f"fp32_vs_fp64_{opname}"] = {"max_endpoint_difference": mx, "count_mismatches": mism,
+                                              "speedup": a["ms"] / b["ms"]}
+    tot64 = out_line["fp64_close"]["ms"] + out_line["fp64_open"]["ms"]
+    line = {
+        "metric": "output dexel columns/s", "value": 2 * n * n / (tot64 / 1e3), "unit": "columns/s",
+        "n_gpus": 1, "steps": max(1, args.steps), "warmup": 1, "ms_per_step": tot64,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "4096x4096 grid, 550 seeded spheres/boxes/hollow shells (61.6 M "
+                               "segments, <=15 segs/col), closing and opening at k=128 spacings "
+                               "(a step: one closing and one opening, FP64)",
+                   "nseg_in": g64.nseg, "l2": "inputs larger than L2", "parallelism": "replica x1"},
+        **out_line,
+        "clocks": clk.summary(),
+        "generate_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -696,11 +823,15 @@ def main():
     ap.add_argument("--profile-k", type=float, default=64.0)
     ap.add_argument("--profile-rows", type=int, default=0,
                     help="--profile-case on a strip of this many rows of the 2048^2 workload")
+    ap.add_argument("--profile-row0", type=int, default=-1,
+                    help="first row of the --profile-rows strip (default: centred)")
     ap.add_argument("--profile-mode", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--profile-op", choices=["dilate", "erode"], default="dilate")
-    ap.add_argument("--workload", choices=["single", "offsets512", "batched"], default="single",
+    ap.add_argument("--workload", choices=["single", "offsets512", "batched", "morph4096"],
+                    default="single",
                     help="single: the 2048^2 k=64 dilation (default line); offsets512: the 512^2 "
-                         "six-offset step alone; batched: the 256-shape batched configuration")
+                         "six-offset step alone; batched: the 256-shape batched configuration; "
+                         "morph4096: closing and opening of the 4096^2 grid at k=128")
     args = ap.parse_args()
     rank, ws = dist_init(args)
     if args.profile_case:
@@ -708,6 +839,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched_workload(args)
+        return
+    if args.workload == "morph4096":
+        run_morph_workload(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, ws)
@@ -741,7 +875,7 @@ def run_profile_case(args):
     g = workload()
     if args.profile_rows:
         r = args.profile_rows
-        j0 = (g.ny - r) // 2
+        j0 = (g.ny - r) // 2 if args.profile_row0 < 0 else min(args.profile_row0, g.ny - r)
         c0, c1 = g.col_off[j0 * g.nx], g.col_off[(j0 + r) * g.nx]
         g = shapes.DexelGrid(g.nx, r, g.h, g.col_off[j0 * g.nx:(j0 + r) * g.nx + 1] - c0, g.z[c0:c1])
     if args.profile_mode == "fp32":

@@ -90,7 +90,7 @@ typedef struct dexel_ctx dexel_ctx;
  *   DEXEL_PASS1=sweep|gather|lane   pass 1 as the per-row sweep, the per-column window
  *                                   kernel, or the lane-per-column window kernel at every
  *                                   reach (default: per-lane merges up to reach 2, the
- *                                   lane-per-column window kernel up to 127, the sweep beyond)
+ *                                   lane-per-column window kernel up to 128, the sweep beyond)
  *   DEXEL_PASS1_GW=1|2|4|8          warps a pass-1 tile (default by reach)
  *   DEXEL_PASS1_ECAP=256..16384     events a pass-1 tile holds (a power of two; default by
  *                                   density)
@@ -98,6 +98,15 @@ typedef struct dexel_ctx dexel_ctx;
  *                                   default) or in a counting and a writing walk
  *   DEXEL_PASS1_RING_CAP=16..128    pieces a lane's ring region holds (a tile with a lane
  *                                   beyond it is walked again into place)
+ *   DEXEL_PASS1_ECAP_RULE=mean|max  event room a tile by the mean density of the windows, the
+ *                                   few denser columns redone by a second launch (mean,
+ *                                   default), or room for the densest window from the start
+ *   DEXEL_BLOCK_MB=n                split an offset into blocks of whole y lines when its
+ *                                   S_mid, packed copy and level lists would take more than
+ *                                   n MB (default 48000)
+ *   DEXEL_PASS1_PRUNE=0|1           drop S_mid pieces whose capsule slice a neighbouring
+ *                                   piece with a smaller dx contains at every level (1,
+ *                                   default; the result is the same)
  *   DEXEL_PASS2=sweep|tiled         pass 2 as the per-line sweep or the tiled gather instead
  *                                   of the level unions
  *   DEXEL_LANE_GATHER_MAX=R         the pass-2 gather with one lane a column up to reach R
@@ -172,7 +181,7 @@ void dexel_set_batch_autotune(dexel_ctx* ctx, int on);
  * offset -- an application whose own pool owns the GPU's memory, a real-time loop that must
  * not pay cudaMalloc's implicit synchronisation, code running where allocation is
  * forbidden.  It runs the per-line sweep kernels of dexel_dilate / dexel_erode, but every
- * byte of scratch comes from one static 64 MiB device array inside the library; nothing is
+ * byte of scratch comes from one static 128 MiB device array inside the library; nothing is
  * allocated or freed (no ctx either).  The array is committed when the library's module is
  * loaded on a device (eagerly, or on first use under lazy loading) and is held by every GPU
  * that loads it until the process exits; a failure to load it is reported as DEXEL_ERR_CUDA.
@@ -185,6 +194,8 @@ void dexel_set_batch_autotune(dexel_ctx* ctx, int on);
  *   -1                         DEXEL_ERR_CAPACITY: the grid is beyond the static scratch
  *                              (nx*ny > 65536, k > 32, or data needing more scratch than the
  *                              array holds); retrying cannot help.
+ * The array serves unions of a few spheres or boxes up to 256 x 256 columns at k = 32 (about
+ * 25 MB of intermediate pieces there); dense stacks of segments need more and are refused.
  * On DEXEL_ERR_CAPACITY out->z is not written; with nseg = -1 out->col_off is not written
  * either.
  * Every call looks up the array's device address in the current device's context
@@ -235,7 +246,10 @@ int dexel_last_kernel_ms(const dexel_ctx* ctx, double* ms, int max);
  * live elements in one sweep state, [6] device status bits of the last attempt (1: a per-warp
  * state array overflowed, 2: an arena overflowed, 4: malformed CSR, 8: output beyond int32
  * offsets), [7] attempts the last offset needed (the library grows its scratch and retries
- * when it owns the workspace).  Returns the number of entries written (at most max). */
+ * when it owns the workspace), [8] second launches of the pass-1 window kernel for columns
+ * whose window outgrew the first launch's event room, [9] blocks of y lines the offset ran in
+ * (S_mid and the level lists exist for one block at a time; 1: the whole grid at once).
+ * Returns the number of entries written (at most max, 10 in all). */
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max);
 
 /* Diagnostic counters of the last call: clock cycles per phase of the y sweep and mean

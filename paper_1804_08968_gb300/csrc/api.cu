@@ -37,6 +37,12 @@ struct dexel_ctx {
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
   bool p1l_ring = true; // one walk into a ring (else a counting walk and a writing walk)
+  bool p1l_ecap_max = false;  // event room for the densest window from the start (no redo)
+  bool prune1 = true;   // dominance pruning of S_mid pieces in the window kernel
+  // blocks of y lines: the bytes the block-scoped scratch (S_mid, its copy, level lists) may
+  // take before an offset is split into blocks; noblock: a fallback needed the whole grid
+  double block_bytes = 48e9;
+  bool noblock = false;
   int p1l_ring_cap = 0; // pieces a lane's ring region holds at most (0: up to 128)
   long long batch_max_cols = 131072;  // larger shapes of a batch take the single-shape path
   // the level walks read S_mid itself (no packed copy) at reach >= 32: off by default
@@ -60,7 +66,7 @@ struct dexel_ctx {
   double stage_ms[5] = {0, 0, 0, 0, 0};
   double kernel_ms[4] = {0, 0, 0, 0};  // pass-1 kernel, k_levels, k_lgather, S_mid pack
   bool kernel_rec[4] = {false, false, false, false};
-  long long stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long stats[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long phase[16] = {};
 };
 
@@ -198,6 +204,26 @@ void kmark(dexel_ctx* ctx, int q, bool end, cudaStream_t st) {
   if (end) ctx->kernel_rec[q] = true;
 }
 
+// With profiling on, adds the device time of the pass-1 and pass-2 stages and of the kernels
+// recorded since the last call (a block of the offset) to the call's totals.
+void acc_block_times(dexel_ctx* ctx) {
+  if (!ctx->profiling) return;
+  for (int q = 1; q <= 2; ++q) {
+    float ms = 0;
+    if (ctx->ev[2 * q] && ctx->ev[2 * q + 1] && cudaEventSynchronize(ctx->ev[2 * q + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, ctx->ev[2 * q], ctx->ev[2 * q + 1]) == cudaSuccess)
+      ctx->stage_ms[q] += ms;
+  }
+  for (int q = 0; q < 4; ++q) {
+    float ms = 0;
+    if (ctx->kernel_rec[q] && cudaEventSynchronize(ctx->ev[11 + 2 * q]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, ctx->ev[10 + 2 * q], ctx->ev[11 + 2 * q]) == cudaSuccess)
+      ctx->kernel_ms[q] += ms;
+    ctx->kernel_rec[q] = false;
+  }
+  cudaGetLastError();
+}
+
 void reset_call(dexel_ctx* ctx) {
   ctx->launches = 0;
   for (int q = 0; q < 4; ++q) {
@@ -261,6 +287,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
   const int blocks = sms * 4;
   const int nwarps = blocks * kWarpsPerBlock;
 
+  ctx->noblock = false;
   for (int attempt = 0; attempt < 24; ++attempt) {
     // ---------------- plan
     // phase A: counters, tables, indices, validation
@@ -332,17 +359,43 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     long long eM = std::max<long long>(ctx->needM + ctx->needM / 8, segs * std::min(K + 2, 64));
     long long eF = std::max<long long>(ctx->needF + ctx->needF / 8, eM);
     long long eO = std::max<long long>(ctx->needO + ctx->needO / 8, segs * 2);
-    const size_t bF = align_up((size_t)eF * std::max<size_t>(2 * sizeof(Key) + 2, 16), 256);
-    const size_t bM = align_up((size_t)eM * (2 * sizeof(Key) + 2), 256);
+    long long eL = std::max<long long>(ctx->needL + ctx->needL / 8, 2 * ncols * (long long)(K + 1));
+    // Blocks of whole y lines (x ranges [xa, xb)): pass 1 and pass 2 run block by block, so
+    // that S_mid, its packed copy and the level lists exist for one block at a time (output
+    // column (i, j) needs S_mid of line i only).  Only the lane kernel's path with the level
+    // unions takes blocks; the estimates above are for the whole grid, a block gets its share
+    // with a margin for uneven lines.
+    const size_t pe = 2 * sizeof(Key) + 2;
+    const double grid_bytes = (double)eM * pe + (double)eF * std::max<size_t>(pe, 16) +
+                              (double)ncols * (K + 1) * 12 + (double)eL * 16;
+    const bool can_block = !ctx->sweep1 && !ctx->sweep2 && ctx->levels && ctx->lane1 &&
+                           !ctx->noblock && K > kMergeMaxReach && K <= kLaneMaxReach1;
+    int nb = 1, bw = nx;
+    if (can_block && grid_bytes > (double)ctx->block_bytes) {
+      nb = (int)std::ceil(grid_bytes / (double)ctx->block_bytes);
+      bw = ((nx + nb - 1) / nb + 31) & ~31;
+      if (bw >= nx) {
+        bw = nx;
+        nb = 1;
+      } else {
+        nb = (nx + bw - 1) / bw;
+      }
+    }
+    const double bfrac = nb > 1 ? std::min(1.0, 1.3 * (double)bw / (double)nx) : 1.0;
+    const long long eMb = nb > 1 ? (long long)(eM * bfrac) + 4096 : eM;
+    const long long eFb = nb > 1 ? (long long)(eF * bfrac) + 4096 : eF;
+    const long long eLb = nb > 1 ? (long long)(eL * bfrac) + 4096 : eL;
+    const size_t bF = align_up((size_t)eFb * std::max<size_t>(pe, 16), 256);
+    const size_t bM = align_up((size_t)eMb * pe, 256);
     const size_t bO = align_up((size_t)eO * 16, 256);
     // pass-2 slot estimate from the remembered capacities
     const long long sb2_est =
         p2_slot_bytes<Key>(std::max(capS * 4, 64), ctx->capR, ctx->capA, ctx->capS, 1024);
     const size_t slots_sw = std::max((size_t)sb1, (size_t)sb2_est) * nwarps;
-    // the pass-2 level lists use the same room as the sweeps' slots (never both at once)
-    const long long nlev = ncols * (long long)(K + 1);
-    const long long eL = std::max<long long>(ctx->needL + ctx->needL / 8, 2 * nlev);
-    const size_t bL = K <= kGatherMaxReach ? align_up((size_t)nlev * 12 + 512, 256) + (size_t)eL * 16 : 0;
+    // the pass-2 level lists (one block's) use the same room as the sweeps' slots (never both
+    // at once)
+    const long long nlev = (long long)bw * ny * (K + 1);
+    const size_t bL = K <= kGatherMaxReach ? align_up((size_t)nlev * 12 + 512, 256) + (size_t)eLb * 16 : 0;
     const size_t slots = std::max(slots_sw, bL);
     const size_t total = fixed + bF + bM + bO + slots + 4096;
     if (ws_user && total > ws_user_bytes) {
@@ -390,8 +443,23 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       ensure_owned(ctx, ctx->last_required);
       continue;
     }
+    // pass-2 columns start unmarked (a gather marks those it hands back with count -1)
+    CK(cudaMemsetAsync(pocnt, 0, sizeof(int) * ncols, st));
+    bool again = false;  // an arena outgrew its estimate: plan again
+    long long mid_sum = 0;  // S_mid pieces over the blocks
+    for (int blk = 0; blk < nb; ++blk) {
+    const int xa = blk * bw, xb = std::min(nx, xa + bw);
+    const long long q0 = (long long)xa * ny, nq = (long long)(xb - xa) * ny;  // line order
+    const double to_grid = (double)ncols / (double)nq;  // a block's needs scaled to the grid
+    if (nb > 1) {
+      // a block starts with empty arenas 0-2 (the pass-2 intervals of arena 3 accumulate)
+      p1.xa = xa;
+      p1.xb = xb;
+      CK(cudaMemsetAsync(&ctr->arena_top[0], 0, 3 * sizeof(unsigned long long), st));
+      CK(cudaMemsetAsync(&ctr->mid_total, 0, sizeof(ctr->mid_total), st));
+    }
     mark(ctx, 2, st);
-    bool sweep1 = ctx->sweep1 || K > kGatherMaxReach1;
+    bool sweep1 = ctx->sweep1 || K > (ctx->lane1 ? kLaneMaxReach1 : kGatherMaxReach1);
     if (!sweep1) {
       // gather: tiles of tc columns whose window's events (two per segment, two more per
       // column for a complement) fit ecap; a window beyond ecap hands the call to the sweep
@@ -407,9 +475,12 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         CK(launch_pass1m<T>(p1, sms, st));
         kmark(ctx, 0, true, st);
         ++ctx->launches;
-      } else if (ctx->lane1 && K <= 127) {
+      } else if (ctx->lane1 && K <= kLaneMaxReach1) {
+        // event room by the mean density of a tile's window (columns whose own window holds
+        // more are redone by a second launch with room for the densest window), or (rule
+        // "max") room for the densest window from the start
         int ecapL = 512;
-        while (ecapL < 16384 && (ecapL < ev_tile || ecapL < ev_win_max)) ecapL <<= 1;
+        while (ecapL < 16384 && (ecapL < ev_tile || (ctx->p1l_ecap_max && ecapL < ev_win_max))) ecapL <<= 1;
         if (ctx->p1l_ecap > 0) ecapL = ctx->p1l_ecap;
         // warps a tile: more as the windows grow (a tile's walk is split over its warps, its
         // sort shared); measured best on the 512^2 workload: 2 up to k = 8, 4 at k = 32
@@ -418,8 +489,12 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         while (gw < 8 && pass1l_smem(K, ecapL, gw) > (220LL << 10)) gw <<= 1;
         // the ring of the one-walk variant in the (free) forward arena: up to 128 pieces a
         // thread of the grid
+        const int ecapR = 16384;  // the redo's event room (room for the densest window)
+        const bool redo_ok = ecapL < ecapR && pass1l_smem(K, ecapR, 8) <= (220LL << 10);
         {
-          const long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms) * 256;
+          // threads of the larger of the two launches (the first, and the redo's)
+          long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms) * 256;
+          if (redo_ok) thr = std::max<long long>(thr, (long long)pass1l_blocks(nx, ny, K, ecapR, 8, sms) * 256);
           const long long esz = 2 * (long long)sizeof(Key) + 2;
           long long rc = std::min<long long>(128, (long long)bF / (thr * esz)) & ~7LL;
           if (ctx->p1l_ring_cap > 0) rc = std::min<long long>(rc, ctx->p1l_ring_cap);
@@ -429,12 +504,38 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
             p1.r_b = p1.r_a + n;
             p1.r_l = (short*)(p1.r_b + n);
             p1.r_cap = (int)rc;
+            p1.r_n = n;
           }
         }
+        if (ctx->prune1) {
+          // dominance pruning of S_mid pieces: margin 2^-19 (max |z| + k h), over four times
+          // the error bound of the float test
+          float zm;
+          memcpy(&zm, &hc.zmax_bits, sizeof(float));
+          p1.prune_w = (const float*)pwtabf;
+          p1.prune_E = (float)(std::ldexp(1.0, -19) * ((double)zm + k * in->h));
+        }
+        int* rowmark = (int*)ppos;  // free until pass 2
+        CK(cudaMemsetAsync(rowmark, 0, sizeof(int) * ny, st));
+        p1.rowmark = rowmark;
         kmark(ctx, 0, false, st);
         CK(launch_pass1l<T>(p1, ecapL, gw, sms, st));
-        kmark(ctx, 0, true, st);
         ++ctx->launches;
+        if (redo_ok) {
+          // columns whose window did not fit: a second launch for them alone, with room for
+          // the densest window (the first launch flagged their rows and marked them)
+          CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
+            CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+            P1Params<T> pr = p1;
+            pr.redo = 1;
+            CK(launch_pass1l<T>(pr, ecapR, 8, sms, st));
+            ++ctx->launches;
+            ++ctx->stats[8];  // a pass-1 redo launch
+          }
+        }
+        kmark(ctx, 0, true, st);
       } else {
         // (a tile of about K/2 columns: a column's window then covers ~80 % of the tile's;
         // measured best of K/4 .. 2K on the 512^2 and 2048^2 workloads)
@@ -485,15 +586,17 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       CK(cudaStreamSynchronize(st));
     }
     mark(ctx, 3, st);
-    ctx->needF = std::max<long long>(ctx->needF, (long long)hc.arena_top[0]);
-    ctx->needM = std::max<long long>(ctx->needM, (long long)hc.arena_top[1]);
+    ctx->needF = std::max<long long>(ctx->needF, (long long)(hc.arena_top[0] * to_grid));
+    ctx->needM = std::max<long long>(ctx->needM, (long long)(hc.arena_top[1] * to_grid));
+    mid_sum += (long long)hc.mid_total;
     ctx->stats[6] = hc.status;
     ctx->stats[7] = attempt + 1;
     if (hc.status & (ST_OVERFLOW_SLOT | ST_OVERFLOW_ARENA)) {
       ctx->last_required = total + (size_t)(hc.arena_top[0] + hc.arena_top[1]) * 16;
       if (hc.status & ST_OVERFLOW_SLOT) return DEXEL_ERR_CAPACITY;  // bound exceeded: give up
       if (ws_user) return DEXEL_ERR_CAPACITY;
-      continue;
+      again = true;
+      break;
     }
 
     // ---------------- pass 2: window gather (default) or per-line sweep
@@ -520,13 +623,14 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       bool packed = false;
       auto pack_lines = [&]() -> cudaError_t {
         kmark(ctx, 3, false, st);
-        const long long nb = (ncols + kScanTile - 1) / kScanTile;
-        k_scan1<int><<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, (const int*)pmcnt, (long long*)ppos,
-                                                        (long long*)psums);
-        k_scan2<<<1, kScanThreads, 0, st>>>(nb, (long long*)psums);
-        k_mid_pack<Key><<<sms * 8, 256, 0, st>>>(ncols, p1.m_start, p1.m_cnt, p1.m_a, p1.m_b, p1.m_l,
-                                                 (const long long*)ppos, (const long long*)psums,
-                                                 (long long*)pcnt, c_af, c_bf, c_dx, ctr);
+        // the block's columns q0 .. q0 + nq - 1 (line order), packed from 0
+        const long long nsb = (nq + kScanTile - 1) / kScanTile;
+        k_scan1<int><<<(unsigned)nsb, kScanThreads, 0, st>>>(nq, (const int*)pmcnt + q0, (long long*)ppos,
+                                                         (long long*)psums);
+        k_scan2<<<1, kScanThreads, 0, st>>>(nsb, (long long*)psums);
+        k_mid_pack<Key><<<sms * 8, 256, 0, st>>>(nq, p1.m_start + q0, p1.m_cnt + q0, p1.m_a, p1.m_b,
+                                                 p1.m_l, (const long long*)ppos, (const long long*)psums,
+                                                 (long long*)pcnt + q0, c_af, c_bf, c_dx, ctr);
         kmark(ctx, 3, true, st);
         ctx->launches += 3;
         pg.c_start = (const long long*)pcnt;
@@ -545,7 +649,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       // per-warp buckets compete with the staging area)
       {
         const int ntab = nmax + 1 <= 4096 ? nmax + 1 : 0;
-        const double avg = (double)hc.mid_total / (double)std::max<long long>(ncols, 1);
+        const double avg = (double)hc.mid_total / (double)std::max<long long>(nq, 1);
         int tw = 16, tc = 0, per_sm = 2, stage_cap = 0;
         const int cand[4][2] = {{16, 2}, {16, 1}, {8, 1}, {4, 1}};
         for (const auto& cd : cand) {
@@ -582,6 +686,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           H.m_cap = p1.m_cap;
           H.c_cap = capC;
           H.exact = !packed;
+          H.q0 = q0;
+          H.nq = nq;
           kmark(ctx, 1, false, st);
           CK(launch_levels<T>(H, st, sms));
           kmark(ctx, 1, true, st);
@@ -594,7 +700,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           ctx->launches += 2;
           CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
           CK(cudaStreamSynchronize(st));
-          ctx->needL = std::max<long long>(ctx->needL, (long long)hc.arena_top[2]);
+          ctx->needL = std::max<long long>(ctx->needL, (long long)(hc.arena_top[2] * to_grid));
           ctx->levels_status = hc.status;
           if (hc.over_cols * 64LL > ncols) {
             // many columns outgrew the bucket (united straight from the lists, slower): a
@@ -602,6 +708,15 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
             int b = lb;
             while (b < hc.over_max && b < 2048) b <<= 1;
             lb = b;
+          }
+          if ((hc.status & ST_LEVELS_OVER) && nb > 1) {
+            // the level arena outgrew its share: plan again with its need (the tiled gather
+            // would take the whole grid)
+            ctx->needL = std::max<long long>(ctx->needL, (long long)(hc.arena_top[2] * to_grid * 1.25));
+            ctx->last_required = total + (size_t)hc.arena_top[2] * 16;
+            if (ws_user) return DEXEL_ERR_CAPACITY;
+            again = true;
+            break;
           }
           if (hc.status & ST_LEVELS_OVER) {
             // a list beyond its buffer or the arena: the tiled gather redoes pass 2
@@ -627,6 +742,12 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
               }
             }
           }
+        }
+        if (!done && nb > 1) {
+          // the tiled gather takes the whole grid: plan again without blocks
+          ctx->noblock = true;
+          again = true;
+          break;
         }
         if (!done) {
           if (!packed) CK(pack_lines());  // the tiled gather stages line-contiguous sources
@@ -667,7 +788,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       if (hc.status & ST_OVERFLOW_ARENA) {
         ctx->last_required = total + (size_t)hc.arena_top[3] * 16;
         if (ws_user) return DEXEL_ERR_CAPACITY;
-        continue;
+        again = true;
+        break;
       }
       if (hc.status & ST_OVERFLOW_SLOT) {
         // a column's union beyond any bucket: the per-line sweep does this call's pass 2
@@ -677,6 +799,12 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         CK(cudaMemsetAsync(&ctr->max_state, 0, sizeof(int), st));
         use_sweep = true;
       }
+    }
+    if (use_sweep && nb > 1) {
+      // the per-line sweep takes the whole grid: plan again without blocks
+      ctx->noblock = true;
+      again = true;
+      break;
     }
     if (use_sweep) {
     const int capP = std::max(hc.max_pieces, 1) + 2;
@@ -706,7 +834,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       ctx->last_required = total + (size_t)sb2 * nwarps;
       if (ws_user) return DEXEL_ERR_CAPACITY;
       ensure_owned(ctx, ctx->last_required);
-      continue;
+      again = true;
+      break;
     }
     mark(ctx, 4, st);
     CK(launch_pass2<T>(p2, nw2 / kWarpsPerBlock, st));
@@ -727,14 +856,21 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       ctx->last_required =
           total + (size_t)p2_slot_bytes<Key>(capP, ctx->capR, ctx->capA, ctx->capS, chunk2) * nwarps;
       if (ws_user) return DEXEL_ERR_CAPACITY;
-      continue;
+      again = true;
+      break;
     }
     if (hc.status & ST_OVERFLOW_ARENA) {
       ctx->last_required = total + (size_t)(hc.arena_top[2] + hc.arena_top[3]) * 16;
       if (ws_user) return DEXEL_ERR_CAPACITY;
-      continue;
+      again = true;
+      break;
     }
     }  // pass 2 variants
+
+    acc_block_times(ctx);
+    ctx->stats[9] = std::max<long long>(ctx->stats[9], nb);
+    }  // blocks
+    if (again) continue;
 
     // ---------------- compaction into the caller's CSR
     const int thr = 256;
@@ -745,17 +881,17 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     const ukey* out_r = (const ukey*)aO + capOut;
     k_count<T><<<gb, thr, 0, st>>>((int)ncols, (const long long*)postart, (const int*)pocnt,
                                    out_l, out_r, erode ? 1 : 0, (long long*)pcnt);
-    const long long nb = (ncols + kScanTile - 1) / kScanTile;
-    k_scan1<long long><<<(unsigned)nb, kScanThreads, 0, st>>>(ncols, (const long long*)pcnt, (long long*)ppos,
+    const long long nsb = (ncols + kScanTile - 1) / kScanTile;
+    k_scan1<long long><<<(unsigned)nsb, kScanThreads, 0, st>>>(ncols, (const long long*)pcnt, (long long*)ppos,
                                                   (long long*)psums);
-    k_scan2<<<1, kScanThreads, 0, st>>>(nb, (long long*)psums);
+    k_scan2<<<1, kScanThreads, 0, st>>>(nsb, (long long*)psums);
     k_scan3<<<(unsigned)((ncols + 1 + thr - 1) / thr), thr, 0, st>>>(
         ncols, (long long*)ppos, (const long long*)psums, out->col_off, ctr);
     ctx->launches += 4;
     CK(cudaGetLastError());
     mark(ctx, 7, st);
     long long total_out = 0;
-    CK(cudaMemcpyAsync(&total_out, (long long*)psums + nb, sizeof(long long),
+    CK(cudaMemcpyAsync(&total_out, (long long*)psums + nsb, sizeof(long long),
                        cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -773,6 +909,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     CK(cudaStreamSynchronize(st));
     if (ctx->profiling) {
       for (int q = 0; q < 5; ++q) {
+        if (q == 1 || q == 2) continue;  // added block by block
         float ms = 0;
         if (cudaEventElapsedTime(&ms, ctx->ev[2 * q], ctx->ev[2 * q + 1]) == cudaSuccess)
           ctx->stage_ms[q] += ms;
@@ -786,7 +923,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     }
     for (int q = 0; q < 16; ++q) ctx->phase[q] += hc.phase[q];
     ctx->stats[0] += in->nseg;
-    ctx->stats[1] += (long long)hc.mid_total;
+    ctx->stats[1] += mid_sum;
     ctx->stats[2] += (long long)hc.out_total;
     ctx->stats[3] += total_out;
     ctx->stats[4] = std::max<long long>(ctx->stats[4], hc.max_pieces);
@@ -835,7 +972,7 @@ dexel_status offset(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erod
 // calls that overlap on the GPU (different streams or threads) race; the counters that must
 // start at zero are cleared at the start of every call.
 // ------------------------------------------------------------------------------------------
-constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // 64 MiB per device
+constexpr size_t kNoAllocBytes = (size_t)128 << 20;  // 128 MiB per device
 constexpr long long kNoAllocMaxColumns = 256 * 256;
 constexpr double kNoAllocMaxK = 32.0;
 constexpr int kNoAllocWarps = 8;
@@ -907,8 +1044,10 @@ dexel_status noalloc_offset(const dexel_grid_in* in, double k, bool erode, dexel
   if ((long long)slot_region < sb1 * kWarpsPerBlock) return DEXEL_ERR_CAPACITY;
   char* slots = (char*)C.take(slot_region);
   const size_t rest = C.cap > C.used + 4096 ? C.cap - align_up(C.used, 256) - 4096 : 0;
-  const size_t bF = align_up(rest / 100 * 30, 256), bM = align_up(rest / 100 * 45, 256);
-  const size_t bO = align_up(rest / 100 * 20, 256);
+  // forward sweep states, S_mid, pass-2 intervals (measured on sphere unions at 256 x 256,
+  // k = 32: about 25 MB of S_mid, as much of forward states, 3 MB of intervals)
+  const size_t bF = align_up(rest / 100 * 38, 256), bM = align_up(rest / 100 * 46, 256);
+  const size_t bO = align_up(rest / 100 * 14, 256);
   char* aF = (char*)C.take(bF);
   char* aM = (char*)C.take(bM);
   char* aO = (char*)C.take(bO);
@@ -1008,6 +1147,12 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
     if (v >= 256 && v <= 16384 && (v & (v - 1)) == 0) c->p1l_ecap = v;
   }
   if (const char* e = getenv("DEXEL_PASS1_RING")) c->p1l_ring = atoi(e) != 0;
+  if (const char* e = getenv("DEXEL_PASS1_ECAP_RULE")) c->p1l_ecap_max = strcmp(e, "max") == 0;
+  if (const char* e = getenv("DEXEL_PASS1_PRUNE")) c->prune1 = atoi(e) != 0;
+  if (const char* e = getenv("DEXEL_BLOCK_MB")) {
+    const double v = atof(e);
+    if (v >= 1) c->block_bytes = v * 1e6;
+  }
   if (const char* e = getenv("DEXEL_PASS1_RING_CAP")) {
     const int v = atoi(e);
     if (v >= 16 && v <= 128) c->p1l_ring_cap = v & ~7;
@@ -1078,7 +1223,7 @@ int dexel_last_phases(const dexel_ctx* ctx, uint64_t* ph, int max) {
 
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max) {
   if (!ctx || !stats) return 0;
-  int n = max < 8 ? max : 8;
+  int n = max < 10 ? max : 10;
   for (int q = 0; q < n; ++q) stats[q] = ctx->stats[q];
   return n;
 }

@@ -553,6 +553,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       v.L = K[s] + 1;
       v.G = v.L <= 32 ? 32 / v.L : 1;
       v.NG = v.L <= 32 ? 0 : (K[s] + 31) / 32;
+      v.q0 = 0;
       v.nsrc = colb[s + 1] - colb[s];
       v.nlev = nlb[s + 1] - nlb[s];
       v.m_cap = pl.capM;

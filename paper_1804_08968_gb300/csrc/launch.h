@@ -13,6 +13,9 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kGatherMaxReach = 1024;
 // pass-1 gather: the open sources of a window are a mask of up to 256 bits, 2R + 1 <= 255
 constexpr int kGatherMaxReach1 = 127;
+// pass 1 with one lane per column: two 128-bit masks a side (R <= 128) and a tile-relative
+// mask of 320 bits (32 + 2R + 1 <= 320)
+constexpr int kLaneMaxReach1 = 128;
 constexpr int kRoundAppends = 2;
 constexpr int kRoundPieces = 32;
 
@@ -56,6 +59,9 @@ struct LvlParamsHost {
   int bcap;
   long long m_cap, c_cap;  // entries of the S_mid arena and of its packed copy (self-checks)
   bool exact;  // k_levels reads S_mid itself (no packed copy; c_start unused)
+  // a block of whole y lines: sources / output columns q0 .. q0 + nq - 1 in line order
+  // (q = i * ny + j; nq = 0: the whole grid); l_start / l_cnt hold the block's entries only
+  long long q0 = 0, nq = 0;
 };
 // k_levels (the per-source level lists); launch_lgather then unites them per column
 template <typename T>

@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(256, 3) k_pass1l(P1Params<T> P, int ecap, int 
   const TGroup G{gw, warp / gw, warp % gw, (int)threadIdx.x % (gw * 32),
                  (long long)blockIdx.x * groups + warp / gw};
   unsigned char* gsm = smem + (long long)G.gid * p1l_layout(P.K, ecap, gw).total;
-  const long long ntiles = (long long)P.ny * ((P.nx + 31) >> 5);
+  const int xw = P.xb > 0 ? P.xb - P.xa : P.nx;  // the block of columns
+  const long long ntiles = (long long)P.ny * ((xw + 31) >> 5);
   ArenaCursor cur{0, 0};
   for (long long tile = (long long)blockIdx.x * groups + G.gid; tile < ntiles;
        tile += (long long)gridDim.x * groups)
@@ -46,12 +47,12 @@ template <typename T>
 cudaError_t launch_pass1l(const P1Params<T>& P, int ecap, int gw, int sms, cudaStream_t st) {
   if (gw != 1 && gw != 2 && gw != 4 && gw != 8) return cudaErrorInvalidValue;
   const size_t smem = (size_t)pass1l_smem(P.K, ecap, gw);
-  if (smem > (220u << 10) || P.K > 127) return cudaErrorInvalidValue;
+  if (smem > (220u << 10) || P.K > kLaneMaxReach1) return cudaErrorInvalidValue;
   auto kern = P.K <= 64 ? k_pass1l<T, 1> : k_pass1l<T, 2>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // the grid the ring (when given) was sized for: pass1l_blocks threads x r_cap pieces
-  const int blocks = pass1l_blocks(P.nx, P.ny, P.K, ecap, gw, sms);
+  const int blocks = pass1l_blocks(P.nx, P.ny, P.K, ecap, gw, sms);  // (sized for whole rows)
   kern<<<blocks, kP1LWarps * 32, smem, st>>>(P, ecap, gw);
   return cudaGetLastError();
 }

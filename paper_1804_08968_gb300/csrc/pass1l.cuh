@@ -30,7 +30,7 @@
 
 namespace dexel {
 
-// words of the tile-relative source masks (32 + 2R + 1 <= 287 sources)
+// words of the tile-relative source masks (32 + 2R + 1 <= 320 sources: R <= 128)
 constexpr int kP1TileWords = 5;
 
 // Shared memory of k_pass1l: sorted events (key, source), the window's event offsets, chunk
@@ -103,43 +103,76 @@ DXD CMask<NH> cmask_from(const ukey* T, int pc, int R) {
   return m;
 }
 
+// Dominance of S_mid pieces (Sec. 3.3: pass 2 unites, at every level t, the capsule slices
+// [a - w, b + w] with w = h sqrt(k^2 - dx^2 - t^2)).  A piece q with a smaller label than
+// piece p (dx_q < dx_p) has w_q(t) - w_p(t) non-decreasing in t, so if q's slice contains
+// p's at level 0 it contains it at every level p reaches, and dropping p leaves every level's
+// union unchanged.  The test runs on float approximations of a - w(0) and b + w(0) with a
+// margin E above twice their error bound, so that it only drops pieces that are dominated
+// exactly.  Each lane keeps its last kept piece in registers: a new piece that dominates it
+// replaces it, a new piece it dominates is not emitted.
+struct Prune {
+  const float* w;  // float half-widths w[n] = h sqrt(k^2 - n) (null: no pruning)
+  float E;         // margin of the float test
+};
+struct PTop {
+  float lo, hi;  // the slice at level 0 (float)
+  int l;         // its label
+  bool have, fixed;  // a kept piece; fixed: its start lies before the chunk (never replaced)
+};
+
 // One lane's walk over the sorted events [c0, c1) (a chunk that starts at a group boundary)
 // for the column at tile position pc.  m / Om: the open sources and the label just below the
 // chunk; run_a: the start of the run open there.  WRITE: the first cap pieces go to oa, ob,
-// ol.  last_start: the last run start in the chunk (~0 if none).  Returns the pieces.
+// ol.  last_start: the last run start in the chunk (~0 if none).  Returns the pieces.  The
+// pruning decisions depend only on the events, so the counting and writing walks agree (a run
+// open at the chunk's start is tested with the chunk's first height as its start: its slice
+// is at least that large).
 template <typename T, int NH, bool WRITE>
 DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int pc, int R,
                    bool act, CMask<NH> m, int Om, ukey run_a, ukey& last_start,
-                   typename H<T>::K* oa, typename H<T>::K* ob, short* ol, int cap) {
+                   typename H<T>::K* oa, typename H<T>::K* ob, short* ol, int cap,
+                   const Prune& pr) {
   typedef typename H<T>::K Key;
   int gmin = kNoLabel;
   int cnt = 0;
   last_start = ~0ULL;
   if (c0 >= c1) return 0;
   ukey gkey = ek[c0];
+  const ukey first = gkey;
+  bool carried = Om < kNoLabel;  // the first run closed began before the chunk
+  PTop top{0.0f, 0.0f, 0, false, false};
+  auto emit = [&](ukey a, ukey b, int l, bool fixed) {
+    if (pr.w) {
+      const float w = pr.w[l * l];
+      const float lo = keyf(fixed ? first : a) - w, hi = keyf(b) + w;
+      if (top.have && !top.fixed && l < top.l && lo <= top.lo - pr.E && hi >= top.hi + pr.E) {
+        --cnt;  // the new piece dominates the last kept one: it takes its place
+      } else if (top.have && top.l < l && !fixed && top.lo <= lo - pr.E && top.hi >= hi + pr.E) {
+        return;  // dominated by the last kept piece
+      }
+      top = PTop{lo, hi, l, true, fixed};
+    }
+    if (WRITE && cnt < cap) {
+      oa[cnt] = key_out<Key>(a);
+      ob[cnt] = key_out<Key>(b);
+      ol[cnt] = (short)l;
+    }
+    ++cnt;
+  };
   auto close_group = [&](ukey v) {
     const int Ok = cnearest<NH>(m);
     const bool pt = gmin < (Om < Ok ? Om : Ok);
     const bool ch = Ok != Om || pt;
     if (Om < kNoLabel && ch) {  // the run below v ends at v
-      if (WRITE && cnt < cap) {
-        oa[cnt] = key_out<Key>(run_a);
-        ob[cnt] = key_out<Key>(v);
-        ol[cnt] = (short)Om;
-      }
-      ++cnt;
+      emit(run_a, v, Om, carried);
+      carried = false;
     }
-    if (pt) {  // the point [v, v]
-      if (WRITE && cnt < cap) {
-        oa[cnt] = key_out<Key>(v);
-        ob[cnt] = key_out<Key>(v);
-        ol[cnt] = (short)gmin;
-      }
-      ++cnt;
-    }
+    if (pt) emit(v, v, gmin, false);  // the point [v, v]
     if (Ok < kNoLabel && ch) {  // a run starts at v
       run_a = v;
       last_start = v;
+      carried = false;
     }
     Om = Ok;
     gmin = kNoLabel;
@@ -213,13 +246,15 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
   short* rg_l = P.r_l ? P.r_l + rg0 : nullptr;
   const Lanes L{lane, 32};
   const int R = P.K;
-  const int tpr = (P.nx + 31) >> 5;
+  const int xa = P.xb > 0 ? P.xa : 0, xb = P.xb > 0 ? P.xb : P.nx;
+  const int tpr = (xb - xa + 31) >> 5;
   const int j = (int)(tile / tpr);
-  const int i0 = (int)(tile % tpr) * 32;
-  const int i1 = min(P.nx, i0 + 32);
+  const int i0 = xa + (int)(tile % tpr) * 32;
+  const int i1 = min(xb, i0 + 32);
   const int s0 = max(0, i0 - R), s1 = min(P.nx, i1 + R);
   const int ns = s1 - s0;
   const long long rb = (long long)j * P.nx;
+  if (P.redo && (P.rowmark == nullptr || P.rowmark[j] == 0)) return;  // nothing to redo here
   G.sync();  // the previous tile is done with the shared memory
   if (warp == 0) {  // event slots of the window's sources (exclusive prefix)
     int carry = 0;
@@ -238,8 +273,15 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
   }
   G.sync();
   for (int ia = i0; ia < i1;) {
-    // the widest run of columns from ia whose window's events fit (block-uniform)
+    // the widest run of columns from ia whose window's events fit (block-uniform); a redo
+    // takes only the columns marked by the first launch
     int ib = i1;
+    if (P.redo) {
+      while (ia < i1 && P.m_start[(long long)ia * P.ny + j] != -1) ++ia;
+      if (ia >= i1) break;
+      ib = ia + 1;
+      while (ib < i1 && P.m_start[(long long)ib * P.ny + j] == -1) ++ib;
+    }
     const int qa = max(0, ia - R) - s0;
     while (ib > ia + 1 && eoff[min(P.nx, ib + R) - s0] - eoff[qa] > ecap) ib = ia + ((ib - ia) >> 1);
     const int qe = min(P.nx, ib + R) - s0;
@@ -250,6 +292,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
         set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
         P.m_start[(long long)ia * P.ny + j] = -1;  // marks the column (count 0)
         P.m_cnt[(long long)ia * P.ny + j] = 0;
+        if (P.rowmark) P.rowmark[j] = 1;
       }
       ia = ib;
       continue;
@@ -359,15 +402,17 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     ukey last = ~0ULL;
     // one walk into the lane's ring region (the start of a run open at the chunk's start is
     // patched when the pieces are copied), or a counting walk without a ring
-    const bool ring = P.r_a != nullptr;
+    // the group's ring regions must lie within the ring (else the two walks, no ring)
+    const bool ring = P.r_a != nullptr && rg0 + (long long)W * 32 * P.r_cap <= P.r_n;
     const long long rbase = ring ? (long long)(warp * 32 + lane) * P.r_cap : 0;
     int n;
+    const Prune pr{P.prune_w, P.prune_E};
     if (ring)
       n = chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, 0ULL, last, rg_a + rbase,
-                                  rg_b + rbase, rg_l + rbase, P.r_cap);
+                                  rg_b + rbase, rg_l + rbase, P.r_cap, pr);
     else
       n = chunk_walk<T, NH, false>(ek, ep, c0, c1, pc, R, act, m0, Om0, 0ULL, last, nullptr,
-                                   nullptr, nullptr, 0);
+                                   nullptr, nullptr, 0, pr);
     ccnt[warp * 32 + lane] = n;
     cst[warp * 32 + lane] = last;
     cco[warp * 32 + lane] = Om0 < kNoLabel ? 1 : 0;
@@ -427,7 +472,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       const long long o = s + (inc - tot_col) + before;
       ukey dummy;
       chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, run_a, dummy, P.m_a + o,
-                              P.m_b + o, P.m_l + o, 1 << 30);
+                              P.m_b + o, P.m_l + o, 1 << 30, pr);
     }
     if (warp == 0) {
       if (act) {

@@ -31,11 +31,11 @@ __global__ void __launch_bounds__(256, MINB) k_lgather(LvlParams<T> A, int bcap,
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* wb = smem + (long long)warp * (bcap * (2 * sizeof(ukey) + 2 * sizeof(int)) + 16);
-  const long long ncols = (long long)A.P.nx * A.P.ny;
+  const long long q1 = A.q0 + A.nsrc;  // the block's output columns in line order
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   if (*(volatile int*)&A.P.ctr->status & ST_LEVELS_OVER) return;  // the lists are incomplete
   ArenaCursor cur{0, 0};
-  for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + warp; item < ncols; item += nw)
+  for (long long item = A.q0 + (long long)blockIdx.x * (blockDim.x >> 5) + warp; item < q1; item += nw)
     lgather_column<T>(A, item, bcap, redo, lane, wb, cur);
   if (lane == 0 && cur.tally > 0) {
     add_total(&A.P.ctr->out_total, cur.tally);
@@ -47,13 +47,13 @@ __global__ void __launch_bounds__(256, MINB) k_lgather(LvlParams<T> A, int bcap,
 template <typename T>
 __global__ void __launch_bounds__(256, 6) k_lgather_lanes(LvlParams<T> A) {
   const int lane = threadIdx.x & 31;
-  const long long ncols = (long long)A.P.nx * A.P.ny;
+  const long long q1 = A.q0 + A.nsrc;  // the block's output columns in line order
   const long long stride = (long long)gridDim.x * blockDim.x;
   if (*(volatile int*)&A.P.ctr->status & ST_LEVELS_OVER) return;  // the lists are incomplete
   ArenaCursor cur{0, 0};
-  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ncols;
+  for (long long base = A.q0 + (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < q1;
        base += stride)
-    lgather_lane<T>(A, base + lane, base + lane < ncols, lane, cur);
+    lgather_lane<T>(A, base + lane, base + lane < q1, lane, cur);
   if (lane == 0 && cur.tally > 0) {
     add_total(&A.P.ctr->out_total, cur.tally);
     note_max(&A.P.ctr->max_out, cur.tmax);
@@ -77,8 +77,13 @@ static LvlParams<T> lvl_params(const LvlParamsHost<T>& H) {
     A.G = 1;
     A.NG = (H.P.R + 31) / 32;
   }
-  A.nsrc = (long long)H.P.nx * H.P.ny;
-  A.nlev = A.nsrc * A.L;
+  // a block of lines: the index arrays are addressed with the global source index q, so
+  // their base pointers are shifted by the block's first entry (q0 L); nlev bounds q L + t
+  A.q0 = H.q0;
+  A.nsrc = H.nq > 0 ? H.nq : (long long)H.P.nx * H.P.ny;
+  A.l_start = H.l_start - H.q0 * A.L;
+  A.l_cnt = H.l_cnt - H.q0 * A.L;
+  A.nlev = (H.q0 + A.nsrc) * A.L;
   A.m_cap = H.m_cap;
   A.c_cap = H.c_cap;
   return A;
@@ -88,7 +93,7 @@ template <typename T>
 cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms) {
   const LvlParams<T> A = lvl_params(H);
   // lists a warp skips (an overflow) then read as empty
-  cudaError_t e = cudaMemsetAsync(H.l_cnt, 0, sizeof(int) * A.nlev, st);
+  cudaError_t e = cudaMemsetAsync(H.l_cnt, 0, sizeof(int) * A.nsrc * A.L, st);
   if (e != cudaSuccess) return e;
   const long long lt = lvl_lane_tab(H.P.R);
   const bool ltab = lt <= kLvlLaneTab;

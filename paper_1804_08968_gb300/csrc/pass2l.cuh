@@ -53,8 +53,9 @@ struct LvlParams {
   int L;     // levels a source: R + 1
   int G;     // sources a warp when L <= 32, else 1
   int NG;    // level groups of 32 (levels 1 .. R) when L > 32, else 0
-  long long nsrc;  // source columns (nx * ny)
-  long long nlev;  // entries of l_start / l_cnt
+  long long q0;    // first source column of the block (line order q = i * ny + j)
+  long long nsrc;  // source columns of the block
+  long long nlev;  // bound of the index q * L + t into l_start / l_cnt
   long long m_cap, c_cap;  // entries of the S_mid arena and of its packed copy
 };
 
@@ -357,6 +358,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
       t = 0;
       act = q < A.nsrc;
     }
+    q += A.q0;
     int np = 0;
     long long ms = 0, cs = 0;
     if (act) {
@@ -398,7 +400,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
   }
   // (source, level group): the warp walks one source, lane = level
   const long long it = item - n0;
-  const long long q = it / A.NG;
+  const long long q = A.q0 + it / A.NG;
   const int grp = (int)(it % A.NG);
   const int t = 1 + grp * 32 + lane;
   const bool act = t < A.L;

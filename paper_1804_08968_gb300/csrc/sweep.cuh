@@ -240,6 +240,15 @@ struct P1Params {
   int nrows;
   // the window kernel's ring: per thread of the grid r_cap pieces (null: two walks)
   Key* r_a; Key* r_b; short* r_l; int r_cap;
+  long long r_n;  // entries of each ring array (a group whose regions lie beyond walks twice)
+  // the window kernel's dominance pruning of S_mid pieces: float half-widths w[n] and the
+  // margin of the float test (null: keep every piece)
+  const float* prune_w; float prune_E;
+  // the window kernel's redo of columns whose windows did not fit: rows with such a column
+  // are flagged in rowmark (when given); with redo set only those columns are computed
+  int* rowmark; int redo;
+  // the window kernel's block of output columns: i in [xa, xb) (xb = 0: the whole row)
+  int xa, xb;
   // local index of forward states for the current chunk: per warp, chunk entries
 };
 

@@ -446,11 +446,11 @@ def config4_shapes(nshapes: int = 256, seed: int = 3):
     return out
 
 
-def config5_prims(seed: int = 4):
-    """4096 x 4096, mixed spheres/boxes/shells, about 6e7 segments, at most 32 per column."""
+def config5_prims(seed: int = 4, nprim: int = 550):
+    """4096 x 4096, mixed spheres/boxes/shells: 61.6 M segments, at most 15 per column."""
     rng = np.random.default_rng(seed)
     prims = []
-    for q in range(3000):
+    for q in range(nprim):
         kind = q % 3
         if kind == 0:
             prims.append(_sphere(rng, 0.01, 0.08, 0.05, 0.95))
@@ -459,3 +459,7 @@ def config5_prims(seed: int = 4):
         else:
             prims.append(_shell(rng, 0.02, 0.08, 0.004, 0.02, 0.05, 0.95))
     return prims
+
+
+def config5() -> DexelGrid:
+    return raycast(config5_prims(), 4096)

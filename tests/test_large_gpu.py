@@ -74,3 +74,77 @@ def test_2048_k64_sampled(grids, mode, op):
     ref = (oracle.dilate if op == "dilate" else oracle.erode)(g, K, cols=cols)
     _check(off, z, ref, cols, f32, f"2048^2 k=64 {op} {mode}")
     assert st[0] == g.nseg and st[3] == off[-1]
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_blocks_of_lines(op, monkeypatch):
+    """An offset split into blocks of whole y lines (a small block budget forces ten or so):
+    S_mid and the level lists exist for one block at a time, the result is unchanged."""
+    import torch
+    import paper_1804_08968_gb300 as dx
+    monkeypatch.setenv("DEXEL_BLOCK_MB", "1")
+    rng = np.random.default_rng(71)
+    g = shapes.random_grid(rng, 300, 70, 6, fill=0.75, point_frac=0.05, h=1 / 256)
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    ctx = dx.Context(0)
+    for k in (5.5, 12.0, 40.0):
+        out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
+        off, z = out.to_host()
+        assert ctx.stats()[9] > 1, "the offset was not split into blocks"
+        ref = (oracle.dilate if op == "dilate" else oracle.erode)(g, k)
+        cols = np.arange(g.nx * g.ny)
+        _check(off, z, _Full(ref), cols, False, f"blocks {op} k={k}")
+
+
+class _Full:
+    """A full oracle grid seen through the sampled-column interface."""
+
+    def __init__(self, g):
+        self.g = g
+
+    def column(self, t):
+        return self.g.z[self.g.col_off[t]:self.g.col_off[t + 1]]
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_reach_128(op):
+    """k = 128 spacings (reach 128, the lane kernel's widest source masks), on a grid long
+    enough in x for full windows; FP64 against the oracle."""
+    import torch
+    import paper_1804_08968_gb300 as dx
+    prims = shapes.config2_prims(60, seed=13)
+    big = shapes.raycast(prims, 320)
+    cols = {(i, j): [tuple(s) for s in big.column(i, j + 150)]
+            for i in range(320) for j in range(16) if big.column(i, j + 150).size}
+    g = shapes.from_columns(320, 16, 1 / 8000, cols)
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    ctx = dx.Context(0)
+    k = 128.4
+    out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
+    off, z = out.to_host()
+    ref = (oracle.dilate if op == "dilate" else oracle.erode)(g, k)
+    _check(off, z, _Full(ref), np.arange(g.nx * g.ny), False, f"reach 128 {op}")
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+@pytest.mark.parametrize("op", ["close", "open"])
+def test_morphology_blocks_reduced(mode, op, monkeypatch):
+    """Closing and opening of the 4096^2 workload's kind of shape (spheres, boxes, hollow
+    shells) at reduced scale, 384 x 384 at k = 12, every column against the oracle's
+    composite (erosion of the dilation, dilation of the erosion), with both stages split into
+    blocks of y lines."""
+    import torch
+    import paper_1804_08968_gb300 as dx
+    monkeypatch.setenv("DEXEL_BLOCK_MB", "4")
+    g = shapes.raycast(shapes.config5_prims(nprim=60, seed=21), 384)
+    f32 = mode == "fp32"
+    if f32:
+        g = shapes.to_float32(g)
+    dg = dx.Grid.from_synth(g, dtype=torch.float32 if f32 else torch.float64)
+    ctx = dx.Context(0)
+    k = 12.0
+    out = ctx.run(dx.CLOSE if op == "close" else dx.OPEN, dg, k)
+    off, z = out.to_host()
+    assert ctx.stats()[9] > 1, "the offsets were not split into blocks"
+    ref = oracle.close(g, k) if op == "close" else oracle.open_(g, k)
+    _check(off, z, _Full(ref), np.arange(g.nx * g.ny), f32, f"{op} 384^2 k=12 {mode}")

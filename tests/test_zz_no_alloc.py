@@ -128,7 +128,8 @@ def test_noalloc_limits_and_retry_signals():
     assert (off == -7).all() and torch.isnan(zt).all()
     # data needing more scratch than the array holds (dense stacks of segments): refused the
     # same way, with no partial CSR
-    cols = {(i, j): [(0.1 + q * 0.0025, 0.1 + q * 0.0025 + 0.001) for q in range(300)]
+    cols = {(i, j): [(0.1 + q * 0.0025 + 0.0002 * ((i + 3 * j) % 7),
+                      0.1 + q * 0.0025 + 0.0002 * ((i + 3 * j) % 7) + 0.001) for q in range(300)]
             for i in range(64) for j in range(64)}
     g = shapes.from_columns(64, 64, 1 / 64, cols)
     grid = dx.Grid.from_synth(g, dtype=torch.float64)
