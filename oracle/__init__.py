@@ -9,13 +9,19 @@ The arithmetic lives in ``oracle.c`` (plain brute-force gather, see its header):
                    of [a - w, b + w], w = h sqrt(k^2 - n)  (the Sec. 4 brute force, as a gather);
   * ``erode``   -- Sec. 3.1 "Erosion", written directly: intersection over c' of the union of
                    [a + w, b - w]; zero-length results dropped;
-  * ``close`` = erode(dilate(S)), ``open`` = dilate(erode(S))   (Sec. 4 "Topological Cleaning").
+  * ``close`` = erode(dilate(S)), ``open`` = dilate(erode(S))   (Sec. 4 "Topological Cleaning");
+  * ``union`` / ``intersection`` / ``difference`` -- CSG in dexel space (Sec. 2, "(3)"), from
+                   point membership of each column's elementary intervals, then the closure;
+  * ``shell`` = difference(dilate(S), erode(S))  (Sec. 4 "3D Printing", the teaser figure).
 ``complement`` builds the per-column complement with +-inf sentinels (Sec. 3.1: the complement
 is trivial in a ray representation); tests use it to check erosion/dilation duality.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` (closed forms
 with Pythagorean radii, point-membership brute force against the distance definition,
-duality, monotonicity, union commutation, extensivity, idempotence, k = 0 identity).
+duality, monotonicity, union commutation, extensivity, idempotence, k = 0 identity) and, for
+the Boolean operations and the shell, by ``tests/test_csg_oracle.py`` (closed forms of boxes
+and concentric spheres, additivity of length, set identities, point membership, the golden
+capsule, shell u erosion = dilation).
 """
 from __future__ import annotations
 
@@ -54,6 +60,11 @@ def _load():
                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
         lib.oracle_free.restype = None
         lib.oracle_free.argtypes = [ctypes.c_void_p]
+        lib.oracle_boolean.restype = ctypes.c_int64
+        lib.oracle_boolean.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
+                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
         _lib = lib
     return _lib
 
@@ -133,6 +144,50 @@ def close(grid, k: float, threads=None):
 def open_(grid, k: float, threads=None):
     """Opening = dilation of the erosion."""
     return dilate(erode(grid, k, threads=threads), k, threads=threads)
+
+
+def _boolean(op: int, a, b):
+    if (a.nx, a.ny) != (b.nx, b.ny):
+        raise ValueError("grids of different sizes")
+    lib = _load()
+    oa = np.ascontiguousarray(a.col_off, dtype=np.int64)
+    ob = np.ascontiguousarray(b.col_off, dtype=np.int64)
+    za = np.ascontiguousarray(a.z, dtype=np.float64).reshape(-1)
+    zb = np.ascontiguousarray(b.z, dtype=np.float64).reshape(-1)
+    za = za if za.size else np.zeros(2)
+    zb = zb if zb.size else np.zeros(2)
+    ncols = a.nx * a.ny
+    po = ctypes.POINTER(ctypes.c_int64)()
+    pz = ctypes.POINTER(ctypes.c_double)()
+    total = lib.oracle_boolean(op, ncols, oa.ctypes.data, za.ctypes.data, ob.ctypes.data,
+                               zb.ctypes.data, ctypes.byref(po), ctypes.byref(pz))
+    if total < 0:
+        raise ValueError("oracle_boolean rejected its arguments")
+    off = np.ctypeslib.as_array(po, shape=(ncols + 1,)).copy()
+    z = np.ctypeslib.as_array(pz, shape=(max(total, 1) * 2,))[: 2 * total].copy().reshape(-1, 2)
+    lib.oracle_free(ctypes.cast(po, ctypes.c_void_p))
+    lib.oracle_free(ctypes.cast(pz, ctypes.c_void_p))
+    return _as_grid(a, Columns(off, z, None))
+
+
+def union(a, b):
+    """Closed union of two grids, column by column (CSG in dexel space, Sec. 2)."""
+    return _boolean(0, a, b)
+
+
+def intersection(a, b):
+    """Closed intersection; zero-length results dropped."""
+    return _boolean(1, a, b)
+
+
+def difference(a, b):
+    """Closure of A minus B; zero-length results dropped."""
+    return _boolean(2, a, b)
+
+
+def shell(grid, k: float, threads=None):
+    """Thick shell: the dilation minus the erosion (Sec. 4 "3D Printing", teaser figure)."""
+    return difference(dilate(grid, k, threads=threads), erode(grid, k, threads=threads))
 
 
 def complement(grid):

@@ -269,3 +269,116 @@ int64_t oracle_offset(int32_t nx, int32_t ny, double h, double k, const int64_t*
 }
 
 void oracle_free(void* p) { free(p); }
+
+/*
+ * Boolean operations of two dexel grids of the same size (CSG in dexel space, Sec. 2 "(3)":
+ * carried out column by column on the rays; the thick shell of Sec. 4 "3D Printing" and the
+ * teaser figure is the difference of a dilation and an erosion).
+ *
+ * Written from point membership, one column at a time: the breakpoints of a column are the
+ * endpoints of both inputs, sorted; a breakpoint v is in A when some closed segment of A
+ * holds it, an open elementary interval (v_t, v_t+1) is in A when its midpoint is.  The
+ * result's membership is op(in A, in B) on the elementary intervals: A or B (union), A and
+ * B (intersection), A and not B (difference).  The result is the closure of those open
+ * intervals, consecutive ones joined; for the union a breakpoint held by A or B that joins no
+ * interval is kept as a zero-length segment (a tangent sample); intersection and difference
+ * keep no zero-length results (measure zero, as for erosion).
+ *   op: 0 union, 1 intersection, 2 difference.
+ */
+static int in_column(const double* z, int64_t s0, int64_t s1, double x) {
+  for (int64_t s = s0; s < s1; ++s)
+    if (z[2 * s] <= x && x <= z[2 * s + 1]) return 1;
+  return 0;
+}
+
+static int cmp_double(const void* x, const void* y) {
+  const double a = *(const double*)x, b = *(const double*)y;
+  return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+static int bool_of(int op, int a, int b) {
+  if (op == 0) return a || b;
+  if (op == 1) return a && b;
+  return a && !b;
+}
+
+static int boolean_column(int op, const double* za, int64_t a0, int64_t a1, const double* zb,
+                          int64_t b0, int64_t b1, ivec* out) {
+  const int64_t m = 2 * ((a1 - a0) + (b1 - b0));
+  out->n = 0;
+  if (m == 0) return 0;
+  double* v = (double*)malloc((size_t)m * sizeof(double));
+  if (!v) return -1;
+  int64_t n = 0;
+  for (int64_t s = a0; s < a1; ++s) { v[n++] = za[2 * s]; v[n++] = za[2 * s + 1]; }
+  for (int64_t s = b0; s < b1; ++s) { v[n++] = zb[2 * s]; v[n++] = zb[2 * s + 1]; }
+  qsort(v, (size_t)n, sizeof(double), cmp_double);
+  int64_t u = 0;  /* distinct breakpoints */
+  for (int64_t t = 0; t < n; ++t)
+    if (u == 0 || v[t] != v[u - 1]) v[u++] = v[t];
+  int open = 0;   /* a result interval is being built */
+  double start = 0;
+  for (int64_t t = 0; t < u; ++t) {
+    /* the elementary interval after breakpoint t (none after the last) */
+    int after = 0;
+    if (t + 1 < u) {
+      const double mid = 0.5 * (v[t] + v[t + 1]);
+      after = bool_of(op, in_column(za, a0, a1, mid), in_column(zb, b0, b1, mid));
+    }
+    if (open && !after) {  /* the interval ends at v[t] */
+      if (ivec_push(out, start, v[t])) { free(v); return -1; }
+      open = 0;
+    } else if (!open && after) {  /* an interval starts at v[t] */
+      start = v[t];
+      open = 1;
+    } else if (!open && !after && op == 0) {
+      /* a breakpoint that joins no interval: kept by the union when A or B holds it and the
+         interval before it was out too */
+      const int before = t > 0 && bool_of(op, in_column(za, a0, a1, 0.5 * (v[t - 1] + v[t])),
+                                          in_column(zb, b0, b1, 0.5 * (v[t - 1] + v[t])));
+      if (!before && bool_of(op, in_column(za, a0, a1, v[t]), in_column(zb, b0, b1, v[t])))
+        if (ivec_push(out, v[t], v[t])) { free(v); return -1; }
+    }
+  }
+  free(v);
+  return 0;
+}
+
+/* Boolean op of grids A and B (same nx*ny columns); result as for oracle_offset. */
+int64_t oracle_boolean(int op, int64_t ncols, const int64_t* off_a, const double* za,
+                       const int64_t* off_b, const double* zb, int64_t** out_off, double** out_z) {
+  if (op < 0 || op > 2 || ncols < 0 || !off_a || !off_b || !out_off || !out_z) return -1;
+  ivec* res = (ivec*)calloc((size_t)(ncols > 0 ? ncols : 1), sizeof(ivec));
+  if (!res) return -1;
+  int64_t total = 0;
+  for (int64_t c = 0; c < ncols; ++c) {
+    if (boolean_column(op, za, off_a[c], off_a[c + 1], zb, off_b[c], off_b[c + 1], &res[c])) {
+      for (int64_t t = 0; t <= c; ++t) free(res[t].v);
+      free(res);
+      return -1;
+    }
+    total += res[c].n;
+  }
+  int64_t* off = (int64_t*)malloc((size_t)(ncols + 1) * sizeof(int64_t));
+  double* oz = (double*)malloc((size_t)(total > 0 ? 2 * total : 2) * sizeof(double));
+  if (!off || !oz) {
+    free(off);
+    free(oz);
+    for (int64_t t = 0; t < ncols; ++t) free(res[t].v);
+    free(res);
+    return -1;
+  }
+  off[0] = 0;
+  for (int64_t c = 0; c < ncols; ++c) {
+    for (int64_t s = 0; s < res[c].n; ++s) {
+      oz[2 * (off[c] + s)] = res[c].v[s].a;
+      oz[2 * (off[c] + s) + 1] = res[c].v[s].b;
+    }
+    off[c + 1] = off[c] + res[c].n;
+    free(res[c].v);
+  }
+  free(res);
+  *out_off = off;
+  *out_z = oz;
+  return total;
+}
