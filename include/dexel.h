@@ -64,6 +64,9 @@ typedef enum { DEXEL_FP64 = 0, DEXEL_FP32_PRED64 = 1 } dexel_mode;
 
 typedef enum { DEXEL_DILATE = 0, DEXEL_ERODE = 1, DEXEL_CLOSE = 2, DEXEL_OPEN = 3 } dexel_op;
 
+/* Boolean operations of two grids (CSG in dexel space). */
+typedef enum { DEXEL_UNION = 0, DEXEL_INTERSECT = 1, DEXEL_DIFFERENCE = 2 } dexel_bool_op;
+
 typedef struct {
   int32_t nx, ny;         /* grid size, 1 <= nx, ny <= 32768                                */
   double h;               /* xy spacing, in the same units as z (> 0)                       */
@@ -152,6 +155,27 @@ dexel_status dexel_erode(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
 dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
                          dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
                          void* stream);
+
+/* Boolean operation of two grids of the same size (CSG carried out in dexel space, Sec. 2
+ * "(3)": the rays of a column combine on their own), column by column:
+ *   DEXEL_UNION       closed union of a and b (touching segments join; an isolated
+ *                     zero-length segment stays);
+ *   DEXEL_INTERSECT   closed intersection; results of zero length are dropped;
+ *   DEXEL_DIFFERENCE  the closure of a minus b (b's segments remove their open interiors);
+ *                     results of zero length are dropped.
+ * a, b: device CSR grids with the same nx, ny (h is taken from a) and the precision `mode`;
+ * both are validated (DEXEL_ERR_BAD_CSR).  No arithmetic touches the heights: every output
+ * end is an input end, in either precision.  Output, workspace and retry contract as for
+ * dexel_dilate (ws may be NULL: library-owned scratch of 24 bytes a column). */
+dexel_status dexel_boolean(dexel_ctx* ctx, dexel_bool_op op, const dexel_grid_in* a,
+                           const dexel_grid_in* b, dexel_mode mode, dexel_grid_out* out, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/* Thick shell of controllable thickness: the Boolean difference of the dilation and the
+ * erosion by a ball of radius k*h (Sec. 4 "3D Printing"; the teaser figure's shell).  The two
+ * offsets live in context-owned buffers; same contract as dexel_dilate. */
+dexel_status dexel_shell(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_mode mode,
+                         dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream);
 
 /* Batched offsets: nshapes independent grids, each with its own radius and operation
  * (Sec. 3.3 applied to a table of shapes; no counterpart in the paper, which offsets one

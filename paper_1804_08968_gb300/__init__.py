@@ -19,12 +19,13 @@ import os
 
 import numpy as np
 
-__all__ = ["Grid", "Context", "dilate", "erode", "close", "open_", "lib", "DexelError",
-           "FP64", "FP32_PRED64"]
+__all__ = ["Grid", "Context", "dilate", "erode", "close", "open_", "boolean", "shell", "lib",
+           "DexelError", "FP64", "FP32_PRED64", "UNION", "INTERSECT", "DIFFERENCE"]
 
 FP64 = 0
 FP32_PRED64 = 1
 DILATE, ERODE, CLOSE, OPEN = 0, 1, 2, 3
+UNION, INTERSECT, DIFFERENCE = 0, 1, 2
 STATUS = {0: "ok", -1: "invalid argument", -2: "malformed CSR dexel grid",
           -3: "capacity too small", -4: "CUDA runtime error", -5: "device wait timeout",
           -6: "out of memory"}
@@ -68,6 +69,10 @@ def lib():
         L.dexel_morph.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_validate.argtypes = [P, ctypes.POINTER(_In), ctypes.c_int, P, ctypes.c_size_t, P]
+        L.dexel_boolean.argtypes = [P, ctypes.c_int, ctypes.POINTER(_In), ctypes.POINTER(_In),
+                                    ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
+        L.dexel_shell.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_offset_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(_In),
                                            ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -215,6 +220,43 @@ class Context:
             return Grid(g.nx, g.ny, g.h, off, z[: out.nseg])
         raise DexelError(-3, "dexel offset (output capacity)")
 
+    def _call_out(self, nx, ny, h, like, cap, fn, what):
+        """Run fn(out) with an output of cap segments, growing it once to the reported need."""
+        torch = _torch()
+        for _ in range(3):
+            off = torch.empty(nx * ny + 1, dtype=torch.int32, device=like.col_off.device)
+            z = torch.empty((cap, 2), dtype=like.z.dtype, device=like.z.device)
+            out = _Out(off.data_ptr(), z.data_ptr(), cap, 0)
+            rc = fn(out)
+            if rc == -3 and out.nseg > cap:
+                cap = int(out.nseg) + 16
+                continue
+            if rc != 0:
+                detail = lib().dexel_last_error_detail().decode()
+                raise DexelError(rc, f"{what}{' (' + detail + ')' if detail else ''}")
+            return Grid(nx, ny, h, off, z[: out.nseg])
+        raise DexelError(-3, f"{what} (output capacity)")
+
+    def boolean(self, op: int, a: Grid, b: Grid, stream=None) -> Grid:
+        """op in UNION / INTERSECT / DIFFERENCE (dexel_boolean)."""
+        if (a.nx, a.ny) != (b.nx, b.ny) or a.mode != b.mode:
+            raise ValueError("grids of different sizes or precisions")
+        ia, ib = a._in(), b._in()
+        st = self._stream(stream)
+        cap = max(a.nseg + b.nseg + 16, 1024)
+        return self._call_out(a.nx, a.ny, a.h, a, cap, lambda out: lib().dexel_boolean(
+            self.ptr, op, ctypes.byref(ia), ctypes.byref(ib), a.mode, ctypes.byref(out), None, 0, st),
+            "dexel_boolean")
+
+    def shell(self, g: Grid, k: float, stream=None) -> Grid:
+        """Thick shell: dilation minus erosion by a ball of radius k spacings (dexel_shell)."""
+        gin = g._in()
+        st = self._stream(stream)
+        cap = max(4 * g.nseg + g.nx * g.ny // 4, 1024)
+        return self._call_out(g.nx, g.ny, g.h, g, cap, lambda out: lib().dexel_shell(
+            self.ptr, ctypes.byref(gin), float(k), g.mode, ctypes.byref(out), None, 0, st),
+            "dexel_shell")
+
     def run_batched(self, ops, grids, ks, stream=None, capacities=None):
         """Offsets of many grids in one batched call (dexel_offset_batched): ops[s] in
         DILATE / ERODE / CLOSE / OPEN, grids all FP64 or all FP32.  Returns the output grids;
@@ -297,3 +339,13 @@ def close(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
 def open_(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
     """Opening: dilation of the erosion."""
     return (ctx or _default_ctx(g)).run(OPEN, g, k, stream)
+
+
+def boolean(op: int, a: Grid, b: Grid, ctx: Context | None = None, stream=None) -> Grid:
+    """Union / intersection / difference of two grids (CSG in dexel space)."""
+    return (ctx or _default_ctx(a)).boolean(op, a, b, stream)
+
+
+def shell(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
+    """Thick shell: the dilation minus the erosion by a ball of radius k spacings."""
+    return (ctx or _default_ctx(g)).shell(g, k, stream)

@@ -24,9 +24,12 @@ struct dexel_ctx {
   // library-owned scratch, used when the caller passes ws == NULL
   void* own = nullptr;
   size_t own_bytes = 0;
-  // intermediate grid of closing / opening
+  // intermediate grid of closing / opening (and the dilation of a shell), and the erosion of
+  // a shell
   void* mid = nullptr;
   size_t mid_bytes = 0;
+  void* aux = nullptr;
+  size_t aux_bytes = 0;
   size_t last_required = 0;
   long long launches = 0;
   // capacities learnt from earlier calls (grown on overflow)
@@ -956,6 +959,92 @@ dexel_status offset(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erod
   return Offset<float>::run(ctx, in, k, erode, out, ws, ws_bytes, st);
 }
 
+// Boolean operation of two grids of the same size into the caller's CSR (csg.cu): both
+// inputs validated, per-column counts, scan, then the segments.
+template <typename T>
+dexel_status boolean_run(dexel_ctx* ctx, int op, const dexel_grid_in* a, const dexel_grid_in* b,
+                         dexel_grid_out* out, void* ws_user, size_t ws_bytes, cudaStream_t st) {
+  const long long ncols = (long long)a->nx * a->ny;
+  auto plan = [&](Carver& C, void** pctr, void** pcnt, void** ppos, void** psums) {
+    *pctr = C.take(sizeof(Counters));
+    *pcnt = C.take(sizeof(long long) * (ncols + 1));
+    *ppos = C.take(sizeof(long long) * (ncols + 1));
+    *psums = C.take(sizeof(long long) * ((ncols + kScanTile) / kScanTile + 2));
+  };
+  Carver probe{nullptr, (size_t)-1};
+  void *pctr, *pcnt, *ppos, *psums;
+  plan(probe, &pctr, &pcnt, &ppos, &psums);
+  const size_t need = align_up(probe.used, 256) + 256;
+  void* base = ws_user;
+  size_t bytes = ws_bytes;
+  if (ws_user) {
+    if (ws_bytes < need) {
+      ctx->last_required = need;
+      return DEXEL_ERR_CAPACITY;
+    }
+  } else {
+    dexel_status s = ensure_owned(ctx, need);
+    if (s != DEXEL_OK) return s;
+    base = ctx->own;
+    bytes = ctx->own_bytes;
+  }
+  Carver C{(char*)base, bytes};
+  plan(C, &pctr, &pcnt, &ppos, &psums);
+  if (!C.ok) return DEXEL_ERR_CAPACITY;
+  ctx->last_required = need;
+  Counters* ctr = (Counters*)pctr;
+  CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+  const unsigned g = (unsigned)((ncols + 255) / 256);
+  k_validate<T><<<g, 256, 0, st>>>((int)ncols, a->col_off, (const T*)a->z, a->nseg, ctr);
+  k_validate<T><<<g, 256, 0, st>>>((int)ncols, b->col_off, (const T*)b->z, b->nseg, ctr);
+  CK(launch_bool_count<T>(op, ncols, a->col_off, (const T*)a->z, b->col_off, (const T*)b->z,
+                          (long long*)pcnt, st));
+  const long long nsb = (ncols + kScanTile - 1) / kScanTile;
+  k_scan1<long long><<<(unsigned)nsb, kScanThreads, 0, st>>>(ncols, (const long long*)pcnt,
+                                                            (long long*)ppos, (long long*)psums);
+  k_scan2<<<1, kScanThreads, 0, st>>>(nsb, (long long*)psums);
+  k_scan3<<<(unsigned)((ncols + 1 + 255) / 256), 256, 0, st>>>(ncols, (long long*)ppos,
+                                                              (const long long*)psums, out->col_off, ctr);
+  ctx->launches += 6;
+  CK(cudaGetLastError());
+  long long total = 0;
+  Counters hc;
+  CK(cudaMemcpyAsync(&total, (long long*)psums + nsb, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hc.status & ST_BAD_CSR) return DEXEL_ERR_BAD_CSR;
+  out->nseg = total;
+  if ((hc.status & ST_TOO_MANY_OUT) || total > out->capacity_seg) return DEXEL_ERR_CAPACITY;
+  CK(launch_bool_write<T>(op, ncols, a->col_off, (const T*)a->z, b->col_off, (const T*)b->z,
+                          (const long long*)ppos, (T*)out->z, st));
+  ++ctx->launches;
+  CK(cudaStreamSynchronize(st));
+  ctx->stats[0] += a->nseg + b->nseg;
+  ctx->stats[3] += total;
+  return DEXEL_OK;
+}
+
+dexel_status boolean_run_any(dexel_ctx* ctx, int op, const dexel_grid_in* a, const dexel_grid_in* b,
+                             dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
+                             cudaStream_t st) {
+  if (mode == DEXEL_FP64) return boolean_run<double>(ctx, op, a, b, out, ws, ws_bytes, st);
+  return boolean_run<float>(ctx, op, a, b, out, ws, ws_bytes, st);
+}
+
+// A device buffer of the context, grown to `need` bytes.
+dexel_status grow_buffer(void** p, size_t* bytes, size_t need) {
+  if (*bytes >= need) return DEXEL_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *bytes = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    cudaGetLastError();
+    return DEXEL_ERR_NOMEM;
+  }
+  *bytes = need;
+  return DEXEL_OK;
+}
+
 }  // namespace
 
 
@@ -1173,6 +1262,7 @@ void dexel_ctx_destroy(dexel_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->own) cudaFree(ctx->own);
   if (ctx->mid) cudaFree(ctx->mid);
+  if (ctx->aux) cudaFree(ctx->aux);
   batch_engine_destroy(ctx->batch);
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
@@ -1306,6 +1396,59 @@ dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
     return offset(ctx, &in2, k, !first_erode, mode, out, ws, ws_bytes, stream);
   }
   return DEXEL_ERR_CAPACITY;
+}
+
+dexel_status dexel_boolean(dexel_ctx* ctx, dexel_bool_op op, const dexel_grid_in* a,
+                           const dexel_grid_in* b, dexel_mode mode, dexel_grid_out* out, void* ws,
+                           size_t ws_bytes, void* stream) {
+  if (!ctx || !out || !out->col_off || (out->capacity_seg > 0 && !out->z) || out->capacity_seg < 0)
+    return DEXEL_ERR_INVALID_ARG;
+  if (op != DEXEL_UNION && op != DEXEL_INTERSECT && op != DEXEL_DIFFERENCE) return DEXEL_ERR_INVALID_ARG;
+  if (mode != DEXEL_FP64 && mode != DEXEL_FP32_PRED64) return DEXEL_ERR_INVALID_ARG;
+  reset_call(ctx);
+  if (check_in(a, 0.0) != DEXEL_OK || check_in(b, 0.0) != DEXEL_OK) return DEXEL_ERR_INVALID_ARG;
+  if (a->nx != b->nx || a->ny != b->ny) return DEXEL_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DEXEL_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mode == DEXEL_FP64) return boolean_run<double>(ctx, (int)op, a, b, out, ws, ws_bytes, st);
+  return boolean_run<float>(ctx, (int)op, a, b, out, ws, ws_bytes, st);
+}
+
+dexel_status dexel_shell(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_mode mode,
+                         dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !out || !out->col_off || (out->capacity_seg > 0 && !out->z) || out->capacity_seg < 0)
+    return DEXEL_ERR_INVALID_ARG;
+  if (mode != DEXEL_FP64 && mode != DEXEL_FP32_PRED64) return DEXEL_ERR_INVALID_ARG;
+  reset_call(ctx);
+  dexel_status s = check_in(in, k);
+  if (s != DEXEL_OK) return s;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DEXEL_ERR_CUDA;
+  const long long ncols = (long long)in->nx * in->ny;
+  const size_t es = mode == DEXEL_FP64 ? 8 : 4;
+  const size_t offb = align_up((size_t)(ncols + 1) * 4, 256);
+  // the dilation and the erosion in two context buffers, each grown until its grid fits
+  dexel_grid_out g[2];
+  void** buf[2] = {&ctx->mid, &ctx->aux};
+  size_t* len[2] = {&ctx->mid_bytes, &ctx->aux_bytes};
+  for (int q = 0; q < 2; ++q) {
+    long long cap = std::max<long long>(2 * in->nseg + ncols / 4, 1024);
+    if (*len[q] > offb) cap = std::max<long long>(cap, (long long)((*len[q] - offb) / (2 * es)));
+    for (int attempt = 0;; ++attempt) {
+      s = grow_buffer(buf[q], len[q], offb + (size_t)cap * 2 * es);
+      if (s != DEXEL_OK) return s;
+      g[q] = dexel_grid_out{(int32_t*)*buf[q], (char*)*buf[q] + offb, cap, 0};
+      s = offset(ctx, in, k, q == 1, mode, &g[q], ws, ws_bytes, stream);
+      if (s == DEXEL_ERR_CAPACITY && g[q].nseg > cap && attempt < 3) {
+        cap = g[q].nseg + 1024;
+        continue;
+      }
+      if (s != DEXEL_OK) return s;
+      break;
+    }
+  }
+  const dexel_grid_in d{in->nx, in->ny, in->h, g[0].col_off, g[0].z, g[0].nseg};
+  const dexel_grid_in e{in->nx, in->ny, in->h, g[1].col_off, g[1].z, g[1].nseg};
+  return boolean_run_any(ctx, kBoolDifference, &d, &e, mode, out, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_in* ins,

@@ -75,6 +75,16 @@ cudaError_t launch_lgather_lanes(const LvlParamsHost<T>& H, cudaStream_t st, int
 template <typename T>
 cudaError_t launch_pass2c(const P2GParams<T>& P, int warps_per_block, int blocks, cudaStream_t st);
 
+// Boolean operations of two grids (csg.cu): per-column counts, then the segments at the
+// scanned positions
+constexpr int kBoolUnion = 0, kBoolIntersect = 1, kBoolDifference = 2;
+template <typename T>
+cudaError_t launch_bool_count(int op, long long ncols, const int* oa, const T* za, const int* ob,
+                              const T* zb, long long* cnt, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bool_write(int op, long long ncols, const int* oa, const T* za, const int* ob,
+                              const T* zb, const long long* pos, T* zo, cudaStream_t st);
+
 // Batched offsets (batch.cu): one launch per stage over many shapes.  An item's status after
 // batch_run: DEXEL_OK, DEXEL_ERR_BAD_CSR, DEXEL_ERR_CAPACITY (nseg holds the need), or 1 when
 // the item needs the single-shape path (a window beyond the batch kernels' limits).  An item
