@@ -12,7 +12,9 @@ The arithmetic lives in ``oracle.c`` (plain brute-force gather, see its header):
   * ``close`` = erode(dilate(S)), ``open`` = dilate(erode(S))   (Sec. 4 "Topological Cleaning");
   * ``union`` / ``intersection`` / ``difference`` -- CSG in dexel space (Sec. 2, "(3)"), from
                    point membership of each column's elementary intervals, then the closure;
-  * ``shell`` = difference(dilate(S), erode(S))  (Sec. 4 "3D Printing", the teaser figure).
+  * ``shell`` = difference(dilate(S), erode(S))  (Sec. 4 "3D Printing", the teaser figure);
+  * ``dilate_slices`` / ``erode_slices`` -- Sec. 3.2's 2D offsets for every row at once: the
+                   same gather over the output column's own row only (a disk in the x-z plane).
 ``complement`` builds the per-column complement with +-inf sentinels (Sec. 3.1: the complement
 is trivial in a ray representation); tests use it to check erosion/dilation duality.
 
@@ -58,6 +60,8 @@ def _load():
                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
+        lib.oracle_offset_slices.restype = ctypes.c_int64
+        lib.oracle_offset_slices.argtypes = lib.oracle_offset.argtypes
         lib.oracle_free.restype = None
         lib.oracle_free.argtypes = [ctypes.c_void_p]
         lib.oracle_boolean.restype = ctypes.c_int64
@@ -91,7 +95,8 @@ class Columns:
         return len(self.off) - 1
 
 
-def _run(grid, k: float, erode: int, cols=None, threads: int | None = None) -> Columns:
+def _run(grid, k: float, erode: int, cols=None, threads: int | None = None,
+         slices: bool = False) -> Columns:
     lib = _load()
     off_in = np.ascontiguousarray(grid.col_off, dtype=np.int64)
     z_in = np.ascontiguousarray(grid.z, dtype=np.float64).reshape(-1)
@@ -107,9 +112,10 @@ def _run(grid, k: float, erode: int, cols=None, threads: int | None = None) -> C
         cptr = None
     po = ctypes.POINTER(ctypes.c_int64)()
     pz = ctypes.POINTER(ctypes.c_double)()
-    total = lib.oracle_offset(grid.nx, grid.ny, float(grid.h), float(k), off_in.ctypes.data,
-                              z_in.ctypes.data, erode, cptr, ncols,
-                              threads or default_threads(), ctypes.byref(po), ctypes.byref(pz))
+    fn = lib.oracle_offset_slices if slices else lib.oracle_offset
+    total = fn(grid.nx, grid.ny, float(grid.h), float(k), off_in.ctypes.data,
+               z_in.ctypes.data, erode, cptr, ncols,
+               threads or default_threads(), ctypes.byref(po), ctypes.byref(pz))
     if total < 0:
         raise ValueError("oracle_offset rejected its arguments")
     off = np.ctypeslib.as_array(po, shape=(ncols + 1,)).copy()
@@ -133,6 +139,18 @@ def dilate(grid, k: float, cols=None, threads=None):
 def erode(grid, k: float, cols=None, threads=None):
     """Erosion by a ball of radius k*h (direct intersection form)."""
     r = _run(grid, k, 1, cols, threads)
+    return _as_grid(grid, r) if cols is None else r
+
+
+def dilate_slices(grid, k: float, cols=None, threads=None):
+    """Every row of the grid a 2D dexel image dilated by a disk of radius k*h (Sec. 3.2)."""
+    r = _run(grid, k, 0, cols, threads, slices=True)
+    return _as_grid(grid, r) if cols is None else r
+
+
+def erode_slices(grid, k: float, cols=None, threads=None):
+    """Every row of the grid a 2D dexel image eroded by a disk of radius k*h."""
+    r = _run(grid, k, 1, cols, threads, slices=True)
     return _as_grid(grid, r) if cols is None else r
 
 

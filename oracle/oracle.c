@@ -96,6 +96,7 @@ typedef struct {
   const double* z;
   int erode;
   const int64_t* cols; /* output columns to compute; NULL = all, in order */
+  int slices;          /* 1: every row is its own 2D image, offset by a disk (dj = 0 only) */
   int64_t ncols;
   ivec* res; /* one result vector per requested column */
   int64_t next;
@@ -108,7 +109,8 @@ static void dilate_column(const job* J, int64_t c, ivec* out) {
   const int64_t i = c % nx, j = c / nx;
   const double kk = J->k * J->k;
   const int64_t R = reach(kk);
-  for (int64_t dj = -R; dj <= R; ++dj) {
+  const int64_t Rj = J->slices ? 0 : R;
+  for (int64_t dj = -Rj; dj <= Rj; ++dj) {
     const int64_t jj = j + dj;
     if (jj < 0 || jj >= ny) continue;
     for (int64_t di = -R; di <= R; ++di) {
@@ -153,7 +155,8 @@ static void erode_column(const job* J, int64_t c, ivec* out) {
   const int64_t R = reach(kk);
   ivec part = {0}, tmp = {0};
   int first = 1;
-  for (int64_t dj = -R; dj <= R; ++dj) {
+  const int64_t Rj = J->slices ? 0 : R;
+  for (int64_t dj = -Rj; dj <= Rj; ++dj) {
     const int64_t jj = j + dj;
     if (jj < 0 || jj >= ny) continue;
     for (int64_t di = -R; di <= R; ++di) {
@@ -211,9 +214,33 @@ static void* worker(void* arg) {
  * *out_z (2*total doubles); free both with oracle_free.  Returns -1 on bad arguments or
  * allocation failure.
  */
+int64_t oracle_offset_any(int32_t nx, int32_t ny, double h, double k, const int64_t* col_off,
+                          const double* z, int erode, int slices, const int64_t* cols,
+                          int64_t ncols, int nthreads, int64_t** out_off, double** out_z);
+
 int64_t oracle_offset(int32_t nx, int32_t ny, double h, double k, const int64_t* col_off,
                       const double* z, int erode, const int64_t* cols, int64_t ncols,
                       int nthreads, int64_t** out_off, double** out_z) {
+  return oracle_offset_any(nx, ny, h, k, col_off, z, erode, 0, cols, ncols, nthreads, out_off,
+                           out_z);
+}
+
+/*
+ * The 2D offsets of Sec. 3.2 ("2D Offsets": a 2D shape given as parallel segments on a regular
+ * grid, dilated by a disk), for every row of the grid at once: slices = 1 takes only the
+ * columns of the output column's own row (dj = 0), so each row is offset by a disk of radius
+ * k h in its (x, z) plane.  Otherwise as oracle_offset.
+ */
+int64_t oracle_offset_slices(int32_t nx, int32_t ny, double h, double k, const int64_t* col_off,
+                             const double* z, int erode, const int64_t* cols, int64_t ncols,
+                             int nthreads, int64_t** out_off, double** out_z) {
+  return oracle_offset_any(nx, ny, h, k, col_off, z, erode, 1, cols, ncols, nthreads, out_off,
+                           out_z);
+}
+
+int64_t oracle_offset_any(int32_t nx, int32_t ny, double h, double k, const int64_t* col_off,
+                          const double* z, int erode, int slices, const int64_t* cols,
+                          int64_t ncols, int nthreads, int64_t** out_off, double** out_z) {
   if (nx <= 0 || ny <= 0 || !(h > 0) || !(k >= 0) || !col_off || !out_off || !out_z) return -1;
   if (!cols) ncols = (int64_t)nx * ny;
   for (int64_t t = 0; cols && t < ncols; ++t)
@@ -227,6 +254,7 @@ int64_t oracle_offset(int32_t nx, int32_t ny, double h, double k, const int64_t*
   J.col_off = col_off;
   J.z = z;
   J.erode = erode;
+  J.slices = slices ? 1 : 0;
   J.cols = cols;
   J.ncols = ncols;
   J.res = (ivec*)calloc((size_t)(ncols > 0 ? ncols : 1), sizeof(ivec));
