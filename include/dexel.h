@@ -156,6 +156,20 @@ dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
                          dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
                          void* stream);
 
+/* 2D offsets of dexel images (Sec. 3.2, "Half-Space Voronoi Diagram of Segments and 2D
+ * Offsets": a 2D shape given as parallel segments on a regular grid, dilated by a disk), for
+ * every row of the grid at once: row j (the nx columns with this j) is an independent 2D image
+ * in its (x, z) plane -- a slice of a CT stack, a layer of a print -- offset by a disk of
+ * radius k*h (k in spacings, as for dexel_dilate).  op: DEXEL_DILATE, or DEXEL_ERODE (the
+ * complement of the dilation of the complement, within each row).  Pass 1 (the extrusion
+ * along x) is the 3D one; the y pass keeps, for every column, its own pieces' slices
+ * [a - w, b + w], w = h sqrt(k^2 - dx^2).  Same layout, workspace and retry contract as
+ * dexel_dilate (k at most 1024; DEXEL_ERR_CAPACITY when a column's union outgrows every
+ * gather bucket). */
+dexel_status dexel_offset_slices(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
+                                 dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
+                                 void* stream);
+
 /* Boolean operation of two grids of the same size (CSG carried out in dexel space, Sec. 2
  * "(3)": the rays of a column combine on their own), column by column:
  *   DEXEL_UNION       closed union of a and b (touching segments join; an isolated

@@ -20,7 +20,8 @@ import os
 import numpy as np
 
 __all__ = ["Grid", "Context", "dilate", "erode", "close", "open_", "boolean", "shell", "lib",
-           "DexelError", "FP64", "FP32_PRED64", "UNION", "INTERSECT", "DIFFERENCE"]
+           "DexelError", "FP64", "FP32_PRED64", "UNION", "INTERSECT", "DIFFERENCE",
+           "dilate_slices", "erode_slices"]
 
 FP64 = 0
 FP32_PRED64 = 1
@@ -69,6 +70,8 @@ def lib():
         L.dexel_morph.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_validate.argtypes = [P, ctypes.POINTER(_In), ctypes.c_int, P, ctypes.c_size_t, P]
+        L.dexel_offset_slices.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_boolean.argtypes = [P, ctypes.c_int, ctypes.POINTER(_In), ctypes.POINTER(_In),
                                     ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_shell.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
@@ -248,6 +251,16 @@ class Context:
             self.ptr, op, ctypes.byref(ia), ctypes.byref(ib), a.mode, ctypes.byref(out), None, 0, st),
             "dexel_boolean")
 
+    def slices(self, op: int, g: Grid, k: float, stream=None) -> Grid:
+        """Every row of g a 2D image, dilated (op DILATE) or eroded (ERODE) by a disk of radius
+        k spacings (dexel_offset_slices)."""
+        gin = g._in()
+        st = self._stream(stream)
+        cap = max(2 * g.nseg + g.nx * g.ny // 4, 1024)
+        return self._call_out(g.nx, g.ny, g.h, g, cap, lambda out: lib().dexel_offset_slices(
+            self.ptr, ctypes.byref(gin), float(k), op, g.mode, ctypes.byref(out), None, 0, st),
+            "dexel_offset_slices")
+
     def shell(self, g: Grid, k: float, stream=None) -> Grid:
         """Thick shell: dilation minus erosion by a ball of radius k spacings (dexel_shell)."""
         gin = g._in()
@@ -349,3 +362,13 @@ def boolean(op: int, a: Grid, b: Grid, ctx: Context | None = None, stream=None) 
 def shell(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
     """Thick shell: the dilation minus the erosion by a ball of radius k spacings."""
     return (ctx or _default_ctx(g)).shell(g, k, stream)
+
+
+def dilate_slices(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
+    """Every row a 2D dexel image dilated by a disk of radius k spacings (Sec. 3.2)."""
+    return (ctx or _default_ctx(g)).slices(DILATE, g, k, stream)
+
+
+def erode_slices(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
+    """Every row a 2D dexel image eroded by a disk of radius k spacings."""
+    return (ctx or _default_ctx(g)).slices(ERODE, g, k, stream)

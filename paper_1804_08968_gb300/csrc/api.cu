@@ -272,14 +272,17 @@ dexel_status ensure_owned(dexel_ctx* ctx, size_t bytes) {
 template <typename T>
 struct Offset {
   // one offset (dilation of S or of its complement) of a grid into the output CSR
+  // slices: every row of the grid a 2D image, offset by a disk (Sec. 3.2): pass 1 as usual,
+  // pass 2 takes only the column's own level-0 list
   static dexel_status run(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erode,
-                          dexel_grid_out* out, void* ws, size_t ws_bytes, cudaStream_t st);
+                          dexel_grid_out* out, void* ws, size_t ws_bytes, cudaStream_t st,
+                          bool slices);
 };
 
 template <typename T>
 dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erode,
                             dexel_grid_out* out, void* ws_user, size_t ws_user_bytes,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool slices) {
   typedef typename H<T>::K Key;
   const int nx = in->nx, ny = in->ny;
   const long long ncols = (long long)nx * ny;
@@ -603,7 +606,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     }
 
     // ---------------- pass 2: window gather (default) or per-line sweep
-    bool use_sweep = ctx->sweep2 || K > kGatherMaxReach;
+    bool use_sweep = (ctx->sweep2 && !slices) || K > kGatherMaxReach;
+    if (use_sweep && slices) return DEXEL_ERR_INVALID_ARG;  // beyond the slices' reach
     if (!use_sweep) {
       P2GParams<T> pg{};
       pg.nx = nx; pg.ny = ny; pg.R = K; pg.kk = kk; pg.nmax = nmax;
@@ -673,7 +677,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         const int tblocks = std::max(1, std::min(sms * per_sm, ntiles_cap));
         mark(ctx, 4, st);  // the stage covers the pass-2 kernels only (not the copy above)
         bool done = false;
-        if (ctx->levels && slot_room >= bL && bL > 0) {
+        if ((ctx->levels || slices) && slot_room >= bL && bL > 0) {
           // per-source level unions in the sweeps' slot room, then the per-column gather
           LvlParamsHost<T> H;
           H.P = pg;
@@ -691,6 +695,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           H.exact = !packed;
           H.q0 = q0;
           H.nq = nq;
+          H.yw = slices ? 0 : -1;
           kmark(ctx, 1, false, st);
           CK(launch_levels<T>(H, st, sms));
           kmark(ctx, 1, true, st);
@@ -712,7 +717,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
             while (b < hc.over_max && b < 2048) b <<= 1;
             lb = b;
           }
-          if ((hc.status & ST_LEVELS_OVER) && nb > 1) {
+          if ((hc.status & ST_LEVELS_OVER) && (nb > 1 || slices)) {
             // the level arena outgrew its share: plan again with its need (the tiled gather
             // would take the whole grid)
             ctx->needL = std::max<long long>(ctx->needL, (long long)(hc.arena_top[2] * to_grid * 1.25));
@@ -746,6 +751,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
             }
           }
         }
+        if (!done && slices) return DEXEL_ERR_CAPACITY;  // the level path's room (not reached)
         if (!done && nb > 1) {
           // the tiled gather takes the whole grid: plan again without blocks
           ctx->noblock = true;
@@ -762,6 +768,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       int redo = 0;
+      if (slices && (hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA))
+        return DEXEL_ERR_CAPACITY;  // a column's own union beyond every bucket
       if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
         // columns whose union outgrew the bucket: k_pass2c with one bucket for the whole window
         redo = hc.redo_cols;
@@ -947,7 +955,8 @@ dexel_status check_in(const dexel_grid_in* in, double k) {
 }
 
 dexel_status offset(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erode, dexel_mode mode,
-                    dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream) {
+                    dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream,
+                    bool slices = false) {
   if (!ctx || !out || !out->col_off || (out->capacity_seg > 0 && !out->z) || out->capacity_seg < 0)
     return DEXEL_ERR_INVALID_ARG;
   dexel_status s = check_in(in, k);
@@ -955,8 +964,8 @@ dexel_status offset(dexel_ctx* ctx, const dexel_grid_in* in, double k, bool erod
   if (mode != DEXEL_FP64 && mode != DEXEL_FP32_PRED64) return DEXEL_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return DEXEL_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
-  if (mode == DEXEL_FP64) return Offset<double>::run(ctx, in, k, erode, out, ws, ws_bytes, st);
-  return Offset<float>::run(ctx, in, k, erode, out, ws, ws_bytes, st);
+  if (mode == DEXEL_FP64) return Offset<double>::run(ctx, in, k, erode, out, ws, ws_bytes, st, slices);
+  return Offset<float>::run(ctx, in, k, erode, out, ws, ws_bytes, st, slices);
 }
 
 // Boolean operation of two grids of the same size into the caller's CSR (csg.cu): both
@@ -1396,6 +1405,14 @@ dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
     return offset(ctx, &in2, k, !first_erode, mode, out, ws, ws_bytes, stream);
   }
   return DEXEL_ERR_CAPACITY;
+}
+
+dexel_status dexel_offset_slices(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
+                                 dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  if (op != DEXEL_DILATE && op != DEXEL_ERODE) return DEXEL_ERR_INVALID_ARG;
+  if (ctx) reset_call(ctx);
+  return offset(ctx, in, k, op == DEXEL_ERODE, mode, out, ws, ws_bytes, stream, true);
 }
 
 dexel_status dexel_boolean(dexel_ctx* ctx, dexel_bool_op op, const dexel_grid_in* a,

@@ -554,6 +554,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       v.G = v.L <= 32 ? 32 / v.L : 1;
       v.NG = v.L <= 32 ? 0 : (K[s] + 31) / 32;
       v.q0 = 0;
+      v.yw = K[s];
       v.nsrc = colb[s + 1] - colb[s];
       v.nlev = nlb[s + 1] - nlb[s];
       v.m_cap = pl.capM;

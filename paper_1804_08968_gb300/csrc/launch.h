@@ -62,6 +62,8 @@ struct LvlParamsHost {
   // a block of whole y lines: sources / output columns q0 .. q0 + nq - 1 in line order
   // (q = i * ny + j; nq = 0: the whole grid); l_start / l_cnt hold the block's entries only
   long long q0 = 0, nq = 0;
+  // reach of the output window along y (-1: R; 0: the 2D slices, a column's own level 0)
+  int yw = -1;
 };
 // k_levels (the per-source level lists); launch_lgather then unites them per column
 template <typename T>

@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(256, 4) k_levels(LvlParams<T> A, int tab_float
                                       A.P.wtabf);
   __syncthreads();
   const float E = 9.5367432e-7f * (__uint_as_float(A.P.ctr->zmax_bits) + A.P.wtabf[0]);  // 2^-20
-  const long long nitems = lvl_items(A.nsrc, A.L);
+  const long long nitems = lvl_items(A.nsrc, A.L, A.yw);
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   ArenaCursor cur{0, 0};
   for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + warp; item < nitems; item += nw)
@@ -79,6 +79,7 @@ static LvlParams<T> lvl_params(const LvlParamsHost<T>& H) {
   }
   // a block of lines: the index arrays are addressed with the global source index q, so
   // their base pointers are shifted by the block's first entry (q0 L); nlev bounds q L + t
+  A.yw = H.yw >= 0 ? H.yw : H.P.R;
   A.q0 = H.q0;
   A.nsrc = H.nq > 0 ? H.nq : (long long)H.P.nx * H.P.ny;
   A.l_start = H.l_start - H.q0 * A.L;

@@ -53,6 +53,8 @@ struct LvlParams {
   int L;     // levels a source: R + 1
   int G;     // sources a warp when L <= 32, else 1
   int NG;    // level groups of 32 (levels 1 .. R) when L > 32, else 0
+  int yw;          // reach of the output column's window along y (R; 0: the 2D slices, each
+                   // column its own level-0 list)
   long long q0;    // first source column of the block (line order q = i * ny + j)
   long long nsrc;  // source columns of the block
   long long nlev;  // bound of the index q * L + t into l_start / l_cnt
@@ -61,8 +63,12 @@ struct LvlParams {
 
 // Work items of k_levels: L <= 32, groups of G = 32 / L sources (lane = (source, level));
 // L > 32, first the level-0 items (32 sources, lane = source), then (source, level group).
-DXI long long lvl_level0_items(long long nsrc, int L) { return L <= 32 ? 0 : (nsrc + 31) / 32; }
-DXI long long lvl_items(long long nsrc, int L) {
+// yw = 0 (the 2D slices): the level-0 items only, one lane a source, at every L.
+DXI long long lvl_level0_items(long long nsrc, int L, int yw = -1) {
+  return (L <= 32 && yw != 0) ? 0 : (nsrc + 31) / 32;
+}
+DXI long long lvl_items(long long nsrc, int L, int yw = -1) {
+  if (yw == 0) return lvl_level0_items(nsrc, L, yw);
   if (L <= 32) return (nsrc + (32 / L) - 1) / (32 / L);
   return lvl_level0_items(nsrc, L) + nsrc * ((L - 1 + 31) / 32);
 }
@@ -342,13 +348,14 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
                      float E, float* tab, ArenaCursor& cur) {
   const P2GParams<T>& P = A.P;
   const int R1 = P.R + 1;
-  const long long n0 = lvl_level0_items(A.nsrc, A.L);
-  if (A.NG == 0 || item < n0) {
+  const long long n0 = lvl_level0_items(A.nsrc, A.L, A.yw);
+  const bool pairs = A.NG == 0 && A.yw != 0;  // lane = (source, level)
+  if (pairs || item < n0) {
     // lane = (source, level): a walk of its own
     long long q;
     int t;
     bool act;
-    if (A.NG == 0) {
+    if (pairs) {
       const int g = lane / A.L;
       q = item * A.G + g;
       t = lane % A.L;
@@ -381,7 +388,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
         lvl_warp_table(tab, P.R, P.nmax, P.wtabf, lane, t, act);
         wl = STab{tab + lane, 5};
       } else {
-        wl = A.NG == 0 ? STab{tab + lane, 5} : STab{tab + (long long)A.NG * R1 * 32, 0};
+        wl = pairs ? STab{tab + lane, 5} : STab{tab + (long long)max(A.NG, 1) * R1 * 32, 0};
       }
       walk_global<T>(P, src, 0, np, E, wl, s, pe);
       lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
@@ -551,7 +558,7 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
   const int i = (int)(item / P.ny), j = (int)(item % P.ny);
   const long long c = (long long)j * P.nx + i;
   if (redo && P.o_cnt[c] != -1) return;
-  const int s0 = max(0, j - R), s1 = min(P.ny - 1, j + R);
+  const int s0 = max(0, j - A.yw), s1 = min(P.ny - 1, j + A.yw);
   const long long qb = (long long)i * P.ny;
   int carry = 0;
   for (int base = s0; base <= s1; base += 32) {
@@ -679,8 +686,8 @@ DXD void lgather_lane(const LvlParams<T>& A, long long item, bool act, int lane,
     i = (int)(item / P.ny);
     j = (int)(item % P.ny);
     c = (long long)j * P.nx + i;
-    s0 = max(0, j - R);
-    s1 = min(P.ny - 1, j + R);
+    s0 = max(0, j - A.yw);
+    s1 = min(P.ny - 1, j + A.yw);
     qb = (long long)i * P.ny;
   }
   // f(l, pointer to r) over the column's intervals
