@@ -14,7 +14,9 @@ The arithmetic lives in ``oracle.c`` (plain brute-force gather, see its header):
                    point membership of each column's elementary intervals, then the closure;
   * ``shell`` = difference(dilate(S), erode(S))  (Sec. 4 "3D Printing", the teaser figure);
   * ``dilate_slices`` / ``erode_slices`` -- Sec. 3.2's 2D offsets for every row at once: the
-                   same gather over the output column's own row only (a disk in the x-z plane).
+                   same gather over the output column's own row only (a disk in the x-z plane);
+  * ``raycast`` -- analytic spheres, boxes and hollow spheres cast at the column centres
+                   (Sec. 1: implicit shapes to ray representations), chords united per column.
 ``complement`` builds the per-column complement with +-inf sentinels (Sec. 3.1: the complement
 is trivial in a ray representation); tests use it to check erosion/dilation duality.
 
@@ -62,6 +64,11 @@ def _load():
                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
         lib.oracle_offset_slices.restype = ctypes.c_int64
         lib.oracle_offset_slices.argtypes = lib.oracle_offset.argtypes
+        lib.oracle_raycast.restype = ctypes.c_int64
+        lib.oracle_raycast.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
+                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]
         lib.oracle_free.restype = None
         lib.oracle_free.argtypes = [ctypes.c_void_p]
         lib.oracle_boolean.restype = ctypes.c_int64
@@ -206,6 +213,39 @@ def difference(a, b):
 def shell(grid, k: float, threads=None):
     """Thick shell: the dilation minus the erosion (Sec. 4 "3D Printing", teaser figure)."""
     return difference(dilate(grid, k, threads=threads), erode(grid, k, threads=threads))
+
+
+_KIND = {"sphere": 0, "box": 1, "shell": 2}
+
+
+def prim_arrays(prims):
+    """(kind int32[n], params float64[n, 8]) of primitive tuples ("sphere", cx, cy, cz, R),
+    ("box", x0, x1, y0, y1, z0, z1), ("shell", cx, cy, cz, R, t)."""
+    kind = np.array([_KIND[p[0]] for p in prims], np.int32)
+    prm = np.zeros((max(len(prims), 1), 8), np.float64)
+    for q, p in enumerate(prims):
+        prm[q, : len(p) - 1] = p[1:]
+    return kind, prm
+
+
+def raycast(prims, nx: int, ny: int, h: float):
+    """Ray-cast primitives at the column centres of an nx x ny grid of spacing h (Sec. 1,
+    implicit shapes to ray representations; Sec. 3.1 dexels)."""
+    from synth.shapes import DexelGrid  # container only
+    lib = _load()
+    kind, prm = prim_arrays(prims)
+    po = ctypes.POINTER(ctypes.c_int64)()
+    pz = ctypes.POINTER(ctypes.c_double)()
+    total = lib.oracle_raycast(nx, ny, float(h), kind.ctypes.data, prm.ctypes.data, len(prims),
+                               ctypes.byref(po), ctypes.byref(pz))
+    if total < 0:
+        raise ValueError("oracle_raycast rejected its arguments")
+    n = nx * ny
+    off = np.ctypeslib.as_array(po, shape=(n + 1,)).copy()
+    z = np.ctypeslib.as_array(pz, shape=(max(total, 1) * 2,))[: 2 * total].copy().reshape(-1, 2)
+    lib.oracle_free(ctypes.cast(po, ctypes.c_void_p))
+    lib.oracle_free(ctypes.cast(pz, ctypes.c_void_p))
+    return DexelGrid(nx, ny, h, off, z)
 
 
 def complement(grid):

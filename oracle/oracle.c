@@ -410,3 +410,82 @@ int64_t oracle_boolean(int op, int64_t ncols, const int64_t* off_a, const double
   *out_z = oz;
   return total;
 }
+
+/*
+ * Ray casting of analytic primitives into a dexel grid (Sec. 1: implicit shapes are turned
+ * into ray representations directly, without meshing; Sec. 3.1 "Dexel Representation": the
+ * segments where the vertical ray of each column is inside the solid).  Column (i, j) of an
+ * nx x ny grid of spacing h casts the ray x = (i + 1/2) h, y = (j + 1/2) h.  Primitives, 8
+ * doubles each after an int kind:
+ *   0 sphere (cx cy cz R): chord cz -+ sqrt(R^2 - d^2) where d^2 = (x-cx)^2 + (y-cy)^2 < R^2;
+ *   1 box (x0 x1 y0 y1 z0 z1): [z0, z1] where x0 < x < x1 and y0 < y < y1;
+ *   2 shell (cx cy cz R t): the sphere of radius R minus the open sphere of radius R - t:
+ *     one chord where the ray misses the inner sphere, else the two chords between them.
+ * Tangent rays (zero-length chords) are excluded by the strict inequalities.  The chords of a
+ * column are united (closed union, as everywhere else here).
+ */
+static void raycast_column(const int* kind, const double* prm, int nprim, double x, double y,
+                           ivec* out) {
+  out->n = 0;
+  for (int p = 0; p < nprim; ++p) {
+    const double* q = prm + 8 * (size_t)p;
+    if (kind[p] == 1) {
+      if (x > q[0] && x < q[1] && y > q[2] && y < q[3]) ivec_push(out, q[4], q[5]);
+      continue;
+    }
+    const double d2 = (x - q[0]) * (x - q[0]) + (y - q[1]) * (y - q[1]);
+    const double R = q[3];
+    if (!(d2 < R * R)) continue;
+    const double so = sqrt(R * R - d2);
+    if (kind[p] == 0) {
+      ivec_push(out, q[2] - so, q[2] + so);
+    } else {
+      const double Ri = R - q[4];
+      if (d2 < Ri * Ri) {
+        const double si = sqrt(Ri * Ri - d2);
+        ivec_push(out, q[2] - so, q[2] - si);
+        ivec_push(out, q[2] + si, q[2] + so);
+      } else {
+        ivec_push(out, q[2] - so, q[2] + so);
+      }
+    }
+  }
+  sort_merge(out);
+}
+
+/* Ray-cast nprim primitives on an nx x ny grid of spacing h; result as for oracle_offset. */
+int64_t oracle_raycast(int32_t nx, int32_t ny, double h, const int* kind, const double* prm,
+                       int nprim, int64_t** out_off, double** out_z) {
+  if (nx <= 0 || ny <= 0 || !(h > 0) || nprim < 0 || !out_off || !out_z) return -1;
+  const int64_t ncols = (int64_t)nx * ny;
+  ivec* res = (ivec*)calloc((size_t)ncols, sizeof(ivec));
+  if (!res) return -1;
+  int64_t total = 0;
+  for (int64_t c = 0; c < ncols; ++c) {
+    const double x = ((double)(c % nx) + 0.5) * h, y = ((double)(c / nx) + 0.5) * h;
+    raycast_column(kind, prm, nprim, x, y, &res[c]);
+    total += res[c].n;
+  }
+  int64_t* off = (int64_t*)malloc((size_t)(ncols + 1) * sizeof(int64_t));
+  double* oz = (double*)malloc((size_t)(total > 0 ? 2 * total : 2) * sizeof(double));
+  if (!off || !oz) {
+    free(off);
+    free(oz);
+    for (int64_t t = 0; t < ncols; ++t) free(res[t].v);
+    free(res);
+    return -1;
+  }
+  off[0] = 0;
+  for (int64_t c = 0; c < ncols; ++c) {
+    for (int64_t s = 0; s < res[c].n; ++s) {
+      oz[2 * (off[c] + s)] = res[c].v[s].a;
+      oz[2 * (off[c] + s) + 1] = res[c].v[s].b;
+    }
+    off[c + 1] = off[c] + res[c].n;
+    free(res[c].v);
+  }
+  free(res);
+  *out_off = off;
+  *out_z = oz;
+  return total;
+}
