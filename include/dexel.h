@@ -64,6 +64,16 @@ typedef enum { DEXEL_FP64 = 0, DEXEL_FP32_PRED64 = 1 } dexel_mode;
 
 typedef enum { DEXEL_DILATE = 0, DEXEL_ERODE = 1, DEXEL_CLOSE = 2, DEXEL_OPEN = 3 } dexel_op;
 
+/* Analytic primitives for dexel_raycast (world units; the grid's columns sit at
+ * ((i + 1/2) h, (j + 1/2) h)). */
+typedef enum { DEXEL_SPHERE = 0, DEXEL_BOX = 1, DEXEL_SHELL = 2 } dexel_prim_kind;
+typedef struct {
+  int32_t kind;  /* dexel_prim_kind */
+  int32_t pad;
+  double p[7];   /* sphere: cx cy cz R; box: x0 x1 y0 y1 z0 z1; shell (hollow sphere, outer
+                    radius R, inner radius R - t): cx cy cz R t */
+} dexel_prim;
+
 /* Boolean operations of two grids (CSG in dexel space). */
 typedef enum { DEXEL_UNION = 0, DEXEL_INTERSECT = 1, DEXEL_DIFFERENCE = 2 } dexel_bool_op;
 
@@ -169,6 +179,21 @@ dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
 dexel_status dexel_offset_slices(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
                                  dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
                                  void* stream);
+
+/* Ray casting of analytic primitives into a dexel grid (Sec. 1: implicit shapes turn into
+ * ray representations directly, without meshing; Sec. 3.1 "Dexel Representation").  Column
+ * (i, j) of the nx x ny grid of spacing h casts the vertical ray through ((i+1/2)h,
+ * (j+1/2)h): a sphere gives the chord cz -+ sqrt(R^2 - d^2) where d^2 < R^2, a box [z0, z1]
+ * where x0 < x < x1 and y0 < y < y1, a hollow sphere the sphere's chord minus the inner
+ * sphere's open chord; tangent rays give nothing.  The chords of a column are united (closed
+ * union); FP32 mode rounds the united ends to the nearest float and joins segments that then
+ * touch.  The heights are computed with correctly rounded double operations, one at a time.
+ *   prims : DEVICE array of nprim primitives (caller-owned).
+ *   out   : as for dexel_dilate; out->nseg = -1 with DEXEL_ERR_CAPACITY when a column is hit by
+ *           more than 160 chords (not an output-size problem). */
+dexel_status dexel_raycast(dexel_ctx* ctx, const dexel_prim* prims, int32_t nprim, int32_t nx,
+                           int32_t ny, double h, dexel_mode mode, dexel_grid_out* out, void* ws,
+                           size_t ws_bytes, void* stream);
 
 /* Boolean operation of two grids of the same size (CSG carried out in dexel space, Sec. 2
  * "(3)": the rays of a column combine on their own), column by column:

@@ -248,6 +248,27 @@ def raycast(prims, nx: int, ny: int, h: float):
     return DexelGrid(nx, ny, h, off, z)
 
 
+def round_float32(grid):
+    """Each end rounded to the nearest float32, then segments that touch or overlap joined
+    (a valid float32 grid: strictly positive gaps)."""
+    from synth.shapes import DexelGrid  # container only
+    n = grid.nx * grid.ny
+    out_off = np.zeros(n + 1, np.int64)
+    cols = []
+    for c in range(n):
+        segs = np.asarray(grid.z[grid.col_off[c]:grid.col_off[c + 1]], np.float64).astype(np.float32)
+        res = []
+        for a, b in segs:
+            if res and a <= res[-1][1]:
+                res[-1][1] = max(res[-1][1], b)
+            else:
+                res.append([a, b])
+        cols.append(res)
+        out_off[c + 1] = out_off[c] + len(res)
+    z = np.array([s for col in cols for s in col], np.float32).reshape(-1, 2)
+    return DexelGrid(grid.nx, grid.ny, grid.h, out_off, z)
+
+
 def complement(grid):
     """Per-column complement within the grid: (-inf, a1], [b1, a2], ..., [bn, +inf).
 

@@ -21,12 +21,15 @@ import numpy as np
 
 __all__ = ["Grid", "Context", "dilate", "erode", "close", "open_", "boolean", "shell", "lib",
            "DexelError", "FP64", "FP32_PRED64", "UNION", "INTERSECT", "DIFFERENCE",
-           "dilate_slices", "erode_slices"]
+           "dilate_slices", "erode_slices", "raycast"]
 
 FP64 = 0
 FP32_PRED64 = 1
 DILATE, ERODE, CLOSE, OPEN = 0, 1, 2, 3
 UNION, INTERSECT, DIFFERENCE = 0, 1, 2
+# dexel_prim: int32 kind, int32 pad, 7 doubles
+PRIM_DTYPE = np.dtype([("kind", "<i4"), ("pad", "<i4"), ("p", "<f8", (7,))])
+PRIM_KIND = {"sphere": 0, "box": 1, "shell": 2}
 STATUS = {0: "ok", -1: "invalid argument", -2: "malformed CSR dexel grid",
           -3: "capacity too small", -4: "CUDA runtime error", -5: "device wait timeout",
           -6: "out of memory"}
@@ -70,6 +73,9 @@ def lib():
         L.dexel_morph.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_validate.argtypes = [P, ctypes.POINTER(_In), ctypes.c_int, P, ctypes.c_size_t, P]
+        L.dexel_raycast.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Out), P,
+                                    ctypes.c_size_t, P]
         L.dexel_offset_slices.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_boolean.argtypes = [P, ctypes.c_int, ctypes.POINTER(_In), ctypes.POINTER(_In),
@@ -251,6 +257,27 @@ class Context:
             self.ptr, op, ctypes.byref(ia), ctypes.byref(ib), a.mode, ctypes.byref(out), None, 0, st),
             "dexel_boolean")
 
+    def raycast(self, prims, nx: int, ny: int, h: float, dtype=None, stream=None) -> Grid:
+        """Ray-cast primitives ("sphere", cx, cy, cz, R) / ("box", x0, x1, y0, y1, z0, z1) /
+        ("shell", cx, cy, cz, R, t) at the column centres of an nx x ny grid of spacing h
+        (dexel_raycast); dtype float64 (default) or float32 endpoints."""
+        torch = _torch()
+        dtype = dtype or torch.float64
+        rec = np.zeros(len(prims), dtype=PRIM_DTYPE)
+        for q, p in enumerate(prims):
+            rec["kind"][q] = PRIM_KIND[p[0]]
+            rec["p"][q, : len(p) - 1] = p[1:]
+        dev = torch.device("cuda", self.device)
+        buf = torch.from_numpy(rec.view(np.uint8).copy()).to(dev) if len(prims) else None
+        st = self._stream(stream)
+        mode = FP64 if dtype == torch.float64 else FP32_PRED64
+        like = Grid(nx, ny, h, torch.empty(1, dtype=torch.int32, device=dev),
+                    torch.empty((0, 2), dtype=dtype, device=dev))
+        ptr = buf.data_ptr() if buf is not None else None
+        return self._call_out(nx, ny, h, like, max(4 * nx * ny, 1024), lambda out: lib().dexel_raycast(
+            self.ptr, ptr, len(prims), nx, ny, float(h), mode, ctypes.byref(out), None, 0, st),
+            "dexel_raycast")
+
     def slices(self, op: int, g: Grid, k: float, stream=None) -> Grid:
         """Every row of g a 2D image, dilated (op DILATE) or eroded (ERODE) by a disk of radius
         k spacings (dexel_offset_slices)."""
@@ -372,3 +399,10 @@ def dilate_slices(g: Grid, k: float, ctx: Context | None = None, stream=None) ->
 def erode_slices(g: Grid, k: float, ctx: Context | None = None, stream=None) -> Grid:
     """Every row a 2D dexel image eroded by a disk of radius k spacings."""
     return (ctx or _default_ctx(g)).slices(ERODE, g, k, stream)
+
+
+def raycast(prims, nx: int, ny: int, h: float, dtype=None, device: int = 0) -> Grid:
+    """Ray-cast analytic primitives into a dexel grid on the GPU (dexel_raycast)."""
+    if device not in _ctx:
+        _ctx[device] = Context(device)
+    return _ctx[device].raycast(prims, nx, ny, h, dtype)

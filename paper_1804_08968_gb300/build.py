@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdexel.so")
-SOURCES = ["api.cu", "batch.cu", "csg.cu", "pass1.cu", "pass1g.cu", "pass1l.cu", "pass1m.cu", "pass2.cu", "pass2g.cu", "pass2l.cu"]
+SOURCES = ["api.cu", "batch.cu", "csg.cu", "pass1.cu", "pass1g.cu", "pass1l.cu", "pass1m.cu", "pass2.cu", "pass2g.cu", "pass2l.cu", "raycast.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

@@ -1415,6 +1415,79 @@ dexel_status dexel_offset_slices(dexel_ctx* ctx, const dexel_grid_in* in, double
   return offset(ctx, in, k, op == DEXEL_ERODE, mode, out, ws, ws_bytes, stream, true);
 }
 
+dexel_status dexel_raycast(dexel_ctx* ctx, const dexel_prim* prims, int32_t nprim, int32_t nx,
+                           int32_t ny, double h, dexel_mode mode, dexel_grid_out* out, void* ws,
+                           size_t ws_bytes, void* stream) {
+  if (!ctx || !out || !out->col_off || (out->capacity_seg > 0 && !out->z) || out->capacity_seg < 0)
+    return DEXEL_ERR_INVALID_ARG;
+  if (nx < 1 || ny < 1 || nx > 32768 || ny > 32768 || (long long)nx * ny > (1LL << 30))
+    return DEXEL_ERR_INVALID_ARG;
+  if (!(h > 0) || !std::isfinite(h) || nprim < 0 || (nprim > 0 && !prims)) return DEXEL_ERR_INVALID_ARG;
+  if (mode != DEXEL_FP64 && mode != DEXEL_FP32_PRED64) return DEXEL_ERR_INVALID_ARG;
+  reset_call(ctx);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DEXEL_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long ncols = (long long)nx * ny;
+  auto plan = [&](Carver& C, void** pctr, void** pcnt, void** ppos, void** psums) {
+    *pctr = C.take(sizeof(Counters));
+    *pcnt = C.take(sizeof(long long) * (ncols + 1));
+    *ppos = C.take(sizeof(long long) * (ncols + 1));
+    *psums = C.take(sizeof(long long) * ((ncols + kScanTile) / kScanTile + 2));
+  };
+  Carver probe{nullptr, (size_t)-1};
+  void *pctr, *pcnt, *ppos, *psums;
+  plan(probe, &pctr, &pcnt, &ppos, &psums);
+  const size_t need = align_up(probe.used, 256) + 256;
+  void* base = ws;
+  size_t bytes = ws_bytes;
+  ctx->last_required = need;
+  if (ws) {
+    if (ws_bytes < need) return DEXEL_ERR_CAPACITY;
+  } else {
+    dexel_status s = ensure_owned(ctx, need);
+    if (s != DEXEL_OK) return s;
+    base = ctx->own;
+    bytes = ctx->own_bytes;
+  }
+  Carver C{(char*)base, bytes};
+  plan(C, &pctr, &pcnt, &ppos, &psums);
+  if (!C.ok) return DEXEL_ERR_CAPACITY;
+  Counters* ctr = (Counters*)pctr;
+  CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+  const bool f64 = mode == DEXEL_FP64;
+  CK(f64 ? launch_raycast<double>(prims, nprim, nx, ncols, h, (long long*)pcnt, nullptr, nullptr, ctr,
+                                  false, st)
+         : launch_raycast<float>(prims, nprim, nx, ncols, h, (long long*)pcnt, nullptr, nullptr, ctr,
+                                 false, st));
+  const long long nsb = (ncols + kScanTile - 1) / kScanTile;
+  k_scan1<long long><<<(unsigned)nsb, kScanThreads, 0, st>>>(ncols, (const long long*)pcnt,
+                                                            (long long*)ppos, (long long*)psums);
+  k_scan2<<<1, kScanThreads, 0, st>>>(nsb, (long long*)psums);
+  k_scan3<<<(unsigned)((ncols + 1 + 255) / 256), 256, 0, st>>>(ncols, (long long*)ppos,
+                                                              (const long long*)psums, out->col_off, ctr);
+  ctx->launches += 4;
+  CK(cudaGetLastError());
+  long long total = 0;
+  Counters hc;
+  CK(cudaMemcpyAsync(&total, (long long*)psums + nsb, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hc.status & ST_OVERFLOW_SLOT) {
+    out->nseg = -1;  // a column beyond the chords a thread holds
+    return DEXEL_ERR_CAPACITY;
+  }
+  out->nseg = total;
+  if ((hc.status & ST_TOO_MANY_OUT) || total > out->capacity_seg) return DEXEL_ERR_CAPACITY;
+  CK(f64 ? launch_raycast<double>(prims, nprim, nx, ncols, h, nullptr, (const long long*)ppos,
+                                  (double*)out->z, ctr, true, st)
+         : launch_raycast<float>(prims, nprim, nx, ncols, h, nullptr, (const long long*)ppos,
+                                 (float*)out->z, ctr, true, st));
+  ++ctx->launches;
+  CK(cudaStreamSynchronize(st));
+  ctx->stats[3] = total;
+  return DEXEL_OK;
+}
+
 dexel_status dexel_boolean(dexel_ctx* ctx, dexel_bool_op op, const dexel_grid_in* a,
                            const dexel_grid_in* b, dexel_mode mode, dexel_grid_out* out, void* ws,
                            size_t ws_bytes, void* stream) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <vector>
+#include "../../include/dexel.h"
 #include "gather2.cuh"
 
 namespace dexel {
@@ -86,6 +87,14 @@ cudaError_t launch_bool_count(int op, long long ncols, const int* oa, const T* z
 template <typename T>
 cudaError_t launch_bool_write(int op, long long ncols, const int* oa, const T* za, const int* ob,
                               const T* zb, const long long* pos, T* zo, cudaStream_t st);
+
+// Ray casting of primitives into a grid (raycast.cu): a counting launch (write false: cnt[c]
+// = segments of column c) or a writing launch at the scanned positions pos; a column with more
+// chords than a thread holds sets ST_OVERFLOW_SLOT
+template <typename T>
+cudaError_t launch_raycast(const dexel_prim* prims, int nprim, int nx, long long ncols, double h,
+                           long long* cnt, const long long* pos, T* zo, Counters* ctr, bool write,
+                           cudaStream_t st);
 
 // Batched offsets (batch.cu): one launch per stage over many shapes.  An item's status after
 // batch_run: DEXEL_OK, DEXEL_ERR_BAD_CSR, DEXEL_ERR_CAPACITY (nseg holds the need), or 1 when
