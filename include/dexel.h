@@ -109,8 +109,8 @@ typedef struct dexel_ctx dexel_ctx;
  *                                   density)
  *   DEXEL_PASS1_RING=0|1            pass 1 in one walk through per-lane ring regions (1,
  *                                   default) or in a counting and a writing walk
- *   DEXEL_PASS1_RING_CAP=16..128    pieces a lane's ring region holds (a tile with a lane
- *                                   beyond it is walked again into place)
+ *   DEXEL_PASS1_RING_CAP=16..1024   pieces a lane's ring region holds (default up to 128;
+ *                                   a tile with a lane beyond it is walked again into place)
  *   DEXEL_PASS1_ECAP_RULE=mean|max  event room a tile by the mean density of the windows, the
  *                                   few denser columns redone by a second launch (mean,
  *                                   default), or room for the densest window from the start
@@ -311,8 +311,9 @@ int dexel_last_kernel_ms(const dexel_ctx* ctx, double* ms, int max);
  * offsets), [7] attempts the last offset needed (the library grows its scratch and retries
  * when it owns the workspace), [8] second launches of the pass-1 window kernel for columns
  * whose window outgrew the first launch's event room, [9] blocks of y lines the offset ran in
- * (S_mid and the level lists exist for one block at a time; 1: the whole grid at once).
- * Returns the number of entries written (at most max, 10 in all). */
+ * (S_mid and the level lists exist for one block at a time; 1: the whole grid at once),
+ * [10] pass-1 tiles walked twice because a lane outgrew its ring region.  Returns the number
+ * of entries written (at most max, 11 in all). */
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max);
 
 /* Diagnostic counters of the last call: clock cycles per phase of the y sweep and mean

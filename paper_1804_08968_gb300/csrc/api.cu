@@ -46,7 +46,8 @@ struct dexel_ctx {
   // take before an offset is split into blocks; noblock: a fallback needed the whole grid
   double block_bytes = 48e9;
   bool noblock = false;
-  int p1l_ring_cap = 0; // pieces a lane's ring region holds at most (0: up to 128)
+  int p1l_ring_cap = 0; // pieces a lane's ring region holds at most (0: up to p1l_ring_max)
+  int p1l_ring_max = 128;
   long long batch_max_cols = 131072;  // larger shapes of a batch take the single-shape path
   // the level walks read S_mid itself (no packed copy) at reach >= 32: off by default
   // (measured: 0.04 ms a k = 32 offset faster on the 512^2 workload, 20 % slower at k = 64
@@ -69,7 +70,7 @@ struct dexel_ctx {
   double stage_ms[5] = {0, 0, 0, 0, 0};
   double kernel_ms[4] = {0, 0, 0, 0};  // pass-1 kernel, k_levels, k_lgather, S_mid pack
   bool kernel_rec[4] = {false, false, false, false};
-  long long stats[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  long long stats[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long phase[16] = {};
 };
 
@@ -502,7 +503,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms) * 256;
           if (redo_ok) thr = std::max<long long>(thr, (long long)pass1l_blocks(nx, ny, K, ecapR, 8, sms) * 256);
           const long long esz = 2 * (long long)sizeof(Key) + 2;
-          long long rc = std::min<long long>(128, (long long)bF / (thr * esz)) & ~7LL;
+          long long rc = std::min<long long>(ctx->p1l_ring_max, (long long)bF / (thr * esz)) & ~7LL;
           if (ctx->p1l_ring_cap > 0) rc = std::min<long long>(rc, ctx->p1l_ring_cap);
           if (rc >= 16 && ctx->p1l_ring) {
             const long long n = thr * rc;
@@ -592,6 +593,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       CK(cudaStreamSynchronize(st));
     }
     mark(ctx, 3, st);
+    ctx->stats[10] += hc.ring_spills;
     ctx->needF = std::max<long long>(ctx->needF, (long long)(hc.arena_top[0] * to_grid));
     ctx->needM = std::max<long long>(ctx->needM, (long long)(hc.arena_top[1] * to_grid));
     mid_sum += (long long)hc.mid_total;
@@ -1253,7 +1255,10 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   }
   if (const char* e = getenv("DEXEL_PASS1_RING_CAP")) {
     const int v = atoi(e);
-    if (v >= 16 && v <= 128) c->p1l_ring_cap = v & ~7;
+    if (v >= 16 && v <= 1024) {
+      c->p1l_ring_cap = v & ~7;
+      c->p1l_ring_max = std::max(c->p1l_ring_max, c->p1l_ring_cap);
+    }
   }
   if (const char* e = getenv("DEXEL_BATCH_MAX_COLS")) c->batch_max_cols = atoll(e);
   if (const char* e = getenv("DEXEL_LEVELS_EXACT")) c->levels_exact = atoi(e) != 0;
@@ -1322,7 +1327,7 @@ int dexel_last_phases(const dexel_ctx* ctx, uint64_t* ph, int max) {
 
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max) {
   if (!ctx || !stats) return 0;
-  int n = max < 10 ? max : 10;
+  int n = max < 11 ? max : 11;
   for (int q = 0; q < n; ++q) stats[q] = ctx->stats[q];
   return n;
 }

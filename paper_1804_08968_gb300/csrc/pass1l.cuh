@@ -37,7 +37,7 @@ constexpr int kP1TileWords = 5;
 // bounds, chunk toggle masks, per (chunk, lane) counts, last run starts and open-run flags,
 // the columns' offsets in the tile, tile base and ring-overflow flag.
 struct P1LLayout {
-  long long ek, ep, eoff, cb, cm, ccnt, cst, cco, cex, misc, total;
+  long long ek, ep, eoff, cb, cm, ccnt, cst, cco, cex, misc, wt, total;
 };
 DXI long long p1l_align(long long x) { return (x + 15) & ~15LL; }
 DXI P1LLayout p1l_layout(int R, int ecap, int warps) {
@@ -53,6 +53,7 @@ DXI P1LLayout p1l_layout(int R, int ecap, int warps) {
   o.cco = x; x = p1l_align(x + (long long)warps * 32 * sizeof(int));
   o.cex = x; x = p1l_align(x + 32 * sizeof(int));
   o.misc = x; x = p1l_align(x + 2 * sizeof(long long));
+  o.wt = x; x = p1l_align(x + (long long)(R + 1) * sizeof(float));  // pruning: w(dx) at level 0
   o.total = x;
   return o;
 }
@@ -112,7 +113,8 @@ DXD CMask<NH> cmask_from(const ukey* T, int pc, int R) {
 // exactly.  Each lane keeps its last kept piece in registers: a new piece that dominates it
 // replaces it, a new piece it dominates is not emitted.
 struct Prune {
-  const float* w;  // float half-widths w[n] = h sqrt(k^2 - n) (null: no pruning)
+  const float* w;  // float half-widths at level 0 by label: w[dx] = h sqrt(k^2 - dx^2) (null:
+                   // no pruning)
   float E;         // margin of the float test
 };
 struct PTop {
@@ -139,13 +141,15 @@ DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int
   last_start = ~0ULL;
   if (c0 >= c1) return 0;
   ukey gkey = ek[c0];
-  const ukey first = gkey;
   bool carried = Om < kNoLabel;  // the first run closed began before the chunk
   PTop top{0.0f, 0.0f, 0, false, false};
-  auto emit = [&](ukey a, ukey b, int l, bool fixed) {
+  // float approximations of the current run's start (for a carried run: the chunk's first
+  // height) and of the current height, converted once a group
+  float run_af = pr.w ? keyf(gkey) : 0.0f;
+  auto emit = [&](ukey a, ukey b, float af, float bf, int l, bool fixed) {
     if (pr.w) {
-      const float w = pr.w[l * l];
-      const float lo = keyf(fixed ? first : a) - w, hi = keyf(b) + w;
+      const float w = pr.w[l];
+      const float lo = af - w, hi = bf + w;
       if (top.have && !top.fixed && l < top.l && lo <= top.lo - pr.E && hi >= top.hi + pr.E) {
         --cnt;  // the new piece dominates the last kept one: it takes its place
       } else if (top.have && top.l < l && !fixed && top.lo <= lo - pr.E && top.hi >= hi + pr.E) {
@@ -164,13 +168,15 @@ DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int
     const int Ok = cnearest<NH>(m);
     const bool pt = gmin < (Om < Ok ? Om : Ok);
     const bool ch = Ok != Om || pt;
+    const float vf = (pr.w && (ch || pt)) ? keyf(v) : 0.0f;
     if (Om < kNoLabel && ch) {  // the run below v ends at v
-      emit(run_a, v, Om, carried);
+      emit(run_a, v, run_af, vf, Om, carried);
       carried = false;
     }
-    if (pt) emit(v, v, gmin, false);  // the point [v, v]
+    if (pt) emit(v, v, vf, vf, gmin, false);  // the point [v, v]
     if (Ok < kNoLabel && ch) {  // a run starts at v
       run_a = v;
+      run_af = vf;
       last_start = v;
       carried = false;
     }
@@ -256,6 +262,10 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
   const long long rb = (long long)j * P.nx;
   if (P.redo && (P.rowmark == nullptr || P.rowmark[j] == 0)) return;  // nothing to redo here
   G.sync();  // the previous tile is done with the shared memory
+  if (P.prune_w) {  // the pruning test's half-widths at level 0, by label
+    float* wt = (float*)(smem + Lo.wt);
+    for (int l = G.gtid; l <= R; l += W * 32) wt[l] = P.prune_w[l * l];
+  }
   if (warp == 0) {  // event slots of the window's sources (exclusive prefix)
     int carry = 0;
     for (int base = 0; base < ns; base += 32) {
@@ -406,7 +416,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     const bool ring = P.r_a != nullptr && rg0 + (long long)W * 32 * P.r_cap <= P.r_n;
     const long long rbase = ring ? (long long)(warp * 32 + lane) * P.r_cap : 0;
     int n;
-    const Prune pr{P.prune_w, P.prune_E};
+    const Prune pr{P.prune_w ? (const float*)(smem + Lo.wt) : nullptr, P.prune_E};
     if (ring)
       n = chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, 0ULL, last, rg_a + rbase,
                                   rg_b + rbase, rg_l + rbase, P.r_cap, pr);
@@ -449,6 +459,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     const long long s = misc[0];
     const bool fits = s + tot <= P.m_cap;
     const bool spilled = ((const int*)misc)[2] != 0;
+    if (ring && spilled && fits && G.gtid == 0) atomicAdd(&P.ctr->ring_spills, 1);  // walked twice
     if (fits && ring && !spilled) {
       // the ring regions into the arena: a warp a column, lanes over its pieces (coalesced)
       for (int x = warp; x < 32; x += W) {

@@ -54,6 +54,8 @@ struct Counters {
   unsigned zmax_bits;             // gather: bits of max |finite height| of S_mid (float >= 0)
   int over_cols;                  // level gather: columns whose lists outgrew the bucket
   int over_max;                   //   and the most intervals one of them collected
+  int ring_spills;                // pass-1 window kernel: tiles walked twice (a lane's ring
+                                  // region overflowed)
   unsigned long long phase[16];   // optional per-phase clock totals (DEXEL_PHASES builds)
 };
 
