@@ -116,7 +116,8 @@ typedef struct dexel_ctx dexel_ctx;
  *                                   default), or room for the densest window from the start
  *   DEXEL_BLOCK_MB=n                split an offset into blocks of whole y lines when its
  *                                   S_mid, packed copy and level lists would take more than
- *                                   n MB (default 48000)
+ *                                   n MB (default: 0.45 of the device memory free when the
+ *                                   context is created)
  *   DEXEL_PASS1_PRUNE=0|1           drop S_mid pieces whose capsule slice a neighbouring
  *                                   piece with a smaller dx contains at every level (1,
  *                                   default; the result is the same)
@@ -194,6 +195,26 @@ dexel_status dexel_offset_slices(dexel_ctx* ctx, const dexel_grid_in* in, double
 dexel_status dexel_raycast(dexel_ctx* ctx, const dexel_prim* prims, int32_t nprim, int32_t nx,
                            int32_t ny, double h, dexel_mode mode, dexel_grid_out* out, void* ws,
                            size_t ws_bytes, void* stream);
+
+/* The same with rays along axis 0 (x), 1 (y) or 2 (z, as dexel_raycast): the grid then spans
+ * the other two axes in cyclic order -- x rays: columns over (y, z), heights are x; y rays:
+ * columns over (z, x), heights are y -- so that the three views of one solid form a layered
+ * depth image (three dexel sets, one an axis; Sec. 5, future work). */
+dexel_status dexel_raycast_axis(dexel_ctx* ctx, const dexel_prim* prims, int32_t nprim,
+                                int32_t axis, int32_t nx, int32_t ny, double h, dexel_mode mode,
+                                dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Offset of a three-view layered depth image (Sec. 5: "directly work on a LDI offset, i.e.
+ * representing the shape with 3 dexel representations, one for each axis"; Sec. 4 notes the
+ * threefold cost).  views[0..2] are the dexel sets of one solid along z, x and y (as made by
+ * dexel_raycast_axis with axis 2, 0, 1), all with the same spacing h; the ball is isotropic,
+ * so each view is offset on its own by the two-pass method: outs[v] receives
+ * op(views[v]) for op in DEXEL_DILATE / ERODE / CLOSE / OPEN.  Host arrays of 3 entries with
+ * device buffers; each output follows dexel_dilate's contract (outs[v].nseg the need on
+ * DEXEL_ERR_CAPACITY).  Returns the first failing status.  Stats sum over the views. */
+dexel_status dexel_offset_ldi(dexel_ctx* ctx, const dexel_grid_in* views, double k, dexel_op op,
+                              dexel_mode mode, dexel_grid_out* outs, void* ws, size_t ws_bytes,
+                              void* stream);
 
 /* Boolean operation of two grids of the same size (CSG carried out in dexel space, Sec. 2
  * "(3)": the rays of a column combine on their own), column by column:

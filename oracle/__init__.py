@@ -269,6 +269,29 @@ def round_float32(grid):
     return DexelGrid(grid.nx, grid.ny, grid.h, out_off, z)
 
 
+def view_prims(prims, axis: int):
+    """The primitives seen from rays along axis 0 (x) or 1 (y): coordinates cycled so that the
+    ray runs along the third one (x rays: columns over (y, z); y rays: columns over (z, x));
+    axis 2 leaves them as they are."""
+    if axis == 2:
+        return list(prims)
+    u, v, w = (1, 2, 0) if axis == 0 else (2, 0, 1)
+    out = []
+    for p in prims:
+        if p[0] == "box":
+            b = p[1:]
+            out.append(("box", b[2 * u], b[2 * u + 1], b[2 * v], b[2 * v + 1], b[2 * w], b[2 * w + 1]))
+        else:
+            c = p[1:4]
+            out.append((p[0], c[u], c[v], c[w]) + tuple(p[4:]))
+    return out
+
+
+def raycast_axis(prims, axis: int, nx: int, ny: int, h: float):
+    """Ray casting along axis 0, 1 or 2 (a view of a layered depth image, Sec. 5)."""
+    return raycast(view_prims(prims, axis), nx, ny, h)
+
+
 def complement(grid):
     """Per-column complement within the grid: (-inf, a1], [b1, a2], ..., [bn, +inf).
 

@@ -76,6 +76,11 @@ def lib():
         L.dexel_raycast.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Out), P,
                                     ctypes.c_size_t, P]
+        L.dexel_raycast_axis.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_double, ctypes.c_int,
+                                         ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
+        L.dexel_offset_ldi.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_offset_slices.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_boolean.argtypes = [P, ctypes.c_int, ctypes.POINTER(_In), ctypes.POINTER(_In),
@@ -258,7 +263,7 @@ class Context:
             self.ptr, op, ctypes.byref(ia), ctypes.byref(ib), a.mode, ctypes.byref(out), None, 0, st),
             "dexel_boolean")
 
-    def raycast(self, prims, nx: int, ny: int, h: float, dtype=None, stream=None) -> Grid:
+    def raycast(self, prims, nx: int, ny: int, h: float, dtype=None, stream=None, axis: int = 2) -> Grid:
         """Ray-cast primitives ("sphere", cx, cy, cz, R) / ("box", x0, x1, y0, y1, z0, z1) /
         ("shell", cx, cy, cz, R, t) at the column centres of an nx x ny grid of spacing h
         (dexel_raycast); dtype float64 (default) or float32 endpoints."""
@@ -275,9 +280,36 @@ class Context:
         like = Grid(nx, ny, h, torch.empty(1, dtype=torch.int32, device=dev),
                     torch.empty((0, 2), dtype=dtype, device=dev))
         ptr = buf.data_ptr() if buf is not None else None
-        return self._call_out(nx, ny, h, like, max(4 * nx * ny, 1024), lambda out: lib().dexel_raycast(
-            self.ptr, ptr, len(prims), nx, ny, float(h), mode, ctypes.byref(out), None, 0, st),
-            "dexel_raycast")
+        return self._call_out(nx, ny, h, like, max(4 * nx * ny, 1024), lambda out: lib().dexel_raycast_axis(
+            self.ptr, ptr, len(prims), axis, nx, ny, float(h), mode, ctypes.byref(out), None, 0, st),
+            "dexel_raycast_axis")
+
+    def offset_ldi(self, op: int, views, k: float, stream=None):
+        """The three views of a layered depth image (rays along z, x, y) each offset by op
+        (dexel_offset_ldi); returns three grids."""
+        torch = _torch()
+        if len(views) != 3 or any(v.mode != views[0].mode for v in views):
+            raise ValueError("three views of one precision")
+        ins = (_In * 3)(*[v._in() for v in views])
+        st = self._stream(stream)
+        caps = [max(4 * v.nseg + v.nx * v.ny // 4, 1024) for v in views]
+        for _ in range(3):
+            outs_t = []
+            outs = (_Out * 3)()
+            for q, v in enumerate(views):
+                off = torch.empty(v.nx * v.ny + 1, dtype=torch.int32, device=v.col_off.device)
+                z = torch.empty((caps[q], 2), dtype=v.z.dtype, device=v.z.device)
+                outs_t.append((off, z))
+                outs[q] = _Out(off.data_ptr(), z.data_ptr(), caps[q], 0)
+            rc = lib().dexel_offset_ldi(self.ptr, ins, float(k), op, views[0].mode, outs, None, 0, st)
+            if rc == -3 and any(outs[q].nseg > caps[q] for q in range(3)):
+                caps = [max(caps[q], int(outs[q].nseg) + 16) for q in range(3)]
+                continue
+            if rc != 0:
+                raise DexelError(rc, "dexel_offset_ldi")
+            return [Grid(v.nx, v.ny, v.h, outs_t[q][0], outs_t[q][1][: outs[q].nseg])
+                    for q, v in enumerate(views)]
+        raise DexelError(-3, "dexel_offset_ldi (output capacity)")
 
     def slices(self, op: int, g: Grid, k: float, stream=None) -> Grid:
         """Every row of g a 2D image, dilated (op DILATE) or eroded (ERODE) by a disk of radius
@@ -402,8 +434,9 @@ def erode_slices(g: Grid, k: float, ctx: Context | None = None, stream=None) -> 
     return (ctx or _default_ctx(g)).slices(ERODE, g, k, stream)
 
 
-def raycast(prims, nx: int, ny: int, h: float, dtype=None, device: int = 0) -> Grid:
-    """Ray-cast analytic primitives into a dexel grid on the GPU (dexel_raycast)."""
+def raycast(prims, nx: int, ny: int, h: float, dtype=None, device: int = 0, axis: int = 2) -> Grid:
+    """Ray-cast analytic primitives into a dexel grid on the GPU (dexel_raycast_axis; rays
+    along axis 2 = z by default)."""
     if device not in _ctx:
         _ctx[device] = Context(device)
-    return _ctx[device].raycast(prims, nx, ny, h, dtype)
+    return _ctx[device].raycast(prims, nx, ny, h, dtype, axis=axis)

@@ -43,7 +43,8 @@ struct dexel_ctx {
   bool p1l_ecap_max = false;  // event room for the densest window from the start (no redo)
   bool prune1 = true;   // dominance pruning of S_mid pieces in the window kernel
   // blocks of y lines: the bytes the block-scoped scratch (S_mid, its copy, level lists) may
-  // take before an offset is split into blocks; noblock: a fallback needed the whole grid
+  // take before an offset is split into blocks (0.45 of the device memory free when the
+  // context is created, or DEXEL_BLOCK_MB); noblock: a fallback needed the whole grid
   double block_bytes = 48e9;
   bool noblock = false;
   int p1l_ring_cap = 0; // pieces a lane's ring region holds at most (0: up to p1l_ring_max)
@@ -1249,6 +1250,12 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   if (const char* e = getenv("DEXEL_PASS1_RING")) c->p1l_ring = atoi(e) != 0;
   if (const char* e = getenv("DEXEL_PASS1_ECAP_RULE")) c->p1l_ecap_max = strcmp(e, "max") == 0;
   if (const char* e = getenv("DEXEL_PASS1_PRUNE")) c->prune1 = atoi(e) != 0;
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaSetDevice(device) == cudaSuccess && cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+      c->block_bytes = std::max(1e9, 0.45 * (double)fr);
+    cudaGetLastError();
+  }
   if (const char* e = getenv("DEXEL_BLOCK_MB")) {
     const double v = atof(e);
     if (v >= 1) c->block_bytes = v * 1e6;
@@ -1423,6 +1430,13 @@ dexel_status dexel_offset_slices(dexel_ctx* ctx, const dexel_grid_in* in, double
 dexel_status dexel_raycast(dexel_ctx* ctx, const dexel_prim* prims, int32_t nprim, int32_t nx,
                            int32_t ny, double h, dexel_mode mode, dexel_grid_out* out, void* ws,
                            size_t ws_bytes, void* stream) {
+  return dexel_raycast_axis(ctx, prims, nprim, 2, nx, ny, h, mode, out, ws, ws_bytes, stream);
+}
+
+dexel_status dexel_raycast_axis(dexel_ctx* ctx, const dexel_prim* prims, int32_t nprim,
+                                int32_t axis, int32_t nx, int32_t ny, double h, dexel_mode mode,
+                                dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream) {
+  if (axis < 0 || axis > 2) return DEXEL_ERR_INVALID_ARG;
   if (!ctx || !out || !out->col_off || (out->capacity_seg > 0 && !out->z) || out->capacity_seg < 0)
     return DEXEL_ERR_INVALID_ARG;
   if (nx < 1 || ny < 1 || nx > 32768 || ny > 32768 || (long long)nx * ny > (1LL << 30))
@@ -1460,10 +1474,10 @@ dexel_status dexel_raycast(dexel_ctx* ctx, const dexel_prim* prims, int32_t npri
   Counters* ctr = (Counters*)pctr;
   CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
   const bool f64 = mode == DEXEL_FP64;
-  CK(f64 ? launch_raycast<double>(prims, nprim, nx, ncols, h, (long long*)pcnt, nullptr, nullptr, ctr,
-                                  false, st)
-         : launch_raycast<float>(prims, nprim, nx, ncols, h, (long long*)pcnt, nullptr, nullptr, ctr,
-                                 false, st));
+  CK(f64 ? launch_raycast<double>(prims, nprim, axis, nx, ncols, h, (long long*)pcnt, nullptr,
+                                  nullptr, ctr, false, st)
+         : launch_raycast<float>(prims, nprim, axis, nx, ncols, h, (long long*)pcnt, nullptr,
+                                 nullptr, ctr, false, st));
   const long long nsb = (ncols + kScanTile - 1) / kScanTile;
   k_scan1<long long><<<(unsigned)nsb, kScanThreads, 0, st>>>(ncols, (const long long*)pcnt,
                                                             (long long*)ppos, (long long*)psums);
@@ -1483,14 +1497,43 @@ dexel_status dexel_raycast(dexel_ctx* ctx, const dexel_prim* prims, int32_t npri
   }
   out->nseg = total;
   if ((hc.status & ST_TOO_MANY_OUT) || total > out->capacity_seg) return DEXEL_ERR_CAPACITY;
-  CK(f64 ? launch_raycast<double>(prims, nprim, nx, ncols, h, nullptr, (const long long*)ppos,
+  CK(f64 ? launch_raycast<double>(prims, nprim, axis, nx, ncols, h, nullptr, (const long long*)ppos,
                                   (double*)out->z, ctr, true, st)
-         : launch_raycast<float>(prims, nprim, nx, ncols, h, nullptr, (const long long*)ppos,
+         : launch_raycast<float>(prims, nprim, axis, nx, ncols, h, nullptr, (const long long*)ppos,
                                  (float*)out->z, ctr, true, st));
   ++ctx->launches;
   CK(cudaStreamSynchronize(st));
   ctx->stats[3] = total;
   return DEXEL_OK;
+}
+
+dexel_status dexel_offset_ldi(dexel_ctx* ctx, const dexel_grid_in* views, double k, dexel_op op,
+                              dexel_mode mode, dexel_grid_out* outs, void* ws, size_t ws_bytes,
+                              void* stream) {
+  if (!ctx || !views || !outs) return DEXEL_ERR_INVALID_ARG;
+  if (op < DEXEL_DILATE || op > DEXEL_OPEN) return DEXEL_ERR_INVALID_ARG;
+  for (int v = 0; v < 3; ++v) {
+    if (check_in(&views[v], k) != DEXEL_OK) return DEXEL_ERR_INVALID_ARG;
+    if (!(views[v].h == views[0].h)) return DEXEL_ERR_INVALID_ARG;  // one spacing for the solid
+  }
+  long long launches = 0;
+  long long st[11] = {};
+  dexel_status first = DEXEL_OK;
+  for (int v = 0; v < 3; ++v) {
+    dexel_status s;
+    if (op == DEXEL_DILATE || op == DEXEL_ERODE) {
+      reset_call(ctx);
+      s = offset(ctx, &views[v], k, op == DEXEL_ERODE, mode, &outs[v], ws, ws_bytes, stream);
+    } else {
+      s = dexel_morph(ctx, &views[v], k, op, mode, &outs[v], ws, ws_bytes, stream);
+    }
+    launches += ctx->launches;
+    for (int q = 0; q < 11; ++q) st[q] += ctx->stats[q];
+    if (s != DEXEL_OK && first == DEXEL_OK) first = s;
+  }
+  ctx->launches = launches;
+  for (int q = 0; q < 11; ++q) ctx->stats[q] = st[q];
+  return first;
 }
 
 dexel_status dexel_boolean(dexel_ctx* ctx, dexel_bool_op op, const dexel_grid_in* a,

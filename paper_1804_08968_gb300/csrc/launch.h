@@ -92,9 +92,9 @@ cudaError_t launch_bool_write(int op, long long ncols, const int* oa, const T* z
 // = segments of column c) or a writing launch at the scanned positions pos; a column with more
 // chords than a thread holds sets ST_OVERFLOW_SLOT
 template <typename T>
-cudaError_t launch_raycast(const dexel_prim* prims, int nprim, int nx, long long ncols, double h,
-                           long long* cnt, const long long* pos, T* zo, Counters* ctr, bool write,
-                           cudaStream_t st);
+cudaError_t launch_raycast(const dexel_prim* prims, int nprim, int axis, int nx, long long ncols,
+                           double h, long long* cnt, const long long* pos, T* zo, Counters* ctr,
+                           bool write, cudaStream_t st);
 
 // Batched offsets (batch.cu): one launch per stage over many shapes.  An item's status after
 // batch_run: DEXEL_OK, DEXEL_ERR_BAD_CSR, DEXEL_ERR_CAPACITY (nseg holds the need), or 1 when

@@ -23,9 +23,30 @@ namespace dexel {
 constexpr int kRcChunk = 128;  // primitives staged in shared memory at a time
 constexpr int kRayChords = 160;  // chords a column may hold before they are united
 
+// A primitive seen from rays along axis `axis` (0: x, 1: y, 2: z): the coordinates cycled so
+// that the ray runs along the third one, the grid over the other two in cyclic order (x rays:
+// grid (y, z); y rays: grid (z, x)).
+__device__ __forceinline__ dexel_prim view_of(dexel_prim q, int axis) {
+  if (axis == 2) return q;
+  dexel_prim r = q;
+  if (q.kind == DEXEL_BOX) {
+    // bounds (x0 x1 y0 y1 z0 z1) -> (u0 u1 v0 v1 w0 w1)
+    const int u = axis == 0 ? 1 : 2, v = axis == 0 ? 2 : 0, w = axis;
+    r.p[0] = q.p[2 * u]; r.p[1] = q.p[2 * u + 1];
+    r.p[2] = q.p[2 * v]; r.p[3] = q.p[2 * v + 1];
+    r.p[4] = q.p[2 * w]; r.p[5] = q.p[2 * w + 1];
+  } else {
+    const double c[3] = {q.p[0], q.p[1], q.p[2]};
+    r.p[0] = c[axis == 0 ? 1 : 2];
+    r.p[1] = c[axis == 0 ? 2 : 0];
+    r.p[2] = c[axis];
+  }
+  return r;
+}
+
 template <typename T, bool WRITE>
-__global__ void __launch_bounds__(256) k_raycast(const dexel_prim* prims, int nprim, int nx,
-                                                 long long ncols, double h, long long* cnt,
+__global__ void __launch_bounds__(256) k_raycast(const dexel_prim* prims, int nprim, int axis,
+                                                 int nx, long long ncols, double h, long long* cnt,
                                                  const long long* pos, T* zo, Counters* ctr) {
   __shared__ dexel_prim sp[kRcChunk];
   __shared__ int sn;
@@ -51,7 +72,7 @@ __global__ void __launch_bounds__(256) k_raycast(const dexel_prim* prims, int np
     bool mine = false;
     dexel_prim own{};
     if (p0 + (int)threadIdx.x < nprim) {
-      own = prims[p0 + threadIdx.x];
+      own = view_of(prims[p0 + threadIdx.x], axis);
       double fx0, fx1, fy0, fy1;
       if (own.kind == DEXEL_BOX) {
         fx0 = own.p[0]; fx1 = own.p[1]; fy0 = own.p[2]; fy1 = own.p[3];
@@ -175,22 +196,22 @@ __global__ void __launch_bounds__(256) k_raycast(const dexel_prim* prims, int np
 }
 
 template <typename T>
-cudaError_t launch_raycast(const dexel_prim* prims, int nprim, int nx, long long ncols, double h,
-                           long long* cnt, const long long* pos, T* zo, Counters* ctr, bool write,
-                           cudaStream_t st) {
+cudaError_t launch_raycast(const dexel_prim* prims, int nprim, int axis, int nx, long long ncols,
+                           double h, long long* cnt, const long long* pos, T* zo, Counters* ctr,
+                           bool write, cudaStream_t st) {
   if (ncols <= 0) return cudaSuccess;
   const unsigned g = (unsigned)((ncols + 255) / 256);
   if (write)
-    k_raycast<T, true><<<g, 256, 0, st>>>(prims, nprim, nx, ncols, h, cnt, pos, zo, ctr);
+    k_raycast<T, true><<<g, 256, 0, st>>>(prims, nprim, axis, nx, ncols, h, cnt, pos, zo, ctr);
   else
-    k_raycast<T, false><<<g, 256, 0, st>>>(prims, nprim, nx, ncols, h, cnt, pos, zo, ctr);
+    k_raycast<T, false><<<g, 256, 0, st>>>(prims, nprim, axis, nx, ncols, h, cnt, pos, zo, ctr);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_raycast<float>(const dexel_prim*, int, int, long long, double,
+template cudaError_t launch_raycast<float>(const dexel_prim*, int, int, int, long long, double,
                                            long long*, const long long*, float*, Counters*, bool,
                                            cudaStream_t);
-template cudaError_t launch_raycast<double>(const dexel_prim*, int, int, long long, double,
+template cudaError_t launch_raycast<double>(const dexel_prim*, int, int, int, long long, double,
                                             long long*, const long long*, double*, Counters*, bool,
                                             cudaStream_t);
 
