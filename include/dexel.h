@@ -109,7 +109,7 @@ typedef struct dexel_ctx dexel_ctx;
  *                                   density)
  *   DEXEL_PASS1_RING=0|1            pass 1 in one walk through per-lane ring regions (1,
  *                                   default) or in a counting and a writing walk
- *   DEXEL_PASS1_RING_CAP=16..1024   pieces a lane's ring region holds (default up to 128;
+ *   DEXEL_PASS1_RING_CAP=16..1024   pieces a lane's ring region holds (default up to 256;
  *                                   a tile with a lane beyond it is walked again into place)
  *   DEXEL_PASS1_ECAP_RULE=mean|max  event room a tile by the mean density of the windows, the
  *                                   few denser columns redone by a second launch (mean,

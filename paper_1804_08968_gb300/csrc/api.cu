@@ -48,7 +48,9 @@ struct dexel_ctx {
   double block_bytes = 48e9;
   bool noblock = false;
   int p1l_ring_cap = 0; // pieces a lane's ring region holds at most (0: up to p1l_ring_max)
-  int p1l_ring_max = 128;
+  // (measured on the 2048^2 k = 64 workload: 128 pieces left 94 k tiles walked twice and pass
+  // 1 at 345 ms, 256 pieces 72 tiles and 283 ms, 512 none and 282 ms)
+  int p1l_ring_max = 256;
   long long batch_max_cols = 131072;  // larger shapes of a batch take the single-shape path
   // the level walks read S_mid itself (no packed copy) at reach >= 32: off by default
   // (measured: 0.04 ms a k = 32 offset faster on the 512^2 workload, 20 % slower at k = 64
