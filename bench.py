@@ -525,8 +525,10 @@ def oracle_sample(g, ncols, seed=0, k=K_MAIN):
 
 
 def calibrated_columns(g, seconds):
-    """Output columns the oracle takes about `seconds` for on this host."""
-    n0, t0 = oracle_sample(g, 200, seed=7)
+    """Output columns the oracle takes about `seconds` for on this host (the probe gives every
+    thread two of the oracle's 64-column work chunks, so that all cores are busy)."""
+    import oracle
+    n0, t0 = oracle_sample(g, 128 * oracle.default_threads(), seed=7)
     return int(min(g.nx * g.ny, max(200, n0 * seconds / max(t0, 1e-3))))
 
 
