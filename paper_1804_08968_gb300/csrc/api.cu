@@ -377,7 +377,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     // with a margin for uneven lines.
     const size_t pe = 2 * sizeof(Key) + 2;
     const double grid_bytes = (double)eM * pe + (double)eF * std::max<size_t>(pe, 16) +
-                              (double)ncols * (K + 1) * 12 + (double)eL * 16;
+                              (double)ncols * (2 * K + 1) * 8 + (double)eL * 16;
     const bool can_block = !ctx->sweep1 && !ctx->sweep2 && ctx->levels && ctx->lane1 &&
                            !ctx->noblock && K > kMergeMaxReach && K <= kLaneMaxReach1;
     int nb = 1, bw = nx;
@@ -404,8 +404,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     const size_t slots_sw = std::max((size_t)sb1, (size_t)sb2_est) * nwarps;
     // the pass-2 level lists (one block's) use the same room as the sweeps' slots (never both
     // at once)
-    const long long nlev = (long long)bw * ny * (K + 1);
-    const size_t bL = K <= kGatherMaxReach ? align_up((size_t)nlev * 12 + 512, 256) + (size_t)eLb * 16 : 0;
+    const long long nlev = (long long)bw * ny * (2 * K + 1);  // index entries (8 B each)
+    const size_t bL = K <= kGatherMaxReach ? align_up((size_t)nlev * 8 + 512, 256) + (size_t)eLb * 16 : 0;
     const size_t slots = std::max(slots_sw, bL);
     const size_t total = fixed + bF + bM + bO + slots + 4096;
     if (ws_user && total > ws_user_bytes) {
@@ -686,9 +686,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           // per-source level unions in the sweeps' slot room, then the per-column gather
           LvlParamsHost<T> H;
           H.P = pg;
-          H.l_start = (long long*)pslots;
-          H.l_cnt = (int*)(H.l_start + nlev);
-          const size_t ib = align_up((size_t)nlev * 12 + 512, 256);
+          H.l_idx = (unsigned long long*)pslots;
+          const size_t ib = align_up((size_t)nlev * 8 + 512, 256);
           H.l_cap = (long long)((slot_room - ib) / 16);
           H.l_l = (ukey*)(pslots + ib);
           H.l_r = H.l_l + H.l_cap;

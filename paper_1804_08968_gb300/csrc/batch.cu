@@ -369,7 +369,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       const int L = K[s] + 1;
       const long long items = lvl_items(nc, L);
       lvb[s + 1] = lvb[s] + items;
-      nlb[s + 1] = nlb[s] + nc * L;
+      nlb[s + 1] = nlb[s] + nc * (2LL * K[s] + 1);  // index entries by output column
     }
     tabb[s + 1] = tabb[s] + nmax[s] + 2;
     nseg_all += it.nseg;
@@ -464,9 +464,10 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     pl.o_O = take((size_t)pl.capO * 16);
     const bool levels = !E->no_levels.count(sig);
     const long long nlev_all = nlb[ns];
-    pl.capL = levels ? std::max<long long>(std::max(E->needL + E->needL / 8, 2 * nlev_all), 1024) : 0;
-    pl.o_lst = take(levels ? sizeof(long long) * nlev_all : 0);
-    pl.o_lcnt = take(levels ? sizeof(int) * nlev_all : 0);
+    // level-list intervals: about two a (source, level) pair, half the index entries
+    pl.capL = levels ? std::max<long long>(std::max(E->needL + E->needL / 8, nlev_all), 1024) : 0;
+    pl.o_lst = take(levels ? sizeof(unsigned long long) * nlev_all : 0);
+    pl.o_lcnt = take(0);
     pl.o_L = take((size_t)pl.capL * 16);
     pl.total = x + 256;
     if (pl.total > E->ws_bytes) {
@@ -505,8 +506,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     short* c_dx = (short*)(c_bf + pl.capF);
     ukey* o_l = (ukey*)(W + pl.o_O);
     ukey* o_r = o_l + pl.capO;
-    long long* l_start = (long long*)(W + pl.o_lst);
-    int* l_cnt = (int*)(W + pl.o_lcnt);
+    unsigned long long* l_idx = (unsigned long long*)(W + pl.o_lst);
     ukey* l_l = (ukey*)(W + pl.o_L);
     ukey* l_r = l_l + pl.capL;
 
@@ -549,7 +549,8 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       LvlParams<T>& v = B.lv;
       v.P = q;
       v.l_l = l_l; v.l_r = l_r; v.l_cap = pl.capL;
-      v.l_start = l_start + nlb[s]; v.l_cnt = l_cnt + nlb[s];
+      v.l_idx = l_idx + nlb[s];
+      v.W = 2 * K[s] + 1;
       v.L = K[s] + 1;
       v.G = v.L <= 32 ? 32 / v.L : 1;
       v.NG = v.L <= 32 ? 0 : (K[s] + 31) / 32;
@@ -624,7 +625,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       }
       const unsigned b2 = (unsigned)std::max<long long>(1, std::min<long long>((long long)E->sms * minb, nt2));
       if (levels && ncols > 0) {
-        if ((e = cudaMemsetAsync(l_cnt, 0, sizeof(int) * nlev_all, s_)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(l_idx, 0, sizeof(unsigned long long) * nlev_all, s_)) != cudaSuccess) return e;
         if (warp_tab)
           k_b_levels<T, kTabWarp><<<E->sms * 4, 256, smL, s_>>>(dS, d_lvb, ns, lvb[ns], tstride, d_sst);
         else

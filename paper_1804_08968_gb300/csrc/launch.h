@@ -47,21 +47,21 @@ cudaError_t launch_pass2(const P2Params<T>& P, int blocks, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pass2t(const P2GParams<T>& P, int warps_per_block, int tc, int ntab,
                           int stage_cap, int Q, int M, int minb, int blocks, cudaStream_t st);
-// Pass 2 by levels (pass2l.cu): per-source level unions into l_l / l_r (index l_start /
-// l_cnt, [q * (R + 1) + t]) then the per-column gather with buckets of bcap intervals.
+// Pass 2 by levels (pass2l.cu): per-source level unions into l_l / l_r, indexed by output
+// column (l_idx: 2R + 1 packed entries a column, entry u the list of source j - R + u at level
+// |u - R|), then the per-column gather with buckets of bcap intervals.
 template <typename T>
 struct LvlParamsHost {
   P2GParams<T> P;
   ukey* l_l;
   ukey* l_r;
   long long l_cap;
-  long long* l_start;
-  int* l_cnt;
+  unsigned long long* l_idx;
   int bcap;
   long long m_cap, c_cap;  // entries of the S_mid arena and of its packed copy (self-checks)
   bool exact;  // k_levels reads S_mid itself (no packed copy; c_start unused)
   // a block of whole y lines: sources / output columns q0 .. q0 + nq - 1 in line order
-  // (q = i * ny + j; nq = 0: the whole grid); l_start / l_cnt hold the block's entries only
+  // (q = i * ny + j; nq = 0: the whole grid); l_idx holds the block's entries only
   long long q0 = 0, nq = 0;
   // reach of the output window along y (-1: R; 0: the 2D slices, a column's own level 0)
   int yw = -1;

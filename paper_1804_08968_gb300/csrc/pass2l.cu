@@ -68,7 +68,7 @@ static LvlParams<T> lvl_params(const LvlParamsHost<T>& H) {
   LvlParams<T> A;
   A.P = H.P;
   A.l_l = H.l_l; A.l_r = H.l_r; A.l_cap = H.l_cap;
-  A.l_start = H.l_start; A.l_cnt = H.l_cnt;
+  A.W = 2 * H.P.R + 1;
   A.L = H.P.R + 1;
   if (A.L <= 32) {
     A.G = 32 / A.L;
@@ -77,14 +77,13 @@ static LvlParams<T> lvl_params(const LvlParamsHost<T>& H) {
     A.G = 1;
     A.NG = (H.P.R + 31) / 32;
   }
-  // a block of lines: the index arrays are addressed with the global source index q, so
-  // their base pointers are shifted by the block's first entry (q0 L); nlev bounds q L + t
+  // a block of lines: the index is addressed with the global column index q, so its base
+  // pointer is shifted by the block's first entry (q0 W); nlev bounds q W + u
   A.yw = H.yw >= 0 ? H.yw : H.P.R;
   A.q0 = H.q0;
   A.nsrc = H.nq > 0 ? H.nq : (long long)H.P.nx * H.P.ny;
-  A.l_start = H.l_start - H.q0 * A.L;
-  A.l_cnt = H.l_cnt - H.q0 * A.L;
-  A.nlev = (H.q0 + A.nsrc) * A.L;
+  A.l_idx = H.l_idx - H.q0 * A.W;
+  A.nlev = (H.q0 + A.nsrc) * A.W;
   A.m_cap = H.m_cap;
   A.c_cap = H.c_cap;
   return A;
@@ -94,7 +93,7 @@ template <typename T>
 cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms) {
   const LvlParams<T> A = lvl_params(H);
   // lists a warp skips (an overflow) then read as empty
-  cudaError_t e = cudaMemsetAsync(H.l_cnt, 0, sizeof(int) * A.nsrc * A.L, st);
+  cudaError_t e = cudaMemsetAsync(H.l_idx, 0, sizeof(unsigned long long) * A.nsrc * A.W, st);
   if (e != cudaSuccess) return e;
   const long long lt = lvl_lane_tab(H.P.R);
   const bool ltab = lt <= kLvlLaneTab;

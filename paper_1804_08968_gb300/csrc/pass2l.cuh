@@ -38,6 +38,8 @@ constexpr int kLvlStage = 64;
 constexpr int kLvlTable = 4097;
 // shared memory for the per-lane tables (floats): (level groups) x (R + 1) x 32 lanes
 constexpr int kLvlLaneTab = 12288;
+// a level list's index entry: start << 24 | count (counts below 2^24)
+constexpr unsigned long long kLvlIdxMaxCount = (1ULL << 24) - 1;
 // piece index and |dx| packed in one word: index < 2^21, |dx| < 2^11
 constexpr int kLvlDxBits = 11;
 constexpr int kLvlMaxPieces = 1 << (32 - kLvlDxBits);
@@ -48,8 +50,11 @@ struct LvlParams {
   ukey* l_l;  // level-list arena: left keys
   ukey* l_r;  //                   right keys
   long long l_cap;
-  long long* l_start;  // [q * L + t]: first interval of source q (line-2 index) at level t
-  int* l_cnt;
+  // index of the lists by output column: entry u of output column q (line order) is the list
+  // of source j - R + u at level |u - R| of the same line, packed as start << 24 | count
+  // ((2R + 1) entries a column, contiguous: a column's gather reads them coalesced)
+  unsigned long long* l_idx;
+  int W;     // entries a column, 2R + 1
   int L;     // levels a source: R + 1
   int G;     // sources a warp when L <= 32, else 1
   int NG;    // level groups of 32 (levels 1 .. R) when L > 32, else 0
@@ -57,7 +62,7 @@ struct LvlParams {
                    // column its own level-0 list)
   long long q0;    // first source column of the block (line order q = i * ny + j)
   long long nsrc;  // source columns of the block
-  long long nlev;  // bound of the index q * L + t into l_start / l_cnt
+  long long nlev;  // bound of the index q * W + u into l_idx
   long long m_cap, c_cap;  // entries of the S_mid arena and of its packed copy
 };
 
@@ -299,8 +304,14 @@ DXD bool lvl_flush(const LvlParams<T>& A, int lane, const unsigned* ws, int cnt,
   }
   if (cnt > kLvlSlots) redo(A.l_l + s + ex, A.l_r + s + ex);
   if (act) {
-    A.l_start[q * A.L + t] = s + ex;
-    A.l_cnt[q * A.L + t] = cnt;
+    // the list serves output columns j +- t of its line: entry R - t of column j + t and entry
+    // R + t of column j - t
+    if (cnt > kLvlIdxMaxCount) set_status(&P.ctr->status, ST_LEVELS_OVER);  // beyond the packing
+    const unsigned long long e = ((unsigned long long)(s + ex) << 24) | (unsigned long long)(cnt & kLvlIdxMaxCount);
+    const int jj = (int)(q % P.ny);
+    const long long qb = q - jj;
+    if (jj + t < P.ny) A.l_idx[(qb + jj + t) * A.W + (P.R - t)] = e;
+    if (t > 0 && jj - t >= 0) A.l_idx[(qb + jj - t) * A.W + (P.R + t)] = e;
   }
   wsync();
   return true;
@@ -370,7 +381,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     long long ms = 0, cs = 0;
     if (act) {
       np = P.m_cnt[q];
-      if (!lvl_src_ok<T, EXACT>(A, q, np) || q * A.L + t >= A.nlev) {
+      if (!lvl_src_ok<T, EXACT>(A, q, np) || q < A.q0 || q >= A.q0 + A.nsrc) {
         set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
         act = false;
         np = 0;
@@ -412,7 +423,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
   const int t = 1 + grp * 32 + lane;
   const bool act = t < A.L;
   const int np = P.m_cnt[q];
-  if (!lvl_src_ok<T, EXACT>(A, q, np) || q * A.L + A.L > A.nlev) {
+  if (!lvl_src_ok<T, EXACT>(A, q, np) || q < A.q0 || q >= A.q0 + A.nsrc) {
     if (lane == 0) set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
     return;
   }
@@ -566,11 +577,11 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
     int n = 0;
     long long st = 0;
     if (jj <= s1) {
-      const int t = jj > j ? jj - j : j - jj;
-      const long long li = (qb + jj) * A.L + t;
+      const long long li = (qb + j) * A.W + (jj - j + P.R);  // coalesced over the lanes
       if (li < A.nlev) {
-        n = A.l_cnt[li];
-        st = A.l_start[li];
+        const unsigned long long e = A.l_idx[li];
+        n = (int)(e & kLvlIdxMaxCount);
+        st = (long long)(e >> 24);
       }
       if (li >= A.nlev || n < 0 || st < 0 || st + n > A.l_cap) {
         set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
@@ -591,11 +602,11 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
     nj = jump_union(
         [&](auto f) {
           for (int jj = s0 + lane; jj <= s1; jj += 32) {
-            const int t = jj > j ? jj - j : j - jj;
-            const long long li = (qb + jj) * A.L + t;
+            const long long li = (qb + j) * A.W + (jj - j + P.R);
             if (li >= A.nlev) continue;
-            const int n = A.l_cnt[li];
-            const long long st = A.l_start[li];
+            const unsigned long long e = A.l_idx[li];
+            const int n = (int)(e & kLvlIdxMaxCount);
+            const long long st = (long long)(e >> 24);
             if (n < 0 || st < 0 || st + n > A.l_cap) continue;  // flagged by the gather above
             for (int k = 0; k < n; ++k) f(A.l_l[st + k], A.l_r + st + k);
           }
@@ -693,11 +704,11 @@ DXD void lgather_lane(const LvlParams<T>& A, long long item, bool act, int lane,
   // f(l, pointer to r) over the column's intervals
   auto visit = [&](auto f) {
     for (int jj = s0; jj <= s1; ++jj) {
-      const int t = jj > j ? jj - j : j - jj;
-      const long long li = (qb + jj) * A.L + t;
+      const long long li = (qb + j) * A.W + (jj - j + R);  // the column's entries, in order
       if (li >= A.nlev) continue;
-      const int n = A.l_cnt[li];
-      const long long st = A.l_start[li];
+      const unsigned long long e = A.l_idx[li];
+      const int n = (int)(e & kLvlIdxMaxCount);
+      const long long st = (long long)(e >> 24);
       if (n < 0 || st < 0 || st + n > A.l_cap) {
         set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
         continue;
