@@ -496,15 +496,17 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         // sort shared); measured best on the 512^2 workload: 2 up to k = 8, 4 at k = 32
         int gw = K <= 12 ? 2 : (K <= 48 ? 4 : 8);
         if (ctx->p1l_gw > 0) gw = ctx->p1l_gw;
-        while (gw < 8 && pass1l_smem(K, ecapL, gw) > (220LL << 10)) gw <<= 1;
+        const int ksz = sizeof(T) == 4 ? 4 : 8;  // the window kernel's event keys
+        while (gw < 8 && pass1l_smem(K, ecapL, gw, ksz) > (220LL << 10)) gw <<= 1;
         // the ring of the one-walk variant in the (free) forward arena: up to 128 pieces a
         // thread of the grid
         const int ecapR = 16384;  // the redo's event room (room for the densest window)
-        const bool redo_ok = ecapL < ecapR && pass1l_smem(K, ecapR, 8) <= (220LL << 10);
+        const bool redo_ok = ecapL < ecapR && pass1l_smem(K, ecapR, 8, ksz) <= (220LL << 10);
         {
           // threads of the larger of the two launches (the first, and the redo's)
-          long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms) * 256;
-          if (redo_ok) thr = std::max<long long>(thr, (long long)pass1l_blocks(nx, ny, K, ecapR, 8, sms) * 256);
+          long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms, ksz) * 256;
+          if (redo_ok)
+            thr = std::max<long long>(thr, (long long)pass1l_blocks(nx, ny, K, ecapR, 8, sms, ksz) * 256);
           const long long esz = 2 * (long long)sizeof(Key) + 2;
           long long rc = std::min<long long>(ctx->p1l_ring_max, (long long)bF / (thr * esz)) & ~7LL;
           if (ctx->p1l_ring_cap > 0) rc = std::min<long long>(rc, ctx->p1l_ring_cap);

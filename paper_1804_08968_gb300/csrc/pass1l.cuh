@@ -33,6 +33,39 @@ namespace dexel {
 // words of the tile-relative source masks (32 + 2R + 1 <= 320 sources: R <= 128)
 constexpr int kP1TileWords = 5;
 
+// Event keys of the window kernel: the order-preserving 64-bit key of a double (double
+// inputs), or the order-preserving 32-bit key of a float (float inputs: 6 bytes an event in
+// shared memory instead of 10, a cheaper sort and 32-bit compares).  of: the key of a height;
+// none: the sentinel that sorts last; ninf / pinf: the complement's unbounded ends; out: the
+// S_mid key of an event key (exact); approx: a float approximation (the pruning test).
+template <typename T>
+struct EvK;
+template <>
+struct EvK<double> {
+  typedef ukey type;
+  DXD static ukey of(double x) { return dkey(x); }
+  DXD static ukey none() { return ~0ULL; }
+  DXD static ukey ninf() { return KEY_NINF; }
+  DXD static ukey pinf() { return KEY_PINF; }
+  DXD static ukey out(ukey k) { return k; }
+  DXD static float approx(ukey k) { return keyf(k); }
+};
+template <>
+struct EvK<float> {
+  typedef unsigned type;
+  DXD static unsigned of(float x) {
+    const unsigned b = __float_as_uint(x == 0.0f ? 0.0f : x);  // -0 folded into +0
+    return b ^ ((b >> 31) ? 0xFFFFFFFFu : 0x80000000u);
+  }
+  DXD static unsigned none() { return 0xFFFFFFFFu; }  // above the key of +inf (0xFF800000)
+  DXD static unsigned ninf() { return 0x007FFFFFu; }  // the key of -inf
+  DXD static unsigned pinf() { return 0xFF800000u; }  // the key of +inf
+  DXD static float out(unsigned k) {
+    return __uint_as_float((k >> 31) ? (k ^ 0x80000000u) : ~k);
+  }
+  DXD static float approx(unsigned k) { return out(k); }
+};
+
 // Shared memory of k_pass1l: sorted events (key, source), the window's event offsets, chunk
 // bounds, chunk toggle masks, per (chunk, lane) counts, last run starts and open-run flags,
 // the columns' offsets in the tile, tile base and ring-overflow flag.
@@ -40,16 +73,17 @@ struct P1LLayout {
   long long ek, ep, eoff, cb, cm, ccnt, cst, cco, cex, misc, wt, total;
 };
 DXI long long p1l_align(long long x) { return (x + 15) & ~15LL; }
-DXI P1LLayout p1l_layout(int R, int ecap, int warps) {
+// ksz: bytes of an event key (8 for double inputs, 4 for float)
+DXI P1LLayout p1l_layout(int R, int ecap, int warps, int ksz = 8) {
   P1LLayout o;
   long long x = 0;
-  o.ek = x; x = p1l_align(x + (long long)ecap * sizeof(ukey));
+  o.ek = x; x = p1l_align(x + (long long)ecap * ksz);
   o.ep = x; x = p1l_align(x + (long long)ecap * sizeof(unsigned short));
   o.eoff = x; x = p1l_align(x + (long long)(32 + 2 * R + 2) * sizeof(int));
   o.cb = x; x = p1l_align(x + (long long)(warps + 1) * sizeof(int));
   o.cm = x; x = p1l_align(x + (long long)warps * kP1TileWords * sizeof(ukey));
   o.ccnt = x; x = p1l_align(x + (long long)warps * 32 * sizeof(int));
-  o.cst = x; x = p1l_align(x + (long long)warps * 32 * sizeof(ukey));
+  o.cst = x; x = p1l_align(x + (long long)warps * 32 * ksz);
   o.cco = x; x = p1l_align(x + (long long)warps * 32 * sizeof(int));
   o.cex = x; x = p1l_align(x + 32 * sizeof(int));
   o.misc = x; x = p1l_align(x + 2 * sizeof(long long));
@@ -131,22 +165,22 @@ struct PTop {
 // open at the chunk's start is tested with the chunk's first height as its start: its slice
 // is at least that large).
 template <typename T, int NH, bool WRITE>
-DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int pc, int R,
-                   bool act, CMask<NH> m, int Om, ukey run_a, ukey& last_start,
-                   typename H<T>::K* oa, typename H<T>::K* ob, short* ol, int cap,
-                   const Prune& pr) {
-  typedef typename H<T>::K Key;
+DXD int chunk_walk(const typename EvK<T>::type* ek, const unsigned short* ep, int c0, int c1,
+                   int pc, int R, bool act, CMask<NH> m, int Om, typename EvK<T>::type run_a,
+                   typename EvK<T>::type& last_start, typename H<T>::K* oa,
+                   typename H<T>::K* ob, short* ol, int cap, const Prune& pr) {
+  typedef typename EvK<T>::type EK;
   int gmin = kNoLabel;
   int cnt = 0;
-  last_start = ~0ULL;
+  last_start = EvK<T>::none();
   if (c0 >= c1) return 0;
-  ukey gkey = ek[c0];
+  EK gkey = ek[c0];
   bool carried = Om < kNoLabel;  // the first run closed began before the chunk
   PTop top{0.0f, 0.0f, 0, false, false};
   // float approximations of the current run's start (for a carried run: the chunk's first
   // height) and of the current height, converted once a group
-  float run_af = pr.w ? keyf(gkey) : 0.0f;
-  auto emit = [&](ukey a, ukey b, float af, float bf, int l, bool fixed) {
+  float run_af = pr.w ? EvK<T>::approx(gkey) : 0.0f;
+  auto emit = [&](EK a, EK b, float af, float bf, int l, bool fixed) {
     if (pr.w) {
       const float w = pr.w[l];
       const float lo = af - w, hi = bf + w;
@@ -158,17 +192,17 @@ DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int
       top = PTop{lo, hi, l, true, fixed};
     }
     if (WRITE && cnt < cap) {
-      oa[cnt] = key_out<Key>(a);
-      ob[cnt] = key_out<Key>(b);
+      oa[cnt] = EvK<T>::out(a);
+      ob[cnt] = EvK<T>::out(b);
       ol[cnt] = (short)l;
     }
     ++cnt;
   };
-  auto close_group = [&](ukey v) {
+  auto close_group = [&](EK v) {
     const int Ok = cnearest<NH>(m);
     const bool pt = gmin < (Om < Ok ? Om : Ok);
     const bool ch = Ok != Om || pt;
-    const float vf = (pr.w && (ch || pt)) ? keyf(v) : 0.0f;
+    const float vf = (pr.w && (ch || pt)) ? EvK<T>::approx(v) : 0.0f;
     if (Om < kNoLabel && ch) {  // the run below v ends at v
       emit(run_a, v, run_af, vf, Om, carried);
       carried = false;
@@ -184,7 +218,7 @@ DXD int chunk_walk(const ukey* ek, const unsigned short* ep, int c0, int c1, int
     gmin = kNoLabel;
   };
   for (int t = c0; t < c1; ++t) {
-    const ukey key = ek[t];
+    const EK key = ek[t];
     const int src = ep[t];
     if (key != gkey) {  // warp-uniform: every lane reads the same event
       close_group(gkey);
@@ -233,14 +267,15 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
   const int lane = threadIdx.x & 31, warp = G.warp;
   const int W = G.W;
   const int gthreads = W * 32;
-  const P1LLayout Lo = p1l_layout(P.K, ecap, W);
-  ukey* ek = (ukey*)(smem + Lo.ek);
+  typedef typename EvK<T>::type EK;
+  const P1LLayout Lo = p1l_layout(P.K, ecap, W, (int)sizeof(EK));
+  EK* ek = (EK*)(smem + Lo.ek);
   unsigned short* ep = (unsigned short*)(smem + Lo.ep);
   int* eoff = (int*)(smem + Lo.eoff);
   int* cb = (int*)(smem + Lo.cb);
   ukey* cm = (ukey*)(smem + Lo.cm);
   int* ccnt = (int*)(smem + Lo.ccnt);
-  ukey* cst = (ukey*)(smem + Lo.cst);
+  EK* cst = (EK*)(smem + Lo.cst);
   int* cco = (int*)(smem + Lo.cco);
   int* cex = (int*)(smem + Lo.cex);
   long long* misc = (long long*)(smem + Lo.misc);
@@ -318,17 +353,17 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       const unsigned short src = (unsigned short)q;
       if (!P.erode) {
         for (int g = g0; g < g1; ++g) {
-          ek[o] = event_key(P.z[2LL * g]);
+          ek[o] = EvK<T>::of(P.z[2LL * g]);
           ep[o++] = src;
-          ek[o] = event_key(P.z[2LL * g + 1]);
+          ek[o] = EvK<T>::of(P.z[2LL * g + 1]);
           ep[o++] = src;
         }
       } else {
         // closure of the complement: (-inf, a0], [b0, a1], ..., [b_last, +inf); zero-length
         // segments leave no gap
-        ukey lo = KEY_NINF;
+        EK lo = EvK<T>::ninf();
         for (int g = g0; g < g1; ++g) {
-          const ukey a = event_key(P.z[2LL * g]), b = event_key(P.z[2LL * g + 1]);
+          const EK a = EvK<T>::of(P.z[2LL * g]), b = EvK<T>::of(P.z[2LL * g + 1]);
           if (a == b) continue;
           ek[o] = lo;
           ep[o++] = src;
@@ -338,12 +373,12 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
         }
         ek[o] = lo;
         ep[o++] = src;
-        ek[o] = KEY_PINF;
+        ek[o] = EvK<T>::pinf();
         ep[o++] = src;
       }
-      for (; o < oend; ++o) { ek[o] = ~0ULL; ep[o] = 0xFFFFu; }
+      for (; o < oend; ++o) { ek[o] = EvK<T>::none(); ep[o] = 0xFFFFu; }
     }
-    for (int t = E + G.gtid; t < n2; t += gthreads) { ek[t] = ~0ULL; ep[t] = 0xFFFFu; }
+    for (int t = E + G.gtid; t < n2; t += gthreads) { ek[t] = EvK<T>::none(); ep[t] = 0xFFFFu; }
     G.sync();
     PHASE(0);
     // block bitonic sort by height (the order within a height does not matter)
@@ -353,7 +388,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
           const int t = ((p & ~(jj - 1)) << 1) | (p & (jj - 1));
           const int x = t | jj;
           const bool up = (t & k) == 0;
-          const ukey kt = ek[t], kx = ek[x];
+          const EK kt = ek[t], kx = ek[x];
           if ((kt > kx) == up) {
             ek[t] = kx; ek[x] = kt;
             const unsigned short vt = ep[t]; ep[t] = ep[x]; ep[x] = vt;
@@ -364,7 +399,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     }
     PHASE(1);
     // real events (the padding sorts last); chunk bounds at group boundaries
-    const int Er = lower_bound(ek, n2, ~0ULL);
+    const int Er = lower_bound(ek, n2, EvK<T>::none());
     if (G.gtid == 0) ((int*)misc)[2] = 0;  // no ring region overflowed yet
     if (warp == 0 && lane <= W) {
       int b = (int)((long long)lane * Er / W);
@@ -409,7 +444,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       for (int q = 0; q < NH; ++q) { m0.up[q] = 0; m0.dn[q] = 0; }
     }
     const int Om0 = cnearest<NH>(m0);
-    ukey last = ~0ULL;
+    EK last = EvK<T>::none();
     // one walk into the lane's ring region (the start of a run open at the chunk's start is
     // patched when the pieces are copied), or a counting walk without a ring
     // the group's ring regions must lie within the ring (else the two walks, no ring)
@@ -418,10 +453,10 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     int n;
     const Prune pr{P.prune_w ? (const float*)(smem + Lo.wt) : nullptr, P.prune_E};
     if (ring)
-      n = chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, 0ULL, last, rg_a + rbase,
+      n = chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, (EK)0, last, rg_a + rbase,
                                   rg_b + rbase, rg_l + rbase, P.r_cap, pr);
     else
-      n = chunk_walk<T, NH, false>(ek, ep, c0, c1, pc, R, act, m0, Om0, 0ULL, last, nullptr,
+      n = chunk_walk<T, NH, false>(ek, ep, c0, c1, pc, R, act, m0, Om0, (EK)0, last, nullptr,
                                    nullptr, nullptr, 0, pr);
     ccnt[warp * 32 + lane] = n;
     cst[warp * 32 + lane] = last;
@@ -433,13 +468,13 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     // the column's pieces before this chunk, its total, and the start of the run open at the
     // chunk's start
     int before = 0, tot_col = 0;
-    ukey run_a = 0ULL;
+    EK run_a = (EK)0;
     for (int c = 0; c < W; ++c) {
       const int v = ccnt[c * 32 + lane];
       if (c < warp) {
         before += v;
-        const ukey st = cst[c * 32 + lane];
-        if (st != ~0ULL) run_a = st;
+        const EK st = cst[c * 32 + lane];
+        if (st != EvK<T>::none()) run_a = st;
       }
       tot_col += v;
     }
@@ -464,24 +499,24 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       // the ring regions into the arena: a warp a column, lanes over its pieces (coalesced)
       for (int x = warp; x < 32; x += W) {
         long long d = s + cex[x];
-        ukey carry = ~0ULL;
+        EK carry = EvK<T>::none();
         for (int c = 0; c < W; ++c) {
           const int cn = ccnt[c * 32 + x];
           const long long sb = (long long)(c * 32 + x) * P.r_cap;
-          const bool patch = cco[c * 32 + x] != 0 && carry != ~0ULL;
+          const bool patch = cco[c * 32 + x] != 0 && carry != EvK<T>::none();
           for (int k = lane; k < cn; k += 32) {
-            P.m_a[d + k] = (k == 0 && patch) ? key_out<Key>(carry) : rg_a[sb + k];
+            P.m_a[d + k] = (k == 0 && patch) ? EvK<T>::out(carry) : rg_a[sb + k];
             P.m_b[d + k] = rg_b[sb + k];
             P.m_l[d + k] = rg_l[sb + k];
           }
           d += cn;
-          const ukey st = cst[c * 32 + x];
-          if (st != ~0ULL) carry = st;
+          const EK st = cst[c * 32 + x];
+          if (st != EvK<T>::none()) carry = st;
         }
       }
     } else if (fits && n > 0) {
       const long long o = s + (inc - tot_col) + before;
-      ukey dummy;
+      EK dummy;
       chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, run_a, dummy, P.m_a + o,
                               P.m_b + o, P.m_l + o, 1 << 30, pr);
     }
