@@ -691,8 +691,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           H.l_idx = (unsigned long long*)pslots;
           const size_t ib = align_up((size_t)nlev * 8 + 512, 256);
           H.l_cap = (long long)((slot_room - ib) / 16);
-          H.l_l = (ukey*)(pslots + ib);
-          H.l_r = H.l_l + H.l_cap;
+          H.l_p = (ulonglong2*)(pslots + ib);
           int& lb = ctx->ccap[2 * K + (erode ? 1 : 0)];
           if (lb < 256) lb = 256;
           H.bcap = lb;

@@ -507,8 +507,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     ukey* o_l = (ukey*)(W + pl.o_O);
     ukey* o_r = o_l + pl.capO;
     unsigned long long* l_idx = (unsigned long long*)(W + pl.o_lst);
-    ukey* l_l = (ukey*)(W + pl.o_L);
-    ukey* l_r = l_l + pl.capL;
+    ulonglong2* l_p = (ulonglong2*)(W + pl.o_L);
 
     // ---- shape table
     std::vector<BShape<T>> hs(ns);
@@ -548,7 +547,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       q.c_start = cst + colb[s]; q.c_af = c_af; q.c_bf = c_bf; q.c_dx = c_dx;
       LvlParams<T>& v = B.lv;
       v.P = q;
-      v.l_l = l_l; v.l_r = l_r; v.l_cap = pl.capL;
+      v.l_p = l_p; v.l_cap = pl.capL;
       v.l_idx = l_idx + nlb[s];
       v.W = 2 * K[s] + 1;
       v.L = K[s] + 1;

@@ -48,14 +48,13 @@ cudaError_t launch_pass2(const P2Params<T>& P, int blocks, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pass2t(const P2GParams<T>& P, int warps_per_block, int tc, int ntab,
                           int stage_cap, int Q, int M, int minb, int blocks, cudaStream_t st);
-// Pass 2 by levels (pass2l.cu): per-source level unions into l_l / l_r, indexed by output
+// Pass 2 by levels (pass2l.cu): per-source level unions into l_p, indexed by output
 // column (l_idx: 2R + 1 packed entries a column, entry u the list of source j - R + u at level
 // |u - R|), then the per-column gather with buckets of bcap intervals.
 template <typename T>
 struct LvlParamsHost {
   P2GParams<T> P;
-  ukey* l_l;
-  ukey* l_r;
+  ulonglong2* l_p;  // (left, right) keys of the level lists' intervals
   long long l_cap;
   unsigned long long* l_idx;
   int bcap;

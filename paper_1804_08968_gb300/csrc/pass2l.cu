@@ -67,7 +67,7 @@ template <typename T>
 static LvlParams<T> lvl_params(const LvlParamsHost<T>& H) {
   LvlParams<T> A;
   A.P = H.P;
-  A.l_l = H.l_l; A.l_r = H.l_r; A.l_cap = H.l_cap;
+  A.l_p = H.l_p; A.l_cap = H.l_cap;
   A.W = 2 * H.P.R + 1;
   A.L = H.P.R + 1;
   if (A.L <= 32) {

@@ -47,8 +47,7 @@ constexpr int kLvlMaxPieces = 1 << (32 - kLvlDxBits);
 template <typename T>
 struct LvlParams {
   P2GParams<T> P;
-  ukey* l_l;  // level-list arena: left keys
-  ukey* l_r;  //                   right keys
+  ulonglong2* l_p;  // level-list arena: (left, right) keys of each interval, interleaved
   long long l_cap;
   // index of the lists by output column: entry u of output column q (line order) is the list
   // of source j - R + u at level |u - R| of the same line, packed as start << 24 | count
@@ -190,12 +189,11 @@ struct ExactEmit {
   const P2GParams<T>* P;
   long long ms;
   int tt;
-  ukey* ol;
-  ukey* orr;
+  ulonglong2* o;
   DXD void operator()(const LvlRun& s) const {
     const unsigned m = (1u << kLvlDxBits) - 1;
-    ol[s.cnt] = lvl_left<T>(*P, ms, (int)(s.pl >> kLvlDxBits), (int)(s.pl & m), tt);
-    orr[s.cnt] = lvl_right<T>(*P, ms, (int)(s.pr >> kLvlDxBits), (int)(s.pr & m), tt);
+    o[s.cnt] = make_ulonglong2(lvl_left<T>(*P, ms, (int)(s.pl >> kLvlDxBits), (int)(s.pl & m), tt),
+                               lvl_right<T>(*P, ms, (int)(s.pr >> kLvlDxBits), (int)(s.pr & m), tt));
   }
 };
 
@@ -311,11 +309,11 @@ DXD bool lvl_flush(const LvlParams<T>& A, int lane, const unsigned* ws, int cnt,
       const unsigned pl = ws[(k << 5) + own];
       const unsigned pr = ws[(k << 5) + own + kLvlSlots * 32];
       const unsigned m = (1u << kLvlDxBits) - 1;
-      A.l_l[s + idx] = lvl_left<T>(P, mso, (int)(pl >> kLvlDxBits), (int)(pl & m), tto);
-      A.l_r[s + idx] = lvl_right<T>(P, mso, (int)(pr >> kLvlDxBits), (int)(pr & m), tto);
+      A.l_p[s + idx] = make_ulonglong2(lvl_left<T>(P, mso, (int)(pl >> kLvlDxBits), (int)(pl & m), tto),
+                                       lvl_right<T>(P, mso, (int)(pr >> kLvlDxBits), (int)(pr & m), tto));
     }
   }
-  if (cnt > kLvlSlots) redo(A.l_l + s + ex, A.l_r + s + ex);
+  if (cnt > kLvlSlots) redo(A.l_p + s + ex);
   if (act) {
     // the list serves output columns j +- t of its line: entry R - t of column j + t and entry
     // R + t of column j - t
@@ -415,16 +413,16 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
         wl = pairs ? STab{tab + lane, 5} : STab{tab + (long long)max(A.NG, 1) * R1 * 32, 0};
       }
       walk_global<T>(P, src, 0, np, E, wl, s, pe);
-      lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
+      lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
         LvlRun s2 = lvl_run();
-        walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+        walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
       });
     } else {
       const FlatTab wl{tab, t * t, P.nmax};
       walk_global<T>(P, src, 0, np, E, wl, s, pe);
-      lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
+      lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
         LvlRun s2 = lvl_run();
-        walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+        walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
       });
     }
     return;
@@ -453,16 +451,16 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
       wl = STab{tab + (long long)grp * R1 * 32 + lane, 5};
     }
     walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe, 1 + grp * 32);
-    lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
+    lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
       LvlRun s2 = lvl_run();
-      walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+      walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
     });
   } else {
     const FlatTab wl{tab, t * t, P.nmax};
     walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe, 1 + grp * 32);
-    lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ukey* ol, ukey* orr) {
+    lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
       LvlRun s2 = lvl_run();
-      walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol, orr});
+      walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
     });
   }
 }
@@ -603,7 +601,12 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
     }
     const int inc = w_incl_add(n, lane);
     const int o = carry + inc - n;
-    for (int k = 0; k < n && o + k < bcap; ++k) { bl[o + k] = A.l_l[st + k]; br[o + k] = A.l_r[st + k]; }
+#pragma unroll 4
+    for (int k = 0; k < n && o + k < bcap; ++k) {
+      const ulonglong2 v = A.l_p[st + k];  // one 16-byte load an interval
+      bl[o + k] = v.x;
+      br[o + k] = v.y;
+    }
     carry += w_bcast(inc, 31);
   }
   wsync();
@@ -621,7 +624,7 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
             const int n = (int)(e & kLvlIdxMaxCount);
             const long long st = (long long)(e >> 24);
             if (n < 0 || st < 0 || st + n > A.l_cap) continue;  // flagged by the gather above
-            for (int k = 0; k < n; ++k) f(A.l_l[st + k], A.l_r + st + k);
+            for (int k = 0; k < n; ++k) f(A.l_p[st + k].x, &A.l_p[st + k].y);
           }
         },
         lane, run_l, run_r);
@@ -726,7 +729,7 @@ DXD void lgather_lane(const LvlParams<T>& A, long long item, bool act, int lane,
         set_status(&P.ctr->status, ST_BOUNDS | ST_LEVELS_OVER);
         continue;
       }
-      for (int k = 0; k < n; ++k) f(A.l_l[st + k], A.l_r + st + k);
+      for (int k = 0; k < n; ++k) f(A.l_p[st + k].x, &A.l_p[st + k].y);
     }
   };
   ukey rl[kLaneRuns], rr[kLaneRuns];
