@@ -236,35 +236,24 @@ DXD void walk_global(const P2GParams<T>& P, const Src& src, int p0, int p1, floa
 }
 
 // The warp's walk over the np pieces of one source (all lanes, each its own level): the
-// pieces pass through shared memory in chunks (coalesced loads, broadcast reads).  tmin > 0:
-// the lanes' levels start at tmin, and a piece whose reach in levels ends below it (empty
-// slices at every level of the group) is not staged (compacted by warp ballots, in order).
+// pieces pass through shared memory in chunks (coalesced loads, broadcast reads).  (Staging
+// only the pieces that reach a level group's first level was measured slower: 269 -> 281 ms
+// on the 2048^2 k = 64 workload.)
 template <typename T, typename W, typename Emit, typename Src>
 DXD void walk_staged(const P2GParams<T>& P, const Src& src, int np, int lane, float4* stg, float E,
-                     const W& wl, LvlRun& s, const Emit& emit, int tmin = 0) {
-  const bool filter = tmin > 0 && P.reach != nullptr;
+                     const W& wl, LvlRun& s, const Emit& emit) {
   for (int base = 0; base < np; base += kLvlStage) {
     const int m = min(kLvlStage, np - base);
     wsync();
-    int kept = 0;
-    for (int k0 = 0; k0 < m; k0 += 32) {
-      const int k = k0 + lane;
-      bool keep = false;
-      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      if (k < m) {
-        const int dx = src.dx(base + k);
-        const int adx = min(dx < 0 ? -dx : dx, P.R);  // labels lie in [-R, R]
-        keep = !filter || P.reach[adx] >= tmin;
-        v = make_float4(src.af(base + k), src.bf(base + k), __int_as_float(adx),
-                        __uint_as_float(lvl_pack(base + k, adx)));
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      if (keep) stg[kept + __popc(bal & ((1u << lane) - 1u))] = v;
-      kept += __popc(bal);
+    for (int k = lane; k < m; k += 32) {
+      const int dx = src.dx(base + k);
+      const int adx = min(dx < 0 ? -dx : dx, P.R);  // labels lie in [-R, R]
+      stg[k] = make_float4(src.af(base + k), src.bf(base + k), __int_as_float(adx),
+                           __uint_as_float(lvl_pack(base + k, adx)));
     }
     wsync();
 #pragma unroll 2
-    for (int k = 0; k < kept; ++k) {
+    for (int k = 0; k < m; ++k) {
       const float4 v = stg[k];
       lvl_step(s, v.x, v.y, __float_as_uint(v.w), wl(__float_as_int(v.z)), E, emit);
     }
@@ -450,14 +439,14 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     } else {
       wl = STab{tab + (long long)grp * R1 * 32 + lane, 5};
     }
-    walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe, 1 + grp * 32);
+    walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe);
     lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
       LvlRun s2 = lvl_run();
       walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
     });
   } else {
     const FlatTab wl{tab, t * t, P.nmax};
-    walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe, 1 + grp * 32);
+    walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe);
     lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
       LvlRun s2 = lvl_run();
       walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
