@@ -44,6 +44,7 @@ struct BShape {
   T* out_z;
   long long out_cap;
   long long nseg_in;
+  unsigned zmax_bits;  // max |z| of the shape's input (float bits), for the pruning margin
 };
 
 // largest s in [0, ns) with base[s] <= x (base has ns + 1 entries)
@@ -58,11 +59,33 @@ __device__ __forceinline__ int find_base(const long long* base, int ns, long lon
 }
 
 template <typename T>
-__global__ void k_b_validate(const BShape<T>* S, const long long* colb, int ns, long long ncols,
+__global__ void k_b_validate(BShape<T>* S, const long long* colb, int ns, long long ncols,
                              int* sst) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncols) return;
+  const long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long c = c0 < ncols ? c0 : ncols - 1;  // (every lane takes part in the reduction)
   const int s = find_base(colb, ns, c);
+  float zm = 0.0f;  // max |z| of the column, reduced per shape below
+  {
+    const BShape<T>& B0 = S[s];
+    const int s0 = B0.p1.col_off[c - colb[s]], s1 = B0.p1.col_off[c - colb[s] + 1];
+    if (c0 < ncols && s0 >= 0 && s1 <= B0.nseg_in)
+      for (int g = s0; g < s1; ++g) {
+        const float a = fabsf((float)B0.p1.z[2LL * g]), b = fabsf((float)B0.p1.z[2LL * g + 1]);
+        if (a < __builtin_huge_valf()) zm = fmaxf(zm, a);
+        if (b < __builtin_huge_valf()) zm = fmaxf(zm, b);
+      }
+  }
+  {
+    // one atomic a warp when its columns are one shape's, else one a lane
+    const int s_first = __shfl_sync(0xffffffffu, s, 0);
+    if (__all_sync(0xffffffffu, s == s_first)) {
+      const unsigned zb = __reduce_max_sync(0xffffffffu, __float_as_uint(zm));
+      if ((threadIdx.x & 31) == 0 && zb > 0) atomicMax(&S[s].zmax_bits, zb);
+    } else if (zm > 0.0f) {
+      atomicMax(&S[s].zmax_bits, __float_as_uint(zm));
+    }
+  }
+  if (c0 >= ncols) return;
   const BShape<T>& B = S[s];
   const long long cl = c - colb[s];
   B.p1.m_cnt[cl] = 0;
@@ -99,6 +122,16 @@ __global__ void k_b_tables(const BShape<T>* S, const long long* tabb, int ns, lo
     wtab[e] = w;
     wtabf[e] = (float)w;
   }
+}
+
+// the pass-1 pruning margin of every shape: 2^-19 (max |z| + k h), over four times the error
+// bound of the float dominance test (as for single shapes)
+template <typename T>
+__global__ void k_b_prune(BShape<T>* S, int ns) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns || S[s].p1.prune_w == nullptr) return;
+  const double zm = (double)__uint_as_float(S[s].zmax_bits);
+  S[s].p1.prune_E = (float)(1.9073486328125e-6 * (zm + sqrt(S[s].kk) * S[s].h));  // 2^-19
 }
 
 // pass 1, one lane per output column: groups of gw warps, each a tile of 32 columns of one
@@ -271,6 +304,7 @@ __global__ void k_b_write(const BShape<T>* S, const long long* colb, int ns, lon
 struct BatchEngine {
   int device = 0, sms = 152;
   bool autotune = true;
+  bool prune = true;  // dominance pruning of S_mid pieces in pass 1
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -282,6 +316,8 @@ struct BatchEngine {
   std::map<std::vector<long long>, bool> no_levels;  // signatures whose level lists overflowed
   // recorded launch sequences by signature (shapes, scratch, tile scales)
   std::map<std::vector<long long>, cudaGraphExec_t> graphs;
+  std::map<std::vector<long long>, bool> graph_writes;  // the graph ends with the output write
+  std::map<std::vector<long long>, std::vector<long long>> last_tot;  // totals of the last call
   // autotuned tile scales per signature (x 1/2: 0 = half, 1 = default, 2 = double)
   std::map<std::vector<long long>, std::pair<int, int>> scales;
 };
@@ -438,6 +474,14 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     return DEXEL_OK;
   }
 
+  // outputs the engine provides (the first offset of a closing / opening), fixed before the
+  // attempts (an attempt may point them into the engine's buffer)
+  std::vector<char> internal(ns, 0);
+  bool have_internal = false;
+  for (int s = 0; s < ns; ++s) {
+    internal[s] = items[s].out_z == nullptr;
+    have_internal = have_internal || internal[s];
+  }
   for (int attempt = 0; attempt < 8; ++attempt) {
     // ---- workspace plan
     Plan pl;
@@ -534,6 +578,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       p.m_start = m_start + colb[s]; p.m_cnt = m_cnt + colb[s];
       p.blk = 256;
       p.ctr = ctr;
+      p.prune_w = E->prune ? wtabf + tabb[s] : nullptr;  // margin set on the device (k_b_prune)
       P2GParams<T>& q = B.p2;
       q.nx = it.nx; q.ny = it.ny; q.R = K[s]; q.kk = B.kk; q.nmax = nmax[s];
       q.wtab = wtab + tabb[s]; q.wtabf = wtabf + tabb[s]; q.reach = nullptr;
@@ -560,6 +605,50 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       v.m_cap = pl.capM;
       v.c_cap = pl.capF;
     }
+    // internal outputs (first offset of a closing / opening) sized from the last call of this
+    // signature, so that the device checks their capacity and the output write can be part of
+    // the recorded sequence (a shape that outgrows its room is written again below)
+    bool pre_assigned = false;
+    // room in the engine's buffer for every internal output (tot: segments each; margin: room
+    // to grow)
+    auto assign_mid = [&](const std::vector<long long>& tot, bool margin) -> int {
+      size_t need = 0;
+      std::vector<long long> cap(ns, 0);
+      for (int s = 0; s < ns; ++s) {
+        if (!internal[s]) continue;
+        cap[s] = std::max<long long>(margin ? tot[s] + tot[s] / 4 + 1024 : tot[s], 1);
+        need += bal(sizeof(int) * (colb[s + 1] - colb[s] + 1)) + bal(sizeof(T) * 2 * cap[s]);
+      }
+      if (need > E->mid_bytes) {
+        if (E->mid) cudaFree(E->mid);
+        E->mid = nullptr;
+        E->mid_bytes = 0;
+        if (cudaMalloc(&E->mid, need + need / 4) != cudaSuccess) return DEXEL_ERR_NOMEM;
+        E->mid_bytes = need + need / 4;
+      }
+      size_t o = 0;
+      for (int s = 0; s < ns; ++s) {
+        if (!internal[s]) continue;
+        items[s].out_col_off = (int*)((char*)E->mid + o);
+        o += bal(sizeof(int) * (colb[s + 1] - colb[s] + 1));
+        items[s].out_z = (char*)E->mid + o;
+        items[s].out_cap = cap[s];
+        o += bal(sizeof(T) * 2 * cap[s]);
+        hs[s].out_col_off = items[s].out_col_off;
+        hs[s].out_z = (T*)items[s].out_z;
+        hs[s].out_cap = items[s].out_cap;
+      }
+      return DEXEL_OK;
+    };
+    if (have_internal) {
+      auto lt = E->last_tot.find(sig);
+      if (lt != E->last_tot.end() && (int)lt->second.size() == ns) {
+        const int rc = assign_mid(lt->second, true);
+        if (rc != DEXEL_OK) return rc;
+        pre_assigned = true;
+      }
+    }
+    const bool write_in_seq = !have_internal || pre_assigned;
     const size_t up_bytes = sizeof(BShape<T>) * ns + sizeof(long long) * 5 * (ns + 1);
     if (up_bytes > E->host_bytes) {
       if (E->host) cudaFreeHost(E->host);
@@ -604,6 +693,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
         k_b_validate<T><<<(unsigned)((ncols + thr - 1) / thr), thr, 0, s_>>>(dS, d_colb, ns, ncols, d_sst);
       if (ntab > 0)
         k_b_tables<T><<<(unsigned)((ntab + thr - 1) / thr), thr, 0, s_>>>(dS, d_tabb, ns, ntab, wtab, wtabf);
+      k_b_prune<T><<<(ns + 127) / 128, 128, 0, s_>>>(dS, ns);
       const int per1 = (int)std::max<long long>(1, std::min<long long>(3, (220LL << 10) / sm1));
       const long long want1 = (nt1 + (8 / gw1) - 1) / (8 / gw1);
       const unsigned b1 = (unsigned)std::max<long long>(1, std::min<long long>((long long)E->sms * per1, want1));
@@ -644,7 +734,14 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
         k_scan2<<<1, kScanThreads, 0, s_>>>(nb, sums);
       }
       k_b_totals<T><<<(ns + 127) / 128, 128, 0, s_>>>(dS, d_colb, ns, ncols, pos, sums, d_tot, d_sst);
-      if (nl) *nl += 12;
+      if (nl) *nl += 13;
+      if (write_in_seq && ncols > 0) {
+        // every output has its room: the write ends the sequence (shapes over capacity, or
+        // handed to a redo or the single-shape path, are skipped by it)
+        k_b_write<T><<<(unsigned)((ncols + thr - 1) / thr), thr, 0, s_>>>(dS, d_colb, ns, ncols, pos,
+                                                                          sums, d_tot, d_sst);
+        if (nl) ++*nl;
+      }
       return cudaGetLastError();
     };
     BK(cudaFuncSetAttribute(k_b_pass1<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
@@ -658,14 +755,16 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
     fullsig.push_back(sc1);
     fullsig.push_back(sc2);
     fullsig.push_back(levels ? 1 : 0);
+    fullsig.push_back(write_in_seq ? 1 : 0);
     auto gi = E->graphs.find(fullsig);
     const bool replay = gi != E->graphs.end();
     if (replay) {
       BK(cudaGraphLaunch(gi->second, st));
-      if (launches) *launches += 12;
+      if (launches) *launches += 13 + (write_in_seq ? 1 : 0);
     } else {
       BK(seq(st, launches));
     }
+    bool rewrite = false;  // the write must run (again) after the sequence
     Counters hc;
     std::vector<int> hsst(ns);
     std::vector<long long> htot(ns);
@@ -705,6 +804,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
         k_b_totals<T><<<(ns + 127) / 128, 128, 0, st>>>(dS, d_colb, ns, ncols, pos, sums, d_tot, d_sst);
         BK(cudaGetLastError());
         if (launches) *launches += 5;
+        rewrite = true;
         BK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         BK(cudaMemcpyAsync(hsst.data(), d_sst, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
         BK(cudaMemcpyAsync(htot.data(), d_tot, sizeof(long long) * ns, cudaMemcpyDeviceToHost, st));
@@ -742,43 +842,31 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       return batch_run_t<T>(E, items, st, status, nseg, launches, 1);
     }
 
-    // internal outputs (first offset of a closing / opening): space from the engine
-    size_t need_mid = 0;
-    for (int s = 0; s < ns; ++s)
-      if (!items[s].out_z)
-        need_mid += bal(sizeof(int) * (colb[s + 1] - colb[s] + 1)) + bal(sizeof(T) * 2 * std::max<long long>(htot[s], 1));
-    if (need_mid > 0) {
-      if (need_mid > E->mid_bytes) {
-        if (E->mid) cudaFree(E->mid);
-        E->mid = nullptr;
-        E->mid_bytes = 0;
-        if (cudaMalloc(&E->mid, need_mid + need_mid / 4) != cudaSuccess) return DEXEL_ERR_NOMEM;
-        E->mid_bytes = need_mid + need_mid / 4;
+    // internal outputs without room yet (first call of a signature) or beyond the room of the
+    // last call's totals: space from the engine, then the write
+    if (have_internal) {
+      bool regrow = !pre_assigned;
+      for (int s = 0; s < ns; ++s)
+        if (internal[s] && (hsst[s] & BS_CAP)) regrow = true;
+      if (regrow) {
+        BK(cudaStreamSynchronize(st));
+        const int rc = assign_mid(htot, false);
+        if (rc != DEXEL_OK) return rc;
+        for (int s = 0; s < ns; ++s)
+          if (internal[s]) hsst[s] &= ~BS_CAP;
+        memcpy(E->host, hs.data(), sizeof(BShape<T>) * ns);
+        BK(cudaMemcpyAsync(dS, E->host, sizeof(BShape<T>) * ns, cudaMemcpyHostToDevice, st));
+        BK(cudaMemcpyAsync(d_sst, hsst.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+        rewrite = true;
       }
-      size_t o = 0;
-      for (int s = 0; s < ns; ++s) {
-        if (items[s].out_z) continue;
-        items[s].out_col_off = (int*)((char*)E->mid + o);
-        o += bal(sizeof(int) * (colb[s + 1] - colb[s] + 1));
-        items[s].out_z = (char*)E->mid + o;
-        items[s].out_cap = std::max<long long>(htot[s], 1);
-        o += bal(sizeof(T) * 2 * items[s].out_cap);
-        hs[s].out_col_off = items[s].out_col_off;
-        hs[s].out_z = (T*)items[s].out_z;
-        hs[s].out_cap = items[s].out_cap;
-        hsst[s] &= ~BS_CAP;
-      }
-      BK(cudaStreamSynchronize(st));
-      memcpy(E->host, hs.data(), sizeof(BShape<T>) * ns);
-      BK(cudaMemcpyAsync(dS, E->host, sizeof(BShape<T>) * ns, cudaMemcpyHostToDevice, st));
-      BK(cudaMemcpyAsync(d_sst, hsst.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
     }
-    if (ncols > 0) {
+    if ((rewrite || !write_in_seq) && ncols > 0) {
       k_b_write<T><<<(unsigned)((ncols + thr - 1) / thr), thr, 0, st>>>(dS, d_colb, ns, ncols, pos,
                                                                         sums, d_tot, d_sst);
       if (launches) ++*launches;
       BK(cudaGetLastError());
     }
+    E->last_tot[sig] = htot;
     // record the sequence for the next call with this signature (recording does not run it)
     if (!replay) {
       if (!E->cap_stream) BK(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));

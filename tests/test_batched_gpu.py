@@ -2,8 +2,8 @@
 
 Shapes of uneven size with their own radius and operation run in one batched call (one
 launch per stage over all shapes); every shape's result is compared with the oracle with the
-tolerances of the other parity tests.  The second call with the same shapes replays the
-recorded CUDA graph; its results must be the same.
+tolerances of the other parity tests.  Later calls with the same shapes replay the recorded
+CUDA graph (through the output write); their results must be the same.
 """
 import math
 
@@ -90,7 +90,9 @@ def test_batched_random_shapes(dx, f32):
     dt = torch.float32 if f32 else torch.float64
     grids = [dx.Grid.from_synth(g, dtype=dt) for g, _, _ in items]
     ctx = dx.Context(0)
-    for rep in range(2):  # the second call replays the recorded graph
+    # the second call sizes the closings' and openings' internal grids from the first call's
+    # totals and records the sequence through the output write; the third replays that graph
+    for rep in range(3):
         outs = ctx.run_batched([code[op] for _, op, _ in items], grids, [k for _, _, k in items])
         for (g, op, k), o in zip(items, outs):
             off, z = o.to_host()
