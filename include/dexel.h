@@ -241,17 +241,21 @@ dexel_status dexel_shell(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
  * (Sec. 3.3 applied to a table of shapes; no counterpart in the paper, which offsets one
  * model at a time).  ins / k / ops / outs are HOST arrays of nshapes entries whose grid
  * pointers are device pointers; outs[s].nseg receives each shape's segment count (the
- * needed count when its status is DEXEL_ERR_CAPACITY).  All shapes run together, one launch
- * per stage; the sequence is recorded as a CUDA graph and replayed when the next call has
- * the same shapes (sizes, radii, operations); tile shapes are autotuned on the first call of
- * such a signature (see dexel_set_batch_autotune).  Shapes of more than 131072 columns
- * (environment DEXEL_BATCH_MAX_COLS at context creation) take the single-shape path, one
- * call each: their kernels are sized for them, and batching pays off for the small shapes.
+ * needed count when its status is DEXEL_ERR_CAPACITY).  All shapes run together: one
+ * grid-strided launch per stage over the table of every shape's tiles (validation, tables,
+ * pass 1 with dominance pruning, packing, level unions, gather, count, scan, totals, write).
+ * A closing / opening runs as two such sequences (its intermediate grid in engine memory,
+ * sized from the last call of the same shapes).  The sequence is recorded as a CUDA graph
+ * and replayed, through the output write, when the next call has the same shapes (sizes,
+ * radii, operations): such a call synchronises the host once a sequence, to read the status
+ * words.  Tile shapes are autotuned on the first call of a signature (see
+ * dexel_set_batch_autotune).  Shapes of more than 131072 columns (environment
+ * DEXEL_BATCH_MAX_COLS at context creation) take the single-shape path, one call each.
  * Scratch is library-owned (ws is used only by shapes on the single-shape path: the large
- * ones, reach above 127 spacings, or a window beyond the batch kernels' limits).  d_status (device, nshapes int32, may be NULL)
- * receives each shape's dexel_status.  Returns the first failing status (or DEXEL_OK);
- * DEXEL_ERR_INVALID_ARG when any argument is invalid (nothing runs).  Synchronises the
- * stream before returning. */
+ * ones, reach above 127 spacings, or a window beyond the batch kernels' limits).  d_status
+ * (device, nshapes int32, may be NULL) receives each shape's dexel_status.  Returns the
+ * first failing status (or DEXEL_OK); DEXEL_ERR_INVALID_ARG when any argument is invalid
+ * (nothing runs).  Synchronises the stream before returning. */
 dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_in* ins,
                                   const double* k, const dexel_op* ops, dexel_mode mode,
                                   dexel_grid_out* outs, void* ws, size_t ws_bytes,

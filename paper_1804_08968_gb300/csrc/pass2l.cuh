@@ -29,8 +29,12 @@
 
 namespace dexel {
 
-// per-lane interval slots in shared memory (a slot: the pieces and |dx| of the two ends)
-constexpr int kLvlSlots = 16;
+// per-lane interval slots in shared memory (a slot: the pieces and |dx| of the two ends); a
+// list longer than this is walked again straight into place
+#ifndef DEXEL_LVL_SLOTS
+#define DEXEL_LVL_SLOTS 16
+#endif
+constexpr int kLvlSlots = DEXEL_LVL_SLOTS;
 // pieces a warp stages in shared memory at a time (a level group walks one source)
 constexpr int kLvlStage = 64;
 // w-table entries kept in shared memory when the per-lane tables do not fit (n <= k^2:
