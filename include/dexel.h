@@ -337,8 +337,10 @@ int dexel_last_kernel_ms(const dexel_ctx* ctx, double* ms, int max);
  * when it owns the workspace), [8] second launches of the pass-1 window kernel for columns
  * whose window outgrew the first launch's event room, [9] blocks of y lines the offset ran in
  * (S_mid and the level lists exist for one block at a time; 1: the whole grid at once),
- * [10] pass-1 tiles walked twice because a lane outgrew its ring region.  Returns the number
- * of entries written (at most max, 11 in all). */
+ * [10] pass-1 tiles walked twice because a lane outgrew its ring region, [11] output columns
+ * whose level lists outgrew the gather's bucket (united straight from the lists), [12] that
+ * bucket's size in intervals.  Returns the number of entries written (at most max, 13 in
+ * all). */
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max);
 
 /* Diagnostic counters of the last call: clock cycles per phase of the y sweep and mean

@@ -197,10 +197,10 @@ class Context:
     def stats(self):
         """[input segments, S_mid pieces, pass-2 intervals, output segments, max pieces per
         S_mid column, columns redone by the fallback gather (sweep: max live state), status
-        bits, attempts, pass-1 redo launches, blocks of y lines, pass-1 tiles walked twice] of
-        the last call."""
-        a = (ctypes.c_int64 * 11)()
-        n = lib().dexel_last_stats(self.ptr, a, 11)
+        bits, attempts, pass-1 redo launches, blocks of y lines, pass-1 tiles walked twice,
+        columns whose lists outgrew the gather's bucket, that bucket's size] of the last call."""
+        a = (ctypes.c_int64 * 13)()
+        n = lib().dexel_last_stats(self.ptr, a, 13)
         return [int(a[i]) for i in range(n)]
 
     def _stream(self, stream):

@@ -73,7 +73,7 @@ struct dexel_ctx {
   double stage_ms[5] = {0, 0, 0, 0, 0};
   double kernel_ms[4] = {0, 0, 0, 0};  // pass-1 kernel, k_levels, k_lgather, S_mid pack
   bool kernel_rec[4] = {false, false, false, false};
-  long long stats[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  long long stats[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long phase[16] = {};
 };
 
@@ -714,6 +714,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
           CK(cudaStreamSynchronize(st));
           ctx->needL = std::max<long long>(ctx->needL, (long long)(hc.arena_top[2] * to_grid));
+          ctx->stats[11] = std::max<long long>(ctx->stats[11], hc.over_cols);
+          ctx->stats[12] = std::max<long long>(ctx->stats[12], H.bcap);
           ctx->levels_status = hc.status;
           if (hc.over_cols * 64LL > ncols) {
             // many columns outgrew the bucket (united straight from the lists, slower): a
@@ -1336,7 +1338,7 @@ int dexel_last_phases(const dexel_ctx* ctx, uint64_t* ph, int max) {
 
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max) {
   if (!ctx || !stats) return 0;
-  int n = max < 11 ? max : 11;
+  int n = max < 13 ? max : 13;
   for (int q = 0; q < n; ++q) stats[q] = ctx->stats[q];
   return n;
 }
