@@ -57,6 +57,9 @@ struct dexel_ctx {
   // on the 2048^2 one, where each source is staged three times)
   bool levels_exact = false;
   int lane_gather_max = 4;  // pass-2 gather with one lane a column up to this reach
+  // largest bucket (intervals a column) the level gather grows to for later calls when many
+  // columns had to unite their bucket part way (DEXEL_GATHER_BUCKET_MAX)
+  int bucket_max = 2048;
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
   // needed the redo launch
@@ -721,7 +724,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
             // many columns outgrew the bucket (united straight from the lists, slower): a
             // bucket for their need in the next calls of this reach and operation
             int b = lb;
-            while (b < hc.over_max && b < 2048) b <<= 1;
+            while (b < hc.over_max && b < ctx->bucket_max) b <<= 1;
             lb = b;
           }
           if ((hc.status & ST_LEVELS_OVER) && (nb > 1 || slices)) {
@@ -1274,6 +1277,10 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   if (const char* e = getenv("DEXEL_BATCH_MAX_COLS")) c->batch_max_cols = atoll(e);
   if (const char* e = getenv("DEXEL_LEVELS_EXACT")) c->levels_exact = atoi(e) != 0;
   if (const char* e = getenv("DEXEL_LANE_GATHER_MAX")) c->lane_gather_max = atoi(e);
+  if (const char* e = getenv("DEXEL_GATHER_BUCKET_MAX")) {
+    const int v = atoi(e);
+    if (v >= 256 && v <= 8192 && (v & (v - 1)) == 0) c->bucket_max = v;
+  }
   if (const char* e = getenv("DEXEL_PASS1_GW")) {
     const int v = atoi(e);
     if (v == 1 || v == 2 || v == 4 || v == 8) c->p1l_gw = v;

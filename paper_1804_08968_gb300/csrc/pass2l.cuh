@@ -32,7 +32,7 @@ namespace dexel {
 // per-lane interval slots in shared memory (a slot: the pieces and |dx| of the two ends); a
 // list longer than this is walked again straight into place
 #ifndef DEXEL_LVL_SLOTS
-#define DEXEL_LVL_SLOTS 16
+#define DEXEL_LVL_SLOTS 8  // measured: 16 slots 261 ms, 8 slots 220 ms (2048^2 k = 64 levels)
 #endif
 constexpr int kLvlSlots = DEXEL_LVL_SLOTS;
 // pieces a warp stages in shared memory at a time (a level group walks one source)
@@ -575,7 +575,12 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
   if (redo && P.o_cnt[c] != -1) return;
   const int s0 = max(0, j - A.yw), s1 = min(P.ny - 1, j + A.yw);
   const long long qb = (long long)i * P.ny;
+  // the window's lists into the bucket, 32 sources at a time; when the next 32 would not fit,
+  // the bucket is first united into its runs (by jumps) and the runs stay as its first entries
+  // (a redo with its larger bucket does not collapse)
   int carry = 0;
+  bool failed = false, collapsed = false;
+  int need = 0;
   for (int base = s0; base <= s1; base += 32) {
     const int jj = base + lane;
     int n = 0;
@@ -593,49 +598,61 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
       }
     }
     const int inc = w_incl_add(n, lane);
+    const int chunk = w_bcast(inc, 31);
+    if (carry + chunk > bcap) {
+      need = carry + chunk;
+      int nr = -1;
+      ukey rl = 0, rr = 0;
+      if (!redo && carry > 0) {
+        const int cur_n = carry;
+        nr = jump_union(
+            [&](auto f) {
+              for (int t = lane; t < cur_n; t += 32) f(bl[t], br + t);
+            },
+            lane, rl, rr);
+      }
+      if (nr < 0 || nr + chunk > bcap) {  // warp-uniform
+        failed = true;
+        break;
+      }
+      wsync();  // the bucket is read
+      if (lane < nr) {
+        bl[lane] = rl;
+        br[lane] = rr;
+      }
+      wsync();
+      carry = nr;
+      collapsed = true;
+    }
     const int o = carry + inc - n;
 #pragma unroll 4
-    for (int k = 0; k < n && o + k < bcap; ++k) {
+    for (int k = 0; k < n; ++k) {
       const ulonglong2 v = A.l_p[st + k];  // one 16-byte load an interval
       bl[o + k] = v.x;
       br[o + k] = v.y;
     }
-    carry += w_bcast(inc, 31);
+    carry += chunk;
   }
   wsync();
+  if (failed) {
+    // more runs than a collapse keeps, or the redo's bucket is too small: handed on
+    if (lane == 0) {
+      P.o_cnt[c] = -1;
+      note_max(&P.ctr->max_state, need);
+      set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
+      atomicAdd(&P.ctr->redo_cols, 1);
+    }
+    wsync();
+    return;
+  }
+  if (collapsed && lane == 0) {  // the host sizes the next call's bucket by these
+    atomicAdd(&P.ctr->over_cols, 1);
+    note_max(&P.ctr->over_max, need);
+  }
   const int total = carry;
   ukey run_l = 0, run_r = 0;
   int nj = -1;
-  if (total > bcap) {
-    // beyond the bucket: the union by jumps straight over the window's lists
-    nj = jump_union(
-        [&](auto f) {
-          for (int jj = s0 + lane; jj <= s1; jj += 32) {
-            const long long li = (qb + j) * A.W + (jj - j + P.R);
-            if (li >= A.nlev) continue;
-            const unsigned long long e = A.l_idx[li];
-            const int n = (int)(e & kLvlIdxMaxCount);
-            const long long st = (long long)(e >> 24);
-            if (n < 0 || st < 0 || st + n > A.l_cap) continue;  // flagged by the gather above
-            for (int k = 0; k < n; ++k) f(A.l_p[st + k].x, &A.l_p[st + k].y);
-          }
-        },
-        lane, run_l, run_r);
-    if (nj < 0) {
-      if (lane == 0) {
-        P.o_cnt[c] = -1;
-        note_max(&P.ctr->max_state, total);
-        set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
-        atomicAdd(&P.ctr->redo_cols, 1);
-      }
-      wsync();
-      return;
-    }
-    if (lane == 0) {  // done from the lists; the host sizes the next call's bucket by these
-      atomicAdd(&P.ctr->over_cols, 1);
-      note_max(&P.ctr->over_max, total);
-    }
-  } else if (total > kJumpMin) {
+  if (total > kJumpMin) {
     nj = jump_union(
         [&](auto f) {
           for (int t = lane; t < total; t += 32) f(bl[t], br + t);
