@@ -148,3 +148,30 @@ def test_morphology_blocks_reduced(mode, op, monkeypatch):
     assert ctx.stats()[9] > 1, "the offsets were not split into blocks"
     ref = oracle.close(g, k) if op == "close" else oracle.open_(g, k)
     _check(off, z, _Full(ref), np.arange(g.nx * g.ny), f32, f"{op} 384^2 k=12 {mode}")
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_gather_collapse(op, monkeypatch):
+    """Windows whose level lists hold more intervals than the gather's bucket (kept at 256):
+    81 lists of 6-7 intervals a column, united into their runs part way; the result is still
+    the oracle's."""
+    import torch
+    import paper_1804_08968_gb300 as dx
+    monkeypatch.setenv("DEXEL_GATHER_BUCKET_MAX", "256")
+    rng = np.random.default_rng(91)
+    cols = {}
+    for i in range(24):
+        for j in range(96):
+            ph = float(rng.uniform(0.0, 0.01))
+            cols[(i, j)] = [(0.2 + q * 0.1 + ph, 0.25 + q * 0.1 + ph) for q in range(6)]
+    g = shapes.from_columns(24, 96, 1 / 8192, cols)
+    dg = dx.Grid.from_synth(g, dtype=torch.float64)
+    ctx = dx.Context(0)
+    for k in (40.0, 33.3):
+        for _ in range(2):  # the second call keeps the 256-interval bucket
+            out = ctx.run(dx.DILATE if op == "dilate" else dx.ERODE, dg, k)
+        off, z = out.to_host()
+        st = ctx.stats()
+        assert st[12] <= 256 and st[11] > 0, st  # columns united part way
+        ref = (oracle.dilate if op == "dilate" else oracle.erode)(g, k)
+        _check(off, z, _Full(ref), np.arange(g.nx * g.ny), False, f"collapse {op} k={k}")
