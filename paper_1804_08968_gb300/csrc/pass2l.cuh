@@ -575,13 +575,13 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
   if (redo && P.o_cnt[c] != -1) return;
   const int s0 = max(0, j - A.yw), s1 = min(P.ny - 1, j + A.yw);
   const long long qb = (long long)i * P.ny;
-  // the window's lists into the bucket, 32 sources at a time; when the next 32 would not fit,
-  // the bucket is first united into its runs (by jumps) and the runs stay as its first entries
-  // (a redo with its larger bucket does not collapse)
+  // the window's lists into the bucket, 32 sources at a time; lists that do not fit wait, the
+  // bucket is united into its runs (by jumps; the runs stay as its first entries) and they go
+  // in after them
   int carry = 0;
   bool failed = false, collapsed = false;
   int need = 0;
-  for (int base = s0; base <= s1; base += 32) {
+  for (int base = s0; base <= s1 && !failed; base += 32) {
     const int jj = base + lane;
     int n = 0;
     long long st = 0;
@@ -597,48 +597,61 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
         n = 0;
       }
     }
-    const int inc = w_incl_add(n, lane);
-    const int chunk = w_bcast(inc, 31);
-    if (carry + chunk > bcap) {
-      need = carry + chunk;
-      int nr = -1;
-      ukey rl = 0, rr = 0;
-      if (!redo && carry > 0) {
-        const int cur_n = carry;
-        nr = jump_union(
-            [&](auto f) {
-              for (int t = lane; t < cur_n; t += 32) f(bl[t], br + t);
-            },
-            lane, rl, rr);
+    bool pending = n > 0;
+    while (__any_sync(0xffffffffu, pending)) {
+      // the pending lists in lane order; those that fit after the bucket's entries go in
+      const int inc = w_incl_add(pending ? n : 0, lane);
+      bool fit = pending && carry + inc <= bcap;
+      if (!__any_sync(0xffffffffu, fit)) {
+        need = max(need, carry + w_bcast(inc, 31));
+        int nr = -1;
+        ukey rl = 0, rr = 0;
+        if (carry > 0) {
+          const int cur_n = carry;
+          nr = jump_union(
+              [&](auto f) {
+                for (int t = lane; t < cur_n; t += 32) f(bl[t], br + t);
+              },
+              lane, rl, rr);
+        }
+        if (nr < 0) {  // warp-uniform: more runs than a collapse keeps, or one long list
+          failed = true;
+          break;
+        }
+        wsync();  // the bucket is read
+        if (lane < nr) {
+          bl[lane] = rl;
+          br[lane] = rr;
+        }
+        wsync();
+        carry = nr;
+        collapsed = true;
+        fit = pending && carry + inc <= bcap;
+        if (!__any_sync(0xffffffffu, fit)) {  // a list longer than the bucket's room
+          failed = true;
+          break;
+        }
       }
-      if (nr < 0 || nr + chunk > bcap) {  // warp-uniform
-        failed = true;
-        break;
-      }
-      wsync();  // the bucket is read
-      if (lane < nr) {
-        bl[lane] = rl;
-        br[lane] = rr;
-      }
-      wsync();
-      carry = nr;
-      collapsed = true;
-    }
-    const int o = carry + inc - n;
+      if (fit) {
+        const int o = carry + inc - n;
 #pragma unroll 4
-    for (int k = 0; k < n; ++k) {
-      const ulonglong2 v = A.l_p[st + k];  // one 16-byte load an interval
-      bl[o + k] = v.x;
-      br[o + k] = v.y;
+        for (int k = 0; k < n; ++k) {
+          const ulonglong2 v = A.l_p[st + k];  // one 16-byte load an interval
+          bl[o + k] = v.x;
+          br[o + k] = v.y;
+        }
+      }
+      carry += __reduce_max_sync(0xffffffffu, fit ? inc : 0);
+      pending = pending && !fit;
     }
-    carry += chunk;
   }
   wsync();
   if (failed) {
-    // more runs than a collapse keeps, or the redo's bucket is too small: handed on
+    // more runs than a collapse keeps, or a list beyond the bucket: handed on (the redo takes
+    // a bucket at least twice as large)
     if (lane == 0) {
       P.o_cnt[c] = -1;
-      note_max(&P.ctr->max_state, need);
+      note_max(&P.ctr->max_state, max(need, 2 * bcap));
       set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
       atomicAdd(&P.ctr->redo_cols, 1);
     }
