@@ -128,7 +128,7 @@ typedef struct dexel_ctx dexel_ctx;
  *   DEXEL_LEVELS_EXACT=0|1          level walks at reach >= 32 read S_mid itself (default 0)
  *   DEXEL_GATHER_BUCKET_MAX=256..8192  largest bucket (intervals a column, a power of two) the
  *                                   level gather grows to when many columns had to unite
- *                                   their bucket part way (default 2048)
+ *                                   their bucket part way (default 512)
  *   DEXEL_BATCH_MAX_COLS=n          batched calls: shapes above n columns take the
  *                                   single-shape path (default 131072) */
 dexel_status dexel_ctx_create(dexel_ctx** ctx, int device);

@@ -59,7 +59,7 @@ struct dexel_ctx {
   int lane_gather_max = 4;  // pass-2 gather with one lane a column up to this reach
   // largest bucket (intervals a column) the level gather grows to for later calls when many
   // columns had to unite their bucket part way (DEXEL_GATHER_BUCKET_MAX)
-  int bucket_max = 2048;
+  int bucket_max = 512;  // (measured: 4096^2 k = 128, the gather 700 ms at 2048, 320 ms at 512)
   bool sweep2 = false;  // pass 2 as the per-line sweep instead of the window gather
   // gather: bucket entries per column, learnt per (radius, op): grown when many columns
   // needed the redo launch
@@ -750,7 +750,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
               // with a bucket for their need
               int b = 2 * H.bcap;
               while (b < hc.max_state && b < 8192) b <<= 1;
-              if (hc.redo_cols * 64LL > ncols) lb = std::min(2 * lb, 2048);  // next calls
+              if (hc.redo_cols * 64LL > ncols) lb = std::min(2 * lb, ctx->bucket_max);  // next calls
               if (b >= hc.max_state) {
                 CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
                 CK(launch_lgather<T>(H, b, 1, st, sms));

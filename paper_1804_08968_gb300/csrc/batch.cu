@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_b_levels(const BShape<T>* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const LvlLayout Lo = lvl_layout(blockDim.x >> 5, 0);
-  unsigned* ws = (unsigned*)(smem + Lo.slots) + warp * 2 * kLvlSlots * 32;
+  unsigned* ws = (unsigned*)(smem + Lo.slots) + warp * 2 * kLvlSlots * 32;  // room for any shape's
   float4* stg = (float4*)(smem + Lo.stage) + warp * kLvlStage;
   float* wt = (float*)(smem + Lo.total) + (long long)warp * tstride;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
@@ -595,6 +595,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       v.l_p = l_p; v.l_cap = pl.capL;
       v.l_idx = l_idx + nlb[s];
       v.W = 2 * K[s] + 1;
+      v.slots = lvl_slots_for(K[s]);
       v.L = K[s] + 1;
       v.G = v.L <= 32 ? 32 / v.L : 1;
       v.NG = v.L <= 32 ? 0 : (K[s] + 31) / 32;

@@ -10,8 +10,8 @@ template <typename T, bool LTAB, bool EXACT>
 __global__ void __launch_bounds__(256, 4) k_levels(LvlParams<T> A, int tab_floats) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const LvlLayout Lo = lvl_layout(blockDim.x >> 5, tab_floats);
-  unsigned* ws = (unsigned*)(smem + Lo.slots) + warp * 2 * kLvlSlots * 32;
+  const LvlLayout Lo = lvl_layout(blockDim.x >> 5, tab_floats, A.slots);
+  unsigned* ws = (unsigned*)(smem + Lo.slots) + warp * 2 * A.slots * 32;
   float4* stg = (float4*)(smem + Lo.stage) + warp * kLvlStage;
   const float* tab = lvl_tables<LTAB>((float*)(smem + Lo.tab), A.P.R, A.L, A.G, A.NG, A.P.nmax,
                                       A.P.wtabf);
@@ -69,6 +69,7 @@ static LvlParams<T> lvl_params(const LvlParamsHost<T>& H) {
   A.P = H.P;
   A.l_p = H.l_p; A.l_cap = H.l_cap;
   A.W = 2 * H.P.R + 1;
+  A.slots = lvl_slots_for(H.P.R);
   A.L = H.P.R + 1;
   if (A.L <= 32) {
     A.G = 32 / A.L;
@@ -98,7 +99,7 @@ cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms) {
   const long long lt = lvl_lane_tab(H.P.R);
   const bool ltab = lt <= kLvlLaneTab;
   const int tab_floats = ltab ? (int)lt : (H.P.nmax + 1 <= kLvlTable ? H.P.nmax + 1 : 0);
-  const size_t sm1 = (size_t)lvl_layout(8, tab_floats).total;
+  const size_t sm1 = (size_t)lvl_layout(8, tab_floats, A.slots).total;
   auto kern = ltab ? (H.exact ? k_levels<T, true, true> : k_levels<T, true, false>)
                    : (H.exact ? k_levels<T, false, true> : k_levels<T, false, false>);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);

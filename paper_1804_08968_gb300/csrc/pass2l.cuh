@@ -31,10 +31,11 @@ namespace dexel {
 
 // per-lane interval slots in shared memory (a slot: the pieces and |dx| of the two ends); a
 // list longer than this is walked again straight into place
-#ifndef DEXEL_LVL_SLOTS
-#define DEXEL_LVL_SLOTS 8  // measured: 16 slots 261 ms, 8 slots 220 ms (2048^2 k = 64 levels)
-#endif
-constexpr int kLvlSlots = DEXEL_LVL_SLOTS;
+// list longer than this is walked again straight into place.  The count a launch uses
+// (LvlParams::slots) follows the reach: longer windows give longer lists (measured: 2048^2
+// k = 64, 16 slots 261 ms, 8 slots 220 ms; 4096^2 k = 128, 16 slots 1541 ms, 8 slots 2110 ms)
+constexpr int kLvlSlots = 16;  // the most a launch uses
+DXI int lvl_slots_for(int R) { return R <= 64 ? 8 : 16; }
 // pieces a warp stages in shared memory at a time (a level group walks one source)
 constexpr int kLvlStage = 64;
 // w-table entries kept in shared memory when the per-lane tables do not fit (n <= k^2:
@@ -61,6 +62,7 @@ struct LvlParams {
   int L;     // levels a source: R + 1
   int G;     // sources a warp when L <= 32, else 1
   int NG;    // level groups of 32 (levels 1 .. R) when L > 32, else 0
+  int slots;       // per-lane interval slots of the level walks (at most kLvlSlots)
   int yw;          // reach of the output column's window along y (R; 0: the 2D slices, each
                    // column its own level-0 list)
   long long q0;    // first source column of the block (line order q = i * ny + j)
@@ -93,10 +95,10 @@ DXI long long lvl_lane_tab(int R) {
 struct LvlLayout {
   long long slots, stage, tab, total;
 };
-DXI LvlLayout lvl_layout(int warps, int tab_floats) {
+DXI LvlLayout lvl_layout(int warps, int tab_floats, int slots = kLvlSlots) {
   LvlLayout o;
   o.slots = 0;
-  o.stage = (long long)warps * 2 * kLvlSlots * 32 * sizeof(unsigned);
+  o.stage = (long long)warps * 2 * slots * 32 * sizeof(unsigned);
   o.tab = o.stage + (long long)warps * kLvlStage * 16;
   o.total = o.tab + (long long)tab_floats * sizeof(float);
   return o;
@@ -169,10 +171,11 @@ DXD void lvl_close(LvlRun& s, const Emit& emit) {
 // its right end kLvlSlots * 32 words further
 struct PackEmit {
   unsigned* sl;  // ws + lane
+  int slots;
   DXD void operator()(const LvlRun& s) const {
-    if (s.cnt < kLvlSlots) {
+    if (s.cnt < slots) {
       sl[s.cnt << 5] = s.pl;
-      sl[(s.cnt << 5) + kLvlSlots * 32] = s.pr;
+      sl[(s.cnt << 5) + slots * 32] = s.pr;
     }
   }
 };
@@ -297,16 +300,16 @@ DXD bool lvl_flush(const LvlParams<T>& A, int lane, const unsigned* ws, int cnt,
     const int cno = __shfl_sync(0xffffffffu, cnt, own);
     const int tto = __shfl_sync(0xffffffffu, tt, own);
     const long long mso = __shfl_sync(0xffffffffu, ms, own);
-    if (idx < tot && cno <= kLvlSlots) {
+    if (idx < tot && cno <= A.slots) {
       const int k = idx - exo;
       const unsigned pl = ws[(k << 5) + own];
-      const unsigned pr = ws[(k << 5) + own + kLvlSlots * 32];
+      const unsigned pr = ws[(k << 5) + own + A.slots * 32];
       const unsigned m = (1u << kLvlDxBits) - 1;
       A.l_p[s + idx] = make_ulonglong2(lvl_left<T>(P, mso, (int)(pl >> kLvlDxBits), (int)(pl & m), tto),
                                        lvl_right<T>(P, mso, (int)(pr >> kLvlDxBits), (int)(pr & m), tto));
     }
   }
-  if (cnt > kLvlSlots) redo(A.l_p + s + ex);
+  if (cnt > A.slots) redo(A.l_p + s + ex);
   if (act) {
     // the list serves output columns j +- t of its line: entry R - t of column j + t and entry
     // R + t of column j - t
@@ -396,7 +399,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     }
     const auto src = lvl_src<T, EXACT>(P, ms, cs);
     LvlRun s = lvl_run();
-    const PackEmit pe{ws + lane};
+    const PackEmit pe{ws + lane, A.slots};
     if (TABM != kTabFlat) {
       STab wl;
       if (TABM == kTabWarp) {
@@ -434,7 +437,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
   const long long ms = P.m_start[q], cs = EXACT ? 0 : P.c_start[q];
   const auto src = lvl_src<T, EXACT>(P, ms, cs);
   LvlRun s = lvl_run();
-  const PackEmit pe{ws + lane};
+  const PackEmit pe{ws + lane, A.slots};
   if (TABM != kTabFlat) {
     STab wl;
     if (TABM == kTabWarp) {
@@ -614,16 +617,26 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
               },
               lane, rl, rr);
         }
-        if (nr < 0) {  // warp-uniform: more runs than a collapse keeps, or one long list
+        if (nr >= 0) {
+          wsync();  // the bucket is read
+          if (lane < nr) {
+            bl[lane] = rl;
+            br[lane] = rr;
+          }
+          wsync();
+        } else if (carry > 0) {
+          // more runs than the jumps keep (or a long chain): the bucket sorted and united in
+          // place
+          const int n2 = pow2_at_least(carry);
+          for (int t = carry + lane; t < n2; t += 32) { bl[t] = ~0ULL; br[t] = ~0ULL; }
+          wsync();
+          warp_sort_pairs(L, bl, br, n2);
+          nr = union_count(L, bl, br, carry, f0, f1);
+          union_write_inplace(L, bl, br, carry, f0, f1);
+        } else {  // one list longer than the bucket
           failed = true;
           break;
         }
-        wsync();  // the bucket is read
-        if (lane < nr) {
-          bl[lane] = rl;
-          br[lane] = rr;
-        }
-        wsync();
         carry = nr;
         collapsed = true;
         fit = pending && carry + inc <= bcap;
