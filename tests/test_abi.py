@@ -26,9 +26,32 @@ def libpath():
 def test_header_declares_the_boundary():
     syms = declared_symbols()
     for s in ["dexel_ctx_create", "dexel_ctx_destroy", "dexel_dilate", "dexel_erode",
-              "dexel_offset_batched", "dexel_workspace_size", "dexel_validate",
-              "dexel_status_string"]:
+              "dexel_morph", "dexel_offset_batched", "dexel_workspace_size", "dexel_validate",
+              "dexel_status_string", "dexel_boolean", "dexel_shell", "dexel_offset_slices",
+              "dexel_raycast", "dexel_raycast_axis", "dexel_offset_ldi", "dexel_offset_noalloc"]:
         assert s in syms
+
+
+def test_entry_points_reject_missing_arguments(libpath):
+    """Every compute entry point returns DEXEL_ERR_INVALID_ARG for a null context or output
+    before touching the device (host-side checks only)."""
+    import paper_1804_08968_gb300 as dx
+    L = dx.lib()
+    P = ctypes.c_void_p
+    gin = dx._In(4, 4, 0.1, 1, 1, 0)
+    out = dx._Out(1, 1, 10, 0)
+    assert L.dexel_dilate(None, ctypes.byref(gin), 1.0, 0, ctypes.byref(out), None, 0, None) == -1
+    assert L.dexel_boolean(None, 0, ctypes.byref(gin), ctypes.byref(gin), 0, ctypes.byref(out),
+                           None, 0, None) == -1
+    assert L.dexel_shell(None, ctypes.byref(gin), 1.0, 0, ctypes.byref(out), None, 0, None) == -1
+    assert L.dexel_offset_slices(None, ctypes.byref(gin), 1.0, 0, 0, ctypes.byref(out), None, 0,
+                                 None) == -1
+    assert L.dexel_raycast_axis(None, None, 0, 2, 4, 4, 0.25, 0, ctypes.byref(out), None, 0,
+                                None) == -1
+    assert L.dexel_offset_ldi(None, None, 1.0, 0, 0, None, None, 0, None) == -1
+    # a bad operation is refused the same way
+    assert L.dexel_offset_slices(None, ctypes.byref(gin), 1.0, 7, 0, ctypes.byref(out), None, 0,
+                                 None) == -1
 
 
 def test_library_exports_every_declared_symbol(libpath):
