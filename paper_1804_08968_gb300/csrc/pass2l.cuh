@@ -634,6 +634,7 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
           nr = union_count(L, bl, br, carry, f0, f1);
           union_write_inplace(L, bl, br, carry, f0, f1);
         } else {  // one list longer than the bucket
+          need = max(need, __reduce_max_sync(0xffffffffu, pending ? n : 0) + 32);
           failed = true;
           break;
         }
@@ -641,6 +642,7 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
         collapsed = true;
         fit = pending && carry + inc <= bcap;
         if (!__any_sync(0xffffffffu, fit)) {  // a list longer than the bucket's room
+          need = max(need, carry + __reduce_max_sync(0xffffffffu, pending ? n : 0));
           failed = true;
           break;
         }
