@@ -747,17 +747,16 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
             done = true;
             if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
               // columns whose lists outgrew the bucket: the gather again, those columns only,
-              // with a bucket for their need
+              // with a bucket for their need (8192 entries at most: columns beyond it are
+              // left for the window gather below)
               int b = 2 * H.bcap;
               while (b < hc.max_state && b < 8192) b <<= 1;
               if (hc.redo_cols * 64LL > ncols) lb = std::min(2 * lb, ctx->bucket_max);  // next calls
-              if (b >= hc.max_state) {
-                CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
-                CK(launch_lgather<T>(H, b, 1, st, sms));
-                ++ctx->launches;
-                CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-              }
+              CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+              CK(launch_lgather<T>(H, b, 1, st, sms));
+              ++ctx->launches;
+              CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+              CK(cudaStreamSynchronize(st));
             }
           }
         }

@@ -583,7 +583,8 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
   // in after them
   int carry = 0;
   bool failed = false, collapsed = false;
-  int need = 0;
+  int need = 0;   // the window's entries before a collapse (sizes the next calls' bucket)
+  int fneed = 0;  // a bucket that would have held the list that did not fit (the redo's)
   for (int base = s0; base <= s1 && !failed; base += 32) {
     const int jj = base + lane;
     int n = 0;
@@ -634,7 +635,7 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
           nr = union_count(L, bl, br, carry, f0, f1);
           union_write_inplace(L, bl, br, carry, f0, f1);
         } else {  // one list longer than the bucket
-          need = max(need, __reduce_max_sync(0xffffffffu, pending ? n : 0) + 32);
+          fneed = __reduce_max_sync(0xffffffffu, pending ? n : 0) + 32;
           failed = true;
           break;
         }
@@ -642,7 +643,7 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
         collapsed = true;
         fit = pending && carry + inc <= bcap;
         if (!__any_sync(0xffffffffu, fit)) {  // a list longer than the bucket's room
-          need = max(need, carry + __reduce_max_sync(0xffffffffu, pending ? n : 0));
+          fneed = carry + __reduce_max_sync(0xffffffffu, pending ? n : 0);
           failed = true;
           break;
         }
@@ -666,7 +667,7 @@ __device__ __forceinline__ void lgather_column(const LvlParams<T>& A, long long 
     // a bucket at least twice as large)
     if (lane == 0) {
       P.o_cnt[c] = -1;
-      note_max(&P.ctr->max_state, max(need, 2 * bcap));
+      note_max(&P.ctr->max_state, max(fneed, 2 * bcap));
       set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
       atomicAdd(&P.ctr->redo_cols, 1);
     }
