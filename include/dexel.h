@@ -114,6 +114,14 @@ typedef struct dexel_ctx dexel_ctx;
  *   DEXEL_PASS1_ECAP_RULE=mean|max  event room a tile by the mean density of the windows, the
  *                                   few denser columns redone by a second launch (mean,
  *                                   default), or room for the densest window from the start
+ *   DEXEL_PASS1_ECAP_MUL=x          rule "mean": room for x times twice the mean window's
+ *                                   events (0.5 .. 64; default: twice the mean, then more
+ *                                   while the windows beyond the room hold more than 2 % of
+ *                                   all windows' events)
+ *   DEXEL_PASS1_NBUF=1|2            event buffers a pass-1 tile (2: every window that fits is
+ *                                   merged from its sources' runs; 1: those of up to half the
+ *                                   room, the others sorted; default 2 where it costs no block
+ *                                   an SM)
  *   DEXEL_BLOCK_MB=n                split an offset into blocks of whole y lines when its
  *                                   S_mid, packed copy and level lists would take more than
  *                                   n MB (default: 0.45 of the device memory free when the
@@ -342,8 +350,8 @@ int dexel_last_kernel_ms(const dexel_ctx* ctx, double* ms, int max);
  * (S_mid and the level lists exist for one block at a time; 1: the whole grid at once),
  * [10] pass-1 tiles walked twice because a lane outgrew its ring region, [11] output columns
  * whose level lists outgrew the gather's bucket (united straight from the lists), [12] that
- * bucket's size in intervals.  Returns the number of entries written (at most max, 13 in
- * all). */
+ * bucket's size in intervals, [13] the event room of a pass-1 tile.  Returns the number of
+ * entries written (at most max, 14 in all). */
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max);
 
 /* Diagnostic counters of the last call: clock cycles per phase of the y sweep and mean

@@ -198,9 +198,10 @@ class Context:
         """[input segments, S_mid pieces, pass-2 intervals, output segments, max pieces per
         S_mid column, columns redone by the fallback gather (sweep: max live state), status
         bits, attempts, pass-1 redo launches, blocks of y lines, pass-1 tiles walked twice,
-        columns whose lists outgrew the gather's bucket, that bucket's size] of the last call."""
-        a = (ctypes.c_int64 * 13)()
-        n = lib().dexel_last_stats(self.ptr, a, 13)
+        columns whose lists outgrew the gather's bucket, that bucket's size, the event room of a
+        pass-1 tile] of the last call."""
+        a = (ctypes.c_int64 * 14)()
+        n = lib().dexel_last_stats(self.ptr, a, 14)
         return [int(a[i]) for i in range(n)]
 
     def _stream(self, stream):

@@ -38,6 +38,8 @@ struct dexel_ctx {
   bool lane1 = true;    // pass 1 with one lane per column where the windows fit
   bool merge1 = true;   // short reaches: the per-lane merge instead
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
+  int p1l_nbuf = 0;     // its event buffers (0: two where they cost no block an SM)
+  double p1l_ecap_mul = 0;  // its event room: this many times twice the mean window's events (0: by reach)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
   bool p1l_ring = true; // one walk into a ring (else a counting walk and a writing walk)
   bool p1l_ecap_max = false;  // event room for the densest window from the start (no redo)
@@ -76,7 +78,7 @@ struct dexel_ctx {
   double stage_ms[5] = {0, 0, 0, 0, 0};
   double kernel_ms[4] = {0, 0, 0, 0};  // pass-1 kernel, k_levels, k_lgather, S_mid pack
   bool kernel_rec[4] = {false, false, false, false};
-  long long stats[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  long long stats[14] = {};
   unsigned long long phase[16] = {};
 };
 
@@ -119,6 +121,28 @@ __global__ void k_validate(int ncols, const int* off, const T* z, long long nseg
   }
   const unsigned zb = __reduce_max_sync(0xffffffffu, __float_as_uint(zm));  // zm >= 0
   if ((threadIdx.x & 31) == 0 && zb > 0) atomicMax(&ctr->zmax_bits, zb);
+}
+
+// The events of every pass-1 tile window (32 output columns of a row and the K sources on
+// either side; two events a segment, two more a column for a complement), summed by the
+// power-of-two bin of the window's size: the planner sizes the tiles' event room by them.
+__global__ void k_win_hist(int nx, int ny, int K, int erode, const int* off, Counters* ctr) {
+  __shared__ unsigned long long hb[kWinBins];
+  if (threadIdx.x < kWinBins) hb[threadIdx.x] = 0;
+  __syncthreads();
+  const int tpr = (nx + 31) >> 5;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (long long)tpr * ny) {
+    const int j = (int)(t / tpr), i0 = (int)(t % tpr) * 32;
+    const int s0 = max(0, i0 - K), s1 = min(nx, i0 + 32 + K);
+    const long long rb = (long long)j * nx;
+    const long long E = 2LL * (off[rb + s1] - off[rb + s0]) + (erode ? 2LL * (s1 - s0) : 0);
+    int b = 0;
+    while (b < kWinBins - 1 && E > (512LL << b)) ++b;
+    atomicAdd(&hb[b], (unsigned long long)E);
+  }
+  __syncthreads();
+  if (threadIdx.x < kWinBins && hb[threadIdx.x]) atomicAdd(&ctr->win_hist[threadIdx.x], hb[threadIdx.x]);
 }
 
 // rows of the grid with a column marked for the pass-1 sweep (line-2 index q = i * ny + j)
@@ -350,6 +374,11 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
       k_tables<<<(std::max(nmax, K) + 1 + 255) / 256, 256, 0, st>>>(
           kk, in->h, nmax, K, (double*)pwtab, (int*)preach, (float*)pwtabf);
       ++ctx->launches;
+      if (ctx->lane1 && K > kMergeMaxReach && K <= kLaneMaxReach1) {
+        const long long ntl = (long long)ny * ((nx + 31) / 32);
+        k_win_hist<<<(unsigned)((ntl + 255) / 256), 256, 0, st>>>(nx, ny, K, erode ? 1 : 0, in->col_off, ctr);
+        ++ctx->launches;
+      }
       CK(cudaGetLastError());
     }
     mark(ctx, 1, st);
@@ -492,8 +521,30 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         // event room by the mean density of a tile's window (columns whose own window holds
         // more are redone by a second launch with room for the densest window), or (rule
         // "max") room for the densest window from the start
+        // (ev_tile is twice the mean window; the room is p1l_ecap_mul times that: a window
+        // beyond the room is split into narrower runs of columns that stage their events
+        // again, and one within half of it is merged from its sources' runs in the other half)
+        // A window beyond the room costs more the wider the reach (halving a run of columns
+        // barely narrows a window of 2K + 1 + 32 sources), a larger room costs blocks an SM:
+        // the room grows while the windows beyond it hold more than 2 % of the events
+        // (measured: 2048^2 k = 64, 58 segments in the densest column: 16384, pass 1 246 ->
+        // 233 ms; 4096^2 k = 128, 15 segments at most: 8192, 437 against 731 ms at 16384).
+        const double mul = ctx->p1l_ecap_mul > 0 ? ctx->p1l_ecap_mul : 1.0;
         int ecapL = 512;
-        while (ecapL < 16384 && (ecapL < ev_tile || (ctx->p1l_ecap_max && ecapL < ev_win_max))) ecapL <<= 1;
+        while (ecapL < 16384 && (ecapL < mul * ev_tile || (ctx->p1l_ecap_max && ecapL < ev_win_max))) ecapL <<= 1;
+        if (ctx->p1l_ecap_mul <= 0) {
+          // more room while the windows beyond it hold more than 2 % of all window events
+          double all = 0;
+          for (int b = 0; b < kWinBins; ++b) all += (double)hc.win_hist[b];
+          auto beyond = [&](int room) {
+            double x = 0;
+            for (int b = 0; b < kWinBins; ++b)
+              if ((512LL << b) > room) x += (double)hc.win_hist[b];
+            return x;
+          };
+          while (ecapL < 16384 && beyond(ecapL) > 0.02 * all) ecapL <<= 1;
+        }
+        ctx->stats[13] = ecapL;
         if (ctx->p1l_ecap > 0) ecapL = ctx->p1l_ecap;
         // warps a tile: more as the windows grow (a tile's walk is split over its warps, its
         // sort shared); measured best on the 512^2 workload: 2 up to k = 8, 4 at k = 32
@@ -501,13 +552,21 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         if (ctx->p1l_gw > 0) gw = ctx->p1l_gw;
         const int ksz = sizeof(T) == 4 ? 4 : 8;  // the window kernel's event keys
         while (gw < 8 && pass1l_smem(K, ecapL, gw, ksz) > (220LL << 10)) gw <<= 1;
+        // a second event buffer, where it fits: every window is merged from its sources' runs
+        // (one buffer: windows of up to half of it are)
+        // (where it costs no block an SM)
+        auto per_sm = [&](int nb) { return std::min<long long>(3, (220LL << 10) / pass1l_smem(K, ecapL, gw, ksz, nb)); };
+        int nbuf = per_sm(2) >= 1 && per_sm(2) == per_sm(1) ? 2 : 1;
+        if (ctx->p1l_nbuf > 0) nbuf = ctx->p1l_nbuf;
+        if (pass1l_smem(K, ecapL, gw, ksz, nbuf) > (220LL << 10)) nbuf = 1;
+        p1.nbuf = nbuf;
         // the ring of the one-walk variant in the (free) forward arena: up to 128 pieces a
         // thread of the grid
         const int ecapR = 16384;  // the redo's event room (room for the densest window)
         const bool redo_ok = ecapL < ecapR && pass1l_smem(K, ecapR, 8, ksz) <= (220LL << 10);
         {
           // threads of the larger of the two launches (the first, and the redo's)
-          long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms, ksz) * 256;
+          long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms, ksz, nbuf) * 256;
           if (redo_ok)
             thr = std::max<long long>(thr, (long long)pass1l_blocks(nx, ny, K, ecapR, 8, sms, ksz) * 256);
           const long long esz = 2 * (long long)sizeof(Key) + 2;
@@ -545,6 +604,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
             CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
             P1Params<T> pr = p1;
             pr.redo = 1;
+            pr.nbuf = 1;  // (the densest windows: one buffer of ecapR events)
             CK(launch_pass1l<T>(pr, ecapR, 8, sms, st));
             ++ctx->launches;
             ++ctx->stats[8];  // a pass-1 redo launch
@@ -1280,6 +1340,14 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
     const int v = atoi(e);
     if (v >= 256 && v <= 8192 && (v & (v - 1)) == 0) c->bucket_max = v;
   }
+  if (const char* e = getenv("DEXEL_PASS1_ECAP_MUL")) {
+    const double v = atof(e);
+    if (v >= 0.5 && v <= 64.0) c->p1l_ecap_mul = v;
+  }
+  if (const char* e = getenv("DEXEL_PASS1_NBUF")) {
+    const int v = atoi(e);
+    if (v == 1 || v == 2) c->p1l_nbuf = v;
+  }
   if (const char* e = getenv("DEXEL_PASS1_GW")) {
     const int v = atoi(e);
     if (v == 1 || v == 2 || v == 4 || v == 8) c->p1l_gw = v;
@@ -1344,7 +1412,7 @@ int dexel_last_phases(const dexel_ctx* ctx, uint64_t* ph, int max) {
 
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max) {
   if (!ctx || !stats) return 0;
-  int n = max < 13 ? max : 13;
+  int n = max < 14 ? max : 14;
   for (int q = 0; q < n; ++q) stats[q] = ctx->stats[q];
   return n;
 }

@@ -31,8 +31,9 @@ long long pass1g_smem(int tc, int R, int ecap, int obuf);
 // gw (1, 2, 4, 8) warps a tile
 template <typename T>
 cudaError_t launch_pass1l(const P1Params<T>& P, int ecap, int gw, int sms, cudaStream_t st);
-// ksz: bytes of an event key (8 for double inputs, 4 for float)
-long long pass1l_smem(int R, int ecap, int gw, int ksz = 8);
+// ksz: bytes of an event key (8 for double inputs, 4 for float); nbuf: event buffers (2:
+// room to merge the sources' runs of any window that fits one buffer)
+long long pass1l_smem(int R, int ecap, int gw, int ksz = 8, int nbuf = 1);
 // pass 1 for reaches up to kMergeMaxReach, one lane a column merging its window's sources
 // (pass1m.cu); measured faster than the window kernel at reach 2 (0.35 against 0.57 ms on
 // the 512^2 workload), much slower at reach 8 (each step advances one of 17 slots
@@ -42,7 +43,7 @@ template <typename T>
 cudaError_t launch_pass1m(const P1Params<T>& P, int sms, cudaStream_t st);
 // blocks of 256 threads launch_pass1l starts (its ring, when given, holds r_cap pieces for
 // each of their threads)
-int pass1l_blocks(int nx, int ny, int R, int ecap, int gw, int sms, int ksz = 8);
+int pass1l_blocks(int nx, int ny, int R, int ecap, int gw, int sms, int ksz = 8, int nbuf = 1);
 template <typename T>
 cudaError_t launch_pass2(const P2Params<T>& P, int blocks, cudaStream_t st);
 template <typename T>

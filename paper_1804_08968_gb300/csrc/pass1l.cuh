@@ -73,12 +73,14 @@ struct P1LLayout {
   long long ek, ep, eoff, cb, cm, ccnt, cst, cco, cex, misc, wt, total;
 };
 DXI long long p1l_align(long long x) { return (x + 15) & ~15LL; }
-// ksz: bytes of an event key (8 for double inputs, 4 for float)
-DXI P1LLayout p1l_layout(int R, int ecap, int warps, int ksz = 8) {
+// ksz: bytes of an event key (8 for double inputs, 4 for float); nbuf: event buffers of ecap
+// events (2: the merge of the sources' runs has room for any window that fits one buffer)
+DXI P1LLayout p1l_layout(int R, int ecap, int warps, int ksz = 8, int nbuf = 1) {
   P1LLayout o;
   long long x = 0;
-  o.ek = x; x = p1l_align(x + (long long)ecap * ksz);
-  o.ep = x; x = p1l_align(x + (long long)ecap * sizeof(unsigned short));
+  const long long room = (long long)ecap * (nbuf == 2 ? 2 : 1);
+  o.ek = x; x = p1l_align(x + room * ksz);
+  o.ep = x; x = p1l_align(x + room * sizeof(unsigned short));
   o.eoff = x; x = p1l_align(x + (long long)(32 + 2 * R + 2) * sizeof(int));
   o.cb = x; x = p1l_align(x + (long long)(warps + 1) * sizeof(int));
   o.cm = x; x = p1l_align(x + (long long)warps * kP1TileWords * sizeof(ukey));
@@ -261,6 +263,47 @@ struct TGroup {
 };
 
 // One tile of k_pass1l: columns i0 .. i0 + 31 of row j, the group's warps one chunk each.
+// One level of the merge of the window's event runs: the events of source r (in height order)
+// span [bo[r] - e0, bo[r + 1] - e0) of ks / ps; after the levels of widths 1, 2, 4, ... (runs
+// of w sources merged in pairs into runs of 2w) the events are in height order.  The thread
+// writes the outputs [o0, o1) of the level into kd / pd: for each pair of runs its output
+// position is split into the two runs by a binary search along the merge path (ties: the
+// lower run first), then the two runs are merged one output at a time.
+template <typename EK>
+DXD void p1l_merge_level(const EK* ks, const unsigned short* ps, EK* kd, unsigned short* pd,
+                         const int* bo, int e0, int nr, int w, int o0, int o1) {
+  auto bnd = [&](int r) { return bo[r < nr ? r : nr] - e0; };
+  const int np = (nr + 2 * w - 1) / (2 * w);
+  // the pair that holds output o0: the last whose start is at or below it
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bnd(2 * w * mid) <= o0) lo = mid; else hi = mid - 1;
+  }
+  int o = o0;
+  for (int p = lo; o < o1 && p < np; ++p) {
+    const int a0 = bnd(2 * w * p), a1 = bnd(2 * w * p + w), a2 = bnd(2 * w * p + 2 * w);
+    if (o >= a2) continue;
+    const int nL = a1 - a0, nR = a2 - a1, k = o - a0;
+    // left events among the pair's first k outputs
+    int i0 = k - nR > 0 ? k - nR : 0, i1 = k < nL ? k : nL;
+    while (i0 < i1) {
+      const int mid = (i0 + i1) >> 1;
+      if (ks[a0 + mid] <= ks[a1 + k - 1 - mid]) i0 = mid + 1; else i1 = mid;
+    }
+    int i = i0, j = k - i0;
+    const int oe = o1 < a2 ? o1 : a2;
+    for (; o < oe; ++o) {
+      const bool left = j >= nR || (i < nL && ks[a0 + i] <= ks[a1 + j]);
+      const int src = left ? a0 + i : a1 + j;
+      kd[o] = ks[src];
+      pd[o] = ps[src];
+      i += left ? 1 : 0;
+      j += left ? 0 : 1;
+    }
+  }
+}
+
 template <typename T, int NH>
 DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned char* smem,
                      const TGroup& G, ArenaCursor& cur) {
@@ -268,7 +311,9 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
   const int W = G.W;
   const int gthreads = W * 32;
   typedef typename EvK<T>::type EK;
-  const P1LLayout Lo = p1l_layout(P.K, ecap, W, (int)sizeof(EK));
+  const int nbuf = P.nbuf == 2 ? 2 : 1;
+  const P1LLayout Lo = p1l_layout(P.K, ecap, W, (int)sizeof(EK), nbuf);
+  const int room = nbuf * ecap;  // events of the buffers
   EK* ek = (EK*)(smem + Lo.ek);
   unsigned short* ep = (unsigned short*)(smem + Lo.ep);
   int* eoff = (int*)(smem + Lo.eoff);
@@ -378,32 +423,57 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       }
       for (; o < oend; ++o) { ek[o] = EvK<T>::none(); ep[o] = 0xFFFFu; }
     }
-    for (int t = E + G.gtid; t < n2; t += gthreads) { ek[t] = EvK<T>::none(); ep[t] = 0xFFFFu; }
+    // the events in height order (the order within a height does not matter): merged from
+    // the sources' runs when the buffers hold the window twice, else a bitonic sort in place
+    const bool merge = 2 * E <= room;
+    if (!merge)
+      for (int t = E + G.gtid; t < n2; t += gthreads) { ek[t] = EvK<T>::none(); ep[t] = 0xFFFFu; }
     G.sync();
     PHASE(0);
-    // block bitonic sort by height (the order within a height does not matter)
-    for (int k = 2; k <= n2; k <<= 1) {
-      for (int jj = k >> 1; jj > 0; jj >>= 1) {
-        for (int p = G.gtid; p < (n2 >> 1); p += gthreads) {
-          const int t = ((p & ~(jj - 1)) << 1) | (p & (jj - 1));
-          const int x = t | jj;
-          const bool up = (t & k) == 0;
-          const EK kt = ek[t], kx = ek[x];
-          if ((kt > kx) == up) {
-            ek[t] = kx; ek[x] = kt;
-            const unsigned short vt = ep[t]; ep[t] = ep[x]; ep[x] = vt;
-          }
-        }
+    const EK* eks = ek;
+    const unsigned short* eps = ep;
+    int Er;
+    if (merge) {
+      EK* ka = ek;
+      unsigned short* pa = ep;
+      EK* kb = ek + (room >> 1);
+      unsigned short* pb = ep + (room >> 1);
+      const int nr = qe - qa;
+      const int per = (E + gthreads - 1) / gthreads;
+      const int o0 = min(E, G.gtid * per), o1 = min(E, o0 + per);
+      for (int w = 1; w < nr; w <<= 1) {
+        p1l_merge_level<EK>(ka, pa, kb, pb, eoff + qa, e0, nr, w, o0, o1);
         G.sync();
+        EK* tk = ka; ka = kb; kb = tk;
+        unsigned short* tp = pa; pa = pb; pb = tp;
       }
+      eks = ka;
+      eps = pa;
+      Er = lower_bound(eks, E, EvK<T>::none());  // (a complement's padding sorts last)
+    } else {
+      for (int k = 2; k <= n2; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+          for (int p = G.gtid; p < (n2 >> 1); p += gthreads) {
+            const int t = ((p & ~(jj - 1)) << 1) | (p & (jj - 1));
+            const int x = t | jj;
+            const bool up = (t & k) == 0;
+            const EK kt = ek[t], kx = ek[x];
+            if ((kt > kx) == up) {
+              ek[t] = kx; ek[x] = kt;
+              const unsigned short vt = ep[t]; ep[t] = ep[x]; ep[x] = vt;
+            }
+          }
+          G.sync();
+        }
+      }
+      Er = lower_bound(ek, n2, EvK<T>::none());  // real events (the padding sorts last)
     }
     PHASE(1);
-    // real events (the padding sorts last); chunk bounds at group boundaries
-    const int Er = lower_bound(ek, n2, EvK<T>::none());
+    // chunk bounds at group boundaries
     if (G.gtid == 0) ((int*)misc)[2] = 0;  // no ring region overflowed yet
     if (warp == 0 && lane <= W) {
       int b = (int)((long long)lane * Er / W);
-      while (b > 0 && b < Er && ek[b] == ek[b - 1]) ++b;
+      while (b > 0 && b < Er && eks[b] == eks[b - 1]) ++b;
       cb[lane] = b;
     }
     G.sync();
@@ -414,7 +484,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
 #pragma unroll
       for (int q = 0; q < kP1TileWords; ++q) lm[q] = 0;
       for (int t = c0 + lane; t < c1; t += 32) {
-        const int src = ep[t];
+        const int src = eps[t];
         const ukey bit = 1ULL << (src & 63);
 #pragma unroll
         for (int q = 0; q < kP1TileWords; ++q) lm[q] ^= (src >> 6) == q ? bit : 0ULL;
@@ -453,10 +523,10 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     int n;
     const Prune pr{P.prune_w ? (const float*)(smem + Lo.wt) : nullptr, P.prune_E};
     if (ring)
-      n = chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, (EK)0, last, rg_a + rbase,
+      n = chunk_walk<T, NH, true>(eks, eps, c0, c1, pc, R, act, m0, Om0, (EK)0, last, rg_a + rbase,
                                   rg_b + rbase, rg_l + rbase, P.r_cap, pr);
     else
-      n = chunk_walk<T, NH, false>(ek, ep, c0, c1, pc, R, act, m0, Om0, (EK)0, last, nullptr,
+      n = chunk_walk<T, NH, false>(eks, eps, c0, c1, pc, R, act, m0, Om0, (EK)0, last, nullptr,
                                    nullptr, nullptr, 0, pr);
     ccnt[warp * 32 + lane] = n;
     cst[warp * 32 + lane] = last;
@@ -517,7 +587,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     } else if (fits && n > 0) {
       const long long o = s + (inc - tot_col) + before;
       EK dummy;
-      chunk_walk<T, NH, true>(ek, ep, c0, c1, pc, R, act, m0, Om0, run_a, dummy, P.m_a + o,
+      chunk_walk<T, NH, true>(eks, eps, c0, c1, pc, R, act, m0, Om0, run_a, dummy, P.m_a + o,
                               P.m_b + o, P.m_l + o, 1 << 30, pr);
     }
     if (warp == 0) {

@@ -400,6 +400,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     const auto src = lvl_src<T, EXACT>(P, ms, cs);
     LvlRun s = lvl_run();
     const PackEmit pe{ws + lane, A.slots};
+    PHASE_BEGIN();
     if (TABM != kTabFlat) {
       STab wl;
       if (TABM == kTabWarp) {
@@ -413,6 +414,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
         LvlRun s2 = lvl_run();
         walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
       });
+      PHASE(8);
     } else {
       const FlatTab wl{tab, t * t, P.nmax};
       walk_global<T>(P, src, 0, np, E, wl, s, pe);
@@ -439,6 +441,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
   LvlRun s = lvl_run();
   const PackEmit pe{ws + lane, A.slots};
   if (TABM != kTabFlat) {
+    PHASE_BEGIN();
     STab wl;
     if (TABM == kTabWarp) {
       lvl_warp_table(tab, P.R, P.nmax, P.wtabf, lane, t, act);
@@ -447,10 +450,17 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
       wl = STab{tab + (long long)grp * R1 * 32 + lane, 5};
     }
     walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe);
+    PHASE(6);
+#if defined(DEXEL_PHASES) && defined(__CUDA_ARCH__)
+    const unsigned ph_cnt = __reduce_add_sync(0xffffffffu, (unsigned)s.cnt);  // (all lanes)
+    PHASE_COUNT(12, ph_cnt);
+#endif
+    PHASE_COUNT(13, np);
     lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
       LvlRun s2 = lvl_run();
       walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
     });
+    PHASE(7);
   } else {
     const FlatTab wl{tab, t * t, P.nmax};
     walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe);

@@ -39,6 +39,7 @@ enum : int {
   ST_BOUNDS = 32,          // a self-check found an index out of its array (access skipped)
 };
 
+constexpr int kWinBins = 8;
 struct Counters {
   unsigned long long arena_top[4];  // bump pointers of the arenas
   unsigned long long work_next[2];  // persistent work queues
@@ -56,6 +57,9 @@ struct Counters {
   int over_max;                   //   and the most intervals one of them collected
   int ring_spills;                // pass-1 window kernel: tiles walked twice (a lane's ring
                                   // region overflowed)
+  unsigned long long win_hist[kWinBins];  // pass-1 window events by tile: bin b holds the
+                                          // events of the tiles with 2^(8+b) < E <= 2^(9+b)
+                                          // (bin 0: E <= 512; the last: E > 2^(8+kWinBins-1))
   unsigned long long phase[16];   // optional per-phase clock totals (DEXEL_PHASES builds)
 };
 
@@ -69,6 +73,7 @@ struct Counters {
     if ((threadIdx.x & 31) == 0) atomicAdd(&P.ctr->phase[k], (unsigned long long)(ph_t1_ - ph_t0_)); \
     ph_t0_ = ph_t1_;                                                      \
   } while (0)
+// (v is evaluated by lane 0 alone: no warp-collective operation may appear in it)
 #define PHASE_COUNT(k, v) \
   do { if ((threadIdx.x & 31) == 0) atomicAdd(&P.ctr->phase[k], (unsigned long long)(v)); } while (0)
 #else
@@ -251,6 +256,8 @@ struct P1Params {
   int* rowmark; int redo;
   // the window kernel's block of output columns: i in [xa, xb) (xb = 0: the whole row)
   int xa, xb;
+  // the window kernel's event buffers (1 or 2; 0 counts as 1)
+  int nbuf;
   // local index of forward states for the current chunk: per warp, chunk entries
 };
 
