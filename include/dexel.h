@@ -118,6 +118,9 @@ typedef struct dexel_ctx dexel_ctx;
  *                                   events (0.5 .. 64; default: twice the mean, then more
  *                                   while the windows beyond the room hold more than 2 % of
  *                                   all windows' events)
+ *   DEXEL_LEVEL_SLOTS=2..16         interval slots a lane of the pass-2 level walks holds in
+ *                                   shared memory (a longer list is walked again straight
+ *                                   into place; default 8 up to reach 64, 16 beyond)
  *   DEXEL_PASS1_NBUF=1|2            event buffers a pass-1 tile (2: every window that fits is
  *                                   merged from its sources' runs; 1: those of up to half the
  *                                   room, the others sorted; default 2 where it costs no block

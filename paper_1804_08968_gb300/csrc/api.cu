@@ -38,6 +38,7 @@ struct dexel_ctx {
   bool lane1 = true;    // pass 1 with one lane per column where the windows fit
   bool merge1 = true;   // short reaches: the per-lane merge instead
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
+  int lvl_slots = 0;    // interval slots a lane of the level walks (0: by reach)
   int p1l_nbuf = 0;     // its event buffers (0: two where they cost no block an SM)
   double p1l_ecap_mul = 0;  // its event room: this many times twice the mean window's events (0: by reach)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
@@ -764,6 +765,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           H.q0 = q0;
           H.nq = nq;
           H.yw = slices ? 0 : -1;
+          H.slots = ctx->lvl_slots;
           kmark(ctx, 1, false, st);
           CK(launch_levels<T>(H, st, sms));
           kmark(ctx, 1, true, st);
@@ -1343,6 +1345,10 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   if (const char* e = getenv("DEXEL_PASS1_ECAP_MUL")) {
     const double v = atof(e);
     if (v >= 0.5 && v <= 64.0) c->p1l_ecap_mul = v;
+  }
+  if (const char* e = getenv("DEXEL_LEVEL_SLOTS")) {
+    const int v = atoi(e);
+    if (v >= 2 && v <= 16) c->lvl_slots = v;
   }
   if (const char* e = getenv("DEXEL_PASS1_NBUF")) {
     const int v = atoi(e);

@@ -66,6 +66,8 @@ struct LvlParamsHost {
   long long q0 = 0, nq = 0;
   // reach of the output window along y (-1: R; 0: the 2D slices, a column's own level 0)
   int yw = -1;
+  // interval slots a lane of the level walks (0: by reach; at most 16)
+  int slots = 0;
 };
 // k_levels (the per-source level lists); launch_lgather then unites them per column
 template <typename T>

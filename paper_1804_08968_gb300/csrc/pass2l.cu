@@ -69,7 +69,7 @@ static LvlParams<T> lvl_params(const LvlParamsHost<T>& H) {
   A.P = H.P;
   A.l_p = H.l_p; A.l_cap = H.l_cap;
   A.W = 2 * H.P.R + 1;
-  A.slots = lvl_slots_for(H.P.R);
+  A.slots = H.slots > 0 && H.slots <= kLvlSlots ? H.slots : lvl_slots_for(H.P.R);
   A.L = H.P.R + 1;
   if (A.L <= 32) {
     A.G = 32 / A.L;
