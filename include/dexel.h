@@ -115,12 +115,17 @@ typedef struct dexel_ctx dexel_ctx;
  *                                   few denser columns redone by a second launch (mean,
  *                                   default), or room for the densest window from the start
  *   DEXEL_PASS1_ECAP_MUL=x          rule "mean": room for x times twice the mean window's
- *                                   events (0.5 .. 64; default: twice the mean, then more
- *                                   while the windows beyond the room hold more than 2 % of
- *                                   all windows' events)
+ *                                   events (0.5 .. 64).  Default (none of the three set):
+ *                                   at reach >= 48 the room with the least window events per
+ *                                   resident warp over the first launch and the redo launch,
+ *                                   from a histogram of the tiles' window sizes; below, x = 1
+ *   DEXEL_PASS1_TILE_REDO=0|1       a tile whose window exceeds the room goes whole to the
+ *                                   redo launch (1, default) or is split into narrower runs
+ *                                   of columns (0)
  *   DEXEL_LEVEL_SLOTS=2..16         interval slots a lane of the pass-2 level walks holds in
  *                                   shared memory (a longer list is walked again straight
- *                                   into place; default 8 up to reach 64, 16 beyond)
+ *                                   into place; default 8 below reach 48, 10 up to 64,
+ *                                   16 beyond)
  *   DEXEL_PASS1_NBUF=1|2            event buffers a pass-1 tile (2: every window that fits is
  *                                   merged from its sources' runs; 1: those of up to half the
  *                                   room, the others sorted; default 2 where it costs no block
@@ -353,8 +358,9 @@ int dexel_last_kernel_ms(const dexel_ctx* ctx, double* ms, int max);
  * (S_mid and the level lists exist for one block at a time; 1: the whole grid at once),
  * [10] pass-1 tiles walked twice because a lane outgrew its ring region, [11] output columns
  * whose level lists outgrew the gather's bucket (united straight from the lists), [12] that
- * bucket's size in intervals, [13] the event room of a pass-1 tile.  Returns the number of
- * entries written (at most max, 14 in all). */
+ * bucket's size in intervals, [13] the event room of a pass-1 tile, [14] level lists of pass
+ * 2 longer than a lane's slots (walked again straight into place).  Returns the number of
+ * entries written (at most max, 15 in all). */
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max);
 
 /* Diagnostic counters of the last call: clock cycles per phase of the y sweep and mean

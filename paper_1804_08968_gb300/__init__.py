@@ -199,9 +199,9 @@ class Context:
         S_mid column, columns redone by the fallback gather (sweep: max live state), status
         bits, attempts, pass-1 redo launches, blocks of y lines, pass-1 tiles walked twice,
         columns whose lists outgrew the gather's bucket, that bucket's size, the event room of a
-        pass-1 tile] of the last call."""
-        a = (ctypes.c_int64 * 14)()
-        n = lib().dexel_last_stats(self.ptr, a, 14)
+        pass-1 tile, level lists longer than a lane's slots] of the last call."""
+        a = (ctypes.c_int64 * 15)()
+        n = lib().dexel_last_stats(self.ptr, a, 15)
         return [int(a[i]) for i in range(n)]
 
     def _stream(self, stream):

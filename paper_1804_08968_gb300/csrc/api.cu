@@ -39,6 +39,7 @@ struct dexel_ctx {
   bool merge1 = true;   // short reaches: the per-lane merge instead
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
   int lvl_slots = 0;    // interval slots a lane of the level walks (0: by reach)
+  bool p1l_tile_redo = true;  // pass 1: tiles beyond the room go whole to the redo launch
   int p1l_nbuf = 0;     // its event buffers (0: two where they cost no block an SM)
   double p1l_ecap_mul = 0;  // its event room: this many times twice the mean window's events (0: by reach)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
@@ -79,7 +80,7 @@ struct dexel_ctx {
   double stage_ms[5] = {0, 0, 0, 0, 0};
   double kernel_ms[4] = {0, 0, 0, 0};  // pass-1 kernel, k_levels, k_lgather, S_mid pack
   bool kernel_rec[4] = {false, false, false, false};
-  long long stats[14] = {};
+  long long stats[15] = {};
   unsigned long long phase[16] = {};
 };
 
@@ -519,52 +520,78 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         kmark(ctx, 0, true, st);
         ++ctx->launches;
       } else if (ctx->lane1 && K <= kLaneMaxReach1) {
-        // event room by the mean density of a tile's window (columns whose own window holds
-        // more are redone by a second launch with room for the densest window), or (rule
-        // "max") room for the densest window from the start
-        // (ev_tile is twice the mean window; the room is p1l_ecap_mul times that: a window
-        // beyond the room is split into narrower runs of columns that stage their events
-        // again, and one within half of it is merged from its sources' runs in the other half)
-        // A window beyond the room costs more the wider the reach (halving a run of columns
-        // barely narrows a window of 2K + 1 + 32 sources), a larger room costs blocks an SM:
-        // the room grows while the windows beyond it hold more than 2 % of the events
-        // (measured: 2048^2 k = 64, 58 segments in the densest column: 16384, pass 1 246 ->
-        // 233 ms; 4096^2 k = 128, 15 segments at most: 8192, 437 against 731 ms at 16384).
-        const double mul = ctx->p1l_ecap_mul > 0 ? ctx->p1l_ecap_mul : 1.0;
+        // Event room of a tile.  A window beyond the room is, with a redo launch behind the
+        // first (room ecapR, one group of 8 warps), marked whole for it; else split into
+        // narrower runs of columns, which at wide reaches stage most of the window again.  A
+        // window within half of the room is merged from its sources' runs in the other half.
+        // The walks cost about the same warp cycles an event whatever the room, so the room
+        // is the one with the least events / resident warps over both launches, from the
+        // histogram of the tiles' window sizes (measured, 2048^2 k = 64 FP64: 8192 events at
+        // two blocks an SM with the densest tiles redone against 16384 at one block an SM;
+        // the rules in the else branch are the earlier ones, kept as switches).
+        const int ecapR = 16384;  // the redo's event room (room for the densest window)
+        const int ksz = sizeof(T) == 4 ? 4 : 8;  // the window kernel's event keys
+        const int gw0 = ctx->p1l_gw > 0 ? ctx->p1l_gw : (K <= 12 ? 2 : (K <= 48 ? 4 : 8));
+        // warps a tile (more as the windows grow: a tile's walk is split over its warps, its
+        // sort shared; measured best on the 512^2 workload: 2 up to k = 8, 4 at k = 32), and
+        // event buffers (a second one where it costs no block an SM)
+        struct P1Plan { int gw, nbuf, warps_sm; };
+        auto plan_for = [&](int room) {
+          P1Plan pl{gw0, 1, 0};
+          while (pl.gw < 8 && pass1l_smem(K, room, pl.gw, ksz) > (220LL << 10)) pl.gw <<= 1;
+          auto per_sm = [&](int nb) { return std::min<long long>(3, (220LL << 10) / pass1l_smem(K, room, pl.gw, ksz, nb)); };
+          pl.nbuf = per_sm(2) >= 1 && per_sm(2) == per_sm(1) ? 2 : 1;
+          if (ctx->p1l_nbuf > 0) pl.nbuf = ctx->p1l_nbuf;
+          if (pass1l_smem(K, room, pl.gw, ksz, pl.nbuf) > (220LL << 10)) pl.nbuf = 1;
+          // (a third block an SM runs the 80-register plan, whose spills cost about what the
+          // block gains: measured 136 against 122 ms at 2048^2 FP32, 461 against 434 ms at
+          // 4096^2 k = 128 FP64; counted as two)
+          pl.warps_sm = (int)std::min<long long>(2, per_sm(pl.nbuf)) * 8;
+          return pl;
+        };
+        const bool redo_fits = pass1l_smem(K, ecapR, 8, ksz) <= (220LL << 10);
+        double all = 0;
+        for (int b = 0; b < kWinBins; ++b) all += (double)hc.win_hist[b];
+        auto beyond = [&](int room) {
+          double x = 0;
+          for (int b = 0; b < kWinBins; ++b)
+            if ((512LL << b) > room) x += (double)hc.win_hist[b];
+          return x;
+        };
         int ecapL = 512;
-        while (ecapL < 16384 && (ecapL < mul * ev_tile || (ctx->p1l_ecap_max && ecapL < ev_win_max))) ecapL <<= 1;
-        if (ctx->p1l_ecap_mul <= 0) {
-          // more room while the windows beyond it hold more than 2 % of all window events
-          double all = 0;
-          for (int b = 0; b < kWinBins; ++b) all += (double)hc.win_hist[b];
-          auto beyond = [&](int room) {
-            double x = 0;
-            for (int b = 0; b < kWinBins; ++b)
-              if ((512LL << b) > room) x += (double)hc.win_hist[b];
-            return x;
-          };
-          while (ecapL < 16384 && beyond(ecapL) > 0.02 * all) ecapL <<= 1;
+        // (at reaches below 48 the mean rule: the 512^2 step at k <= 32 took 12.35 ms with it
+        // against 12.66 with the costed room)
+        const bool by_cost = ctx->p1l_ecap_mul <= 0 && !ctx->p1l_ecap_max && ctx->p1l_ecap <= 0 && K >= 48;
+        if (by_cost) {
+          const double wR = (double)std::max(1, plan_for(ecapR).warps_sm);
+          double best = 0;
+          for (int room = 512; room <= ecapR; room <<= 1) {
+            const P1Plan pl = plan_for(room);
+            if (pl.warps_sm <= 0) continue;
+            const double out = beyond(room), in = all - out;
+            // (windows beyond the largest room: narrower runs, about three times the events)
+            const double cost = room < ecapR && redo_fits ? in / pl.warps_sm + out / wR
+                                                          : (in + 3.0 * out) / pl.warps_sm;
+            if (room == 512 || cost <= best * 1.0001) {  // (ties: the larger room)
+              best = cost;
+              ecapL = room;
+            }
+          }
+        } else {
+          // room for p1l_ecap_mul times twice the mean window (rule "mean"), for the densest
+          // window (rule "max"), or as set
+          const double mul = ctx->p1l_ecap_mul > 0 ? ctx->p1l_ecap_mul : 1.0;
+          while (ecapL < 16384 && (ecapL < mul * ev_tile || (ctx->p1l_ecap_max && ecapL < ev_win_max))) ecapL <<= 1;
+          if (ctx->p1l_ecap > 0) ecapL = ctx->p1l_ecap;
         }
         ctx->stats[13] = ecapL;
-        if (ctx->p1l_ecap > 0) ecapL = ctx->p1l_ecap;
-        // warps a tile: more as the windows grow (a tile's walk is split over its warps, its
-        // sort shared); measured best on the 512^2 workload: 2 up to k = 8, 4 at k = 32
-        int gw = K <= 12 ? 2 : (K <= 48 ? 4 : 8);
-        if (ctx->p1l_gw > 0) gw = ctx->p1l_gw;
-        const int ksz = sizeof(T) == 4 ? 4 : 8;  // the window kernel's event keys
-        while (gw < 8 && pass1l_smem(K, ecapL, gw, ksz) > (220LL << 10)) gw <<= 1;
-        // a second event buffer, where it fits: every window is merged from its sources' runs
-        // (one buffer: windows of up to half of it are)
-        // (where it costs no block an SM)
-        auto per_sm = [&](int nb) { return std::min<long long>(3, (220LL << 10) / pass1l_smem(K, ecapL, gw, ksz, nb)); };
-        int nbuf = per_sm(2) >= 1 && per_sm(2) == per_sm(1) ? 2 : 1;
-        if (ctx->p1l_nbuf > 0) nbuf = ctx->p1l_nbuf;
-        if (pass1l_smem(K, ecapL, gw, ksz, nbuf) > (220LL << 10)) nbuf = 1;
+        const P1Plan pl1 = plan_for(ecapL);
+        const int gw = pl1.gw, nbuf = pl1.nbuf;
         p1.nbuf = nbuf;
+        const bool redo_ok = ecapL < ecapR && redo_fits;
+        p1.tile_redo = redo_ok && ctx->p1l_tile_redo ? 1 : 0;
         // the ring of the one-walk variant in the (free) forward arena: up to 128 pieces a
         // thread of the grid
-        const int ecapR = 16384;  // the redo's event room (room for the densest window)
-        const bool redo_ok = ecapL < ecapR && pass1l_smem(K, ecapR, 8, ksz) <= (220LL << 10);
         {
           // threads of the larger of the two launches (the first, and the redo's)
           long long thr = (long long)pass1l_blocks(nx, ny, K, ecapL, gw, sms, ksz, nbuf) * 256;
@@ -781,6 +808,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           ctx->needL = std::max<long long>(ctx->needL, (long long)(hc.arena_top[2] * to_grid));
           ctx->stats[11] = std::max<long long>(ctx->stats[11], hc.over_cols);
           ctx->stats[12] = std::max<long long>(ctx->stats[12], H.bcap);
+          ctx->stats[14] += (long long)hc.lvl_redo;
           ctx->levels_status = hc.status;
           if (hc.over_cols * 64LL > ncols) {
             // many columns outgrew the bucket (united straight from the lists, slower): a
@@ -1346,6 +1374,7 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
     const double v = atof(e);
     if (v >= 0.5 && v <= 64.0) c->p1l_ecap_mul = v;
   }
+  if (const char* e = getenv("DEXEL_PASS1_TILE_REDO")) c->p1l_tile_redo = atoi(e) != 0;
   if (const char* e = getenv("DEXEL_LEVEL_SLOTS")) {
     const int v = atoi(e);
     if (v >= 2 && v <= 16) c->lvl_slots = v;
@@ -1418,7 +1447,7 @@ int dexel_last_phases(const dexel_ctx* ctx, uint64_t* ph, int max) {
 
 int dexel_last_stats(const dexel_ctx* ctx, int64_t* stats, int max) {
   if (!ctx || !stats) return 0;
-  int n = max < 14 ? max : 14;
+  int n = max < 15 ? max : 15;
   for (int q = 0; q < n; ++q) stats[q] = ctx->stats[q];
   return n;
 }

@@ -373,6 +373,19 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       while (ib < i1 && P.m_start[(long long)ib * P.ny + j] == -1) ++ib;
     }
     const int qa = max(0, ia - R) - s0;
+    if (P.tile_redo && !P.redo && eoff[min(P.nx, ib + R) - s0] - eoff[qa] > ecap) {
+      // the whole tile to the redo launch, whose room holds its window (no narrower runs:
+      // at wide reaches they would stage most of the window again)
+      for (int i = ia + G.gtid; i < ib; i += gthreads) {
+        P.m_start[(long long)i * P.ny + j] = -1;
+        P.m_cnt[(long long)i * P.ny + j] = 0;
+      }
+      if (G.gtid == 0) {
+        set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
+        if (P.rowmark) P.rowmark[j] = 1;
+      }
+      break;
+    }
     while (ib > ia + 1 && eoff[min(P.nx, ib + R) - s0] - eoff[qa] > ecap) ib = ia + ((ib - ia) >> 1);
     const int qe = min(P.nx, ib + R) - s0;
     const int e0 = eoff[qa];

@@ -35,7 +35,10 @@ namespace dexel {
 // (LvlParams::slots) follows the reach: longer windows give longer lists (measured: 2048^2
 // k = 64, 16 slots 261 ms, 8 slots 220 ms; 4096^2 k = 128, 16 slots 1541 ms, 8 slots 2110 ms)
 constexpr int kLvlSlots = 16;  // the most a launch uses
-DXI int lvl_slots_for(int R) { return R <= 64 ? 8 : 16; }
+// Interval slots a lane by reach: more slots walk fewer long lists again, fewer leave room
+// for more blocks an SM (measured on the 2048^2 workload at k = 64: 8 slots 218 ms, 10 200,
+// 12 228, 16 258; 4096^2 at k = 128: 8 slots 2114 ms, 12 1547, 16 1535)
+DXI int lvl_slots_for(int R) { return R < 48 ? 8 : (R <= 64 ? 10 : 16); }
 // pieces a warp stages in shared memory at a time (a level group walks one source)
 constexpr int kLvlStage = 64;
 // w-table entries kept in shared memory when the per-lane tables do not fit (n <= k^2:
@@ -308,6 +311,10 @@ DXD bool lvl_flush(const LvlParams<T>& A, int lane, const unsigned* ws, int cnt,
       A.l_p[s + idx] = make_ulonglong2(lvl_left<T>(P, mso, (int)(pl >> kLvlDxBits), (int)(pl & m), tto),
                                        lvl_right<T>(P, mso, (int)(pr >> kLvlDxBits), (int)(pr & m), tto));
     }
+  }
+  {
+    const unsigned long_lists = __ballot_sync(0xffffffffu, cnt > A.slots);
+    if (long_lists && lane == 0) atomicAdd(&P.ctr->lvl_redo, (unsigned long long)__popc(long_lists));
   }
   if (cnt > A.slots) redo(A.l_p + s + ex);
   if (act) {

@@ -57,6 +57,7 @@ struct Counters {
   int over_max;                   //   and the most intervals one of them collected
   int ring_spills;                // pass-1 window kernel: tiles walked twice (a lane's ring
                                   // region overflowed)
+  unsigned long long lvl_redo;    // level walks: lists longer than a lane's slots (walked again)
   unsigned long long win_hist[kWinBins];  // pass-1 window events by tile: bin b holds the
                                           // events of the tiles with 2^(8+b) < E <= 2^(9+b)
                                           // (bin 0: E <= 512; the last: E > 2^(8+kWinBins-1))
@@ -258,6 +259,9 @@ struct P1Params {
   int xa, xb;
   // the window kernel's event buffers (1 or 2; 0 counts as 1)
   int nbuf;
+  // the window kernel's first launch when a redo launch with more room follows: a tile whose
+  // window exceeds the room is marked whole for it (instead of split into narrower runs)
+  int tile_redo;
   // local index of forward states for the current chunk: per warp, chunk entries
 };
 
