@@ -51,7 +51,10 @@ typedef enum {
   DEXEL_ERR_CAPACITY = -3,    /* output or workspace too small; see dexel_last_required  */
   DEXEL_ERR_CUDA = -4,        /* a CUDA runtime call failed                                */
   DEXEL_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up                        */
-  DEXEL_ERR_NOMEM = -6        /* host-side allocation failed                               */
+  DEXEL_ERR_NOMEM = -6,       /* host-side allocation failed                               */
+  DEXEL_ERR_NO_PLAN = -7      /* dexel_offset_enqueue: no plan recorded for this offset, or
+                                 the data needed more than the plan (call dexel_dilate /
+                                 dexel_erode, which plans again)                            */
 } dexel_status;
 
 /* Storage precision of the endpoints (input, intermediate and output).
@@ -179,6 +182,30 @@ dexel_status dexel_dilate(dexel_ctx* ctx, const dexel_grid_in* in, double k, dex
  * dexel_dilate. */
 dexel_status dexel_erode(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_mode mode,
                          dexel_grid_out* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Stream-ordered offset: dexel_dilate (op DEXEL_DILATE) or dexel_erode (DEXEL_ERODE) that
+ * issues no host synchronisation, so that a caller can queue it behind its own work (or
+ * between other kernels of one stream) without a round trip to the host.  It is not in the
+ * paper; the two passes it runs are those of dexel_dilate.
+ *   A synchronous dexel_dilate / dexel_erode on the same context records, for its element
+ *   type, grid size (nx, ny), k and op, the counters it read at its synchronisations (its
+ *   plan).  This call replays that plan: it enqueues the same kernels on `stream`, makes
+ *   every redo launch (a redo finds nothing to do when the first launch finished), and
+ *   returns without waiting.  Without a recorded plan it returns DEXEL_ERR_NO_PLAN and does
+ *   nothing.  Plans whose synchronous call took a fallback fed with host-read data (the
+ *   per-row sweeps, the tiled gather) are not recorded.
+ *   ws must be a caller workspace (no allocation happens); out->capacity_seg bounds the
+ *   output; out->nseg is set to -1.
+ *   d_result : DEVICE int64[2] (caller-owned), written in stream order when the call returns
+ *   DEXEL_OK: [0] DEXEL_OK, DEXEL_ERR_BAD_CSR, DEXEL_ERR_CAPACITY (output beyond
+ *   capacity_seg or int32 offsets; [1] is then the size needed) or DEXEL_ERR_NO_PLAN (the
+ *   data needed more room or another path than the plan: call dexel_dilate / dexel_erode);
+ *   [1] the output's segment count.  out->z is written only when [0] is DEXEL_OK (out->col_off
+ *   always).  A host-side failure (a bad argument, a workspace below the plan's need:
+ *   DEXEL_ERR_CAPACITY with dexel_last_required) returns before anything is queued. */
+dexel_status dexel_offset_enqueue(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
+                                  dexel_mode mode, dexel_grid_out* out, void* ws,
+                                  size_t ws_bytes, void* stream, int64_t* d_result);
 
 /* Closing (erode after dilate) or opening (dilate after erode) by the same radius; the
  * intermediate grid lives in the workspace.  op must be DEXEL_CLOSE or DEXEL_OPEN. */

@@ -26,6 +26,9 @@ __all__ = ["Grid", "Context", "dilate", "erode", "close", "open_", "boolean", "s
 FP64 = 0
 FP32_PRED64 = 1
 DILATE, ERODE, CLOSE, OPEN = 0, 1, 2, 3
+# dexel_status codes
+OK, ERR_INVALID_ARG, ERR_BAD_CSR, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_NO_PLAN = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 UNION, INTERSECT, DIFFERENCE = 0, 1, 2
 # dexel_prim: int32 kind, int32 pad, 7 doubles
 PRIM_DTYPE = np.dtype([("kind", "<i4"), ("pad", "<i4"), ("p", "<f8", (7,))])
@@ -70,6 +73,9 @@ def lib():
             f = getattr(L, name)
             f.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
                           ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
+        L.dexel_offset_enqueue.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t,
+                                           P, P]
         L.dexel_morph.argtypes = [P, ctypes.POINTER(_In), ctypes.c_double, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(_Out), P, ctypes.c_size_t, P]
         L.dexel_validate.argtypes = [P, ctypes.POINTER(_In), ctypes.c_int, P, ctypes.c_size_t, P]
@@ -235,6 +241,24 @@ class Context:
             self._cap_hint[key] = cap
             return Grid(g.nx, g.ny, g.h, off, z[: out.nseg])
         raise DexelError(-3, "dexel offset (output capacity)")
+
+    def last_required(self) -> int:
+        """Workspace bytes the last call needed (dexel_last_required)."""
+        return int(lib().dexel_last_required(self.ptr))
+
+    def enqueue(self, op: int, g: Grid, k: float, ws, out_off, out_z, result, stream=None) -> int:
+        """dexel_offset_enqueue: queue op (DILATE or ERODE) of g by k on the stream with no host
+        synchronisation, replaying the plan a synchronous run() of the same offset recorded on
+        this context.  ws: a uint8 device tensor of at least last_required() bytes after that
+        run; out_off: int32 [nx*ny + 1]; out_z: [capacity, 2] of g's dtype; result: int64 [2]
+        device tensor that receives [status, output segments] in stream order.  Returns the
+        host-side status (0 queued; -7 no plan recorded for this offset)."""
+        gin = g._in()
+        out = _Out(out_off.data_ptr(), out_z.data_ptr(), int(out_z.shape[0]), 0)
+        return int(lib().dexel_offset_enqueue(self.ptr, ctypes.byref(gin), float(k), op, g.mode,
+                                              ctypes.byref(out), ctypes.c_void_p(ws.data_ptr()),
+                                              ws.numel(), self._stream(stream),
+                                              ctypes.c_void_p(result.data_ptr())))
 
     def _call_out(self, nx, ny, h, like, cap, fn, what):
         """Run fn(out) with an output of cap segments, growing it once to the reported need."""

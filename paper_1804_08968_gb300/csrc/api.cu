@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/dexel.h"
@@ -17,6 +18,14 @@
 #include "emit.cuh"
 
 using namespace dexel;
+
+// The counters a synchronous offset read at its host synchronisations, in order, and whether
+// its path can be replayed without them (no fallback whose launches depend on host-read data).
+struct Tape {
+  std::vector<Counters> snaps;
+  size_t pos = 0;
+  bool replayable = true;
+};
 
 struct dexel_ctx {
   int device = 0;
@@ -82,6 +91,12 @@ struct dexel_ctx {
   bool kernel_rec[4] = {false, false, false, false};
   long long stats[15] = {};
   unsigned long long phase[16] = {};
+  // Stream-ordered calls (dexel_offset_enqueue): every synchronous offset records the
+  // counters it read at its host synchronisations (its "tape"); a stream-ordered call of the
+  // same grid size, radius and operation replays that tape instead of reading the device.
+  std::map<std::string, Tape> tapes;
+  Tape* replay = nullptr;        // the tape being replayed (a stream-ordered call), else null
+  long long* replay_result = nullptr;  // its device result words [status, segments]
 };
 
 namespace {
@@ -147,6 +162,29 @@ __global__ void k_win_hist(int nx, int ny, int K, int erode, const int* off, Cou
   if (threadIdx.x < kWinBins && hb[threadIdx.x]) atomicAdd(&ctr->win_hist[threadIdx.x], hb[threadIdx.x]);
 }
 
+// Stream-ordered calls: the status bits in `fatal` are kept in the sticky word (a failure the
+// call cannot recover from on the device), then the status word is cleared if asked (before
+// a redo launch that sets it again for what it could not finish).
+__global__ void k_fold_status(Counters* ctr, int fatal, int clear) {
+  ctr->sticky |= ctr->status & fatal;
+  if (clear) ctr->status = 0;
+}
+
+// Stream-ordered calls: the result words [status, output segments] -- DEXEL_OK, or
+// DEXEL_ERR_BAD_CSR, DEXEL_ERR_CAPACITY (output beyond capacity_seg or int32 offsets),
+// DEXEL_ERR_NO_PLAN (the data needed more than the replayed plan: a synchronous call
+// re-plans) -- from the sticky status and the total (the scan's last block sum).
+__global__ void k_result(Counters* ctr, const long long* total, long long cap, long long* res) {
+  const int f = ctr->sticky | ctr->status;
+  const long long n = *total;
+  long long st = DEXEL_OK;
+  if (f & ST_BAD_CSR) st = DEXEL_ERR_BAD_CSR;
+  else if (f & ~(ST_TOO_MANY_OUT)) st = DEXEL_ERR_NO_PLAN;
+  else if ((f & ST_TOO_MANY_OUT) || n > cap) st = DEXEL_ERR_CAPACITY;
+  res[0] = st;
+  res[1] = n;
+}
+
 // rows of the grid with a column marked for the pass-1 sweep (line-2 index q = i * ny + j)
 __global__ void k_mark_rows(long long ncols, int ny, const long long* m_start, int* rowflag) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -181,9 +219,11 @@ __global__ void k_count(int ncols, const long long* ostart, const int* ocnt, con
 
 template <typename T>
 __global__ void k_write(int ncols, const long long* ostart, const int* ocnt, const ukey* ol,
-                        const ukey* orr, int erode, const long long* pos, T* z) {
+                        const ukey* orr, int erode, const long long* pos, T* z,
+                        const long long* gate = nullptr) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncols) return;
+  if (gate && gate[0] != DEXEL_OK) return;  // (stream-ordered calls: nothing is written on failure)
   const long long s = ostart[c];
   finalize_column<T>(ol + s, orr + s, ocnt[c], erode != 0, z + 2 * pos[c]);
 }
@@ -302,6 +342,14 @@ dexel_status ensure_owned(dexel_ctx* ctx, size_t bytes) {
   return DEXEL_OK;
 }
 
+// the offsets a tape serves: same element type, grid size, radius, operation and kind
+std::string tape_key(const dexel_grid_in* in, double k, bool erode, bool slices, size_t tsize) {
+  char b[128];
+  snprintf(b, sizeof(b), "%zu/%d/%d/%.17g/%d/%d", tsize, in->nx, in->ny, k, erode ? 1 : 0,
+           slices ? 1 : 0);
+  return b;
+}
+
 template <typename T>
 struct Offset {
   // one offset (dilation of S or of its complement) of a grid into the output CSR
@@ -327,7 +375,18 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
   const int nwarps = blocks * kWarpsPerBlock;
 
   ctx->noblock = false;
-  for (int attempt = 0; attempt < 24; ++attempt) {
+  // Stream-ordered replay (ctx->replay): the counters come from the tape of an earlier
+  // synchronous call of the same offset instead of the device, every redo launch is made
+  // (a redo finds nothing to do when the first launch finished everything), the status bits
+  // that would have sent the synchronous call elsewhere are folded into the sticky word, and
+  // the result words report them.  A synchronous call records its tape.
+  Tape* const rt = ctx->replay;
+  const bool replay = rt != nullptr;
+  Tape rec;
+  if (replay && !ws_user) return DEXEL_ERR_INVALID_ARG;
+  for (int attempt = 0; attempt < (replay ? 1 : 24); ++attempt) {
+    rec.snaps.clear();
+    rec.replayable = true;
     // ---------------- plan
     // phase A: counters, tables, indices, validation
     void* pwtabf = nullptr;
@@ -385,8 +444,29 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     }
     mark(ctx, 1, st);
     Counters hc;
-    CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    // the counters at a host synchronisation (recorded), or the tape's (replayed)
+    auto rd = [&](Counters& h) -> dexel_status {
+      if (replay) {
+        if (rt->pos >= rt->snaps.size()) return DEXEL_ERR_NO_PLAN;
+        h = rt->snaps[rt->pos++];
+        return DEXEL_OK;
+      }
+      cudaError_t e = cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_status(e, __LINE__);
+      rec.snaps.push_back(h);
+      return DEXEL_OK;
+    };
+    auto fold = [&](int fatal, bool clear) {
+      k_fold_status<<<1, 1, 0, st>>>(ctr, fatal, clear ? 1 : 0);
+      ++ctx->launches;
+    };
+#define RD(h)                               \
+  do {                                      \
+    const dexel_status rs_ = rd(h);         \
+    if (rs_ != DEXEL_OK) return rs_;        \
+  } while (0)
+    RD(hc);
     if (hc.status & ST_BAD_CSR) return DEXEL_ERR_BAD_CSR;
 
     // ---------------- pass 1 plan
@@ -489,6 +569,11 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     }
     // pass-2 columns start unmarked (a gather marks those it hands back with count -1)
     CK(cudaMemsetAsync(pocnt, 0, sizeof(int) * ncols, st));
+    if (replay) {
+      // (a pass 1 that stops on a malformed input leaves empty columns behind it)
+      CK(cudaMemsetAsync(pmstart, 0, sizeof(long long) * ncols, st));
+      CK(cudaMemsetAsync(pmcnt, 0, sizeof(int) * ncols, st));
+    }
     bool again = false;  // an arena outgrew its estimate: plan again
     long long mid_sum = 0;  // S_mid pieces over the blocks
     for (int blk = 0; blk < nb; ++blk) {
@@ -611,11 +696,11 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         }
         if (ctx->prune1) {
           // dominance pruning of S_mid pieces: margin 2^-19 (max |z| + k h), over four times
-          // the error bound of the float test
-          float zm;
-          memcpy(&zm, &hc.zmax_bits, sizeof(float));
+          // the error bound of the float test (computed on the device from the validation's
+          // max |z|)
           p1.prune_w = (const float*)pwtabf;
-          p1.prune_E = (float)(std::ldexp(1.0, -19) * ((double)zm + k * in->h));
+          p1.prune_zmax = &ctr->zmax_bits;
+          p1.prune_kh = k * in->h;
         }
         int* rowmark = (int*)ppos;  // free until pass 2
         CK(cudaMemsetAsync(rowmark, 0, sizeof(int) * ny, st));
@@ -626,16 +711,18 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         if (redo_ok) {
           // columns whose window did not fit: a second launch for them alone, with room for
           // the densest window (the first launch flagged their rows and marked them)
-          CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-          CK(cudaStreamSynchronize(st));
-          if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
-            CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+          RD(hc);
+          if (replay || ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA))) {
+            if (replay)
+              fold(~ST_OVERFLOW_SLOT, true);
+            else
+              CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
             P1Params<T> pr = p1;
             pr.redo = 1;
             pr.nbuf = 1;  // (the densest windows: one buffer of ecapR events)
             CK(launch_pass1l<T>(pr, ecapR, 8, sms, st));
             ++ctx->launches;
-            ++ctx->stats[8];  // a pass-1 redo launch
+            if (!replay) ++ctx->stats[8];  // a pass-1 redo launch
           }
         }
         kmark(ctx, 0, true, st);
@@ -656,10 +743,12 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         const int b1 = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, ntiles));
         CK(launch_pass1g<T>(p1, tc, ecap, obuf, b1, st));
         ++ctx->launches;
+        rec.replayable = false;  // (its own fallbacks)
       }
-      CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+      RD(hc);
       if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
+        rec.replayable = false;  // (the rows' list comes from the device)
+        if (replay) return DEXEL_ERR_NO_PLAN;
         // columns whose window had more events than fit (marked m_start = -1): the sweep
         // redoes their rows
         int* rowflag = (int*)ppos;  // free until pass 2
@@ -678,16 +767,17 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         pr.nrows = (int)rows.size();
         CK(launch_pass1<T>(pr, nw1 / kWarpsPerBlock, st));
         ++ctx->launches;
-        CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        RD(hc);
       }
     }
     if (sweep1) {
+      rec.replayable = false;
+      if (replay) return DEXEL_ERR_NO_PLAN;
       CK(launch_pass1<T>(p1, nw1 / kWarpsPerBlock, st));
       ++ctx->launches;
-      CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+      RD(hc);
     }
+    if (replay) fold(~0, false);  // (whatever pass 1 could not finish)
     mark(ctx, 3, st);
     ctx->stats[10] += hc.ring_spills;
     ctx->needF = std::max<long long>(ctx->needF, (long long)(hc.arena_top[0] * to_grid));
@@ -735,7 +825,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         k_scan2<<<1, kScanThreads, 0, st>>>(nsb, (long long*)psums);
         k_mid_pack<Key><<<sms * 8, 256, 0, st>>>(nq, p1.m_start + q0, p1.m_cnt + q0, p1.m_a, p1.m_b,
                                                  p1.m_l, (const long long*)ppos, (const long long*)psums,
-                                                 (long long*)pcnt + q0, c_af, c_bf, c_dx, ctr);
+                                                 (long long*)pcnt + q0, c_af, c_bf, c_dx, ctr,
+                                                 p1.m_cap, capC);
         kmark(ctx, 3, true, st);
         ctx->launches += 3;
         pg.c_start = (const long long*)pcnt;
@@ -803,14 +894,13 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
             CK(launch_lgather<T>(H, H.bcap, 0, st, sms));
           kmark(ctx, 2, true, st);
           ctx->launches += 2;
-          CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-          CK(cudaStreamSynchronize(st));
+          RD(hc);
           ctx->needL = std::max<long long>(ctx->needL, (long long)(hc.arena_top[2] * to_grid));
           ctx->stats[11] = std::max<long long>(ctx->stats[11], hc.over_cols);
           ctx->stats[12] = std::max<long long>(ctx->stats[12], H.bcap);
           ctx->stats[14] += (long long)hc.lvl_redo;
           ctx->levels_status = hc.status;
-          if (hc.over_cols * 64LL > ncols) {
+          if (hc.over_cols * 64LL > ncols && !replay) {
             // many columns outgrew the bucket (united straight from the lists, slower): a
             // bucket for their need in the next calls of this reach and operation
             int b = lb;
@@ -828,6 +918,8 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           }
           if (hc.status & ST_LEVELS_OVER) {
             // a list beyond its buffer or the arena: the tiled gather redoes pass 2
+            rec.replayable = false;
+            if (replay) return DEXEL_ERR_NO_PLAN;
             CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
             CK(cudaMemsetAsync(&ctr->arena_top[3], 0, sizeof(unsigned long long), st));
             CK(cudaMemsetAsync(&ctr->out_total, 0, sizeof(unsigned long long), st));
@@ -835,18 +927,23 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
             CK(cudaMemsetAsync(&ctr->redo_cols, 0, sizeof(int), st));
           } else {
             done = true;
-            if ((hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA)) {
+            const bool redo_rec = (hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA);
+            if (replay) {
+              // (the lists' failures are final; columns the gather handed back get their redo)
+              fold(~ST_OVERFLOW_SLOT, true);
+            }
+            if (redo_rec || replay) {
               // columns whose lists outgrew the bucket: the gather again, those columns only,
               // with a bucket for their need (8192 entries at most: columns beyond it are
               // left for the window gather below)
               int b = 2 * H.bcap;
               while (b < hc.max_state && b < 8192) b <<= 1;
-              if (hc.redo_cols * 64LL > ncols) lb = std::min(2 * lb, ctx->bucket_max);  // next calls
-              CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+              if (replay) b = std::max(b, 2048);  // (the data may need more than the tape's)
+              if (hc.redo_cols * 64LL > ncols && !replay) lb = std::min(2 * lb, ctx->bucket_max);  // next calls
+              if (!replay) CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
               CK(launch_lgather<T>(H, b, 1, st, sms));
               ++ctx->launches;
-              CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-              CK(cudaStreamSynchronize(st));
+              if (redo_rec) RD(hc);
             }
           }
         }
@@ -858,14 +955,15 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           break;
         }
         if (!done) {
+          rec.replayable = false;
+          if (replay) return DEXEL_ERR_NO_PLAN;
           if (!packed) CK(pack_lines());  // the tiled gather stages line-contiguous sources
           CK(launch_pass2t<T>(pg, tw, tc, ntab, stage_cap, kRoundAppends, kRoundPieces, per_sm,
                               tblocks, st));
           ++ctx->launches;
         }
       }
-      CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+      RD(hc);
       int redo = 0;
       if (slices && (hc.status & ST_OVERFLOW_SLOT) && !(hc.status & ST_OVERFLOW_ARENA))
         return DEXEL_ERR_CAPACITY;  // a column's own union beyond every bucket
@@ -879,15 +977,17 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           int w = 8;
           while (w > 1 && w * wbytes > (100LL << 10)) w >>= 1;
           const int per_sm = (int)std::max<long long>(1, std::min<long long>(64 / w, (220LL << 10) / (w * wbytes)));
-          if (redo * 64LL > ncols) cc = std::min(2 * cc, 1024);  // next calls: a larger bucket
+          if (redo * 64LL > ncols && !replay) cc = std::min(2 * cc, 1024);  // next calls: a larger bucket
           P2GParams<T> pr = pg;
           pr.bcap = b;
           pr.redo = 1;
-          CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
+          if (replay)
+            fold(~ST_OVERFLOW_SLOT, true);
+          else
+            CK(cudaMemsetAsync(&ctr->status, 0, sizeof(int), st));
           CK(launch_pass2c<T>(pr, w, sms * per_sm, st));
           ++ctx->launches;
-          CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-          CK(cudaStreamSynchronize(st));
+          RD(hc);
         }
       }
       ctx->stats[5] = redo;
@@ -909,6 +1009,10 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         CK(cudaMemsetAsync(&ctr->max_state, 0, sizeof(int), st));
         use_sweep = true;
       }
+    }
+    if (use_sweep) {
+      rec.replayable = false;
+      if (replay) return DEXEL_ERR_NO_PLAN;
     }
     if (use_sweep && nb > 1) {
       // the per-line sweep takes the whole grid: plan again without blocks
@@ -951,8 +1055,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     CK(launch_pass2<T>(p2, nw2 / kWarpsPerBlock, st));
     mark(ctx, 5, st);
     ++ctx->launches;
-    CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    RD(hc);
     ctx->needF = std::max<long long>(ctx->needF, (long long)hc.arena_top[2] * 16 / (long long)(2 * sizeof(Key) + 2) + 1);
     ctx->needO = std::max<long long>(ctx->needO, (long long)hc.arena_top[3]);
     ctx->stats[6] = hc.status;
@@ -977,9 +1080,10 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     }
     }  // pass 2 variants
 
-    acc_block_times(ctx);
+    if (!replay) acc_block_times(ctx);
     ctx->stats[9] = std::max<long long>(ctx->stats[9], nb);
     }  // blocks
+    if (again && replay) return DEXEL_ERR_NO_PLAN;
     if (again) continue;
 
     // ---------------- compaction into the caller's CSR
@@ -1000,11 +1104,26 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     ctx->launches += 4;
     CK(cudaGetLastError());
     mark(ctx, 7, st);
+    if (replay) {
+      // no host read: the result words, then the output written only if they say DEXEL_OK
+      fold(~0, false);
+      long long* res = ctx->replay_result;
+      k_result<<<1, 1, 0, st>>>(ctr, (const long long*)psums + nsb, out->capacity_seg, res);
+      k_write<T><<<gb, thr, 0, st>>>((int)ncols, (const long long*)postart, (const int*)pocnt,
+                                     out_l, out_r, erode ? 1 : 0, (const long long*)ppos,
+                                     (T*)out->z, res);
+      ctx->launches += 3;
+      CK(cudaGetLastError());
+      mark(ctx, 9, st);
+      out->nseg = -1;  // (in the result words)
+      ctx->last_required = total;
+      // (the tape's last entry is the synchronous call's read of the total)
+      return rt->pos + 1 == rt->snaps.size() ? DEXEL_OK : DEXEL_ERR_NO_PLAN;
+    }
     long long total_out = 0;
     CK(cudaMemcpyAsync(&total_out, (long long*)psums + nsb, sizeof(long long),
                        cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    RD(hc);
     out->nseg = total_out;
     ctx->host_ctr = hc;
     if (hc.status & ST_TOO_MANY_OUT) return DEXEL_ERR_CAPACITY;
@@ -1039,10 +1158,12 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     ctx->stats[4] = std::max<long long>(ctx->stats[4], hc.max_pieces);
     ctx->stats[5] = std::max<long long>(ctx->stats[5], hc.max_state);
     ctx->last_required = total;
+    if (rec.replayable) ctx->tapes[tape_key(in, k, erode, slices, sizeof(T))] = std::move(rec);
     return DEXEL_OK;
   }
   return DEXEL_ERR_CAPACITY;
 }
+#undef RD
 
 dexel_status check_in(const dexel_grid_in* in, double k) {
   if (!in || in->nx < 1 || in->ny < 1 || in->nx > 32768 || in->ny > 32768) return DEXEL_ERR_INVALID_ARG;
@@ -1495,6 +1616,27 @@ dexel_status dexel_erode(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
   return offset(ctx, in, k, true, mode, out, ws, ws_bytes, stream);
 }
 
+dexel_status dexel_offset_enqueue(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
+                                  dexel_mode mode, dexel_grid_out* out, void* ws,
+                                  size_t ws_bytes, void* stream, int64_t* d_result) {
+  if (!ctx || !d_result || !ws || (op != DEXEL_DILATE && op != DEXEL_ERODE))
+    return DEXEL_ERR_INVALID_ARG;
+  dexel_status s = check_in(in, k);
+  if (s != DEXEL_OK) return s;
+  if (mode != DEXEL_FP64 && mode != DEXEL_FP32_PRED64) return DEXEL_ERR_INVALID_ARG;
+  const bool erode = op == DEXEL_ERODE;
+  auto it = ctx->tapes.find(tape_key(in, k, erode, false, mode == DEXEL_FP64 ? sizeof(double) : sizeof(float)));
+  if (it == ctx->tapes.end()) return DEXEL_ERR_NO_PLAN;
+  reset_call(ctx);
+  it->second.pos = 0;
+  ctx->replay = &it->second;
+  ctx->replay_result = (long long*)d_result;
+  s = offset(ctx, in, k, erode, mode, out, ws, ws_bytes, stream);
+  ctx->replay = nullptr;
+  ctx->replay_result = nullptr;
+  return s;
+}
+
 dexel_status dexel_morph(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
                          dexel_mode mode, dexel_grid_out* out, void* ws, size_t ws_bytes,
                          void* stream) {
@@ -1840,6 +1982,7 @@ const char* dexel_status_string(dexel_status s) {
     case DEXEL_ERR_CUDA: return "CUDA runtime error";
     case DEXEL_ERR_TIMEOUT: return "bounded device wait gave up";
     case DEXEL_ERR_NOMEM: return "out of memory";
+    case DEXEL_ERR_NO_PLAN: return "no recorded plan fits this offset (call it synchronously)";
   }
   return "unknown status";
 }

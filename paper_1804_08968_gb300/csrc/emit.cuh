@@ -11,6 +11,7 @@ namespace dexel {
 // that touch after rounding.  Returns the count; writes pieces when out != nullptr.
 template <typename T>
 __device__ int finalize_column(const ukey* lk, const ukey* rk, int m, bool erode, T* out) {
+  if (m < 0) m = 0;  // (a column a failed gather left marked: its call reports the failure)
   int cnt = 0;
   T ca = 0, cb = 0;
   bool have = false;
@@ -84,7 +85,8 @@ template <typename Key>
 __global__ void k_mid_pack(long long ncols, const long long* m_start, const int* m_cnt,
                            const Key* m_a, const Key* m_b, const short* m_l,
                            const long long* pos, const long long* sums, long long* c_start,
-                           float* c_af, float* c_bf, short* c_dx, Counters* ctr) {
+                           float* c_af, float* c_bf, short* c_dx, Counters* ctr,
+                           long long m_cap = -1, long long c_cap = -1) {
   const int lane = threadIdx.x & 31;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   float zm = 0.0f;
@@ -92,7 +94,12 @@ __global__ void k_mid_pack(long long ncols, const long long* m_start, const int*
     const long long c = pos[q] + sums[q / kScanTile];
     if (lane == 0) c_start[q] = c;
     const long long ms = m_start[q];
-    const int n = m_cnt[q];
+    int n = m_cnt[q];
+    if (m_cap >= 0 && (ms < 0 || n < 0 || ms + n > m_cap || c + n > c_cap)) {
+      // (the capacities given: a column beyond S_mid or the copy is skipped, status set)
+      if (lane == 0) set_status(&ctr->status, ST_OVERFLOW_ARENA);
+      n = 0;
+    }
     for (int p = lane; p < n; p += 32) {
       const float a = keyf(m_a[ms + p]), b = keyf(m_b[ms + p]);
       c_af[c + p] = a;

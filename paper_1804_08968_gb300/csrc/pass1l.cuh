@@ -534,7 +534,9 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     const bool ring = P.r_a != nullptr && rg0 + (long long)W * 32 * P.r_cap <= P.r_n;
     const long long rbase = ring ? (long long)(warp * 32 + lane) * P.r_cap : 0;
     int n;
-    const Prune pr{P.prune_w ? (const float*)(smem + Lo.wt) : nullptr, P.prune_E};
+    const float pE = P.prune_zmax ? (float)(1.9073486328125e-6 * ((double)__uint_as_float(*P.prune_zmax) + P.prune_kh))
+                                  : P.prune_E;  // (2^-19)
+    const Prune pr{P.prune_w ? (const float*)(smem + Lo.wt) : nullptr, pE};
     if (ring)
       n = chunk_walk<T, NH, true>(eks, eps, c0, c1, pc, R, act, m0, Om0, (EK)0, last, rg_a + rbase,
                                   rg_b + rbase, rg_l + rbase, P.r_cap, pr);

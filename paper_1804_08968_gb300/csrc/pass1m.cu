@@ -10,6 +10,7 @@ namespace dexel {
 // 4 blocks an SM (64 registers): latency-bound, more warps pay (k = 2: 0.35 -> 0.33 ms)
 template <typename T, int NS>
 __global__ void __launch_bounds__(256, 4) k_pass1m(P1Params<T> P) {
+  if (*(volatile int*)&P.ctr->status & ST_BAD_CSR) return;  // (stream-ordered calls: no plan for a bad input)
   const int lane = threadIdx.x & 31;
   const Lanes L{lane, 32};
   const long long ncols = (long long)P.nx * P.ny;

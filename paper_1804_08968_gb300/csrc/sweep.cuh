@@ -58,6 +58,8 @@ struct Counters {
   int ring_spills;                // pass-1 window kernel: tiles walked twice (a lane's ring
                                   // region overflowed)
   unsigned long long lvl_redo;    // level walks: lists longer than a lane's slots (walked again)
+  int sticky;                     // stream-ordered calls: status bits folded in before a
+                                  // status word is cleared (their failures outlive the clear)
   unsigned long long win_hist[kWinBins];  // pass-1 window events by tile: bin b holds the
                                           // events of the tiles with 2^(8+b) < E <= 2^(9+b)
                                           // (bin 0: E <= 512; the last: E > 2^(8+kWinBins-1))
@@ -259,6 +261,10 @@ struct P1Params {
   int xa, xb;
   // the window kernel's event buffers (1 or 2; 0 counts as 1)
   int nbuf;
+  // the pruning margin computed on the device from the input's max |z| (zmax_bits after the
+  // validation) when set: E = 2^-19 (max |z| + prune_kh), else prune_E as given
+  const unsigned* prune_zmax;
+  double prune_kh;
   // the window kernel's first launch when a redo launch with more room follows: a tile whose
   // window exceeds the room is marked whole for it (instead of split into narrower runs)
   int tile_redo;

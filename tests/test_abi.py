@@ -49,6 +49,8 @@ def test_entry_points_reject_missing_arguments(libpath):
     assert L.dexel_raycast_axis(None, None, 0, 2, 4, 4, 0.25, 0, ctypes.byref(out), None, 0,
                                 None) == -1
     assert L.dexel_offset_ldi(None, None, 1.0, 0, 0, None, None, 0, None) == -1
+    assert L.dexel_offset_enqueue(None, ctypes.byref(gin), 1.0, 0, 0, ctypes.byref(out), None, 0,
+                                  None, None) == -1
     # a bad operation is refused the same way
     assert L.dexel_offset_slices(None, ctypes.byref(gin), 1.0, 7, 0, ctypes.byref(out), None, 0,
                                  None) == -1
@@ -67,6 +69,7 @@ def test_status_strings(libpath):
     assert lib.dexel_status_string(0) == b"ok"
     assert b"CSR" in lib.dexel_status_string(-2)
     assert lib.dexel_status_string(-99) == b"unknown status"
+    assert b"plan" in lib.dexel_status_string(-7)
 
 
 def test_workspace_size_rejects_bad_input(libpath):
