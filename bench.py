@@ -174,8 +174,10 @@ def offset_plan(nstreams):
 
 
 def run_offsets512(args, rank, ws, steps=None, warmup=None, with_e2e=True):
-    """The 512 x 512 step: six offsets (dilation and erosion at k = 2, 8, 32), on two host
-    threads with their own contexts and streams.  Returns the line's fields."""
+    """The 512 x 512 step: six offsets (dilation and erosion at k = 2, 8, 32).  Headline: the
+    stream-ordered entry point from one host thread on two streams; beside it the synchronous
+    calls on two host threads with their own contexts and streams (which also give the
+    end-to-end figure).  Returns the line's fields."""
     import numpy as np
     import torch
     from concurrent.futures import ThreadPoolExecutor
@@ -267,14 +269,21 @@ def run_offsets512(args, rank, ws, steps=None, warmup=None, with_e2e=True):
     ctx.set_profiling(False)
     torch.cuda.synchronize()
 
-    res = {"value": units * ws / (ms_step / 1e3), "unit": "columns/s", "ms_per_step": ms_step,
-           "steps": steps, "warmup": warmup, "gpu_launches": launches,
+    # the headline: the same step queued with the stream-ordered entry point (one host thread,
+    # no host synchronisation inside the step); the synchronous two-thread step beside it
+    so = run_offsets512_enqueued(dx, grid, flush, steps, warmup, ws)
+    sync_line = {"value": units * ws / (ms_step / 1e3), "unit": "columns/s",
+                 "ms_per_step": ms_step, "gpu_launches": launches,
+                 "how": f"dexel_dilate / dexel_erode (synchronous) on {ns} host threads, each "
+                        f"its own context and stream: {plan}"}
+    res = {"value": so["value"], "unit": "columns/s", "ms_per_step": so["ms_per_step"],
+           "steps": steps, "warmup": warmup, "gpu_launches": so["gpu_launches"],
+           "synchronous": sync_line,
            "workload": "512x512 grid, 200 seeded primitives (spheres/boxes/hollow shells, <=16 "
                        "segs/col), dilation+erosion at k=2,8,32 spacings, FP64",
            "columns_per_step": units, "nseg_in": g.nseg,
            "l2": "flushed (256 MiB write) before every timed step",
-           "streams": f"{ns} (the six offsets of a step on {ns} host threads, each its own "
-                      f"context and stream: {plan})",
+           "streams": so["how"],
            "kernel_ms": {f"{op}_k{int(k)}": {"pass1_window": km[0], "k_levels": km[1],
                                              "k_lgather": km[2], "smid_pack": km[3]}
                          for (op, k, _, _s, km) in rec},
@@ -305,6 +314,73 @@ def run_offsets512(args, rank, ws, steps=None, warmup=None, with_e2e=True):
                       "d2h_bytes_per_step": d2h}
     pool.shutdown()
     return res
+
+
+def run_offsets512_enqueued(dx, grid, flush, steps, warmup, ws, ns=2):
+    """The same six offsets queued with dexel_offset_enqueue from ONE host thread on ns
+    streams (no host synchronisation inside a step; one at its end): the plans recorded by one
+    synchronous call of each offset on one context, a workspace a stream (its offsets run one
+    after the other there), the results checked against the synchronous ones."""
+    import torch
+    ctx = dx.Context(int(os.environ.get("LOCAL_RANK", "0")))
+    main = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in range(ns)]
+    plan = offset_plan(ns)
+    jobs, need = [], [0] * ns
+    for w in range(ns):
+        for op, k in plan[w]:
+            code = dx.DILATE if op == "dilate" else dx.ERODE
+            ref = ctx.run(code, grid, k, main)
+            need[w] = max(need[w], ctx.last_required())
+            cap = ref.nseg + ref.nseg // 4 + 1024
+            jobs.append((w, code, k, ref,
+                         torch.empty(grid.nx * grid.ny + 1, dtype=torch.int32, device="cuda"),
+                         torch.empty((cap, 2), dtype=grid.z.dtype, device="cuda"),
+                         torch.zeros(2, dtype=torch.int64, device="cuda")))
+    wsb = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in need]
+    order = sorted(range(len(jobs)), key=lambda q: ([j[0] for j in jobs[:q]].count(jobs[q][0]), jobs[q][0]))
+
+    def step():
+        ev = torch.cuda.Event()
+        ev.record(main)
+        for st in streams:
+            st.wait_event(ev)
+        n = 0
+        for q in order:  # (the streams' offsets interleaved: both streams get work at once)
+            w, code, k, _, off, z, r = jobs[q]
+            rc = ctx.enqueue(code, grid, k, wsb[w], off, z, r, streams[w])
+            if rc != 0:
+                raise RuntimeError(f"dexel_offset_enqueue: {rc}")
+            n += ctx.last_launches
+        for st in streams:
+            main.wait_stream(st)
+        return n
+
+    for _ in range(max(warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    for w, code, k, ref, off, z, r in jobs:
+        rr = r.cpu().numpy()
+        if rr[0] != 0 or rr[1] != ref.nseg or not torch.equal(off, ref.col_off) or \
+                not torch.equal(z[: ref.nseg], ref.z):
+            raise RuntimeError(f"stream-ordered offset differs from the synchronous one ({rr})")
+    times, launches = [], 0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        launches += step()
+        e1.record(main)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = allmax(sum(times) / len(times), ws, device="cuda")
+    units = len(jobs) * grid.nx * grid.ny
+    return {"value": units * ws / (ms / 1e3), "unit": "columns/s", "ms_per_step": ms,
+            "gpu_launches": launches, "host_syncs_per_step": 1, "host_threads": 1,
+            "how": f"six dexel_offset_enqueue calls from one host thread on {ns} streams ({plan}), "
+                   "one context, a workspace a stream; results equal to the synchronous calls "
+                   "(checked)"}
 
 
 def kernel_roofline(name, km_ms, g, stats, fp32, peak, peak_kind, clk_mhz):
@@ -861,7 +937,8 @@ def main():
                                "l2": res["l2"], "streams": res["streams"],
                                "parallelism": f"replica x{ws}"},
                     "e2e": res.get("e2e"), "gpu_launches": res["gpu_launches"],
-                    "kernel_ms": res["kernel_ms"], "stats": res["stats"]}
+                    "kernel_ms": res["kernel_ms"], "stats": res["stats"],
+                    "synchronous": res.get("synchronous")}
             print(json.dumps(line), flush=True)
     else:
         run_ours(args, rank, ws)

@@ -25,6 +25,11 @@ struct Tape {
   std::vector<Counters> snaps;
   size_t pos = 0;
   bool replayable = true;
+  // the context's learnt capacities the recorded attempt planned with (the replay plans with
+  // them too, so that it needs the workspace the recorded call reported)
+  long long needF = 0, needM = 0, needO = 0, needL = 0;
+  int capA = 0, capR = 0, capS = 0, ccap = 0;
+  bool noblock = false;
 };
 
 struct dexel_ctx {
@@ -374,7 +379,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
   const int blocks = sms * 4;
   const int nwarps = blocks * kWarpsPerBlock;
 
-  ctx->noblock = false;
+  if (!ctx->replay) ctx->noblock = false;
   // Stream-ordered replay (ctx->replay): the counters come from the tape of an earlier
   // synchronous call of the same offset instead of the device, every redo launch is made
   // (a redo finds nothing to do when the first launch finished everything), the status bits
@@ -384,9 +389,32 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
   const bool replay = rt != nullptr;
   Tape rec;
   if (replay && !ws_user) return DEXEL_ERR_INVALID_ARG;
+  // the learnt capacities: the tape's while replaying (the context's own put back after)
+  struct Saved {
+    dexel_ctx* c;
+    int key;
+    long long nF, nM, nO, nL;
+    int cA, cR, cS, cc;
+    bool nb, on;
+    ~Saved() {
+      if (!on) return;
+      c->needF = nF; c->needM = nM; c->needO = nO; c->needL = nL;
+      c->capA = cA; c->capR = cR; c->capS = cS; c->noblock = nb;
+      c->ccap[key] = cc;
+    }
+  } saved{ctx, 2 * K + (erode ? 1 : 0), ctx->needF, ctx->needM, ctx->needO, ctx->needL,
+          ctx->capA, ctx->capR, ctx->capS, ctx->ccap[2 * K + (erode ? 1 : 0)], ctx->noblock, replay};
+  if (replay) {
+    ctx->needF = rt->needF; ctx->needM = rt->needM; ctx->needO = rt->needO; ctx->needL = rt->needL;
+    ctx->capA = rt->capA; ctx->capR = rt->capR; ctx->capS = rt->capS; ctx->noblock = rt->noblock;
+    ctx->ccap[2 * K + (erode ? 1 : 0)] = rt->ccap;
+  }
   for (int attempt = 0; attempt < (replay ? 1 : 24); ++attempt) {
     rec.snaps.clear();
     rec.replayable = true;
+    rec.needF = ctx->needF; rec.needM = ctx->needM; rec.needO = ctx->needO; rec.needL = ctx->needL;
+    rec.capA = ctx->capA; rec.capR = ctx->capR; rec.capS = ctx->capS; rec.noblock = ctx->noblock;
+    rec.ccap = ctx->ccap[2 * K + (erode ? 1 : 0)];
     // ---------------- plan
     // phase A: counters, tables, indices, validation
     void* pwtabf = nullptr;

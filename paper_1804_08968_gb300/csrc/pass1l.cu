@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(256, MINB) k_pass1l(P1Params<T> P, int ecap, i
   unsigned char* gsm =
       smem + (long long)G.gid * p1l_layout(P.K, ecap, gw, (int)sizeof(typename EvK<T>::type), P.nbuf).total;
   if (*(volatile int*)&P.ctr->status & ST_BAD_CSR) return;  // (stream-ordered calls: no plan for a bad input)
+  if (P.redo && *(volatile int*)&P.ctr->p1_marked == 0) return;  // (a redo with nothing marked)
   const int xw = P.xb > 0 ? P.xb - P.xa : P.nx;  // the block of columns
   const long long ntiles = (long long)P.ny * ((xw + 31) >> 5);
   ArenaCursor cur{0, 0};

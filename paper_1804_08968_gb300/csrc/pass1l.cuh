@@ -383,6 +383,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       if (G.gtid == 0) {
         set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
         if (P.rowmark) P.rowmark[j] = 1;
+        atomicAdd(&P.ctr->p1_marked, 1);
       }
       break;
     }
@@ -394,6 +395,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       if (G.gtid == 0) {
         set_status(&P.ctr->status, ST_OVERFLOW_SLOT);
         P.m_start[(long long)ia * P.ny + j] = -1;  // marks the column (count 0)
+        atomicAdd(&P.ctr->p1_marked, 1);
         P.m_cnt[(long long)ia * P.ny + j] = 0;
         if (P.rowmark) P.rowmark[j] = 1;
       }

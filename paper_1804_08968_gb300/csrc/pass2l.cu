@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(256, MINB) k_lgather(LvlParams<T> A, int bcap,
   const long long q1 = A.q0 + A.nsrc;  // the block's output columns in line order
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   if (*(volatile int*)&A.P.ctr->status & ST_LEVELS_OVER) return;  // the lists are incomplete
+  if (redo && *(volatile int*)&A.P.ctr->redo_cols == 0) return;  // (a redo with nothing marked)
   ArenaCursor cur{0, 0};
   for (long long item = A.q0 + (long long)blockIdx.x * (blockDim.x >> 5) + warp; item < q1; item += nw)
     lgather_column<T>(A, item, bcap, redo, lane, wb, cur);

@@ -49,6 +49,7 @@ struct Counters {
   int max_state;      // max live elements seen in a slot array (for resizing)
   int max_segs_in;    // max input segments per column
   int redo_cols;      // gather: output columns handed to the fallback kernel
+  int p1_marked;      // pass-1 window kernel: tiles or columns marked for its redo launch
   unsigned long long mid_total;   // S_mid pieces written
   unsigned long long out_total;   // pass-2 intervals written
   unsigned long long bucket_sum;  // gather: intervals collected over all columns (sizing)
