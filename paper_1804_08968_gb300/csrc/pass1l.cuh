@@ -30,6 +30,11 @@
 
 namespace dexel {
 
+// a height group of the walk is closed only when some lane saw an event within its label
+#ifndef DEXEL_P1_LAZY
+#define DEXEL_P1_LAZY 1
+#endif
+
 // words of the tile-relative source masks (32 + 2R + 1 <= 320 sources: R <= 128)
 constexpr int kP1TileWords = 5;
 
@@ -219,11 +224,21 @@ DXD int chunk_walk(const typename EvK<T>::type* ek, const unsigned short* ep, in
     Om = Ok;
     gmin = kNoLabel;
   };
+  // A height's events change nothing for a lane when all of them are farther than its label
+  // below (a source beyond the nearest open one neither becomes nearest when it opens nor was
+  // nearest when it closes, and gives no point piece): the height is closed only when some
+  // lane saw an event within its label (warp-uniform vote; exact).
+  bool dirty = false;
   for (int t = c0; t < c1; ++t) {
     const EK key = ek[t];
     const int src = ep[t];
     if (key != gkey) {  // warp-uniform: every lane reads the same event
+#if DEXEL_P1_LAZY
+      if (__any_sync(0xffffffffu, dirty)) close_group(gkey);
+      dirty = false;
+#else
       close_group(gkey);
+#endif
       gkey = key;
     }
     const int d = src - pc;
@@ -241,10 +256,21 @@ DXD int chunk_walk(const typename EvK<T>::type* ek, const unsigned short* ep, in
           m.dn[q] ^= d < 0 ? x : 0ULL;
         }
       }
+#if DEXEL_P1_LAZY
+      if (ad <= Om) {
+        dirty = true;
+        gmin = ad < gmin ? ad : gmin;
+      }
+#else
       gmin = ad < gmin ? ad : gmin;
+#endif
     }
   }
+#if DEXEL_P1_LAZY
+  if (__any_sync(0xffffffffu, dirty)) close_group(gkey);
+#else
   close_group(gkey);
+#endif
   return cnt;
 }
 
@@ -601,7 +627,9 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
           if (st != EvK<T>::none()) carry = st;
         }
       }
-    } else if (fits && n > 0) {
+    } else if (fits) {
+      // (warp-uniform: every lane walks, as the walk's votes need; a lane with no pieces in
+      // this chunk writes none)
       const long long o = s + (inc - tot_col) + before;
       EK dummy;
       chunk_walk<T, NH, true>(eks, eps, c0, c1, pc, R, act, m0, Om0, run_a, dummy, P.m_a + o,
