@@ -146,8 +146,8 @@ __global__ void k_validate(int ncols, const int* off, const T* z, long long nseg
 }
 
 // The events of every pass-1 tile window (32 output columns of a row and the K sources on
-// either side; two events a segment, two more a column for a complement), summed by the
-// power-of-two bin of the window's size: the planner sizes the tiles' event room by them.
+// either side; two events a segment, two more a column for a complement), summed by bins of
+// 1024 events of the window's size: the planner sizes the tiles' event room by them.
 __global__ void k_win_hist(int nx, int ny, int K, int erode, const int* off, Counters* ctr) {
   __shared__ unsigned long long hb[kWinBins];
   if (threadIdx.x < kWinBins) hb[threadIdx.x] = 0;
@@ -159,8 +159,8 @@ __global__ void k_win_hist(int nx, int ny, int K, int erode, const int* off, Cou
     const int s0 = max(0, i0 - K), s1 = min(nx, i0 + 32 + K);
     const long long rb = (long long)j * nx;
     const long long E = 2LL * (off[rb + s1] - off[rb + s0]) + (erode ? 2LL * (s1 - s0) : 0);
-    int b = 0;
-    while (b < kWinBins - 1 && E > (512LL << b)) ++b;
+    const long long bb = E <= 0 ? 0 : (E - 1) >> 10;
+    const int b = bb < kWinBins - 1 ? (int)bb : kWinBins - 1;
     atomicAdd(&hb[b], (unsigned long long)E);
   }
   __syncthreads();
@@ -665,10 +665,10 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         const bool redo_fits = pass1l_smem(K, ecapR, 8, ksz) <= (220LL << 10);
         double all = 0;
         for (int b = 0; b < kWinBins; ++b) all += (double)hc.win_hist[b];
-        auto beyond = [&](int room) {
+        auto beyond = [&](int room) {  // (a bin reaching above the room counts whole)
           double x = 0;
           for (int b = 0; b < kWinBins; ++b)
-            if ((512LL << b) > room) x += (double)hc.win_hist[b];
+            if (1024LL * (b + 1) > room || b == kWinBins - 1) x += (double)hc.win_hist[b];
           return x;
         };
         int ecapL = 512;
@@ -677,17 +677,34 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
         const bool by_cost = ctx->p1l_ecap_mul <= 0 && !ctx->p1l_ecap_max && ctx->p1l_ecap <= 0 && K >= 48;
         if (by_cost) {
           const double wR = (double)std::max(1, plan_for(ecapR).warps_sm);
+          // candidates: the powers of two, and the largest rooms that leave 1, 2 or 3 blocks
+          // an SM (a room need not be a power of two)
+          std::vector<int> rooms;
+          for (int room = 512; room <= ecapR; room <<= 1) rooms.push_back(room);
+          for (int nbk = 1; nbk <= 3; ++nbk) {
+            int lo = 512, hi = ecapR;
+            auto fits = [&](int room) { return pass1l_smem(K, room, gw0, ksz) * nbk <= (220LL << 10); };
+            if (!fits(lo)) continue;
+            while (hi - lo > 64) {
+              const int mid = (lo + hi) / 2 & ~63;
+              if (fits(mid)) lo = mid; else hi = mid;
+            }
+            rooms.push_back(fits(hi) ? hi : lo);
+          }
+          std::sort(rooms.begin(), rooms.end());
           double best = 0;
-          for (int room = 512; room <= ecapR; room <<= 1) {
+          bool first = true;
+          for (int room : rooms) {
             const P1Plan pl = plan_for(room);
             if (pl.warps_sm <= 0) continue;
             const double out = beyond(room), in = all - out;
             // (windows beyond the largest room: narrower runs, about three times the events)
             const double cost = room < ecapR && redo_fits ? in / pl.warps_sm + out / wR
                                                           : (in + 3.0 * out) / pl.warps_sm;
-            if (room == 512 || cost <= best * 1.0001) {  // (ties: the larger room)
+            if (first || cost <= best * 1.0001) {  // (ties: the larger room)
               best = cost;
               ecapL = room;
+              first = false;
             }
           }
         } else {

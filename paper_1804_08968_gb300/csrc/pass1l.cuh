@@ -428,7 +428,7 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       ia = ib;
       continue;
     }
-    const int n2 = pow2_at_least(E);  // <= ecap (a power of two)
+    const int n2 = pow2_at_least(E);  // (the sorting network's width; only E <= ecap events stored)
     PHASE_BEGIN();
     // stage the events, one thread per source (payload: the source's tile position)
     for (int q = qa + G.gtid; q < qe; q += gthreads) {
@@ -467,8 +467,6 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
     // the events in height order (the order within a height does not matter): merged from
     // the sources' runs when the buffers hold the window twice, else a bitonic sort in place
     const bool merge = 2 * E <= room;
-    if (!merge)
-      for (int t = E + G.gtid; t < n2; t += gthreads) { ek[t] = EvK<T>::none(); ep[t] = 0xFFFFu; }
     G.sync();
     PHASE(0);
     const EK* eks = ek;
@@ -492,22 +490,34 @@ DXD void pass1l_tile(const P1Params<T>& P, long long tile, int ecap, unsigned ch
       eps = pa;
       Er = lower_bound(eks, E, EvK<T>::none());  // (a complement's padding sorts last)
     } else {
+      // bitonic sort with every comparator ascending (each merge begins by comparing an
+      // element with its mirror in the block): the positions from E to the network's width
+      // n2 hold a virtual +inf that no comparator moves, so they are neither stored nor
+      // touched (a room need not be a power of two)
       for (int k = 2; k <= n2; k <<= 1) {
         for (int jj = k >> 1; jj > 0; jj >>= 1) {
           for (int p = G.gtid; p < (n2 >> 1); p += gthreads) {
-            const int t = ((p & ~(jj - 1)) << 1) | (p & (jj - 1));
-            const int x = t | jj;
-            const bool up = (t & k) == 0;
-            const EK kt = ek[t], kx = ek[x];
-            if ((kt > kx) == up) {
-              ek[t] = kx; ek[x] = kt;
-              const unsigned short vt = ep[t]; ep[t] = ep[x]; ep[x] = vt;
+            int t, x;
+            if (jj == (k >> 1)) {  // the flip: t against its mirror in the block of k
+              const int i = p & (jj - 1);
+              t = (p >> (__ffs(jj) - 1)) * k + i;
+              x = t - i + (k - 1 - i);
+            } else {
+              t = ((p & ~(jj - 1)) << 1) | (p & (jj - 1));
+              x = t | jj;
+            }
+            if (x < E) {
+              const EK kt = ek[t], kx = ek[x];
+              if (kt > kx) {
+                ek[t] = kx; ek[x] = kt;
+                const unsigned short vt = ep[t]; ep[t] = ep[x]; ep[x] = vt;
+              }
             }
           }
           G.sync();
         }
       }
-      Er = lower_bound(ek, n2, EvK<T>::none());  // real events (the padding sorts last)
+      Er = lower_bound(ek, E, EvK<T>::none());  // real events (a complement's padding sorts last)
     }
     PHASE(1);
     // chunk bounds at group boundaries

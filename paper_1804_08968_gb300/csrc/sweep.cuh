@@ -39,7 +39,7 @@ enum : int {
   ST_BOUNDS = 32,          // a self-check found an index out of its array (access skipped)
 };
 
-constexpr int kWinBins = 8;
+constexpr int kWinBins = 32;
 struct Counters {
   unsigned long long arena_top[4];  // bump pointers of the arenas
   unsigned long long work_next[2];  // persistent work queues
@@ -62,8 +62,8 @@ struct Counters {
   int sticky;                     // stream-ordered calls: status bits folded in before a
                                   // status word is cleared (their failures outlive the clear)
   unsigned long long win_hist[kWinBins];  // pass-1 window events by tile: bin b holds the
-                                          // events of the tiles with 2^(8+b) < E <= 2^(9+b)
-                                          // (bin 0: E <= 512; the last: E > 2^(8+kWinBins-1))
+                                          // events of the tiles with 1024 b < E <= 1024 (b + 1)
+                                          // (the last: E > 1024 (kWinBins - 1))
   unsigned long long phase[16];   // optional per-phase clock totals (DEXEL_PHASES builds)
 };
 
