@@ -37,11 +37,12 @@ OPS = ("dilate", "erode")
 K_MAIN = 64.0  # the 2048^2 workload's radius in grid spacings
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per S_mid piece of the 2048^2
 # k = 64 dilation's kernels, from an ncu capture of the current kernels on a 128-row strip of
-# the workload (rows 450-577, 108.1 M pieces), scaled to a full launch by the pieces processed
-# (None once a kernel changed after its capture)
-TRAFFIC_PER_PIECE = {"k_pass1l": None, "k_levels": 69.81}
+# the workload (rows 450-577, 108.1 M pieces; pass 1: its first and redo launches together),
+# scaled to a full launch by the pieces processed (None once a kernel changed after its
+# capture)
+TRAFFIC_PER_PIECE = {"k_pass1l": 44.95, "k_levels": 68.49}
 # instructions (smsp__inst_executed.sum) per S_mid piece from the same capture
-INST_PER_PIECE = {"k_pass1l": None, "k_levels": 135.66}
+INST_PER_PIECE = {"k_pass1l": 69.11, "k_levels": 127.29}
 # issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock
 ISSUE_PER_CLK = 152 * 4
 
