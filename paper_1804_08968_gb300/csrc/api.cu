@@ -30,6 +30,7 @@ struct Tape {
   long long needF = 0, needM = 0, needO = 0, needL = 0;
   int capA = 0, capR = 0, capS = 0, ccap = 0;
   bool noblock = false;
+  size_t need = 0;  // the workspace the recorded call needed
 };
 
 struct dexel_ctx {
@@ -102,6 +103,11 @@ struct dexel_ctx {
   std::map<std::string, Tape> tapes;
   Tape* replay = nullptr;        // the tape being replayed (a stream-ordered call), else null
   long long* replay_result = nullptr;  // its device result words [status, segments]
+  // batched calls: the large shapes' stream-ordered offsets run on a side stream, their
+  // result words in res_buf
+  cudaStream_t side = nullptr;
+  long long* res_buf = nullptr;
+  size_t res_n = 0;
 };
 
 namespace {
@@ -1203,6 +1209,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
     ctx->stats[4] = std::max<long long>(ctx->stats[4], hc.max_pieces);
     ctx->stats[5] = std::max<long long>(ctx->stats[5], hc.max_state);
     ctx->last_required = total;
+    rec.need = total;
     if (rec.replayable) ctx->tapes[tape_key(in, k, erode, slices, sizeof(T))] = std::move(rec);
     return DEXEL_OK;
   }
@@ -1563,6 +1570,8 @@ void dexel_ctx_destroy(dexel_ctx* ctx) {
   if (ctx->own) cudaFree(ctx->own);
   if (ctx->mid) cudaFree(ctx->mid);
   if (ctx->aux) cudaFree(ctx->aux);
+  if (ctx->res_buf) cudaFree(ctx->res_buf);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   batch_engine_destroy(ctx->batch);
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
@@ -1933,6 +1942,51 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
   std::vector<long long> nA, nB;
   std::vector<int> fin(nshapes, 1);  // 1: the single-shape path
   std::vector<long long> fseg(nshapes, 0);
+  // The shapes beyond the batch whose offset (a dilation or an erosion) has a recorded plan
+  // on this context: stream-ordered (dexel_offset_enqueue) on a side stream, beside the
+  // batch, into the library's workspace; their result words are read once after the batch.
+  std::vector<int> queued;
+  {
+    size_t need = 0;
+    std::vector<int> cand;
+    for (int s = 0; s < nshapes; ++s) {
+      if ((long long)ins[s].nx * ins[s].ny <= ctx->batch_max_cols) continue;
+      if (ops[s] != DEXEL_DILATE && ops[s] != DEXEL_ERODE) continue;
+      auto it = ctx->tapes.find(tape_key(&ins[s], k[s], ops[s] == DEXEL_ERODE, false,
+                                         fp32 ? sizeof(float) : sizeof(double)));
+      if (it == ctx->tapes.end()) continue;
+      need = std::max(need, it->second.need);
+      cand.push_back(s);
+    }
+    bool ok = !cand.empty() && ensure_owned(ctx, need) == DEXEL_OK;
+    if (ok && !ctx->side) ok = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok && ctx->res_n < 2 * cand.size()) {
+      if (ctx->res_buf) cudaFree(ctx->res_buf);
+      ctx->res_buf = nullptr;
+      ctx->res_n = 0;
+      ok = cudaMalloc(&ctx->res_buf, sizeof(long long) * 2 * cand.size()) == cudaSuccess;
+      if (ok) ctx->res_n = 2 * cand.size();
+    }
+    cudaEvent_t ready = nullptr;
+    ok = ok && cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventRecord(ready, st) == cudaSuccess && cudaStreamWaitEvent(ctx->side, ready, 0) == cudaSuccess;
+    if (ready) cudaEventDestroy(ready);
+    cudaGetLastError();
+    if (ok) {
+      for (size_t q = 0; q < cand.size(); ++q) {
+        const int s = cand[q];
+        const dexel_status r = dexel_offset_enqueue(ctx, &ins[s], k[s], ops[s], mode, &outs[s], ctx->own,
+                                                    ctx->own_bytes, ctx->side,
+                                                    (int64_t*)(ctx->res_buf + 2 * queued.size()));
+        launches += ctx->launches;
+        if (r == DEXEL_OK) {
+          queued.push_back(s);
+        } else if (r != DEXEL_ERR_NO_PLAN && r != DEXEL_ERR_CAPACITY) {
+          return r;  // (a CUDA failure)
+        }
+      }
+    }
+  }
   if (!A.empty()) {
     int rc = batch_run(ctx->batch, fp32, A, st, stA, nA, &launches);
     if (rc != DEXEL_OK) return (dexel_status)rc;
@@ -1958,6 +2012,22 @@ dexel_status dexel_offset_batched(dexel_ctx* ctx, int nshapes, const dexel_grid_
       for (size_t q = 0; q < which.size(); ++q) {
         fin[which[q]] = stB[q];
         fseg[which[q]] = nB[q];
+      }
+    }
+  }
+  if (!queued.empty()) {
+    // the side stream's results (a shape the plan did not fit runs synchronously below)
+    std::vector<long long> hr(2 * queued.size());
+    if (cudaMemcpyAsync(hr.data(), ctx->res_buf, sizeof(long long) * hr.size(), cudaMemcpyDeviceToHost,
+                        ctx->side) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->side) != cudaSuccess)
+      return DEXEL_ERR_CUDA;
+    for (size_t q = 0; q < queued.size(); ++q) {
+      const int s = queued[q];
+      if (hr[2 * q] == DEXEL_OK) {
+        fin[s] = DEXEL_OK;
+        fseg[s] = hr[2 * q + 1];
+        outs[s].nseg = hr[2 * q + 1];
       }
     }
   }

@@ -192,3 +192,25 @@ def test_batched_large_shapes_single_path(dx, monkeypatch):
     for (g, op, k), o in zip(items, outs):
         off, z = o.to_host()
         _same(off, z, _ref(g, op, k), TOL64, f"{op} k={k} {g.nx}x{g.ny}")
+
+
+def test_batched_large_shapes_stream_ordered(dx, monkeypatch):
+    """A second batched call on the same context queues the large dilations and erosions
+    stream-ordered (the plans the first call recorded) beside the batch; only the large
+    closings and openings take the synchronous single-shape path; every result matches the
+    oracle on both calls."""
+    import torch
+    monkeypatch.setenv("DEXEL_BATCH_MAX_COLS", "600")
+    items = _batch(7, 12, False)
+    code = {"dilate": dx.DILATE, "erode": dx.ERODE, "close": dx.CLOSE, "open": dx.OPEN}
+    grids = [dx.Grid.from_synth(g, dtype=torch.float64) for g, _, _ in items]
+    ctx = dx.Context(0)
+    big = [op for g, op, _ in items if g.nx * g.ny > 600]
+    big_morph = sum(op in ("close", "open") for op in big)
+    assert len(big) > big_morph
+    for call in range(2):
+        outs = ctx.run_batched([code[op] for _, op, _ in items], grids, [k for _, _, k in items])
+        assert ctx.stats()[5] == (len(big) if call == 0 else big_morph)
+        for (g, op, k), o in zip(items, outs):
+            off, z = o.to_host()
+            _same(off, z, _ref(g, op, k), TOL64, f"call {call}: {op} k={k} {g.nx}x{g.ny}")
