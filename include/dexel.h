@@ -122,6 +122,9 @@ typedef struct dexel_ctx dexel_ctx;
  *                                   at reach >= 48 the room with the least window events per
  *                                   resident warp over the first launch and the redo launch,
  *                                   from a histogram of the tiles' window sizes; below, x = 1
+ *   DEXEL_PASS1_BLOCK_CAP=1..3      the costed room counts at most this many blocks an SM
+ *                                   (default 2: the 80-register plan of a third block spills
+ *                                   about what it gains)
  *   DEXEL_PASS1_TILE_REDO=0|1       a tile whose window exceeds the room goes whole to the
  *                                   redo launch (1, default) or is split into narrower runs
  *                                   of columns (0)

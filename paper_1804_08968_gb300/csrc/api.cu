@@ -55,6 +55,7 @@ struct dexel_ctx {
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
   int lvl_slots = 0;    // interval slots a lane of the level walks (0: by reach)
   bool p1l_tile_redo = true;  // pass 1: tiles beyond the room go whole to the redo launch
+  int p1l_block_cap = 2;      // pass 1's costed room: blocks an SM counted at most
   int p1l_nbuf = 0;     // its event buffers (0: two where they cost no block an SM)
   double p1l_ecap_mul = 0;  // its event room: this many times twice the mean window's events (0: by reach)
   int p1l_gw = 0;       // its warps a tile (0: by the reach)
@@ -665,7 +666,7 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           // (a third block an SM runs the 80-register plan, whose spills cost about what the
           // block gains: measured 136 against 122 ms at 2048^2 FP32, 461 against 434 ms at
           // 4096^2 k = 128 FP64; counted as two)
-          pl.warps_sm = (int)std::min<long long>(2, per_sm(pl.nbuf)) * 8;
+          pl.warps_sm = (int)std::min<long long>(ctx->p1l_block_cap, per_sm(pl.nbuf)) * 8;
           return pl;
         };
         const bool redo_fits = pass1l_smem(K, ecapR, 8, ksz) <= (220LL << 10);
@@ -1548,6 +1549,10 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
     if (v >= 0.5 && v <= 64.0) c->p1l_ecap_mul = v;
   }
   if (const char* e = getenv("DEXEL_PASS1_TILE_REDO")) c->p1l_tile_redo = atoi(e) != 0;
+  if (const char* e = getenv("DEXEL_PASS1_BLOCK_CAP")) {
+    const int v = atoi(e);
+    if (v >= 1 && v <= 3) c->p1l_block_cap = v;
+  }
   if (const char* e = getenv("DEXEL_LEVEL_SLOTS")) {
     const int v = atoi(e);
     if (v >= 2 && v <= 16) c->lvl_slots = v;
