@@ -40,7 +40,16 @@ constexpr int kLvlSlots = 16;  // the most a launch uses
 // 12 228, 16 258; 4096^2 at k = 128: 8 slots 2114 ms, 12 1547, 16 1535)
 DXI int lvl_slots_for(int R) { return R < 48 ? 8 : (R <= 64 ? 10 : 16); }
 // pieces a warp stages in shared memory at a time (a level group walks one source)
-constexpr int kLvlStage = 64;
+// pieces staged a chunk, and the unrolling of the walk over them (measured at 2048^2 k = 64:
+// stage 128 237 ms against 200 at 64; unroll 1 209, 2 200, 4 195, 8 192 ms)
+#ifndef DEXEL_LVL_STAGE
+#define DEXEL_LVL_STAGE 64
+#endif
+#ifndef DEXEL_LVL_UNROLL
+#define DEXEL_LVL_UNROLL 8
+#endif
+constexpr int kLvlStage = DEXEL_LVL_STAGE;
+constexpr int kLvlUnroll = DEXEL_LVL_UNROLL;
 // w-table entries kept in shared memory when the per-lane tables do not fit (n <= k^2:
 // radii up to 64 spacings)
 constexpr int kLvlTable = 4097;
@@ -262,7 +271,7 @@ DXD void walk_staged(const P2GParams<T>& P, const Src& src, int np, int lane, fl
                            __uint_as_float(lvl_pack(base + k, adx)));
     }
     wsync();
-#pragma unroll 2
+#pragma unroll kLvlUnroll
     for (int k = 0; k < m; ++k) {
       const float4 v = stg[k];
       lvl_step(s, v.x, v.y, __float_as_uint(v.w), wl(__float_as_int(v.z)), E, emit);
