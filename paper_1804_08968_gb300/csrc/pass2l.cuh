@@ -41,7 +41,7 @@ constexpr int kLvlSlots = 16;  // the most a launch uses
 DXI int lvl_slots_for(int R) { return R < 48 ? 8 : (R <= 64 ? 10 : 16); }
 // pieces a warp stages in shared memory at a time (a level group walks one source)
 // pieces staged a chunk, and the unrolling of the walk over them (measured at 2048^2 k = 64:
-// stage 128 237 ms against 200 at 64; unroll 1 209, 2 200, 4 195, 8 192 ms)
+// stage 128 237 ms against 200 at 64; unroll 1 209, 2 200, 4 195, 8 192, 16 196 ms)
 #ifndef DEXEL_LVL_STAGE
 #define DEXEL_LVL_STAGE 64
 #endif
