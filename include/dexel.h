@@ -129,9 +129,11 @@ typedef struct dexel_ctx dexel_ctx;
  *                                   redo launch (1, default) or is split into narrower runs
  *                                   of columns (0)
  *   DEXEL_LEVEL_SLOTS=2..16         interval slots a lane of the pass-2 level walks holds in
- *                                   shared memory (a longer list is walked again straight
- *                                   into place; default 8 below reach 48, 10 up to 64,
- *                                   16 beyond)
+ *                                   shared memory (default 8 below reach 48, 6 up to 64, 12
+ *                                   beyond)
+ *   DEXEL_LEVEL_SPILL=0..256        intervals a lane writes beyond its slots to its own
+ *                                   region in global memory (default 64; a list longer than
+ *                                   slots + spill is walked again straight into place)
  *   DEXEL_PASS1_NBUF=1|2            event buffers a pass-1 tile (2: every window that fits is
  *                                   merged from its sources' runs; 1: those of up to half the
  *                                   room, the others sorted; default 2 where it costs no block

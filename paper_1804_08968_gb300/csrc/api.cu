@@ -55,6 +55,7 @@ struct dexel_ctx {
   int p1l_ecap = 0;     // its event room a tile (0: planned from the density)
   int lvl_slots = 0;    // interval slots a lane of the level walks (0: by reach)
   bool p1l_tile_redo = true;  // pass 1: tiles beyond the room go whole to the redo launch
+  int lvl_spill_cap = 64;     // level walks: intervals a lane spills to global memory beyond its slots
   int p1l_block_cap = 2;      // pass 1's costed room: blocks an SM counted at most
   int p1l_nbuf = 0;     // its event buffers (0: two where they cost no block an SM)
   double p1l_ecap_mul = 0;  // its event room: this many times twice the mean window's events (0: by reach)
@@ -924,8 +925,17 @@ dexel_status Offset<T>::run(dexel_ctx* ctx, const dexel_grid_in* in, double k, b
           H.P = pg;
           H.l_idx = (unsigned long long*)pslots;
           const size_t ib = align_up((size_t)nlev * 8 + 512, 256);
-          H.l_cap = (long long)((slot_room - ib) / 16);
+          // the walks' spill regions at the end of the room, when it has them to spare
+          const int scap = ctx->lvl_spill_cap;
+          const size_t sb = scap > 0 ? align_up((size_t)lvl_spill_bytes(sms, scap), 256) : 0;
+          const bool spill = sb > 0 && slot_room > ib + 2 * sb + 256;
+          const size_t so = spill ? (slot_room - sb) / 256 * 256 : slot_room;  // spill offset
+          H.l_cap = (long long)((so - ib) / 16);
           H.l_p = (ulonglong2*)(pslots + ib);
+          if (spill) {
+            H.spill = (unsigned*)(pslots + so);  // [so, so + sb) within the room
+            H.spill_cap = scap;
+          }
           int& lb = ctx->ccap[2 * K + (erode ? 1 : 0)];
           if (lb < 256) lb = 256;
           H.bcap = lb;
@@ -1552,6 +1562,10 @@ dexel_status dexel_ctx_create(dexel_ctx** ctx, int device) {
   if (const char* e = getenv("DEXEL_PASS1_BLOCK_CAP")) {
     const int v = atoi(e);
     if (v >= 1 && v <= 3) c->p1l_block_cap = v;
+  }
+  if (const char* e = getenv("DEXEL_LEVEL_SPILL")) {
+    const int v = atoi(e);
+    if (v >= 0 && v <= 256) c->lvl_spill_cap = v;
   }
   if (const char* e = getenv("DEXEL_LEVEL_SLOTS")) {
     const int v = atoi(e);

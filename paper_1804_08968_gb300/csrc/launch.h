@@ -68,7 +68,13 @@ struct LvlParamsHost {
   int yw = -1;
   // interval slots a lane of the level walks (0: by reach; at most 16)
   int slots = 0;
+  // spill regions of k_levels (lvl_spill_bytes of them; null: none): spill_cap intervals a
+  // lane of every warp of its grid beyond the slots
+  unsigned* spill = nullptr;
+  int spill_cap = 0;
 };
+// bytes of k_levels' spill regions for spill_cap intervals a lane
+long long lvl_spill_bytes(int sms, int spill_cap);
 // k_levels (the per-source level lists); launch_lgather then unites them per column
 template <typename T>
 cudaError_t launch_levels(const LvlParamsHost<T>& H, cudaStream_t st, int sms);

@@ -21,7 +21,8 @@ __global__ void __launch_bounds__(256, 4) k_levels(LvlParams<T> A, int tab_float
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   ArenaCursor cur{0, 0};
   for (long long item = (long long)blockIdx.x * (blockDim.x >> 5) + warp; item < nitems; item += nw)
-    levels_item<T, LTAB ? kTabBlock : kTabFlat, EXACT>(A, item, lane, ws, stg, E, (float*)tab, cur);
+    levels_item<T, LTAB ? kTabBlock : kTabFlat, EXACT>(A, item, lane, ws, stg, E, (float*)tab, cur,
+                                                       (long long)blockIdx.x * (blockDim.x >> 5) + warp);
 }
 
 // MINB blocks an SM: 4 (64 registers, some spilled) pays at short windows (k = 8: 0.47 ->
@@ -71,6 +72,8 @@ static LvlParams<T> lvl_params(const LvlParamsHost<T>& H) {
   A.l_p = H.l_p; A.l_cap = H.l_cap;
   A.W = 2 * H.P.R + 1;
   A.slots = H.slots > 0 && H.slots <= kLvlSlots ? H.slots : lvl_slots_for(H.P.R);
+  A.spill = H.spill;
+  A.spill_cap = H.spill ? H.spill_cap : 0;
   A.L = H.P.R + 1;
   if (A.L <= 32) {
     A.G = 32 / A.L;
@@ -89,6 +92,11 @@ static LvlParams<T> lvl_params(const LvlParamsHost<T>& H) {
   A.m_cap = H.m_cap;
   A.c_cap = H.c_cap;
   return A;
+}
+
+// the grid of launch_levels: sms x 4 blocks of 8 warps
+long long lvl_spill_bytes(int sms, int spill_cap) {
+  return (long long)sms * 4 * 8 * 32 * 2 * spill_cap * (long long)sizeof(unsigned);
 }
 
 template <typename T>

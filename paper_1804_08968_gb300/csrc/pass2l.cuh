@@ -35,10 +35,11 @@ namespace dexel {
 // (LvlParams::slots) follows the reach: longer windows give longer lists (measured: 2048^2
 // k = 64, 16 slots 261 ms, 8 slots 220 ms; 4096^2 k = 128, 16 slots 1541 ms, 8 slots 2110 ms)
 constexpr int kLvlSlots = 16;  // the most a launch uses
-// Interval slots a lane by reach: more slots walk fewer long lists again, fewer leave room
-// for more blocks an SM (measured on the 2048^2 workload at k = 64: 8 slots 218 ms, 10 200,
-// 12 228, 16 258; 4096^2 at k = 128: 8 slots 2114 ms, 12 1547, 16 1535)
-DXI int lvl_slots_for(int R) { return R < 48 ? 8 : (R <= 64 ? 10 : 16); }
+// Interval slots a lane by reach (a longer list spills to the lane's region in global memory):
+// fewer slots leave more of the SM's shared memory to L1 (measured with 64 spilled intervals
+// a lane: 2048^2 at k = 64, 4 slots 129 ms, 6 128, 8 138, 10 138; 4096^2 at k = 128, 6 slots
+// 1415 ms, 8 1402, 10 1397, 12 1394, 16 1509)
+DXI int lvl_slots_for(int R) { return R < 48 ? 8 : (R <= 64 ? 6 : 12); }
 // pieces a warp stages in shared memory at a time (a level group walks one source)
 // pieces staged a chunk, and the unrolling of the walk over them (measured at 2048^2 k = 64:
 // stage 128 237 ms against 200 at 64; unroll 1 209, 2 200, 4 195, 8 192, 16 196 ms)
@@ -75,6 +76,11 @@ struct LvlParams {
   int G;     // sources a warp when L <= 32, else 1
   int NG;    // level groups of 32 (levels 1 .. R) when L > 32, else 0
   int slots;       // per-lane interval slots of the level walks (at most kLvlSlots)
+  // intervals a lane writes beyond its slots go to its spill region in global memory (spill:
+  // 2 x spill_cap words a lane, lanes of a warp of the grid in order; null: none), so that
+  // only a list longer than slots + spill_cap is walked again
+  unsigned* spill;
+  int spill_cap;
   int yw;          // reach of the output column's window along y (R; 0: the 2D slices, each
                    // column its own level-0 list)
   long long q0;    // first source column of the block (line order q = i * ny + j)
@@ -184,13 +190,23 @@ DXD void lvl_close(LvlRun& s, const Emit& emit) {
 struct PackEmit {
   unsigned* sl;  // ws + lane
   int slots;
+  unsigned* sp;  // the lane's spill region (2 words an interval), or null
+  int scap;      // its intervals
   DXD void operator()(const LvlRun& s) const {
     if (s.cnt < slots) {
       sl[s.cnt << 5] = s.pl;
       sl[(s.cnt << 5) + slots * 32] = s.pr;
+    } else if (s.cnt - slots < scap) {
+      sp[2 * (s.cnt - slots)] = s.pl;
+      sp[2 * (s.cnt - slots) + 1] = s.pr;
     }
   }
 };
+// the spill region of lane `lane` of the grid's warp gw (null without one)
+template <typename T>
+DXD unsigned* lvl_spill(const LvlParams<T>& A, long long gw, int lane) {
+  return A.spill ? A.spill + (gw * 32 + lane) * 2LL * A.spill_cap : nullptr;
+}
 
 // the exact ends: a - w(dx^2 + t^2) and b + w(dx^2 + t^2) in double
 template <typename T>
@@ -286,8 +302,12 @@ DXD void walk_staged(const P2GParams<T>& P, const Src& src, int np, int lane, fl
 // longer than the slots is walked again by its lane straight into place (redo).  Returns
 // false when the arena is full (status set).
 template <typename T, typename Redo>
-DXD bool lvl_flush(const LvlParams<T>& A, int lane, const unsigned* ws, int cnt, bool act,
-                   long long q, int t, long long ms, ArenaCursor& cur, const Redo& redo) {
+DXD bool lvl_flush(const LvlParams<T>& A, int lane, const unsigned* ws, const unsigned* sp0,
+                   int cnt, bool act, long long q, int t, long long ms, ArenaCursor& cur,
+                   const Redo& redo) {
+  // sp0: the spill region of the warp's lane 0 (null: none); a lane holds slots + scap
+  const int scap = sp0 ? A.spill_cap : 0;
+  const int held = A.slots + scap;
   const Lanes Ln{lane, 32};
   const P2GParams<T>& P = A.P;
   const int inc = w_incl_add(cnt, lane);
@@ -312,20 +332,27 @@ DXD bool lvl_flush(const LvlParams<T>& A, int lane, const unsigned* ws, int cnt,
     const int cno = __shfl_sync(0xffffffffu, cnt, own);
     const int tto = __shfl_sync(0xffffffffu, tt, own);
     const long long mso = __shfl_sync(0xffffffffu, ms, own);
-    if (idx < tot && cno <= A.slots) {
+    if (idx < tot && cno <= held) {
       const int k = idx - exo;
-      const unsigned pl = ws[(k << 5) + own];
-      const unsigned pr = ws[(k << 5) + own + A.slots * 32];
+      unsigned pl, pr;
+      if (k < A.slots) {
+        pl = ws[(k << 5) + own];
+        pr = ws[(k << 5) + own + A.slots * 32];
+      } else {  // (written by lane own before the warp synchronised)
+        const unsigned* so = sp0 + (long long)own * 2 * scap + 2 * (k - A.slots);
+        pl = so[0];
+        pr = so[1];
+      }
       const unsigned m = (1u << kLvlDxBits) - 1;
       A.l_p[s + idx] = make_ulonglong2(lvl_left<T>(P, mso, (int)(pl >> kLvlDxBits), (int)(pl & m), tto),
                                        lvl_right<T>(P, mso, (int)(pr >> kLvlDxBits), (int)(pr & m), tto));
     }
   }
   {
-    const unsigned long_lists = __ballot_sync(0xffffffffu, cnt > A.slots);
+    const unsigned long_lists = __ballot_sync(0xffffffffu, cnt > held);
     if (long_lists && lane == 0) atomicAdd(&P.ctr->lvl_redo, (unsigned long long)__popc(long_lists));
   }
-  if (cnt > A.slots) redo(A.l_p + s + ex);
+  if (cnt > held) redo(A.l_p + s + ex);
   if (act) {
     // the list serves output columns j +- t of its line: entry R - t of column j + t and entry
     // R + t of column j - t
@@ -379,7 +406,11 @@ DXD void lvl_warp_table(float* tab, int R, int nmax, const float* wtabf, int lan
 // itself (no packed copy).
 template <typename T, int TABM, bool EXACT = false>
 DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* ws, float4* stg,
-                     float E, float* tab, ArenaCursor& cur) {
+                     float E, float* tab, ArenaCursor& cur, long long gw = -1) {
+  // gw: the warp's index in the grid (its spill regions; -1: none)
+  unsigned* const sp0 = gw >= 0 ? lvl_spill(A, gw, 0) : nullptr;
+  unsigned* const spl = sp0 ? sp0 + (long long)lane * 2 * A.spill_cap : nullptr;
+  const int scap = sp0 ? A.spill_cap : 0;
   const P2GParams<T>& P = A.P;
   const int R1 = P.R + 1;
   const long long n0 = lvl_level0_items(A.nsrc, A.L, A.yw);
@@ -415,7 +446,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     }
     const auto src = lvl_src<T, EXACT>(P, ms, cs);
     LvlRun s = lvl_run();
-    const PackEmit pe{ws + lane, A.slots};
+    const PackEmit pe{ws + lane, A.slots, spl, scap};
     PHASE_BEGIN();
     if (TABM != kTabFlat) {
       STab wl;
@@ -426,7 +457,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
         wl = pairs ? STab{tab + lane, 5} : STab{tab + (long long)max(A.NG, 1) * R1 * 32, 0};
       }
       walk_global<T>(P, src, 0, np, E, wl, s, pe);
-      lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
+      lvl_flush(A, lane, ws, sp0, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
         LvlRun s2 = lvl_run();
         walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
       });
@@ -434,7 +465,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     } else {
       const FlatTab wl{tab, t * t, P.nmax};
       walk_global<T>(P, src, 0, np, E, wl, s, pe);
-      lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
+      lvl_flush(A, lane, ws, sp0, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
         LvlRun s2 = lvl_run();
         walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
       });
@@ -455,7 +486,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
   const long long ms = P.m_start[q], cs = EXACT ? 0 : P.c_start[q];
   const auto src = lvl_src<T, EXACT>(P, ms, cs);
   LvlRun s = lvl_run();
-  const PackEmit pe{ws + lane, A.slots};
+  const PackEmit pe{ws + lane, A.slots, spl, scap};
   if (TABM != kTabFlat) {
     PHASE_BEGIN();
     STab wl;
@@ -472,7 +503,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
     PHASE_COUNT(12, ph_cnt);
 #endif
     PHASE_COUNT(13, np);
-    lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
+    lvl_flush(A, lane, ws, sp0, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
       LvlRun s2 = lvl_run();
       walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
     });
@@ -480,7 +511,7 @@ DXD void levels_item(const LvlParams<T>& A, long long item, int lane, unsigned* 
   } else {
     const FlatTab wl{tab, t * t, P.nmax};
     walk_staged<T>(P, src, np, lane, stg, E, wl, s, pe);
-    lvl_flush(A, lane, ws, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
+    lvl_flush(A, lane, ws, sp0, s.cnt, act, q, t, ms, cur, [&](ulonglong2* ol) {
       LvlRun s2 = lvl_run();
       walk_global<T>(P, src, 0, np, E, wl, s2, ExactEmit<T>{&P, ms, t * t, ol});
     });
