@@ -595,7 +595,7 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       v.l_p = l_p; v.l_cap = pl.capL;
       v.l_idx = l_idx + nlb[s];
       v.W = 2 * K[s] + 1;
-      v.slots = lvl_slots_for(K[s]);
+      v.slots = lvl_slots_nospill(K[s]);
       v.L = K[s] + 1;
       v.G = v.L <= 32 ? 32 / v.L : 1;
       v.NG = v.L <= 32 ? 0 : (K[s] + 31) / 32;

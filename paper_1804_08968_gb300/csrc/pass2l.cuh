@@ -40,6 +40,9 @@ constexpr int kLvlSlots = 16;  // the most a launch uses
 // a lane: 2048^2 at k = 64, 4 slots 129 ms, 6 128, 8 138, 10 138; 4096^2 at k = 128, 6 slots
 // 1415 ms, 8 1402, 10 1397, 12 1394, 16 1509)
 DXI int lvl_slots_for(int R) { return R < 48 ? 8 : (R <= 64 ? 6 : 12); }
+// without spill regions (the batched engine): a longer list is walked again, so more slots
+// (measured at 2048^2 k = 64: 8 slots 218 ms, 10 200, 12 228, 16 258)
+DXI int lvl_slots_nospill(int R) { return R < 48 ? 8 : (R <= 64 ? 10 : 16); }
 // pieces a warp stages in shared memory at a time (a level group walks one source)
 // pieces staged a chunk, and the unrolling of the walk over them (measured at 2048^2 k = 64:
 // stage 128 237 ms against 200 at 64; unroll 1 209, 2 200, 4 195, 8 192, 16 196 ms)
