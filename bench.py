@@ -40,9 +40,9 @@ K_MAIN = 64.0  # the 2048^2 workload's radius in grid spacings
 # the workload (rows 450-577, 108.1 M pieces; pass 1: its first and redo launches together),
 # scaled to a full launch by the pieces processed (None once a kernel changed after its
 # capture)
-TRAFFIC_PER_PIECE = {"k_pass1l": 44.95, "k_levels": None}
+TRAFFIC_PER_PIECE = {"k_pass1l": 44.95, "k_levels": 64.43}
 # instructions (smsp__inst_executed.sum) per S_mid piece from the same capture
-INST_PER_PIECE = {"k_pass1l": 69.11, "k_levels": None}
+INST_PER_PIECE = {"k_pass1l": 69.11, "k_levels": 78.53}
 # issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock
 ISSUE_PER_CLK = 152 * 4
 
