@@ -59,12 +59,12 @@ def measured_peaks():
 def workload():
     """The 2048 x 2048 grid of 1000 seeded primitives (FP64 endpoints)."""
     from synth import shapes
-    return shapes.config3()
+    return shapes.grid2048()
 
 
 def workload512():
     from synth import shapes
-    return shapes.config2()
+    return shapes.grid512()
 
 
 def dist_init(args):
@@ -674,7 +674,7 @@ def run_batched_workload(args):
 
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
-    spec = shapes.config4_shapes()
+    spec = shapes.batch256_shapes()
     g64 = [shapes.raycast(prims, n) for (n, k, prims) in spec]
     g32 = [shapes.to_float32(g) for g in g64]
     ks = [k for (n, k, prims) in spec]
@@ -785,7 +785,7 @@ def run_morph_workload(args):
     torch.cuda.set_device(0)
     k = 128.0
     t0 = time.perf_counter()
-    g64 = shapes.config5()
+    g64 = shapes.grid4096()
     g32 = shapes.to_float32(g64)
     gen_s = time.perf_counter() - t0
     n = g64.nx

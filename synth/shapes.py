@@ -345,7 +345,7 @@ def _shell(rng, rlo, rhi, tlo, thi, clo=0.15, chi=0.85):
     return ("shell", c[0], c[1], c[2], R, t)
 
 
-def config1_prims():
+def grid64_prims():
     """64 x 64, union of 8 spheres, centres U[0.2,0.8]^3, radii U[0.05,0.2], seed 0."""
     rng = np.random.default_rng(0)
     prims = []
@@ -356,11 +356,11 @@ def config1_prims():
     return prims
 
 
-def config1() -> DexelGrid:
-    return raycast(config1_prims(), 64)
+def grid64() -> DexelGrid:
+    return raycast(grid64_prims(), 64)
 
 
-def config2_prims(nprim: int = 200, seed: int = 1):
+def grid512_prims(nprim: int = 200, seed: int = 1):
     """512 x 512: 1/3 spheres, 1/3 boxes (sides U[0.02,0.3]), 1/3 hollow shells (t U[0.005,0.03])."""
     rng = np.random.default_rng(seed)
     prims = []
@@ -385,12 +385,12 @@ def capped(prims, n, max_segs):
         prims.pop()
 
 
-def config2() -> DexelGrid:
-    g, _ = capped(config2_prims(), 512, 16)
+def grid512() -> DexelGrid:
+    g, _ = capped(grid512_prims(), 512, 16)
     return g
 
 
-def config3_prims(r_world: float = 64.0 / 2048.0, seed: int = 2):
+def grid2048_prims(r_world: float = 64.0 / 2048.0, seed: int = 2):
     """2048 x 2048, 1000 primitives: spheres, boxes, thin plates (one side U[0.2,0.9] r) and
     groups of nested concentric hollow spheres (up to 32 shells -> up to 64 segments/column)."""
     rng = np.random.default_rng(seed)
@@ -424,11 +424,11 @@ def config3_prims(r_world: float = 64.0 / 2048.0, seed: int = 2):
     return prims
 
 
-def config3() -> DexelGrid:
-    return raycast(config3_prims(), 2048)
+def grid2048() -> DexelGrid:
+    return raycast(grid2048_prims(), 2048)
 
 
-def config4_shapes(nshapes: int = 256, seed: int = 3):
+def batch256_shapes(nshapes: int = 256, seed: int = 3):
     """256 shapes, N log-uniform in [32, 1024], U{4..400} spheres/boxes each, k ~ U[1,48]."""
     rng = np.random.default_rng(seed)
     out = []
@@ -446,7 +446,7 @@ def config4_shapes(nshapes: int = 256, seed: int = 3):
     return out
 
 
-def config5_prims(seed: int = 4, nprim: int = 550):
+def grid4096_prims(seed: int = 4, nprim: int = 550):
     """4096 x 4096, mixed spheres/boxes/shells: 61.6 M segments, at most 15 per column."""
     rng = np.random.default_rng(seed)
     prims = []
@@ -461,5 +461,5 @@ def config5_prims(seed: int = 4, nprim: int = 550):
     return prims
 
 
-def config5() -> DexelGrid:
-    return raycast(config5_prims(), 4096)
+def grid4096() -> DexelGrid:
+    return raycast(grid4096_prims(), 4096)

@@ -130,7 +130,7 @@ def test_batched_capacity_and_bad_shape(dx):
     import ctypes
     import torch
     L = dx.lib()
-    good = shapes.config1()
+    good = shapes.grid64()
     bad = shapes.from_columns(4, 4, 0.25, {(1, 1): [(0.2, 0.4), (0.3, 0.6)]})
     grids = [dx.Grid.from_synth(good), dx.Grid.from_synth(bad), dx.Grid.from_synth(good)]
     ins = (dx._In * 3)(*[g._in() for g in grids])

@@ -52,8 +52,8 @@ def test_boolean_random(dx, seed, f32):
 
 def test_boolean_shapes_and_edges(dx):
     """Boxes and spheres ray-cast at 256 x 256; empty grids; a 1 x 1 grid; size mismatch."""
-    a = shapes.raycast(shapes.config2_prims(60, seed=3), 256)
-    b = shapes.raycast(shapes.config2_prims(60, seed=4), 256)
+    a = shapes.raycast(shapes.grid512_prims(60, seed=3), 256)
+    b = shapes.raycast(shapes.grid512_prims(60, seed=4), 256)
     da, db = _dev(dx, a, False), _dev(dx, b, False)
     for op, fn in ((dx.UNION, oracle.union), (dx.INTERSECT, oracle.intersection),
                    (dx.DIFFERENCE, oracle.difference)):
@@ -81,7 +81,7 @@ def test_shell(dx, f32):
     """Shell = dilation minus erosion, every column against the oracle's composite."""
     import torch
     rng = np.random.default_rng(77)
-    cases = [(shapes.config1(), 4.0), (shapes.raycast(shapes.config2_prims(50, seed=8), 96), 3.7),
+    cases = [(shapes.grid64(), 4.0), (shapes.raycast(shapes.grid512_prims(50, seed=8), 96), 3.7),
              (shapes.random_grid(rng, 30, 41, 5, fill=0.8, point_frac=0.05, h=1 / 64), 6.5)]
     for g, k in cases:
         if f32:

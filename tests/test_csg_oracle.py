@@ -134,7 +134,7 @@ def test_shell_of_a_lone_segment_is_the_capsule():
 
 def test_shell_relations():
     """shell u E = D and |shell| = |D| - |E| (the erosion lies inside the dilation)."""
-    g = shapes.raycast(shapes.config2_prims(40, seed=7), 64)
+    g = shapes.raycast(shapes.grid512_prims(40, seed=7), 64)
     k = 3.0
     d, e = oracle.dilate(g, k), oracle.erode(g, k)
     s = oracle.shell(g, k)

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 def _grid(n, seed, nprim=60, dtype="fp64"):
     import torch
     import paper_1804_08968_gb300 as dx
-    g = shapes.raycast(shapes.config2_prims(nprim=nprim, seed=seed), n)
+    g = shapes.raycast(shapes.grid512_prims(nprim=nprim, seed=seed), n)
     if dtype == "fp32":
         g = shapes.to_float32(g)
     return dx.Grid.from_synth(g, dtype=torch.float32 if dtype == "fp32" else torch.float64)

@@ -24,7 +24,7 @@ K = 64.0
 
 @pytest.fixture(scope="module")
 def grids():
-    g64 = shapes.config3()
+    g64 = shapes.grid2048()
     return {"fp64": g64, "fp32": shapes.to_float32(g64)}
 
 
@@ -112,7 +112,7 @@ def test_reach_128(op):
     enough in x for full windows; FP64 against the oracle."""
     import torch
     import paper_1804_08968_gb300 as dx
-    prims = shapes.config2_prims(60, seed=13)
+    prims = shapes.grid512_prims(60, seed=13)
     big = shapes.raycast(prims, 320)
     cols = {(i, j): [tuple(s) for s in big.column(i, j + 150)]
             for i in range(320) for j in range(16) if big.column(i, j + 150).size}
@@ -136,7 +136,7 @@ def test_morphology_blocks_reduced(mode, op, monkeypatch):
     import torch
     import paper_1804_08968_gb300 as dx
     monkeypatch.setenv("DEXEL_BLOCK_MB", "4")
-    g = shapes.raycast(shapes.config5_prims(nprim=60, seed=21), 384)
+    g = shapes.raycast(shapes.grid4096_prims(nprim=60, seed=21), 384)
     f32 = mode == "fp32"
     if f32:
         g = shapes.to_float32(g)

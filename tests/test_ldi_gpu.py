@@ -19,7 +19,7 @@ def _cmp(off, z, ref, what, tol=1e-10):
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_raycast_axis(axis):
     import paper_1804_08968_gb300 as dx
-    prims = shapes.config2_prims(120, seed=12)
+    prims = shapes.grid512_prims(120, seed=12)
     n, m = 256, 200
     g = dx.raycast(prims, n, m, 1 / 256, axis=axis)
     off, z = g.to_host()
@@ -30,7 +30,7 @@ def test_raycast_axis(axis):
 @pytest.mark.parametrize("op", ["dilate", "close"])
 def test_offset_ldi(op):
     import paper_1804_08968_gb300 as dx
-    prims = shapes.config2_prims(40, seed=14)
+    prims = shapes.grid512_prims(40, seed=14)
     n = 160 if op == "dilate" else 96
     h = 1.0 / n
     views = [dx.raycast(prims, n, n, h, axis=a) for a in (2, 0, 1)]

@@ -34,7 +34,7 @@ def test_views_agree_at_lattice_points():
     """A lattice point ((i+1/2)h, (j+1/2)h, (l+1/2)h) is a ray sample of all three views; away
     from the surfaces its membership is the same in each."""
     from synth import shapes
-    prims = shapes.config2_prims(30, seed=11)
+    prims = shapes.grid512_prims(30, seed=11)
     n = 48
     h = 1 / n
     gz, gx, gy = (oracle.raycast_axis(prims, a, n, n, h) for a in (2, 0, 1))

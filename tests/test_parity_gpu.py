@@ -109,26 +109,26 @@ def test_random_fp32(dx, op):
         _compare_full(off, z, _ref(gg, op, k), True, f"fp32 {op} k={k}")
 
 
-def test_config1_dilation(dx):
+def test_grid64_dilation(dx):
     """64 x 64, 8 spheres, k = 4, FP64 (the smallest workload)."""
-    g = shapes.config1()
+    g = shapes.grid64()
     gg, off, z = _gpu(dx, g, "dilate", 4.0)
-    _compare_full(off, z, _ref(gg, "dilate", 4.0), False, "config1")
+    _compare_full(off, z, _ref(gg, "dilate", 4.0), False, "grid64")
 
 
 @pytest.mark.parametrize("op", ["dilate", "erode"])
 @pytest.mark.parametrize("k", [2.0, 8.0])
-def test_config2_full(dx, op, k):
+def test_grid512_full(dx, op, k):
     """512 x 512, 200 primitives: every column compared with the oracle."""
-    g = shapes.config2()
+    g = shapes.grid512()
     gg, off, z = _gpu(dx, g, op, k)
-    _compare_full(off, z, _ref(gg, op, k), False, f"config2 {op} k={k}")
+    _compare_full(off, z, _ref(gg, op, k), False, f"grid512 {op} k={k}")
 
 
 @pytest.mark.parametrize("op", ["dilate", "erode"])
-def test_config2_k32_sampled(dx, op):
+def test_grid512_k32_sampled(dx, op):
     """k = 32 at 512 x 512: 3000 sampled columns plus two full lines against the oracle."""
-    g = shapes.config2()
+    g = shapes.grid512()
     k = 32.0
     gg, off, z = _gpu(dx, g, op, k)
     rng = np.random.default_rng(5)
@@ -145,7 +145,7 @@ def test_config2_k32_sampled(dx, op):
 
 @pytest.mark.parametrize("op", ["close", "open"])
 def test_morphology_small(dx, op):
-    g = shapes.raycast(shapes.config2_prims(80, seed=3), 96)
+    g = shapes.raycast(shapes.grid512_prims(80, seed=3), 96)
     for k in [2.0, 5.0]:
         gg, off, z = _gpu(dx, g, op, k)
         _compare_full(off, z, _ref(gg, op, k), False, f"{op} k={k}")
@@ -184,7 +184,7 @@ def test_bad_csr_rejected(dx):
 def test_output_capacity_retry(dx):
     """A too-small output buffer reports the needed size; the binding retries."""
     import torch
-    g = shapes.config1()
+    g = shapes.grid64()
     dg = dx.Grid.from_synth(g, dtype=torch.float64)
     ctx = dx.Context(0)
     out = ctx.run(dx.DILATE, dg, 4.0, capacity=3)
@@ -269,7 +269,7 @@ def test_wide_reach(dx, op, k):
     grid long enough in x for the windows to be full; the xy spacing is small against the
     depth (h = 1/4000) so that the results keep their gaps."""
     if op == "dilate":
-        prims = shapes.config2_prims(40, seed=9)
+        prims = shapes.grid512_prims(40, seed=9)
         g = shapes.raycast(prims, 200)
         cols = {(i, j): [tuple(s) for s in g.column(i, j + 88)]
                 for i in range(200) for j in range(24) if g.column(i, j + 88).size}

@@ -10,16 +10,16 @@ from synth import shapes
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("case", ["config1", "config2", "config3", "thin", "empty"])
+@pytest.mark.parametrize("case", ["grid64", "grid512", "grid2048", "thin", "empty"])
 def test_raycast_matches_oracle(case):
     import torch
     import paper_1804_08968_gb300 as dx
-    if case == "config1":
-        prims, nx, ny = shapes.config1_prims(), 64, 64
-    elif case == "config2":
-        prims, nx, ny = shapes.config2_prims(), 512, 512
-    elif case == "config3":
-        prims, nx, ny = shapes.config3_prims(), 768, 768
+    if case == "grid64":
+        prims, nx, ny = shapes.grid64_prims(), 64, 64
+    elif case == "grid512":
+        prims, nx, ny = shapes.grid512_prims(), 512, 512
+    elif case == "grid2048":
+        prims, nx, ny = shapes.grid2048_prims(), 768, 768
     elif case == "thin":
         # a non-square grid, nested shells and boxes thinner than a spacing
         prims = [("shell", 0.5, 0.4, 0.5, 0.3 - 0.02 * q, 0.006) for q in range(12)]

@@ -46,14 +46,14 @@ def test_shell_is_the_difference_of_two_spheres():
     assert np.array_equal(sh.col_off, d.col_off) and np.array_equal(sh.z, d.z)
 
 
-@pytest.mark.parametrize("which", ["config1", "config2", "config3_part"])
+@pytest.mark.parametrize("which", ["grid64", "grid512", "grid2048_part"])
 def test_matches_the_input_generator(which):
-    if which == "config1":
-        prims, n = shapes.config1_prims(), 64
-    elif which == "config2":
-        prims, n = shapes.config2_prims(100, seed=2), 200
+    if which == "grid64":
+        prims, n = shapes.grid64_prims(), 64
+    elif which == "grid512":
+        prims, n = shapes.grid512_prims(100, seed=2), 200
     else:
-        prims, n = shapes.config3_prims()[:150], 128
+        prims, n = shapes.grid2048_prims()[:150], 128
     a = oracle.raycast(prims, n, n, 1.0 / n)
     b = shapes.raycast(prims, n)
     assert np.array_equal(a.col_off, b.col_off) and np.array_equal(a.z, b.z)

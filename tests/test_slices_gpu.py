@@ -56,7 +56,7 @@ def test_slices_shapes_and_rows(dx):
     """A 512 x 48 strip of the 512^2 workload at k = 32: against the oracle, and each row equal
     to the 3D offset of that row alone (a 1-row grid, where disk and ball coincide)."""
     import torch
-    big = shapes.config2()
+    big = shapes.grid512()
     cols = {(i, j): [tuple(s) for s in big.column(i, j + 200)]
             for i in range(512) for j in range(48) if big.column(i, j + 200).size}
     g = shapes.from_columns(512, 48, big.h, cols)

@@ -5,15 +5,15 @@ import pytest
 from synth import shapes
 
 
-@pytest.mark.parametrize("which", ["config1", "config2_small", "config3_crop"])
+@pytest.mark.parametrize("which", ["grid64", "grid512_small", "grid2048_crop"])
 def test_compiled_raycast_matches_numpy(which):
     """The compiled ray caster gives the numpy one's grid bit for bit."""
-    if which == "config1":
-        prims, n = shapes.config1_prims(), 64
-    elif which == "config2_small":
-        prims, n = shapes.config2_prims(120, seed=5), 256
+    if which == "grid64":
+        prims, n = shapes.grid64_prims(), 64
+    elif which == "grid512_small":
+        prims, n = shapes.grid512_prims(120, seed=5), 256
     else:
-        prims, n = shapes.config3_prims()[:200], 160
+        prims, n = shapes.grid2048_prims()[:200], 160
     a = shapes.raycast(prims, n)
     b = shapes.raycast_numpy(prims, n)
     assert np.array_equal(a.col_off, b.col_off)

@@ -66,7 +66,7 @@ def test_noalloc_matches_existing_entry_point_twice():
     import paper_1804_08968_gb300 as dx
     rng = np.random.default_rng(2024)
     cases = [
-        (shapes.config1(), 4.0, dx.DILATE),
+        (shapes.grid64(), 4.0, dx.DILATE),
         (shapes.random_grid(rng, 45, 37, 5, fill=0.8, point_frac=0.05, h=1 / 40), 3.5, dx.ERODE),
     ]
     for g, k, op in cases:  # two calls in a row on different inputs
@@ -100,7 +100,7 @@ def test_noalloc_largest_advertised_grid():
     """256 x 256 columns at k = 32, the edge of the documented envelope, must succeed."""
     import torch
     import paper_1804_08968_gb300 as dx
-    g = shapes.raycast(shapes.config1_prims(), 256)
+    g = shapes.raycast(shapes.grid64_prims(), 256)
     grid = dx.Grid.from_synth(g, dtype=torch.float64)
     rc, nseg, off, z, _ = _noalloc(dx, grid, 32.0, dx.DILATE)
     assert rc == 0, dx.STATUS.get(rc, rc)
@@ -138,7 +138,7 @@ def test_noalloc_limits_and_retry_signals():
     assert (off == -7).all() and torch.isnan(zt).all()
     # an output buffer that is too small: nseg is the size needed, z untouched; a retry with
     # that size succeeds
-    g = shapes.config1()
+    g = shapes.grid64()
     grid = dx.Grid.from_synth(g, dtype=torch.float64)
     rc, nseg, _, _, zt = _noalloc(dx, grid, 4.0, dx.DILATE, cap=3)
     assert rc == -3 and nseg > 3
@@ -153,7 +153,7 @@ def test_noalloc_allocates_nothing():
     """Across calls neither torch's allocator nor the device's free memory changes."""
     import torch
     import paper_1804_08968_gb300 as dx
-    g = shapes.config1()
+    g = shapes.grid64()
     grid = dx.Grid.from_synth(g, dtype=torch.float64)
     L = dx.lib()
     L.dexel_offset_noalloc.argtypes = [ctypes.POINTER(dx._In), ctypes.c_double, ctypes.c_int,
