@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(256) k_b_levels(const BShape<T>* __restrict__ 
     const LvlParams<T> A = S[s].lv;
     const float E = 9.5367432e-7f * (__uint_as_float(A.P.ctr->zmax_bits) + A.P.wtabf[0]);
     levels_item<T, TABM>(A, gi - lvb[s], lane, ws, stg, E,
-                         TABM == kTabWarp ? wt : (float*)A.P.wtabf, cur);
+                         TABM == kTabWarp ? wt : (float*)A.P.wtabf, cur,
+                         (long long)blockIdx.x * (blockDim.x >> 5) + warp);
   }
 }
 
@@ -312,6 +313,7 @@ struct BatchEngine {
   size_t host_bytes = 0;
   void* mid = nullptr;  // internal outputs
   size_t mid_bytes = 0;
+  unsigned* spill = nullptr;  // the level walks' spill regions (every warp of k_b_levels' grid)
   long long needM = 0, needO = 0, needL = 0;  // arena entries learnt
   std::map<std::vector<long long>, bool> no_levels;  // signatures whose level lists overflowed
   // recorded launch sequences by signature (shapes, scratch, tile scales)
@@ -322,11 +324,20 @@ struct BatchEngine {
   std::map<std::vector<long long>, std::pair<int, int>> scales;
 };
 
+// intervals a lane of the batched level walks spills beyond its slots
+constexpr int kBatchSpill = 64;
+
 BatchEngine* batch_engine_create(int device, int sms) {
   BatchEngine* e = new (std::nothrow) BatchEngine;
   if (!e) return nullptr;
   e->device = device;
   e->sms = sms > 0 ? sms : 152;
+  // the level walks' spill regions (the grid of k_b_levels: sms x 4 blocks of 8 warps); without
+  // them a long list is walked again
+  if (cudaMalloc(&e->spill, (size_t)lvl_spill_bytes(e->sms, kBatchSpill)) != cudaSuccess) {
+    cudaGetLastError();
+    e->spill = nullptr;
+  }
   return e;
 }
 
@@ -336,6 +347,7 @@ void batch_engine_destroy(BatchEngine* e) {
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
   if (e->ws) cudaFree(e->ws);
   if (e->mid) cudaFree(e->mid);
+  if (e->spill) cudaFree(e->spill);
   if (e->host) cudaFreeHost(e->host);
   delete e;
 }
@@ -595,7 +607,9 @@ static int batch_run_t(BatchEngine* E, std::vector<BatchItem>& items, cudaStream
       v.l_p = l_p; v.l_cap = pl.capL;
       v.l_idx = l_idx + nlb[s];
       v.W = 2 * K[s] + 1;
-      v.slots = lvl_slots_nospill(K[s]);
+      v.slots = E->spill ? lvl_slots_for(K[s]) : lvl_slots_nospill(K[s]);
+      v.spill = E->spill;
+      v.spill_cap = E->spill ? kBatchSpill : 0;
       v.L = K[s] + 1;
       v.G = v.L <= 32 ? 32 / v.L : 1;
       v.NG = v.L <= 32 ? 0 : (K[s] + 31) / 32;
