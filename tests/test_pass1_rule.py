@@ -82,3 +82,54 @@ def test_point_rule_matches_definition():
                 assert pt == P[v], (trial, v)
             else:
                 assert P[v] == min(below, above), (trial, v)
+
+
+def _by_events_lazy(segs, rng):
+    """The same walk with the window kernel's lazy close: a height is closed only when one of
+    its events came from a source within the label below it (d <= O_below); otherwise the
+    labels and the missing point are taken as unchanged without looking."""
+    ev = [(a, q) for q, (a, b, d) in enumerate(segs)] + [(b, q) for q, (a, b, d) in enumerate(segs)]
+    rng.shuffle(ev)
+    ev.sort(key=lambda e: e[0])
+    open_set = set()
+    Om = NO
+    out = {}
+    i = 0
+    while i < len(ev):
+        v = ev[i][0]
+        gmin, dirty = NO, False
+        while i < len(ev) and ev[i][0] == v:
+            q = ev[i][1]
+            open_set ^= {q}
+            d = segs[q][2]
+            if d <= Om:
+                dirty = True
+                gmin = min(gmin, d)
+            i += 1
+        if not dirty:
+            out[v] = (Om, Om, None)
+            continue
+        Ok = min([segs[q][2] for q in open_set], default=NO)
+        pt = gmin < min(Om, Ok)
+        out[v] = (Om, Ok, gmin if pt else None)
+        Om = Ok
+    return out
+
+
+def test_lazy_close_changes_nothing():
+    """The lazy close gives the same labels and points at every height as closing every
+    height (so skipping the closes of heights no lane needs is exact)."""
+    rng = np.random.default_rng(9)
+    for trial in range(600):
+        segs = []
+        for d in range(int(rng.integers(1, 8))):
+            for _ in range(int(rng.integers(0, 3))):
+                for _ in range(int(rng.integers(1, 4))):
+                    a = int(rng.integers(0, 14))
+                    segs.append((a, a + int(rng.integers(0, 4)), d))
+        if not segs:
+            continue
+        seed = int(rng.integers(1 << 30))
+        eager = _by_events(segs, np.random.default_rng(seed))
+        lazy = _by_events_lazy(segs, np.random.default_rng(seed))
+        assert eager == lazy, (trial, segs)
