@@ -99,7 +99,10 @@ typedef struct {
 typedef struct dexel_ctx dexel_ctx;
 
 /* Create / destroy a context bound to CUDA device `device`.  The context owns only small
- * tables (the half-width table w[n] = h sqrt(k^2 - n), reach table) and status words.
+ * tables (the half-width table w[n] = h sqrt(k^2 - n), reach table) and status words, the
+ * scratch it allocates when a call passes no workspace, and the plans (tapes) its
+ * synchronous offsets recorded for dexel_offset_enqueue.  A context is not thread-safe: one
+ * host thread at a time calls it (threads that need concurrent calls use a context each).
  *
  * Kernel choices are read from the environment when the context is created (for testing
  * and tuning; every choice gives the same result):
