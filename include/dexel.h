@@ -210,7 +210,10 @@ dexel_status dexel_erode(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexe
  *   data needed more room or another path than the plan: call dexel_dilate / dexel_erode);
  *   [1] the output's segment count.  out->z is written only when [0] is DEXEL_OK (out->col_off
  *   always).  A host-side failure (a bad argument, a workspace below the plan's need:
- *   DEXEL_ERR_CAPACITY with dexel_last_required) returns before anything is queued. */
+ *   DEXEL_ERR_CAPACITY with dexel_last_required) returns before anything is queued.  Any
+ *   return other than DEXEL_OK leaves d_result unwritten: the call counts as not made (a
+ *   DEXEL_ERR_NO_PLAN from a plan the context's state no longer matches may follow kernels
+ *   already queued on the stream; they only touch the workspace and out->col_off). */
 dexel_status dexel_offset_enqueue(dexel_ctx* ctx, const dexel_grid_in* in, double k, dexel_op op,
                                   dexel_mode mode, dexel_grid_out* out, void* ws,
                                   size_t ws_bytes, void* stream, int64_t* d_result);
